@@ -1,0 +1,171 @@
+/*
+ * hfsem -- H-matrix-preconditioned Krylov solver for the spectral element
+ * (SEM) system of the 1D two-sided Riemann-Liouville fractional diffusion
+ * equation, for NVIDIA GB300 (sm_103a).
+ *
+ *   -D^2( theta aI_x^{2-alpha} u + (1-theta) xI_b^{2-alpha} u ) + rho u = f
+ *   on (a, b),  u(a) = c1,  u(b) = c2,  1 < alpha < 2,  0 <= theta <= 1
+ *                                                  (Sec. 1, eq. (Model))
+ *
+ * Discretisation (Sec. 2.2): N elements, degree P on every element, hats plus
+ * bubbles psi_p = L_{p-1} - L_{p+1}; N_d = N P - 1 unknowns; the linear
+ * system A X = (rho M + S) X = G, S = theta S_l + (1 - theta) S_l^T
+ * (eq. (lsys)).  The boundary values enter by lifting with the two boundary
+ * hats (the paper's basis spans H^1_0 only).
+ *
+ * Vector layout at this boundary: X's ordering of Sec. 2.2, i.e. all bubbles
+ * element by element (element-major, p = 1..P-1), then the N-1 interior hats
+ * in node order.  Several vectors of one instance are stored column-major
+ * (N_d x nrhs, leading dimension N_d); instances are concatenated in the
+ * order they were assembled.
+ *
+ * Pointers: every vector argument may be host memory or device memory of the
+ * current device; the library finds out with cudaPointerGetAttributes.
+ * Host arrays inside the parameter structs are read during the call only.
+ * Handles are owned by the library and released with the *_free calls.
+ * All work is issued on the stream given to hfsem_assemble; calls return
+ * after that work completes unless stated otherwise.
+ *
+ * Errors: every int-returning call returns an HFSEM_* status and never
+ * throws across this boundary.  On error nothing is written to the outputs
+ * unless stated.
+ */
+#ifndef HFSEM_H
+#define HFSEM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------ */
+#define HFSEM_OK                 0
+#define HFSEM_ERR_INVALID_ARG    1  /* bad size, parameter range, pointer   */
+#define HFSEM_ERR_OOM            2  /* device allocation failed             */
+#define HFSEM_ERR_NOT_CONVERGED  3  /* Krylov hit max_iter; X = last iterate */
+#define HFSEM_ERR_BREAKDOWN      4  /* BiCGSTAB breakdown (rho or omega = 0) */
+#define HFSEM_ERR_DEVICE         6  /* CUDA error                           */
+#define HFSEM_ERR_UNSUPPORTED    7  /* valid request this build cannot do   */
+
+/* ---- enumerations ------------------------------------------------------ */
+#define HFSEM_MATVEC_AUTO      0  /* Toeplitz when the mesh is uniform or
+                                     geometric with a mild ratio, else dense */
+#define HFSEM_MATVEC_DENSE     1  /* O(N_d^2) dense operator (Sec. 4.2)      */
+#define HFSEM_MATVEC_TOEPLITZ  2  /* block-Toeplitz FFT operator (Sec. 4.3);
+                                     needs h_{i+1}/h_i constant               */
+
+#define HFSEM_PREC_FP64   0       /* H-matrix, H-LU and H-solves in FP64     */
+#define HFSEM_PREC_MIXED  1       /* H-matrix, H-LU and H-solves in FP32;
+                                     Krylov loop and operator stay FP64      */
+
+#define HFSEM_RHS_LOAD_VECTOR  0  /* G given directly                        */
+#define HFSEM_RHS_FRAC_POWERS  1  /* f = sum c_k (x-a)^mu_k + sum d_k (b-x)^nu_k */
+#define HFSEM_RHS_LEGENDRE_AB  2  /* f = sum g_k L_k(xi_[a,b](x))           */
+
+/* ---- one problem instance (Sec. 1 eq. (Model), Sec. 2.2 eq. (Partition)) */
+typedef struct {
+  int32_t     n_elem;   /* N >= 1                                            */
+  int32_t     P;        /* polynomial degree on every element, 1 <= P <= 32 */
+  double      a, b;     /* interval, a < b                                   */
+  const double *h;      /* host, N element lengths h_i > 0 with
+                           sum h_i = b - a to 1e-12 relative; copied         */
+  double      alpha;    /* 1 < alpha < 2                                     */
+  double      theta;    /* 0 <= theta <= 1                                   */
+  double      rho;      /* reaction coefficient, >= 0                        */
+  double      c1, c2;   /* boundary values u(a), u(b)                        */
+  int32_t     matvec;   /* HFSEM_MATVEC_*                                    */
+} hfsem_problem;
+
+/* ---- H-matrix / H-LU options (Sec. 3 and Sec. 4.1) ---------------------- */
+typedef struct {
+  int32_t R;          /* Taylor rank of eq. (eqn:Lexpan), 1 <= R <= 32       */
+  double  lambda;     /* admissibility parameter of eq. (admis), > 0 (1.0)  */
+  double  tol_hlu;    /* Tol_HLU: singular values below tol_hlu * sigma_1
+                         are dropped when blocks are recompressed; 0 keeps
+                         every nonzero one (up to kmax). 1e-3 in Sec. 5     */
+  int32_t precision;  /* HFSEM_PREC_*                                        */
+  int32_t leaf_elems; /* elements per leaf cluster; 0 = automatic           */
+  int32_t kmax;       /* rank cap after recompression; 0 = automatic        */
+  int32_t build_only; /* 1: build the H-matrix, do not factor (inspection)  */
+} hfsem_hopts;
+
+/* ---- right-hand sides -------------------------------------------------- */
+typedef struct {
+  int32_t kind;       /* HFSEM_RHS_*                                         */
+  int32_t nrhs;       /* >= 1; must be equal for all instances of a call     */
+  int32_t n_terms;    /* FRAC_POWERS: terms per rhs; LEGENDRE_AB: K + 1      */
+  const double *data; /* host.  LOAD_VECTOR: N_d x nrhs column-major (X's
+                         ordering).  FRAC_POWERS: per rhs, n_terms triples
+                         (coef, exponent > -1, side: 0 = (x-a), 1 = (b-x)).
+                         LEGENDRE_AB: per rhs, K+1 coefficients g_k.         */
+} hfsem_rhs;
+
+typedef struct {
+  int32_t iters;            /* BiCGSTAB iterations taken                    */
+  int32_t status;           /* HFSEM_OK or the failure for this column      */
+  double  rel_residual;     /* recursive ||r|| / ||G_lifted||               */
+  double  rel_true_residual;/* ||G_lifted - A X|| / ||G_lifted|| at exit    */
+} hfsem_stats;
+
+typedef struct hfsem_system_s hfsem_system;
+typedef struct hfsem_factor_s hfsem_factor;
+
+/* Assemble n_inst >= 1 instances (Sec. 2.2): mesh geometry, the element-
+ * pair moment blocks of S_l (dense path) or the block-Toeplitz symbol of
+ * Sec. 4.3 (Toeplitz path), on the CUDA stream `stream` (cudaStream_t,
+ * NULL = legacy default stream).  *out receives a handle owned by the
+ * library.  INVALID_ARG for any parameter outside the ranges above. */
+int hfsem_assemble(int32_t n_inst, const hfsem_problem *probs, void *stream,
+                   hfsem_system **out);
+
+/* N_d of instance `inst` (end of Sec. 2.2) into *nd. */
+int hfsem_ndof(const hfsem_system *sys, int32_t inst, int32_t *nd);
+
+/* y = A x for every instance (the operator of eq. (lsys), with zero boundary
+ * values), x and y N_d x nrhs per instance, concatenated; 1 <= nrhs <= 64. */
+int hfsem_apply(hfsem_system *sys, int32_t nrhs, const double *x, double *y);
+
+/* Load vector G_i = (f, phi_i) of Sec. 2.2 for every instance, rhs[inst].
+ * lifted = 1 subtracts the boundary-hat columns times (c1, c2), i.e. returns
+ * the right-hand side the interior unknowns solve against. */
+int hfsem_load_vector(hfsem_system *sys, const hfsem_rhs *rhs, int32_t lifted,
+                      double *G);
+
+/* Build the H-matrix approximation A~ = rho M + theta H + (1-theta) H^T of
+ * Sec. 3 / eq. (approxsys) for every instance and factor it by H-LU
+ * (Sec. 4.1), L_H unit lower, U_H upper, both in H-matrix format.  The
+ * factor is valid for `sys` only and must be freed before it. */
+int hfsem_hlu_factor(hfsem_system *sys, const hfsem_hopts *opts,
+                     hfsem_factor **out);
+
+/* Dense copy (N_d x N_d, column-major, X's ordering) of instance inst's A~
+ * as built; only for factors made with build_only = 1. */
+int hfsem_hmatrix_dense(const hfsem_factor *fac, int32_t inst, double *out);
+
+/* y = (L_H U_H)^{-1} r for every instance: forward then backward
+ * H-triangular substitution (Sec. 4.1).  r, y: N_d x nrhs per instance. */
+int hfsem_precond_apply(hfsem_factor *fac, int32_t nrhs, const double *r,
+                        double *y);
+
+/* Solve A X = G for every instance by BiCGSTAB (Sec. 4.2) right-
+ * preconditioned with the H-LU factor `fac` (NULL: no preconditioner).
+ * rhs: n_inst entries, equal nrhs.  Stops when the recursive relative
+ * residual is <= tol or after max_iter iterations, then checks the true
+ * residual.  X: N_d x nrhs per instance, concatenated (host or device).
+ * stats: n_inst * nrhs entries (host), instance-major.  Returns the worst
+ * per-column status; X holds the last iterate in every case. */
+int hfsem_solve(hfsem_system *sys, hfsem_factor *fac, const hfsem_rhs *rhs,
+                double tol, int32_t max_iter, double *X, hfsem_stats *stats);
+
+void hfsem_factor_free(hfsem_factor *fac);
+void hfsem_system_free(hfsem_system *sys);
+
+/* Static string for a status code. */
+const char *hfsem_status_str(int status);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HFSEM_H */

@@ -1,0 +1,161 @@
+// Internal declarations shared by the translation units of the hfsem library.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <cstdio>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "hfsem.h"
+
+namespace hf {
+
+struct Error : public std::exception {
+  int code;
+  std::string msg;
+  Error(int c, std::string m) : code(c), msg(std::move(m)) {}
+  const char* what() const noexcept override { return msg.c_str(); }
+};
+
+inline void cuda_check(cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation)
+    throw Error(HFSEM_ERR_OOM, std::string(what) + ": " + cudaGetErrorString(e));
+  if (e != cudaSuccess)
+    throw Error(HFSEM_ERR_DEVICE, std::string(what) + ": " + cudaGetErrorString(e));
+}
+#define HF_CHECK(x) ::hf::cuda_check((x), #x)
+#define HF_LAUNCH_CHECK() ::hf::cuda_check(cudaGetLastError(), "kernel launch")
+
+void set_last_error(const std::string& m);
+
+// Owning device buffer.
+template <class T>
+struct DevBuf {
+  T* p = nullptr;
+  size_t n = 0;
+  DevBuf() = default;
+  DevBuf(const DevBuf&) = delete;
+  DevBuf& operator=(const DevBuf&) = delete;
+  ~DevBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  void alloc(size_t count) {
+    release();
+    if (count == 0) return;
+    HF_CHECK(cudaMalloc(&p, count * sizeof(T)));
+    n = count;
+  }
+  void ensure(size_t count) {
+    if (count > n) alloc(count);
+  }
+};
+
+// Gauss rules (host): weight (1-x)^a (1+x)^b on [-1, 1].
+void gauss_jacobi_rule(int n, double a, double b, std::vector<double>& x,
+                       std::vector<double>& w);
+void gauss_legendre_rule(int n, std::vector<double>& x, std::vector<double>& w);
+
+// Largest Gauss-Legendre rule kept in the device table.
+constexpr int kMaxGL = 96;
+constexpr int kMaxP = 32;
+
+// Kinds of operator storage.
+constexpr int kDense = 0;
+constexpr int kToeplitz = 1;
+
+// Per-instance descriptor as seen by the kernels (plain data).
+struct InstDev {
+  int N, P, Nd, kind;
+  int L, logL;          // FFT length (Toeplitz), power of two >= 2N
+  int uniform;          // Toeplitz with constant row/column scalings
+  int n_gj;             // points of the Gauss-Jacobi (0, 2-alpha) rule
+  double alpha, theta, rho, c1, c2, g0;
+  long long o_h, o_dl, o_dr;   // arena offsets (doubles)
+  long long o_M;               // dense: packed lower blocks; Toeplitz: lags
+  long long o_D;               // P x P self-block reference matrix
+  long long o_gj;              // Gauss-Jacobi nodes then weights
+  long long o_rs, o_cs;        // Toeplitz row / column scalings (N each)
+  long long o_spec;            // Toeplitz symbol offset (complex entries)
+  long long o_vec;             // sum of N_d over earlier instances
+  long long o_z;               // sum of N*P over earlier instances
+  long long o_T;               // dense: sum of N(N+1)/2 * P over earlier
+  long long o_fft;             // Toeplitz: sum of L*P over earlier instances
+  long long o_N;               // sum of N over earlier instances
+};
+
+struct InstHost {
+  int N, P, Nd, kind;
+  double a, b, alpha, theta, rho, c1, c2, g0;
+  std::vector<double> h, dl, dr;   // lengths; node distances to a and to b
+  bool uniform = false;
+  double q = 1.0;
+  double node_diff(int i, int j) const {  // x_i - x_j, i >= j
+    return (dl[i] <= dr[j]) ? dl[i] - dl[j] : dr[j] - dr[i];
+  }
+};
+
+// Per-column BiCGSTAB scalars (one column = one instance x one rhs).
+struct KCol {
+  double rho, rho_old, alpha, omega, beta, bnorm2, res, snorm, true_res;
+  int status, iters;
+};
+
+struct KrylovWork {
+  DevBuf<double> vecs, partial, bx;
+  DevBuf<long long> coff;
+  DevBuf<int> clen, flag;
+  DevBuf<KCol> cols;
+  ~KrylovWork();
+};
+
+// Preconditioner interface: y = M^{-1} r on element-major vectors.
+struct Precond {
+  virtual ~Precond() {}
+  virtual void apply(int nrhs, const double* r_em, double* y_em) = 0;
+};
+
+}  // namespace hf
+
+struct hfsem_system_s {
+  cudaStream_t st = nullptr;
+  int n_inst = 0;
+  std::vector<hf::InstHost> ih;
+  std::vector<hf::InstDev> idv;
+  hf::DevBuf<hf::InstDev> d_inst;
+  hf::DevBuf<double> arena;
+  hf::DevBuf<double2> spec;
+  hf::DevBuf<double> gl;          // Gauss-Legendre table: rule n at gl_off(n)
+  long long total_nd = 0, total_nz = 0, total_T = 0, total_fft = 0, total_N = 0;
+  int max_P = 0, max_N = 0, max_L = 0;
+  bool any_dense = false, any_toep = false;
+  // scratch, grown on demand
+  hf::DevBuf<double> w_x, w_y, w_z, w_w, w_T, w_ylow, w_mom;
+  hf::DevBuf<double2> w_fa, w_fb;
+  hf::DevBuf<double> w_rhsdata;
+  hf::DevBuf<double2> tw;         // FFT twiddles exp(-2 pi i j / tw_L)
+  int tw_L = 0;
+  hf::KrylovWork kry;
+};
+
+namespace hf {
+// offset of the n-point rule in the Gauss-Legendre table (nodes, then weights)
+__host__ __device__ inline long long gl_off(int n) { return (long long)n * (n - 1); }
+
+// device-side pieces used by other translation units
+void apply_operator(hfsem_system* s, int nrhs, const double* x_em, double* y_em,
+                    int lift);
+void ensure_work(hfsem_system* s, int nrhs);
+void perm_to_elem(hfsem_system* s, int nrhs, const double* x_paper, double* x_em);
+void perm_to_paper(hfsem_system* s, int nrhs, const double* x_em, double* x_paper);
+void load_vector_em(hfsem_system* s, const hfsem_rhs* rhs, int lifted, double* G_em);
+bool is_device_ptr(const void* p);
+hf::Precond* precond_of(hfsem_system* s, hfsem_factor* f);
+void bicgstab(hfsem_system* s, Precond* M, int nrhs, const double* b_em, double* x_em,
+              double tol, int max_iter, std::vector<KCol>& out);
+}  // namespace hf

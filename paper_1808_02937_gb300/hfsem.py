@@ -1,0 +1,298 @@
+"""Thin Python binding of the hfsem C ABI (include/hfsem.h).
+
+Argument marshalling only: every step of the solver runs in the CUDA library
+libhfsem.so.  The functions keep the C names.  Vectors may be numpy arrays
+(host) or CUDA torch tensors (device); the library accepts both kinds of
+pointer.  If the shared library has not been built, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libhfsem.so")
+
+HFSEM_OK = 0
+HFSEM_ERR_INVALID_ARG = 1
+HFSEM_ERR_OOM = 2
+HFSEM_ERR_NOT_CONVERGED = 3
+HFSEM_ERR_BREAKDOWN = 4
+HFSEM_ERR_DEVICE = 6
+HFSEM_ERR_UNSUPPORTED = 7
+
+MATVEC_AUTO, MATVEC_DENSE, MATVEC_TOEPLITZ = 0, 1, 2
+PREC_FP64, PREC_MIXED = 0, 1
+RHS_LOAD_VECTOR, RHS_FRAC_POWERS, RHS_LEGENDRE_AB = 0, 1, 2
+
+# every symbol include/hfsem.h declares
+EXPORTED = ["hfsem_assemble", "hfsem_ndof", "hfsem_apply", "hfsem_load_vector",
+            "hfsem_hlu_factor", "hfsem_hmatrix_dense", "hfsem_precond_apply",
+            "hfsem_solve", "hfsem_factor_free", "hfsem_system_free",
+            "hfsem_status_str"]
+
+
+class HfsemError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: status {code}")
+        self.code = code
+
+
+class hfsem_problem(C.Structure):
+    _fields_ = [("n_elem", C.c_int32), ("P", C.c_int32), ("a", C.c_double),
+                ("b", C.c_double), ("h", C.POINTER(C.c_double)),
+                ("alpha", C.c_double), ("theta", C.c_double), ("rho", C.c_double),
+                ("c1", C.c_double), ("c2", C.c_double), ("matvec", C.c_int32)]
+
+
+class hfsem_hopts(C.Structure):
+    _fields_ = [("R", C.c_int32), ("lambda_", C.c_double), ("tol_hlu", C.c_double),
+                ("precision", C.c_int32), ("leaf_elems", C.c_int32),
+                ("kmax", C.c_int32), ("build_only", C.c_int32)]
+
+
+class hfsem_rhs(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("nrhs", C.c_int32), ("n_terms", C.c_int32),
+                ("data", C.POINTER(C.c_double))]
+
+
+class hfsem_stats(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("status", C.c_int32),
+                ("rel_residual", C.c_double), ("rel_true_residual", C.c_double)]
+
+
+_lib = None
+
+
+def load_library():
+    """Load libhfsem.so; raise if it has not been built (no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"CUDA library missing: {LIB_PATH}; run __graft_entry__.build()")
+    lib = C.CDLL(LIB_PATH)
+    vp = C.c_void_p
+    lib.hfsem_assemble.argtypes = [C.c_int32, C.POINTER(hfsem_problem), vp, C.POINTER(vp)]
+    lib.hfsem_ndof.argtypes = [vp, C.c_int32, C.POINTER(C.c_int32)]
+    lib.hfsem_apply.argtypes = [vp, C.c_int32, vp, vp]
+    lib.hfsem_load_vector.argtypes = [vp, C.POINTER(hfsem_rhs), C.c_int32, vp]
+    lib.hfsem_hlu_factor.argtypes = [vp, C.POINTER(hfsem_hopts), C.POINTER(vp)]
+    lib.hfsem_hmatrix_dense.argtypes = [vp, C.c_int32, vp]
+    lib.hfsem_precond_apply.argtypes = [vp, C.c_int32, vp, vp]
+    lib.hfsem_solve.argtypes = [vp, vp, C.POINTER(hfsem_rhs), C.c_double, C.c_int32, vp,
+                                C.POINTER(hfsem_stats)]
+    lib.hfsem_factor_free.argtypes = [vp]
+    lib.hfsem_factor_free.restype = None
+    lib.hfsem_system_free.argtypes = [vp]
+    lib.hfsem_system_free.restype = None
+    lib.hfsem_status_str.argtypes = [C.c_int]
+    lib.hfsem_status_str.restype = C.c_char_p
+    lib.hfsem_last_error.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(code: int, what: str, allow=()):
+    if code != HFSEM_OK and code not in allow:
+        lib = load_library()
+        msg = lib.hfsem_last_error().decode()
+        raise HfsemError(code, f"{what}: {lib.hfsem_status_str(code).decode()} ({msg})")
+    return code
+
+
+def _ptr(a):
+    """(pointer, is_torch) of a contiguous float64 numpy array or tensor."""
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float64 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("need a C-contiguous float64 array")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        import torch
+        if a.dtype != torch.float64 or not a.is_contiguous():
+            raise ValueError("need a contiguous float64 tensor")
+        return a.data_ptr()
+    raise TypeError(type(a))
+
+
+def _stream_handle(stream):
+    if stream is None:
+        try:
+            import torch
+            if torch.cuda.is_available():
+                return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+        except ImportError:
+            pass
+        return None
+    return C.c_void_p(int(stream))
+
+
+class System:
+    """Handle to an assembled batch of instances (hfsem_system*)."""
+
+    def __init__(self, handle, problems):
+        self.h = handle
+        self.problems = problems
+        self.ndofs = [int(p.n_elem) * int(p.P) - 1 for p in problems]
+
+    @property
+    def total_ndof(self):
+        return sum(self.ndofs)
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.hfsem_system_free(self.h)
+            self.h = None
+
+
+class Factor:
+    def __init__(self, handle, system):
+        self.h = handle
+        self.system = system
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.hfsem_factor_free(self.h)
+            self.h = None
+
+
+def make_problem(h, P, alpha, theta, rho, a=0.0, b=None, c1=0.0, c2=0.0,
+                 matvec=MATVEC_AUTO):
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    if b is None:
+        b = a + float(h.sum())
+    return {"h": h, "P": int(P), "alpha": float(alpha), "theta": float(theta),
+            "rho": float(rho), "a": float(a), "b": float(b), "c1": float(c1),
+            "c2": float(c2), "matvec": int(matvec)}
+
+
+def hfsem_assemble(problems, stream=None) -> System:
+    lib = load_library()
+    arr = (hfsem_problem * len(problems))()
+    keep = []
+    for i, p in enumerate(problems):
+        h = np.ascontiguousarray(p["h"], dtype=np.float64)
+        keep.append(h)
+        arr[i] = hfsem_problem(len(h), p["P"], p["a"], p["b"],
+                               h.ctypes.data_as(C.POINTER(C.c_double)), p["alpha"],
+                               p["theta"], p["rho"], p["c1"], p["c2"], p.get("matvec", 0))
+    out = C.c_void_p()
+    _check(lib.hfsem_assemble(len(problems), arr, _stream_handle(stream), C.byref(out)),
+           "hfsem_assemble")
+    return System(out, [arr[i] for i in range(len(problems))])
+
+
+def hfsem_ndof(sys: System, inst: int) -> int:
+    nd = C.c_int32()
+    _check(load_library().hfsem_ndof(sys.h, inst, C.byref(nd)), "hfsem_ndof")
+    return nd.value
+
+
+def _like(x, n):
+    if isinstance(x, np.ndarray):
+        return np.zeros(n, dtype=np.float64)
+    import torch
+    return torch.zeros(n, dtype=torch.float64, device=x.device)
+
+
+def hfsem_apply(sys: System, x, nrhs: int = 1):
+    y = _like(x, sys.total_ndof * nrhs)
+    _check(load_library().hfsem_apply(sys.h, nrhs, _ptr(x), _ptr(y)), "hfsem_apply")
+    return y
+
+
+def _rhs_array(rhs_list):
+    """rhs_list: per instance (kind, nrhs, n_terms, data ndarray)."""
+    arr = (hfsem_rhs * len(rhs_list))()
+    keep = []
+    for i, (kind, nrhs, n_terms, data) in enumerate(rhs_list):
+        d = np.ascontiguousarray(data, dtype=np.float64).ravel()
+        keep.append(d)
+        arr[i] = hfsem_rhs(kind, nrhs, n_terms, d.ctypes.data_as(C.POINTER(C.c_double)))
+    return arr, keep
+
+
+def rhs_frac_powers(terms_per_rhs):
+    """[(coef, exponent, 'a'|'b'), ...] per rhs -> (kind, nrhs, n_terms, data).
+    Right-hand sides with fewer terms are padded with zero terms."""
+    nt = max(len(t) for t in terms_per_rhs)
+    data = np.zeros((len(terms_per_rhs), nt, 3))
+    for r, terms in enumerate(terms_per_rhs):
+        for k, (c, mu, side) in enumerate(terms):
+            data[r, k] = (c, mu, 0.0 if side == "a" else 1.0)
+    return (RHS_FRAC_POWERS, len(terms_per_rhs), nt, data)
+
+
+def rhs_legendre(coeffs_per_rhs):
+    K1 = max(len(c) for c in coeffs_per_rhs)
+    data = np.zeros((len(coeffs_per_rhs), K1))
+    for r, c in enumerate(coeffs_per_rhs):
+        data[r, : len(c)] = c
+    return (RHS_LEGENDRE_AB, len(coeffs_per_rhs), K1, data)
+
+
+def rhs_load_vector(G, nrhs=1):
+    G = np.ascontiguousarray(G, dtype=np.float64)
+    return (RHS_LOAD_VECTOR, nrhs, 0, G)
+
+
+def hfsem_load_vector(sys: System, rhs_list, lifted: int = 0, out=None):
+    arr, keep = _rhs_array(rhs_list)
+    nrhs = rhs_list[0][1]
+    G = np.zeros(sys.total_ndof * nrhs) if out is None else out
+    _check(load_library().hfsem_load_vector(sys.h, arr, lifted, _ptr(G)), "hfsem_load_vector")
+    return G
+
+
+def hopts(R=8, lam=1.0, tol_hlu=1e-3, precision=PREC_MIXED, leaf_elems=0, kmax=0,
+          build_only=0):
+    return hfsem_hopts(R, lam, tol_hlu, precision, leaf_elems, kmax, build_only)
+
+
+def hfsem_hlu_factor(sys: System, opts: hfsem_hopts) -> Factor:
+    out = C.c_void_p()
+    _check(load_library().hfsem_hlu_factor(sys.h, C.byref(opts), C.byref(out)),
+           "hfsem_hlu_factor")
+    return Factor(out, sys)
+
+
+def hfsem_hmatrix_dense(fac: Factor, inst: int):
+    nd = fac.system.ndofs[inst]
+    out = np.zeros(nd * nd)
+    _check(load_library().hfsem_hmatrix_dense(fac.h, inst, _ptr(out)), "hfsem_hmatrix_dense")
+    return out.reshape(nd, nd, order="F")
+
+
+def hfsem_precond_apply(fac: Factor, r, nrhs: int = 1):
+    y = _like(r, fac.system.total_ndof * nrhs)
+    _check(load_library().hfsem_precond_apply(fac.h, nrhs, _ptr(r), _ptr(y)),
+           "hfsem_precond_apply")
+    return y
+
+
+def hfsem_solve(sys: System, fac, rhs_list, tol=1e-14, max_iter=200, X=None,
+                allow_fail=False):
+    arr, keep = _rhs_array(rhs_list)
+    nrhs = rhs_list[0][1]
+    if X is None:
+        X = np.zeros(sys.total_ndof * nrhs)
+    stats = (hfsem_stats * (len(sys.ndofs) * nrhs))()
+    code = load_library().hfsem_solve(sys.h, fac.h if fac is not None else None, arr,
+                                      tol, max_iter, _ptr(X), stats)
+    if not allow_fail:
+        _check(code, "hfsem_solve")
+    st = [dict(iters=s.iters, status=s.status, rel_residual=s.rel_residual,
+               rel_true_residual=s.rel_true_residual) for s in stats]
+    return X, st, code
+
+
+def split(sys: System, v, nrhs: int = 1):
+    """Split a concatenated vector into per-instance (N_d, nrhs) column-major views."""
+    out, off = [], 0
+    v = np.asarray(v)
+    for nd in sys.ndofs:
+        out.append(v[off: off + nd * nrhs].reshape(nrhs, nd).T)
+        off += nd * nrhs
+    return out
