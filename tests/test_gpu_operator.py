@@ -21,7 +21,7 @@ def _cases():
         ("uniform-auto", W.mesh_uniform(16), 0.0, 1.0, 4, 1.5, 0.5, 0.0, 0),
         ("uniform-dense", W.mesh_uniform(16), 0.0, 1.0, 4, 1.5, 0.5, 0.0, 1),
         ("uniform-P1", W.mesh_uniform(9), 0.0, 1.0, 1, 1.3, 0.2, 1.0, 0),
-        ("uniform-P8-rho", W.mesh_uniform(7), -1.0, 1.0, 8, 1.8, 0.3, 2.0, 0),
+        ("uniform-P8-rho", W.mesh_uniform(7, -1.0, 1.0), -1.0, 1.0, 8, 1.8, 0.3, 2.0, 0),
         ("geo1-toep", W.mesh_geometric_one_sided(10, 0.8), 0.0, 1.0, 3, 1.4, 0.7, 0.5, 2),
         ("geo1-dense", W.mesh_geometric_one_sided(10, 0.8), 0.0, 1.0, 3, 1.4, 0.7, 0.5, 1),
         ("geo2", W.mesh_geometric_two_sided(12, 0.5), 0.0, 1.0, 5, 1.3, 0.7, 1.0, 0),
