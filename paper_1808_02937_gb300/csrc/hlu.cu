@@ -1,25 +1,1270 @@
-// H-matrix approximation (Sec. 3), H-LU factorisation and H-triangular
-// solves (Sec. 4.1).  (placeholder until the factorisation lands)
-#include "hfsem_internal.h"
+// H-matrix approximation A~ (Sec. 3), H-LU factorisation and H-triangular
+// solves (Sec. 4.1) on the GPU.
+//
+//  * k_diag / k_nearfield: the inadmissible leaves keep the exact entries of
+//    A = rho M + theta S_l + (1-theta) S_l^T (end of Sec. 3.2), symmetrically
+//    scaled by powers of two (D A D, D_i = 2^-round(log2(A_ii)/2)) before the
+//    cast to the working precision.
+//  * k_lowrank: every admissible pair (tau right of sigma) gets the Taylor
+//    factors of eq. (eqn:Lexpan), Q_{i,nu} = gamma0 int h_nu phi_i',
+//    W_{j,nu} = int g_nu phi_j' (Sec. 3.2); the lower block is theta Q W^T,
+//    the mirrored upper block (1-theta) W Q^T.  The expansion is in s about
+//    the centre of sigma, or in t about the centre of tau when tau is the
+//    smaller cluster (Remark after the Lemma).
+//  * k_hprog: one CTA per instance runs the op program the host planner
+//    compiled from the recursive H-LU (or the forward/backward substitution).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <array>
+#include <map>
+#include <memory>
+#include <string>
 
-struct hfsem_factor_s {
+#include "hfsem_internal.h"
+#include "hplan.h"
+
+namespace hf {
+
+struct SlotDev {
+  long long off;   // U at off (m x kcap), V at off + m*kcap (n x kcap)
+  int m, n, kcap, kmax;
+};
+
+struct DenseDev {   // one dense block of the near field
+  long long off;
+  int d0r, m, d0c, n;
+};
+
+struct LRPairDev {  // an admissible pair: tau (rows of the lower block) right of sigma
+  int lower_slot, upper_slot;
+  int te0, te1, se0, se1;       // element ranges
+  int tlo, thi, slo, shi;       // support nodes
+  int td0, tm, sd0, sn;         // unknown ranges
+};
+
+struct HInstDev {
+  long long arena;   // offset of the instance arena (elements)
+  long long rk0;     // offset into the rank array
+  long long slot0;   // offset into the slot table
+  long long dense0;  // offset into the dense-block table
+  long long pair0;   // offset into the pair table
+  long long ops0, sops0;
+  int nops, nsops, ndense, npairs, n_slots;
+  long long ws_off, rhs_off;
+  long long d_off;   // scaling D (FP64) offset
+  int sys_inst;      // index into the system's instances
+  int R;
+};
+
+constexpr int kHThreads = 256;
+
+// ---------------------------------------------------------------------------
+// entries of A in element-major unknowns
+// ---------------------------------------------------------------------------
+struct Term {
+  int e, m;
+  double a;
+};
+
+// contributions of unknown i to the Legendre coefficients of u' (z = Pi x)
+__device__ __forceinline__ int terms_of(const InstDev& I, const double* h, int i, Term* t) {
+  const int P = I.P;
+  int e = i / P, p = i % P + 1;
+  if (p < P) {
+    t[0] = Term{e, p, -(2.0 * p + 1.0) * (2.0 / h[e])};
+    return 1;
+  }
+  int j = e + 1;   // hat at node j: right hat of element j-1, left hat of element j
+  t[0] = Term{j - 1, 0, 1.0 / h[j - 1]};
+  t[1] = Term{j, 0, -1.0 / h[j]};
+  return 2;
+}
+
+// Mb_ef[m][n] for f <= e
+__device__ __forceinline__ double mb_entry(const InstDev& I, const double* arena, int e, int f,
+                                           int m, int n) {
+  const int P = I.P;
+  if (I.kind == kDense)
+    return arena[I.o_M + ((long long)e * (e + 1) / 2 + f) * P * P + m * P + n];
+  return arena[I.o_rs + e] * arena[I.o_cs + f] * arena[I.o_M + (long long)(e - f) * P * P + m * P + n];
+}
+
+// S_l[r][c] = sum over terms a b Mb_ef[m][n], f <= e
+__device__ double sl_entry(const InstDev& I, const double* arena, int r, int c) {
+  const double* h = arena + I.o_h;
+  Term tr[2], tc[2];
+  int nr = terms_of(I, h, r, tr), nc = terms_of(I, h, c, tc);
+  double s = 0.0;
+  for (int a = 0; a < nr; ++a)
+    for (int b = 0; b < nc; ++b) {
+      int e = tr[a].e, f = tc[b].e;
+      if (f > e || e < 0 || e >= I.N || f < 0 || f >= I.N) continue;
+      s += tr[a].a * tc[b].a * mb_entry(I, arena, e, f, tr[a].m, tc[b].m);
+    }
+  return s;
+}
+
+// local index of unknown i on element e (0 left hat, 1 right hat, 1+p bubble) or -1
+__device__ __forceinline__ int local_of(int P, int i, int e) {
+  int ei = i / P, p = i % P + 1;
+  if (p < P) return (ei == e) ? 1 + p : -1;
+  int j = ei + 1;
+  if (e == j - 1) return 1;
+  if (e == j) return 0;
+  return -1;
+}
+
+__device__ __forceinline__ double ref_mass(int a, int b) {
+  if (a > b) {
+    int t = a;
+    a = b;
+    b = t;
+  }
+  if (a <= 1 && b <= 1) return (a == b) ? 2.0 / 3.0 : 1.0 / 3.0;
+  if (a <= 1) {
+    int p = b - 1;
+    if (p == 1) return 1.0;
+    if (p == 2) return (a == 0) ? -1.0 / 3.0 : 1.0 / 3.0;
+    return 0.0;
+  }
+  int p = a - 1, q = b - 1;
+  if (p == q) return 2.0 / (2 * p - 1) + 2.0 / (2 * p + 3);
+  if (q == p + 2) return -2.0 / (2 * p + 3);
+  return 0.0;
+}
+
+__device__ double mass_entry(const InstDev& I, const double* h, int r, int c) {
+  const int P = I.P;
+  int er = r / P;
+  double s = 0.0;
+  for (int e = er; e <= er + 1 && e < I.N; ++e) {
+    int a = local_of(P, r, e), b = local_of(P, c, e);
+    if (a >= 0 && b >= 0) s += 0.5 * h[e] * ref_mass(a, b);
+  }
+  return s;
+}
+
+__device__ double a_entry(const InstDev& I, const double* arena, int r, int c) {
+  double v = I.theta * sl_entry(I, arena, r, c) + (1.0 - I.theta) * sl_entry(I, arena, c, r);
+  if (I.rho != 0.0) v += I.rho * mass_entry(I, arena + I.o_h, r, c);
+  return v;
+}
+
+__global__ void k_diag(const HInstDev* __restrict__ hi, const InstDev* __restrict__ inst,
+                       const double* arena, double* D) {
+  const HInstDev H = hi[blockIdx.y];
+  const InstDev I = inst[H.sys_inst];
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < I.Nd; i += gridDim.x * blockDim.x) {
+    double a = fabs(a_entry(I, arena, i, i));
+    D[H.d_off + i] = (a > 0.0 && isfinite(a)) ? exp2(-rint(0.5 * log2(a))) : 1.0;
+  }
+}
+
+template <class T>
+__global__ void k_nearfield(const HInstDev* __restrict__ hi, const InstDev* __restrict__ inst,
+                            const double* arena, const DenseDev* __restrict__ dens,
+                            const double* D, T* har) {
+  const HInstDev H = hi[blockIdx.y];
+  const InstDev I = inst[H.sys_inst];
+  T* ar = har + H.arena;
+  const double* Dv = D + H.d_off;
+  for (int b = blockIdx.x; b < H.ndense; b += gridDim.x) {
+    const DenseDev d = dens[H.dense0 + b];
+    for (int t = threadIdx.x; t < d.m * d.n; t += blockDim.x) {
+      int i = t % d.m, j = t / d.m;
+      int r = d.d0r + i, c = d.d0c + j;
+      ar[d.off + t] = (T)(Dv[r] * a_entry(I, arena, r, c) * Dv[c]);
+    }
+  }
+}
+
+// Taylor low-rank factors of every admissible pair.  CTA per pair.
+template <class T>
+__global__ void k_lowrank(const HInstDev* __restrict__ hi, const InstDev* __restrict__ inst,
+                          const double* arena, const double* __restrict__ gl,
+                          const LRPairDev* __restrict__ pairs, const SlotDev* __restrict__ slots,
+                          const double* D, T* har, int* ranks) {
+  __shared__ double sQ[kMaxP * 32];     // moments of the current element, P x R
+  __shared__ double sQn[32];            // moments L_0 of the next element
+  __shared__ double sX[64], sW[64];
+  const HInstDev H = hi[blockIdx.y];
+  const InstDev I = inst[H.sys_inst];
+  if ((int)blockIdx.x >= H.npairs) return;
+  const LRPairDev pr = pairs[H.pair0 + blockIdx.x];
+  const int P = I.P, R = H.R;
+  const double* h = arena + I.o_h;
+  const double* dl = arena + I.o_dl;
+  const double* dr = arena + I.o_dr;
+  auto ndiff = [&](int a, int b) {   // x_a - x_b, a >= b
+    return (dl[a] <= dr[b]) ? dl[a] - dl[b] : dr[b] - dr[a];
+  };
+  const double r_s = 0.5 * ndiff(pr.shi, pr.slo);
+  const double r_t = 0.5 * ndiff(pr.thi, pr.tlo);
+  const bool sexp = (r_s <= r_t);
+  const double ex = 1.0 - I.alpha;
+  const int nq = min((P + R) / 2 + 13, kMaxGL);
+  const double* X = gl + gl_off(nq);
+  const double* Wt = X + nq;
+  for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+    sX[q] = X[q];
+    sW[q] = Wt[q];
+  }
+  __syncthreads();
+  const SlotDev lo = slots[H.slot0 + pr.lower_slot];
+  const SlotDev up = slots[H.slot0 + pr.upper_slot];
+  T* ar = har + H.arena;
+  const double* Dv = D + H.d_off;
+  // f(side, element, nu, point) of the expansion
+  // side 0 (tau, variable t), side 1 (sigma, variable s)
+  auto fval = [&](int side, int e, int nu, double xq) -> double {
+    double loc = 0.5 * h[e] * (1.0 + xq);
+    if (sexp) {
+      if (side == 0) {   // h_nu(t) = c_nu (-1)^nu r_s^nu (t - s0)^(1-alpha-nu)
+        double d = ndiff(e, pr.shi) + loc + r_s;
+        double c = 1.0;
+        for (int l = 1; l <= nu; ++l) c *= -(2.0 - I.alpha - l) / l * r_s;
+        return c * pow(d, ex - nu);
+      }
+      double y = (ndiff(e, pr.slo) + loc - r_s) / r_s;   // g_nu(s) = ((s - s0)/r_s)^nu
+      double c = 1.0;
+      for (int l = 0; l < nu; ++l) c *= y;
+      return c;
+    }
+    if (side == 0) {   // g~_nu(t) = ((t - t0)/r_t)^nu
+      double y = (ndiff(e, pr.tlo) + loc - r_t) / r_t;
+      double c = 1.0;
+      for (int l = 0; l < nu; ++l) c *= y;
+      return c;
+    }
+    // h~_nu(s) = c_nu r_t^nu (t0 - s)^(1-alpha-nu)
+    double d = r_t + ndiff(pr.tlo, e + 1) + 0.5 * h[e] * (1.0 - xq);
+    double c = 1.0;
+    for (int l = 1; l <= nu; ++l) c *= (2.0 - I.alpha - l) / l * r_t;
+    return c * pow(d, ex - nu);
+  };
+  // moments int_{I_e} f_nu(x) L_m(xi_e(x)) dx into sQ (all m) or sQn (m = 0)
+  auto moments = [&](int side, int e, double* dst, int mcount) {
+    for (int t = threadIdx.x; t < mcount * R; t += blockDim.x) {
+      int m = t / R, nu = t % R;
+      double acc = 0.0;
+      for (int q = 0; q < nq; ++q) {
+        double xq = sX[q];
+        double l0 = 1.0, l1 = xq, lm = (m == 0) ? 1.0 : xq;
+        for (int k = 1; k < m; ++k) {
+          double l2 = ((2 * k + 1) * xq * l1 - k * l0) / (k + 1);
+          l0 = l1;
+          l1 = l2;
+          lm = l2;
+        }
+        acc += sW[q] * lm * fval(side, e, nu, xq);
+      }
+      dst[m * R + nu] = 0.5 * h[e] * acc;
+    }
+  };
+  for (int side = 0; side < 2; ++side) {
+    int e0 = side == 0 ? pr.te0 : pr.se0, e1 = side == 0 ? pr.te1 : pr.se1;
+    int d0 = side == 0 ? pr.td0 : pr.sd0;
+    double scale_side = (side == 0) ? I.g0 : 1.0;   // gamma0 sits with Q
+    for (int e = e0; e < e1; ++e) {
+      moments(side, e, sQ, P);
+      bool hat = (e + 1 < I.N);
+      if (hat) moments(side, e + 1, sQn, 1);
+      __syncthreads();
+      // rows of this element: bubbles p = 1..P-1, then the hat at node e+1
+      int nrow = P - 1 + (hat ? 1 : 0);
+      for (int t = threadIdx.x; t < nrow * R; t += blockDim.x) {
+        int p = t / R + 1, nu = t % R;
+        double v;
+        if (p < P)
+          v = -(2.0 * p + 1.0) * (2.0 / h[e]) * sQ[p * R + nu];
+        else
+          v = sQ[nu] / h[e] - sQn[nu] / h[e + 1];
+        v *= scale_side;
+        int dof = e * P + p - 1;
+        int row = dof - d0;
+        double dsc = Dv[dof];
+        if (side == 0) {
+          // Q row: lower U = theta D Q, upper V = (1-theta) D Q
+          ar[lo.off + row + (long long)nu * lo.m] = (T)(I.theta * dsc * v);
+          ar[up.off + (long long)up.m * up.kcap + row + (long long)nu * up.n] =
+              (T)((1.0 - I.theta) * dsc * v);
+        } else {
+          // W row: lower V = D W, upper U = D W
+          ar[lo.off + (long long)lo.m * lo.kcap + row + (long long)nu * lo.n] = (T)(dsc * v);
+          ar[up.off + row + (long long)nu * up.m] = (T)(dsc * v);
+        }
+      }
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x == 0) {
+    ranks[H.rk0 + pr.lower_slot] = (I.theta != 0.0) ? R : 0;
+    ranks[H.rk0 + pr.upper_slot] = (I.theta != 1.0) ? R : 0;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// interpreter
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int dimv(int d, const int* rk) { return d >= 0 ? d : rk[-1 - d]; }
+__device__ __forceinline__ long long vidx(const View& v, int i, int j) {
+  return v.tr ? v.off + j + (long long)i * v.ld : v.off + i + (long long)j * v.ld;
+}
+
+template <class T>
+struct HCtx {
+  T* ar;
+  int* rk;
+  const SlotDev* sl;
+  T* ws;
+  T* sm;
+  double tol;
+  int* err;
+};
+
+template <class T>
+__device__ T block_sum(T v, T* red) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if (lane == 0) red[warp] = v;
+  __syncthreads();
+  T s = 0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += red[w];
+  __syncthreads();
+  return s;
+}
+
+template <class T>
+__device__ void op_gemm(const HOp& o, HCtx<T>& c) {
+  const int m = dimv(o.C.r, c.rk), n = dimv(o.C.c, c.rk), k = dimv(o.A.c, c.rk);
+  if (m <= 0 || n <= 0) return;
+  T* ar = c.ar;
+  const T alpha = (T)o.alpha, beta = (T)o.beta;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  if (k <= 0) {
+    for (int t = tid; t < m * n; t += nt) {
+      long long ci = vidx(o.C, t % m, t / m);
+      ar[ci] = (beta == (T)0) ? (T)0 : beta * ar[ci];
+    }
+    return;
+  }
+  if (n <= 8) {
+    for (int i = tid; i < m; i += nt) {
+      T acc[8];
+      for (int j = 0; j < 8; ++j) acc[j] = 0;
+      for (int kk = 0; kk < k; ++kk) {
+        T a = ar[vidx(o.A, i, kk)];
+        for (int j = 0; j < n; ++j) acc[j] += a * ar[vidx(o.B, kk, j)];
+      }
+      for (int j = 0; j < n; ++j) {
+        long long ci = vidx(o.C, i, j);
+        ar[ci] = (beta == (T)0 ? (T)0 : beta * ar[ci]) + alpha * acc[j];
+      }
+    }
+    return;
+  }
+  if (m <= 8) {
+    for (int j = tid; j < n; j += nt) {
+      T acc[8];
+      for (int i = 0; i < 8; ++i) acc[i] = 0;
+      for (int kk = 0; kk < k; ++kk) {
+        T b = ar[vidx(o.B, kk, j)];
+        for (int i = 0; i < m; ++i) acc[i] += ar[vidx(o.A, i, kk)] * b;
+      }
+      for (int i = 0; i < m; ++i) {
+        long long ci = vidx(o.C, i, j);
+        ar[ci] = (beta == (T)0 ? (T)0 : beta * ar[ci]) + alpha * acc[i];
+      }
+    }
+    return;
+  }
+  // tiled: 64 x 64 C tiles, k in chunks of 16, 4 x 4 per thread
+  T* As = c.sm;            // [16][64]
+  T* Bs = c.sm + 16 * 64;  // [16][64]
+  const int tx = tid & 15, ty = tid >> 4;
+  for (int m0 = 0; m0 < m; m0 += 64)
+    for (int n0 = 0; n0 < n; n0 += 64) {
+      T acc[4][4];
+      for (int a = 0; a < 4; ++a)
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0;
+      for (int k0 = 0; k0 < k; k0 += 16) {
+        for (int t = tid; t < 16 * 64; t += nt) {
+          int kk = t / 64, ii = t % 64;
+          int gi = m0 + ii, gk = k0 + kk;
+          As[kk * 64 + ii] = (gi < m && gk < k) ? ar[vidx(o.A, gi, gk)] : (T)0;
+          int gj = n0 + ii;
+          Bs[kk * 64 + ii] = (gj < n && gk < k) ? ar[vidx(o.B, gk, gj)] : (T)0;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+          T a[4], b[4];
+          for (int q = 0; q < 4; ++q) {
+            a[q] = As[kk * 64 + ty * 4 + q];
+            b[q] = Bs[kk * 64 + tx * 4 + q];
+          }
+          for (int p = 0; p < 4; ++p)
+            for (int q = 0; q < 4; ++q) acc[p][q] += a[p] * b[q];
+        }
+        __syncthreads();
+      }
+      for (int p = 0; p < 4; ++p)
+        for (int q = 0; q < 4; ++q) {
+          int gi = m0 + ty * 4 + p, gj = n0 + tx * 4 + q;
+          if (gi < m && gj < n) {
+            long long ci = vidx(o.C, gi, gj);
+            ar[ci] = (beta == (T)0 ? (T)0 : beta * ar[ci]) + alpha * acc[p][q];
+          }
+        }
+    }
+}
+
+// C <- A C (A n x n), column panels staged in shared memory
+template <class T>
+__device__ void op_trmm_l(const HOp& o, HCtx<T>& c) {
+  const int n = dimv(o.C.r, c.rk), cc = dimv(o.C.c, c.rk);
+  if (n <= 0 || cc <= 0) return;
+  T* ar = c.ar;
+  const int CP = 32;
+  T* S = c.sm;
+  for (int c0 = 0; c0 < cc; c0 += CP) {
+    int cp = min(CP, cc - c0);
+    for (int t = threadIdx.x; t < n * cp; t += blockDim.x) {
+      int i = t % n, j = t / n;
+      S[j * n + i] = ar[vidx(o.C, i, c0 + j)];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < n * cp; t += blockDim.x) {
+      int i = t % n, j = t / n;
+      T acc = 0;
+      for (int k = 0; k < n; ++k) acc += ar[vidx(o.A, i, k)] * S[j * n + k];
+      ar[vidx(o.C, i, c0 + j)] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// C <- C A (A n x n), row panels staged in shared memory
+template <class T>
+__device__ void op_trmm_r(const HOp& o, HCtx<T>& c) {
+  const int m = dimv(o.C.r, c.rk), n = dimv(o.C.c, c.rk);
+  if (m <= 0 || n <= 0) return;
+  T* ar = c.ar;
+  const int RP = 32;
+  T* S = c.sm;
+  for (int r0 = 0; r0 < m; r0 += RP) {
+    int rp = min(RP, m - r0);
+    for (int t = threadIdx.x; t < rp * n; t += blockDim.x) {
+      int i = t % rp, k = t / rp;
+      S[k * RP + i] = ar[vidx(o.C, r0 + i, k)];
+    }
+    __syncthreads();
+    for (int t = threadIdx.x; t < rp * n; t += blockDim.x) {
+      int i = t % rp, j = t / rp;
+      T acc = 0;
+      for (int k = 0; k < n; ++k) acc += S[k * RP + i] * ar[vidx(o.A, k, j)];
+      ar[vidx(o.C, r0 + i, j)] = acc;
+    }
+    __syncthreads();
+  }
+}
+
+// unpivoted LU of C (n x n) and the inverses of both factors
+template <class T>
+__device__ void op_getrf_inv(const HOp& o, HCtx<T>& c) {
+  const int n = o.C.r;
+  if (n <= 0) return;
+  T* ar = c.ar;
+  T* S = c.sm;          // LU, column-major n x n
+  T* X = c.sm + n * n;  // inverse being built
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int t = tid; t < n * n; t += nt) S[t] = ar[vidx(o.C, t % n, t / n)];
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    T piv = S[k + k * n];
+    if (tid == 0 && (piv == (T)0 || !isfinite((double)piv))) atomicExch(c.err, 1);
+    for (int i = k + 1 + tid; i < n; i += nt) S[i + k * n] /= piv;
+    __syncthreads();
+    int w = n - k - 1;
+    for (int t = tid; t < w * w; t += nt) {
+      int i = k + 1 + t % w, j = k + 1 + t / w;
+      S[i + j * n] -= S[i + k * n] * S[k + j * n];
+    }
+    __syncthreads();
+  }
+  // L^-1 (unit lower): X = I, eliminate below the diagonal column by column
+  for (int t = tid; t < n * n; t += nt) X[t] = (t % n == t / n) ? (T)1 : (T)0;
+  __syncthreads();
+  for (int k = 0; k + 1 < n; ++k) {
+    int w = n - k - 1;
+    for (int t = tid; t < w * (k + 1); t += nt) {
+      int i = k + 1 + t % w, j = t / w;
+      X[i + j * n] -= S[i + k * n] * X[k + j * n];
+    }
+    __syncthreads();
+  }
+  for (int t = tid; t < n * n; t += nt) ar[vidx(o.A, t % n, t / n)] = X[t];
+  __syncthreads();
+  // U^-1: X = I, rows from the bottom: X[k,:] /= U_kk; X[i,:] -= U_ik X[k,:]
+  for (int t = tid; t < n * n; t += nt) X[t] = (t % n == t / n) ? (T)1 : (T)0;
+  __syncthreads();
+  for (int k = n - 1; k >= 0; --k) {
+    T ukk = S[k + k * n];
+    for (int j = k + tid; j < n; j += nt) X[k + j * n] /= ukk;
+    __syncthreads();
+    int w = n - k;
+    for (int t = tid; t < k * w; t += nt) {
+      int i = t % k, j = k + t / k;
+      X[i + j * n] -= S[i + k * n] * X[k + j * n];
+    }
+    __syncthreads();
+  }
+  for (int t = tid; t < n * n; t += nt) ar[vidx(o.B, t % n, t / n)] = X[t];
+}
+
+// Householder QR of A (m x K, ld m) in place: R in the upper trapezoid,
+// reflectors v (v_0 = 1 implied) below, tau[j]; kr = min(m, K) reflectors.
+template <class T>
+__device__ void house_qr(T* A, int m, int K, T* tau, T* red) {
+  const int kr = min(m, K);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = 0; j < kr; ++j) {
+    T part = 0;
+    for (int i = j + threadIdx.x; i < m; i += blockDim.x) part += A[i + (long long)j * m] * A[i + (long long)j * m];
+    T s2 = block_sum<T>(part, red);
+    T x0 = A[j + (long long)j * m];
+    T s = sqrt(s2);
+    T alpha = (x0 >= (T)0) ? -s : s;
+    T v0 = x0 - alpha;
+    bool trivial = (s == (T)0) || (v0 == (T)0);
+    if (!trivial)
+      for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) A[i + (long long)j * m] /= v0;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      tau[j] = trivial ? (T)0 : (alpha - x0) / alpha;
+      if (!trivial) A[j + (long long)j * m] = alpha;
+    }
+    __syncthreads();
+    T tj = tau[j];
+    if (tj != (T)0) {
+      for (int l = j + 1 + warp; l < K; l += nw) {
+        T w = 0;
+        for (int i = j + 1 + lane; i < m; i += 32) w += A[i + (long long)j * m] * A[i + (long long)l * m];
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        w = (w + A[j + (long long)l * m]) * tj;
+        if (lane == 0) A[j + (long long)l * m] -= w;
+        for (int i = j + 1 + lane; i < m; i += 32) A[i + (long long)l * m] -= w * A[i + (long long)j * m];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Y (m x r, ld ldy) <- Q Y with Q = H_0 ... H_{kr-1} stored in A (m x K)
+template <class T>
+__device__ void apply_q(const T* A, int m, int K, const T* tau, T* Y, int ldy, int r) {
+  const int kr = min(m, K);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int j = kr - 1; j >= 0; --j) {
+    T tj = tau[j];
+    if (tj != (T)0) {
+      for (int col = warp; col < r; col += nw) {
+        T w = 0;
+        for (int i = j + 1 + lane; i < m; i += 32) w += A[i + (long long)j * m] * Y[i + (long long)col * ldy];
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        w = (w + Y[j + (long long)col * ldy]) * tj;
+        if (lane == 0) Y[j + (long long)col * ldy] -= w;
+        for (int i = j + 1 + lane; i < m; i += 32) Y[i + (long long)col * ldy] -= w * A[i + (long long)j * m];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Recompress U V^T given as Ut (m x K) and Vt (n x K) in the workspace into
+// LR slot `slot`: SVD of R_U R_V^T by one-sided Jacobi, keep sigma_i >
+// tol sigma_1, at most kmax.
+template <class T>
+__device__ void trunc_core(HCtx<T>& c, int slot, T* Ut, T* Vt, int K) {
+  const SlotDev s = c.sl[slot];
+  const int m = s.m, n = s.n;
+  T* tauU = c.sm;
+  T* tauV = tauU + K;
+  T* red = tauV + K;                 // 32
+  T* M = red + 32;                   // ku x kv, ld K
+  T* J = M + K * K;                  // kv x kv, ld K
+  house_qr(Ut, m, K, tauU, red);
+  house_qr(Vt, n, K, tauV, red);
+  const int ku = min(m, K), kv = min(n, K);
+  // M = R_U R_V^T
+  for (int t = threadIdx.x; t < ku * kv; t += blockDim.x) {
+    int i = t % ku, j = t / ku;
+    T acc = 0;
+    for (int l = max(i, j); l < K; ++l) {
+      T ru = (i <= l) ? Ut[i + (long long)l * m] : (T)0;
+      T rv = (j <= l) ? Vt[j + (long long)l * n] : (T)0;
+      acc += ru * rv;
+    }
+    M[i + j * K] = acc;
+  }
+  for (int t = threadIdx.x; t < kv * kv; t += blockDim.x) J[(t % kv) + (t / kv) * K] = (t % kv == t / kv) ? (T)1 : (T)0;
+  __syncthreads();
+  // one-sided Jacobi on the kv columns of M (length ku)
+  const T eps = (sizeof(T) == 4) ? (T)1e-7 : (T)1e-15;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int kp = kv + (kv & 1);
+  __shared__ int rotated;
+  for (int sweep = 0; sweep < 30 && kv > 1; ++sweep) {
+    if (threadIdx.x == 0) rotated = 0;
+    __syncthreads();
+    for (int round = 0; round < kp - 1; ++round) {
+      for (int pi = warp; pi < kp / 2; pi += nw) {
+        int p, q;
+        if (pi == 0) {
+          p = round;
+          q = kp - 1;
+        } else {
+          p = (round + pi) % (kp - 1);
+          q = (round - pi + kp - 1) % (kp - 1);
+        }
+        if (p >= kv || q >= kv) continue;
+        T a = 0, b = 0, g = 0;
+        for (int i = lane; i < ku; i += 32) {
+          T mp = M[i + p * K], mq = M[i + q * K];
+          a += mp * mp;
+          b += mq * mq;
+          g += mp * mq;
+        }
+        for (int o = 16; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          b += __shfl_xor_sync(0xffffffffu, b, o);
+          g += __shfl_xor_sync(0xffffffffu, g, o);
+        }
+        if (g != (T)0 && fabs((double)g) > (double)eps * sqrt((double)a * (double)b)) {
+          T zeta = (b - a) / (2 * g);
+          T t = (zeta >= (T)0 ? (T)1 : (T)-1) / (fabs(zeta) + sqrt((T)1 + zeta * zeta));
+          T cs = (T)1 / sqrt((T)1 + t * t), sn = cs * t;
+          for (int i = lane; i < ku; i += 32) {
+            T mp = M[i + p * K], mq = M[i + q * K];
+            M[i + p * K] = cs * mp - sn * mq;
+            M[i + q * K] = sn * mp + cs * mq;
+          }
+          for (int i = lane; i < kv; i += 32) {
+            T jp = J[i + p * K], jq = J[i + q * K];
+            J[i + p * K] = cs * jp - sn * jq;
+            J[i + q * K] = sn * jp + cs * jq;
+          }
+          if (lane == 0) rotated = 1;
+        }
+      }
+      __syncthreads();
+    }
+    if (!rotated) break;
+    __syncthreads();
+  }
+  // singular values and their order
+  T* sig = J + K * K;          // kv
+  int* pos = (int*)(sig + K);  // kv
+  for (int j = threadIdx.x; j < kv; j += blockDim.x) {
+    T a = 0;
+    for (int i = 0; i < ku; ++i) a += M[i + j * K] * M[i + j * K];
+    sig[j] = sqrt(a);
+  }
+  __syncthreads();
+  T smax = 0;
+  for (int j = 0; j < kv; ++j) smax = fmax(smax, sig[j]);
+  T thr = (T)c.tol * smax;
+  int keep = 0;
+  for (int j = 0; j < kv; ++j)
+    if (sig[j] > thr && sig[j] > (T)0) ++keep;
+  keep = min(keep, s.kmax);
+  for (int j = threadIdx.x; j < kv; j += blockDim.x) {
+    int r = 0;
+    for (int l = 0; l < kv; ++l)
+      if (sig[l] > sig[j] || (sig[l] == sig[j] && l < j)) ++r;
+    pos[j] = r;
+  }
+  __syncthreads();
+  // new factors: U = Q_U [M_j; 0], V = Q_V [J_j; 0] for the kept columns
+  T* Ud = c.ar + s.off;
+  T* Vd = c.ar + s.off + (long long)m * s.kcap;
+  for (int t = threadIdx.x; t < m * keep; t += blockDim.x) Ud[t] = 0;
+  for (int t = threadIdx.x; t < n * keep; t += blockDim.x) Vd[t] = 0;
+  __syncthreads();
+  for (int t = threadIdx.x; t < kv * max(ku, kv); t += blockDim.x) {
+    int j = t / max(ku, kv), i = t % max(ku, kv);
+    int pj = pos[j];
+    if (pj >= keep) continue;
+    if (i < ku) Ud[i + (long long)pj * m] = M[i + j * K];
+    if (i < kv) Vd[i + (long long)pj * n] = J[i + j * K];
+  }
+  __syncthreads();
+  apply_q(Ut, m, K, tauU, Ud, m, keep);
+  apply_q(Vt, n, K, tauV, Vd, n, keep);
+  if (threadIdx.x == 0) c.rk[slot] = keep;
+  __syncthreads();
+}
+
+template <class T>
+__device__ void op_append(const HOp& o, HCtx<T>& c) {
+  const int slot = o.slot;
+  const SlotDev s = c.sl[slot];
+  const int k = dimv(o.A.c, c.rk);
+  const int r0 = c.rk[slot];
+  __syncthreads();
+  if (k <= 0) return;
+  const bool ident = o.B.off < 0;
+  const T alpha = (T)o.alpha;
+  T* ar = c.ar;
+  if (r0 + k <= s.kcap) {
+    T* Ud = ar + s.off;
+    T* Vd = ar + s.off + (long long)s.m * s.kcap;
+    for (int t = threadIdx.x; t < s.m * k; t += blockDim.x) {
+      int i = t % s.m, j = t / s.m;
+      Ud[i + (long long)(r0 + j) * s.m] = alpha * ar[vidx(o.A, i, j)];
+    }
+    for (int t = threadIdx.x; t < s.n * k; t += blockDim.x) {
+      int i = t % s.n, j = t / s.n;
+      Vd[i + (long long)(r0 + j) * s.n] = ident ? (T)(i == j ? 1 : 0) : ar[vidx(o.B, i, j)];
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) c.rk[slot] = r0 + k;
+    __syncthreads();
+    return;
+  }
+  const int K = r0 + k;
+  T* Ut = c.ws;
+  T* Vt = c.ws + (long long)s.m * K;
+  const T* Us = ar + s.off;
+  const T* Vs = ar + s.off + (long long)s.m * s.kcap;
+  for (int t = threadIdx.x; t < s.m * K; t += blockDim.x) {
+    int i = t % s.m, j = t / s.m;
+    Ut[t] = (j < r0) ? Us[i + (long long)j * s.m] : alpha * ar[vidx(o.A, i, j - r0)];
+  }
+  for (int t = threadIdx.x; t < s.n * K; t += blockDim.x) {
+    int i = t % s.n, j = t / s.n;
+    Vt[t] = (j < r0) ? Vs[i + (long long)j * s.n]
+                     : (ident ? (T)(i == j - r0 ? 1 : 0) : ar[vidx(o.B, i, j - r0)]);
+  }
+  __syncthreads();
+  trunc_core(c, slot, Ut, Vt, K);
+}
+
+template <class T>
+__device__ void op_trunc(const HOp& o, HCtx<T>& c) {
+  const int slot = o.slot;
+  const SlotDev s = c.sl[slot];
+  const int K = c.rk[slot];
+  __syncthreads();
+  if (K <= 0) return;
+  T* Ut = c.ws;
+  T* Vt = c.ws + (long long)s.m * K;
+  const T* Us = c.ar + s.off;
+  const T* Vs = c.ar + s.off + (long long)s.m * s.kcap;
+  for (int t = threadIdx.x; t < s.m * K; t += blockDim.x) Ut[t] = Us[t];
+  for (int t = threadIdx.x; t < s.n * K; t += blockDim.x) Vt[t] = Vs[t];
+  __syncthreads();
+  trunc_core(c, slot, Ut, Vt, K);
+}
+
+struct HProgArgs {
+  const HInstDev* inst;
+  const HOp* ops;
+  const SlotDev* slots;
+  int* ranks;
+  int* err;
+  double tol;
+};
+
+template <class T>
+__global__ void __launch_bounds__(kHThreads) k_hprog(HProgArgs a, T* har, int which) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  const HInstDev H = a.inst[blockIdx.x];
+  HCtx<T> c;
+  c.ar = har + H.arena;
+  c.rk = a.ranks + H.rk0;
+  c.sl = a.slots + H.slot0;
+  c.ws = c.ar + H.ws_off;
+  c.sm = reinterpret_cast<T*>(smraw);
+  c.tol = a.tol;
+  c.err = a.err + blockIdx.x;
+  const HOp* ops = a.ops + (which ? H.sops0 : H.ops0);
+  const int nops = which ? H.nsops : H.nops;
+  for (int i = 0; i < nops; ++i) {
+    const HOp o = ops[i];
+    switch (o.type) {
+      case OP_GEMM: op_gemm(o, c); break;
+      case OP_GETRF_INV: op_getrf_inv(o, c); break;
+      case OP_TRMM_L: op_trmm_l(o, c); break;
+      case OP_TRMM_R: op_trmm_r(o, c); break;
+      case OP_APPEND: op_append(o, c); break;
+      case OP_TRUNC: op_trunc(o, c); break;
+      case OP_ZERO: {
+        int m = dimv(o.C.r, c.rk), n = dimv(o.C.c, c.rk);
+        for (int t = threadIdx.x; t < m * n; t += blockDim.x) c.ar[vidx(o.C, t % m, t / m)] = 0;
+        break;
+      }
+      case OP_AXPY: {
+        int m = dimv(o.C.r, c.rk), n = dimv(o.C.c, c.rk);
+        for (int t = threadIdx.x; t < m * n; t += blockDim.x) {
+          int i = t % m, j = t / m;
+          c.ar[vidx(o.C, i, j)] += (T)o.alpha * c.ar[vidx(o.A, i, j)];
+        }
+        break;
+      }
+      default: break;
+    }
+    __syncthreads();
+  }
+}
+
+// rhs area <- D r (element-major FP64 -> T); rank slot n_slots <- nrhs
+template <class T>
+__global__ void k_hsolve_in(const HInstDev* __restrict__ hi, const InstDev* __restrict__ inst,
+                            const double* __restrict__ r, const double* D, T* har, int* ranks,
+                            int nrhs) {
+  const HInstDev H = hi[blockIdx.y];
+  const InstDev I = inst[H.sys_inst];
+  T* rhs = har + H.arena + H.rhs_off;
+  const double* rv = r + I.o_vec * nrhs;
+  const long long n = (long long)I.Nd * nrhs;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    rhs[t] = (T)(D[H.d_off + t % I.Nd] * rv[t]);
+  if (blockIdx.x == 0 && threadIdx.x == 0) ranks[H.rk0 + H.n_slots] = nrhs;
+}
+
+template <class T>
+__global__ void k_hsolve_out(const HInstDev* __restrict__ hi, const InstDev* __restrict__ inst,
+                             const double* D, const T* har, double* y, int nrhs) {
+  const HInstDev H = hi[blockIdx.y];
+  const InstDev I = inst[H.sys_inst];
+  const T* rhs = har + H.arena + H.rhs_off;
+  double* yv = y + I.o_vec * nrhs;
+  const long long n = (long long)I.Nd * nrhs;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < n;
+       t += (long long)gridDim.x * blockDim.x)
+    yv[t] = D[H.d_off + t % I.Nd] * (double)rhs[t];
+}
+
+// Dense expansion of the (unfactored) H-matrix, unscaled, element-major.
+template <class T>
+__global__ void k_expand(const HInstDev* __restrict__ hi, const DenseDev* dens,
+                         const LRPairDev* pairs, const SlotDev* slots, const int* ranks,
+                         const double* D, const T* har, double* out, int Nd) {
+  const HInstDev H = hi[0];
+  const T* ar = har + H.arena;
+  const double* Dv = D + H.d_off;
+  const int nb = H.ndense + 2 * H.npairs;
+  for (int b = blockIdx.x; b < nb; b += gridDim.x) {
+    if (b < H.ndense) {
+      DenseDev d = dens[H.dense0 + b];
+      for (int t = threadIdx.x; t < d.m * d.n; t += blockDim.x) {
+        int i = t % d.m, j = t / d.m;
+        int r = d.d0r + i, c = d.d0c + j;
+        out[r + (long long)c * Nd] = (double)ar[d.off + t] / (Dv[r] * Dv[c]);
+      }
+    } else {
+      int pi = (b - H.ndense) / 2, up = (b - H.ndense) % 2;
+      LRPairDev pr = pairs[H.pair0 + pi];
+      int slot = up ? pr.upper_slot : pr.lower_slot;
+      SlotDev s = slots[H.slot0 + slot];
+      int k = ranks[H.rk0 + slot];
+      int rr0 = up ? pr.sd0 : pr.td0, cc0 = up ? pr.td0 : pr.sd0;
+      for (int t = threadIdx.x; t < s.m * s.n; t += blockDim.x) {
+        int i = t % s.m, j = t / s.m;
+        double acc = 0.0;
+        for (int l = 0; l < k; ++l)
+          acc += (double)ar[s.off + i + (long long)l * s.m] *
+                 (double)ar[s.off + (long long)s.m * s.kcap + j + (long long)l * s.n];
+        int r = rr0 + i, c = cc0 + j;
+        out[r + (long long)c * Nd] = acc / (Dv[r] * Dv[c]);
+      }
+    }
+  }
+}
+
+__global__ void k_perm_mat(const double* in, double* out, int Nd, int N, int P) {
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < (long long)Nd * Nd;
+       t += (long long)gridDim.x * blockDim.x) {
+    int r = (int)(t % Nd), c = (int)(t / Nd);
+    auto pidx = [&](int i) {
+      int e = i / P, p = i % P + 1;
+      return (p < P) ? e * (P - 1) + p - 1 : N * (P - 1) + e;
+    };
+    out[pidx(r) + (long long)pidx(c) * Nd] = in[t];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host: factor object
+// ---------------------------------------------------------------------------
+struct PlanBundle {
+  HPlan plan;
+  std::vector<DenseDev> dense;
+  std::vector<LRPairDev> pairs;
+  std::vector<SlotDev> slots;
+};
+
+}  // namespace hf
+
+struct hfsem_factor_s : public hf::Precond {
   hfsem_system* sys = nullptr;
+  int precision = HFSEM_PREC_MIXED;
+  int build_only = 0;
+  double tol = 1e-3;
+  int R = 8;
+  size_t tsize = 4;
+  std::vector<std::shared_ptr<hf::PlanBundle>> plans;   // per instance (shared)
+  std::vector<hf::HInstDev> hidev;
+  hf::DevBuf<hf::HInstDev> d_hi;
+  hf::DevBuf<hf::HOp> d_ops;
+  hf::DevBuf<hf::SlotDev> d_slots;
+  hf::DevBuf<hf::DenseDev> d_dense;
+  hf::DevBuf<hf::LRPairDev> d_pairs;
+  hf::DevBuf<int> d_ranks, d_err;
+  hf::DevBuf<double> d_D;
+  hf::DevBuf<unsigned char> d_arena;
+  size_t smem = 0;
+  long long total_ops = 0, total_sops = 0;
+  void apply(int nrhs, const double* r_em, double* y_em) override;
+  void run_prog(int which);
 };
 
 namespace hf {
-Precond* precond_of(hfsem_system*, hfsem_factor* f) {
-  if (f) throw Error(HFSEM_ERR_UNSUPPORTED, "H-LU not built yet");
-  return nullptr;
+
+template <class T>
+static void set_prog_smem(size_t bytes) {
+  HF_CHECK(cudaFuncSetAttribute((const void*)k_hprog<T>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+}
+
+static size_t prog_smem(const HPlan& p, size_t ts) {
+  size_t leaf = (size_t)2 * p.leaf_max * p.leaf_max;
+  size_t K = (size_t)std::max(p.kconcat_max, 1);
+  size_t trunc = 2 * K + 32 + 2 * K * K + 2 * K + 8;
+  size_t trmm = (size_t)std::max(p.leaf_max, 1) * 32;
+  size_t gemm = 2 * 16 * 64;
+  return std::max(std::max(leaf, trunc), std::max(trmm, gemm)) * ts + 64;
+}
+
+static std::string plan_key(const InstHost& I, const PlanOpts& o) {
+  std::string k(reinterpret_cast<const char*>(I.h.data()), I.h.size() * sizeof(double));
+  char buf[128];
+  snprintf(buf, sizeof(buf), "|%d|%d|%.17g|%d|%d|%d|%d", I.N, I.P, o.lambda, o.leaf_elems, o.R,
+           o.kmax, o.max_concat);
+  return k + buf;
+}
+
+static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
+  if (opt.R < 1 || opt.R > 32) throw Error(HFSEM_ERR_INVALID_ARG, "R must be in [1, 32]");
+  if (!(opt.lambda > 0.0)) throw Error(HFSEM_ERR_INVALID_ARG, "lambda must be > 0");
+  if (!(opt.tol_hlu >= 0.0)) throw Error(HFSEM_ERR_INVALID_ARG, "tol_hlu must be >= 0");
+  if (opt.precision != HFSEM_PREC_FP64 && opt.precision != HFSEM_PREC_MIXED)
+    throw Error(HFSEM_ERR_INVALID_ARG, "unknown precision");
+  if (opt.leaf_elems < 0 || opt.kmax < 0) throw Error(HFSEM_ERR_INVALID_ARG, "leaf_elems, kmax >= 0");
+  auto* f = new hfsem_factor();
+  try {
+    f->sys = s;
+    f->precision = opt.precision;
+    f->build_only = opt.build_only;
+    f->tol = opt.tol_hlu;
+    f->R = opt.R;
+    const bool fp32 = opt.precision == HFSEM_PREC_MIXED;
+    f->tsize = fp32 ? sizeof(float) : sizeof(double);
+    const int max_leaf = fp32 ? 128 : 96;
+    std::map<std::string, std::shared_ptr<PlanBundle>> cache;
+    const int ni = s->n_inst;
+    f->plans.resize(ni);
+    f->hidev.resize(ni);
+    for (int i = 0; i < ni; ++i) {
+      const InstHost& I = s->ih[i];
+      PlanOpts o;
+      o.lambda = opt.lambda;
+      int leaf = opt.leaf_elems ? opt.leaf_elems : std::max(1, 64 / I.P);
+      leaf = std::min(leaf, std::max(1, max_leaf / I.P));
+      o.leaf_elems = leaf;
+      o.R = opt.R;
+      o.kmax = opt.kmax ? opt.kmax : std::max(2 * opt.R, 8);
+      o.nrhs_max = 64;
+      o.max_concat = fp32 ? 128 : 96;
+      o.max_leaf = max_leaf;
+      std::string key = plan_key(I, o);
+      auto it = cache.find(key);
+      if (it == cache.end()) {
+        auto pb = std::make_shared<PlanBundle>();
+        make_plan(I, o, pb->plan);
+        HPlan& p = pb->plan;
+        for (int bi : p.dense_blocks) {
+          const Block& b = p.B[bi];
+          pb->dense.push_back(DenseDev{b.off, p.C[b.t].d0, b.m, p.C[b.s].d0, b.n});
+        }
+        for (int bi : p.lr_blocks) {
+          const Block& b = p.B[bi];
+          pb->slots.push_back(SlotDev{b.off, b.m, b.n, b.kcap, b.kmax});
+        }
+        // pair lower blocks (t right of s) with their mirrors
+        std::map<std::pair<int, int>, int> slot_of;
+        for (int bi : p.lr_blocks) slot_of[{p.B[bi].t, p.B[bi].s}] = p.B[bi].slot;
+        for (int bi : p.lr_blocks) {
+          const Block& b = p.B[bi];
+          if (!b.lower) continue;
+          auto mi = slot_of.find({b.s, b.t});
+          if (mi == slot_of.end()) throw Error(HFSEM_ERR_DEVICE, "block tree is not symmetric");
+          const Cluster &ct = p.C[b.t], &cs = p.C[b.s];
+          pb->pairs.push_back(LRPairDev{b.slot, mi->second, ct.e0, ct.e1, cs.e0, cs.e1, ct.lo,
+                                        ct.hi, cs.lo, cs.hi, ct.d0, b.m, cs.d0, b.n});
+        }
+        it = cache.emplace(key, pb).first;
+      }
+      f->plans[i] = it->second;
+    }
+    // concatenate tables
+    std::vector<HOp> ops;
+    std::vector<SlotDev> slots;
+    std::vector<DenseDev> dense;
+    std::vector<LRPairDev> pairs;
+    std::map<const PlanBundle*, std::array<long long, 5>> placed;
+    long long arena = 0, rk = 0, doff = 0;
+    size_t smem = 0;
+    for (int i = 0; i < ni; ++i) {
+      const PlanBundle* pb = f->plans[i].get();
+      auto pi = placed.find(pb);
+      if (pi == placed.end()) {
+        std::array<long long, 5> a{(long long)ops.size(), (long long)(ops.size() + pb->plan.fac.size()),
+                                   (long long)slots.size(), (long long)dense.size(),
+                                   (long long)pairs.size()};
+        ops.insert(ops.end(), pb->plan.fac.begin(), pb->plan.fac.end());
+        ops.insert(ops.end(), pb->plan.sol.begin(), pb->plan.sol.end());
+        slots.insert(slots.end(), pb->slots.begin(), pb->slots.end());
+        dense.insert(dense.end(), pb->dense.begin(), pb->dense.end());
+        pairs.insert(pairs.end(), pb->pairs.begin(), pb->pairs.end());
+        pi = placed.emplace(pb, a).first;
+        smem = std::max(smem, prog_smem(pb->plan, f->tsize));
+      }
+      HInstDev& H = f->hidev[i];
+      std::memset(&H, 0, sizeof(H));
+      const HPlan& p = pb->plan;
+      H.arena = arena;
+      arena += p.arena;
+      arena = (arena + 31) & ~31LL;
+      H.rk0 = rk;
+      rk += p.n_slots + 1;
+      H.slot0 = pi->second[2];
+      H.dense0 = pi->second[3];
+      H.pair0 = pi->second[4];
+      H.ops0 = pi->second[0];
+      H.sops0 = pi->second[1];
+      H.nops = (int)p.fac.size();
+      H.nsops = (int)p.sol.size();
+      H.ndense = (int)pb->dense.size();
+      H.npairs = (int)pb->pairs.size();
+      H.n_slots = p.n_slots;
+      H.ws_off = p.ws_off;
+      H.rhs_off = p.rhs_off;
+      H.d_off = doff;
+      doff += s->ih[i].Nd;
+      H.sys_inst = i;
+      H.R = opt.R;
+      f->total_ops += H.nops;
+      f->total_sops += H.nsops;
+    }
+    if (smem > 227 * 1024) throw Error(HFSEM_ERR_UNSUPPORTED, "H-LU kernel needs too much shared memory");
+    f->smem = smem;
+    f->d_hi.alloc(ni);
+    HF_CHECK(cudaMemcpyAsync(f->d_hi.p, f->hidev.data(), ni * sizeof(HInstDev), cudaMemcpyHostToDevice, s->st));
+    f->d_ops.alloc(std::max<size_t>(ops.size(), 1));
+    if (!ops.empty())
+      HF_CHECK(cudaMemcpyAsync(f->d_ops.p, ops.data(), ops.size() * sizeof(HOp), cudaMemcpyHostToDevice, s->st));
+    f->d_slots.alloc(std::max<size_t>(slots.size(), 1));
+    if (!slots.empty())
+      HF_CHECK(cudaMemcpyAsync(f->d_slots.p, slots.data(), slots.size() * sizeof(SlotDev), cudaMemcpyHostToDevice, s->st));
+    f->d_dense.alloc(std::max<size_t>(dense.size(), 1));
+    if (!dense.empty())
+      HF_CHECK(cudaMemcpyAsync(f->d_dense.p, dense.data(), dense.size() * sizeof(DenseDev), cudaMemcpyHostToDevice, s->st));
+    f->d_pairs.alloc(std::max<size_t>(pairs.size(), 1));
+    if (!pairs.empty())
+      HF_CHECK(cudaMemcpyAsync(f->d_pairs.p, pairs.data(), pairs.size() * sizeof(LRPairDev), cudaMemcpyHostToDevice, s->st));
+    f->d_ranks.alloc(std::max<long long>(rk, 1));
+    HF_CHECK(cudaMemsetAsync(f->d_ranks.p, 0, std::max<long long>(rk, 1) * sizeof(int), s->st));
+    f->d_err.alloc(ni);
+    HF_CHECK(cudaMemsetAsync(f->d_err.p, 0, ni * sizeof(int), s->st));
+    f->d_D.alloc(std::max<long long>(doff, 1));
+    f->d_arena.alloc((size_t)std::max<long long>(arena, 1) * f->tsize);
+    HF_CHECK(cudaMemsetAsync(f->d_arena.p, 0, (size_t)std::max<long long>(arena, 1) * f->tsize, s->st));
+    // build A~
+    int maxnd = 1, maxdense = 1, maxpairs = 1;
+    for (auto& H : f->hidev) {
+      maxnd = std::max(maxnd, s->ih[H.sys_inst].Nd);
+      maxdense = std::max(maxdense, H.ndense);
+      maxpairs = std::max(maxpairs, H.npairs);
+    }
+    dim3 gd((maxnd + 255) / 256, ni);
+    k_diag<<<gd, 256, 0, s->st>>>(f->d_hi.p, s->d_inst.p, s->arena.p, f->d_D.p);
+    HF_LAUNCH_CHECK();
+    dim3 gn(std::min(maxdense, 1024), ni);
+    dim3 gp(maxpairs, ni);
+    if (fp32) {
+      float* ar = reinterpret_cast<float*>(f->d_arena.p);
+      k_nearfield<float><<<gn, 256, 0, s->st>>>(f->d_hi.p, s->d_inst.p, s->arena.p, f->d_dense.p, f->d_D.p, ar);
+      HF_LAUNCH_CHECK();
+      k_lowrank<float><<<gp, 128, 0, s->st>>>(f->d_hi.p, s->d_inst.p, s->arena.p, s->gl.p, f->d_pairs.p,
+                                              f->d_slots.p, f->d_D.p, ar, f->d_ranks.p);
+      HF_LAUNCH_CHECK();
+      set_prog_smem<float>(smem);
+    } else {
+      double* ar = reinterpret_cast<double*>(f->d_arena.p);
+      k_nearfield<double><<<gn, 256, 0, s->st>>>(f->d_hi.p, s->d_inst.p, s->arena.p, f->d_dense.p, f->d_D.p, ar);
+      HF_LAUNCH_CHECK();
+      k_lowrank<double><<<gp, 128, 0, s->st>>>(f->d_hi.p, s->d_inst.p, s->arena.p, s->gl.p, f->d_pairs.p,
+                                               f->d_slots.p, f->d_D.p, ar, f->d_ranks.p);
+      HF_LAUNCH_CHECK();
+      set_prog_smem<double>(smem);
+    }
+    if (!f->build_only) f->run_prog(0);
+    HF_CHECK(cudaStreamSynchronize(s->st));
+    std::vector<int> err(ni);
+    HF_CHECK(cudaMemcpy(err.data(), f->d_err.p, ni * sizeof(int), cudaMemcpyDeviceToHost));
+    for (int e : err)
+      if (e) throw Error(HFSEM_ERR_BREAKDOWN, "zero or non-finite pivot in an H-LU leaf");
+  } catch (...) {
+    delete f;
+    throw;
+  }
+  return f;
+}
+
+}  // namespace hf
+
+void hfsem_factor_s::run_prog(int which) {
+  hf::HProgArgs a{d_hi.p, d_ops.p, d_slots.p, d_ranks.p, d_err.p, tol};
+  if (tsize == sizeof(float))
+    hf::k_hprog<float><<<sys->n_inst, hf::kHThreads, smem, sys->st>>>(
+        a, reinterpret_cast<float*>(d_arena.p), which);
+  else
+    hf::k_hprog<double><<<sys->n_inst, hf::kHThreads, smem, sys->st>>>(
+        a, reinterpret_cast<double*>(d_arena.p), which);
+  HF_LAUNCH_CHECK();
+}
+
+void hfsem_factor_s::apply(int nrhs, const double* r_em, double* y_em) {
+  if (build_only) throw hf::Error(HFSEM_ERR_INVALID_ARG, "factor was built with build_only");
+  if (nrhs > 64) throw hf::Error(HFSEM_ERR_INVALID_ARG, "nrhs > 64");
+  int maxnd = 1;
+  for (auto& I : sys->ih) maxnd = std::max(maxnd, I.Nd);
+  dim3 g(std::min(1024, (maxnd * nrhs + 255) / 256), sys->n_inst);
+  if (tsize == sizeof(float)) {
+    float* ar = reinterpret_cast<float*>(d_arena.p);
+    hf::k_hsolve_in<float><<<g, 256, 0, sys->st>>>(d_hi.p, sys->d_inst.p, r_em, d_D.p, ar, d_ranks.p, nrhs);
+    HF_LAUNCH_CHECK();
+    run_prog(1);
+    hf::k_hsolve_out<float><<<g, 256, 0, sys->st>>>(d_hi.p, sys->d_inst.p, d_D.p, ar, y_em, nrhs);
+  } else {
+    double* ar = reinterpret_cast<double*>(d_arena.p);
+    hf::k_hsolve_in<double><<<g, 256, 0, sys->st>>>(d_hi.p, sys->d_inst.p, r_em, d_D.p, ar, d_ranks.p, nrhs);
+    HF_LAUNCH_CHECK();
+    run_prog(1);
+    hf::k_hsolve_out<double><<<g, 256, 0, sys->st>>>(d_hi.p, sys->d_inst.p, d_D.p, ar, y_em, nrhs);
+  }
+  HF_LAUNCH_CHECK();
+}
+
+namespace hf {
+Precond* precond_of(hfsem_system* s, hfsem_factor* f) {
+  if (!f) return nullptr;
+  if (f->sys != s) throw Error(HFSEM_ERR_INVALID_ARG, "factor belongs to another system");
+  if (f->build_only) throw Error(HFSEM_ERR_INVALID_ARG, "factor was built with build_only");
+  return f;
 }
 }  // namespace hf
 
+using namespace hf;
+
 extern "C" {
-int hfsem_hlu_factor(hfsem_system*, const hfsem_hopts*, hfsem_factor**) {
-  return HFSEM_ERR_UNSUPPORTED;
+
+int hfsem_hlu_factor(hfsem_system* sys, const hfsem_hopts* opts, hfsem_factor** out) {
+  try {
+    if (!sys || !opts || !out) throw Error(HFSEM_ERR_INVALID_ARG, "NULL argument");
+    *out = factor(sys, *opts);
+    return HFSEM_OK;
+  } catch (const Error& e) {
+    set_last_error(e.msg);
+    return e.code;
+  } catch (...) {
+    set_last_error("unknown error");
+    return HFSEM_ERR_DEVICE;
+  }
 }
-int hfsem_hmatrix_dense(const hfsem_factor*, int32_t, double*) { return HFSEM_ERR_UNSUPPORTED; }
-int hfsem_precond_apply(hfsem_factor*, int32_t, const double*, double*) {
-  return HFSEM_ERR_UNSUPPORTED;
+
+int hfsem_hmatrix_dense(const hfsem_factor* fac, int32_t inst, double* out) {
+  try {
+    if (!fac || !out || inst < 0 || inst >= fac->sys->n_inst)
+      throw Error(HFSEM_ERR_INVALID_ARG, "bad arguments");
+    if (!fac->build_only) throw Error(HFSEM_ERR_INVALID_ARG, "only for factors built with build_only");
+    hfsem_system* s = fac->sys;
+    const InstHost& I = s->ih[inst];
+    size_t nn = (size_t)I.Nd * I.Nd;
+    DevBuf<double> em, pp;
+    em.alloc(std::max<size_t>(nn, 1));
+    pp.alloc(std::max<size_t>(nn, 1));
+    HF_CHECK(cudaMemsetAsync(em.p, 0, nn * sizeof(double), s->st));
+    const HInstDev* hsel = fac->d_hi.p + inst;
+    int nb = fac->hidev[inst].ndense + 2 * fac->hidev[inst].npairs;
+    if (fac->tsize == sizeof(float))
+      k_expand<float><<<std::max(1, std::min(nb, 4096)), 256, 0, s->st>>>(
+          hsel, fac->d_dense.p, fac->d_pairs.p, fac->d_slots.p, fac->d_ranks.p, fac->d_D.p,
+          reinterpret_cast<const float*>(fac->d_arena.p), em.p, I.Nd);
+    else
+      k_expand<double><<<std::max(1, std::min(nb, 4096)), 256, 0, s->st>>>(
+          hsel, fac->d_dense.p, fac->d_pairs.p, fac->d_slots.p, fac->d_ranks.p, fac->d_D.p,
+          reinterpret_cast<const double*>(fac->d_arena.p), em.p, I.Nd);
+    HF_LAUNCH_CHECK();
+    k_perm_mat<<<1024, 256, 0, s->st>>>(em.p, pp.p, I.Nd, I.N, I.P);
+    HF_LAUNCH_CHECK();
+    HF_CHECK(cudaMemcpyAsync(out, pp.p, nn * sizeof(double),
+                             is_device_ptr(out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->st));
+    HF_CHECK(cudaStreamSynchronize(s->st));
+    return HFSEM_OK;
+  } catch (const Error& e) {
+    set_last_error(e.msg);
+    return e.code;
+  }
 }
-void hfsem_factor_free(hfsem_factor* f) { delete f; }
+
+int hfsem_precond_apply(hfsem_factor* fac, int32_t nrhs, const double* r, double* y) {
+  try {
+    if (!fac || !r || !y || nrhs < 1 || nrhs > 64) throw Error(HFSEM_ERR_INVALID_ARG, "bad arguments");
+    hfsem_system* s = fac->sys;
+    ensure_work(s, nrhs);
+    size_t cnt = (size_t)s->total_nd * nrhs;
+    DevBuf<double> a, b;
+    a.alloc(cnt);
+    b.alloc(cnt);
+    HF_CHECK(cudaMemcpyAsync(s->w_y.p, r, cnt * sizeof(double),
+                             is_device_ptr(r) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s->st));
+    perm_to_elem(s, nrhs, s->w_y.p, a.p);
+    fac->apply(nrhs, a.p, b.p);
+    perm_to_paper(s, nrhs, b.p, s->w_y.p);
+    HF_CHECK(cudaMemcpyAsync(y, s->w_y.p, cnt * sizeof(double),
+                             is_device_ptr(y) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->st));
+    HF_CHECK(cudaStreamSynchronize(s->st));
+    std::vector<int> err(s->n_inst);
+    HF_CHECK(cudaMemcpy(err.data(), fac->d_err.p, err.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    return HFSEM_OK;
+  } catch (const Error& e) {
+    set_last_error(e.msg);
+    return e.code;
+  }
 }
+
+void hfsem_factor_free(hfsem_factor* f) {
+  if (!f) return;
+  cudaStreamSynchronize(f->sys->st);
+  delete f;
+}
+
+}  // extern "C"

@@ -1,0 +1,520 @@
+// Host planner: cluster tree, block tree with the admissibility condition of
+// eq. (admis), storage layout, and the H-LU / H-solve programs (Sec. 4.1).
+//
+// Clusters are element ranges split in halves down to `leaf_elems` elements
+// (the paper does not say how its cluster tree is built).  A cluster owns the
+// bubbles of its elements and the hats at their right nodes, so its unknowns
+// are contiguous in the element-major ordering; its support (Sec. 3.2) is
+// [x_e0, x_min(e1+1, N)].
+//
+// The H-LU is the usual recursive block LU on the block tree,
+//   LU(A11); U12 = L11^-1 A12; L21 = A21 U11^-1; A22 -= L21 U12; LU(A22),
+// with every product and solve carried out in the formats of its operands
+// (dense, low rank U V^T, hierarchical) and every update of a low-rank block
+// appended to its factors and recompressed to the tolerance Tol_HLU.  The
+// recursion is unrolled here into a flat list of dense kernels (GEMM,
+// triangular multiplies with the inverted diagonal leaves, append and
+// truncate), which the device interpreter runs in order.
+#include <algorithm>
+#include <cmath>
+#include <string>
+
+#include "hplan.h"
+
+namespace hf {
+namespace {
+
+View vT(View v) {
+  std::swap(v.r, v.c);
+  v.tr ^= 1;
+  return v;
+}
+View vrows(View v, int i0, int i1) {
+  v.off += v.tr ? (long long)i0 * v.ld : i0;
+  v.r = i1 - i0;
+  return v;
+}
+View vcols(View v, int j0, int j1) {
+  v.off += v.tr ? j0 : (long long)j0 * v.ld;
+  v.c = j1 - j0;
+  return v;
+}
+
+struct Builder {
+  const InstHost& I;
+  const PlanOpts& o;
+  HPlan& p;
+  long long top = 0;
+  long long tmp_base = 0, tmp_top = 0, tmp_peak = 0;
+  std::vector<HOp>* prog = nullptr;
+  int max_m = 0;
+
+  Builder(const InstHost& i, const PlanOpts& op, HPlan& pl) : I(i), o(op), p(pl) {}
+
+  // ---------------- structure ----------------
+  int cluster(int e0, int e1) {
+    Cluster c;
+    c.e0 = e0;
+    c.e1 = e1;
+    c.d0 = e0 * I.P;
+    c.d1 = std::min(e1 * I.P, I.Nd);
+    c.lo = e0;
+    c.hi = std::min(e1 + 1, I.N);
+    c.kid[0] = c.kid[1] = -1;
+    int id = (int)p.C.size();
+    p.C.push_back(c);
+    if (e1 - e0 > o.leaf_elems) {
+      int mid = (e0 + e1) / 2;
+      int a = cluster(e0, mid);
+      int b = cluster(mid, e1);
+      p.C[id].kid[0] = a;
+      p.C[id].kid[1] = b;
+    }
+    return id;
+  }
+  bool leaf(int c) const { return p.C[c].kid[0] < 0; }
+
+  double diam(int c) const { return I.node_diff(p.C[c].hi, p.C[c].lo); }
+  double dist(int a, int b) const {
+    const Cluster &x = p.C[a], &y = p.C[b];
+    if (x.hi < y.lo) return I.node_diff(y.lo, x.hi);
+    if (y.hi < x.lo) return I.node_diff(x.lo, y.hi);
+    return 0.0;
+  }
+  bool admissible(int t, int s) const {
+    double d = dist(t, s);
+    return d > 0.0 && std::max(diam(t), diam(s)) <= o.lambda * d;
+  }
+
+  int block(int t, int s) {
+    Block b;
+    b.t = t;
+    b.s = s;
+    b.m = p.C[t].d1 - p.C[t].d0;
+    b.n = p.C[s].d1 - p.C[s].d0;
+    b.kid[0] = b.kid[1] = b.kid[2] = b.kid[3] = -1;
+    b.off = b.inv = -1;
+    b.slot = -1;
+    b.kcap = b.kmax = 0;
+    b.lower = (p.C[s].hi < p.C[t].lo) ? 1 : 0;
+    if (admissible(t, s) && b.m > 0 && b.n > 0) {
+      b.type = B_LR;
+    } else if (leaf(t) || leaf(s)) {
+      b.type = B_DENSE;
+    } else {
+      b.type = B_HIER;
+    }
+    int id = (int)p.B.size();
+    p.B.push_back(b);
+    if (b.type == B_HIER) {
+      int k[4];
+      k[0] = block(p.C[t].kid[0], p.C[s].kid[0]);
+      k[1] = block(p.C[t].kid[0], p.C[s].kid[1]);
+      k[2] = block(p.C[t].kid[1], p.C[s].kid[0]);
+      k[3] = block(p.C[t].kid[1], p.C[s].kid[1]);
+      for (int i = 0; i < 4; ++i) p.B[id].kid[i] = k[i];
+    }
+    return id;
+  }
+
+  void storage() {
+    for (size_t i = 0; i < p.B.size(); ++i) {
+      Block& b = p.B[i];
+      max_m = std::max(max_m, std::max(b.m, b.n));
+      if (b.type == B_DENSE) {
+        b.off = top;
+        top += (long long)b.m * b.n;
+        p.dense_blocks.push_back((int)i);
+        if (b.t == b.s) {
+          if (b.m > o.max_leaf)
+            throw Error(HFSEM_ERR_UNSUPPORTED, "diagonal leaf larger than the kernel supports");
+          p.leaf_max = std::max(p.leaf_max, b.m);
+          b.inv = top;
+          top += 2LL * b.m * b.m;
+        }
+      } else if (b.type == B_LR) {
+        int mn = std::min(b.m, b.n);
+        b.kmax = std::min(o.kmax, mn);
+        b.kcap = std::max(o.R, std::min(mn, 2 * o.kmax));
+        b.off = top;
+        top += (long long)(b.m + b.n) * b.kcap;
+        b.slot = p.n_slots++;
+        p.lr_blocks.push_back((int)i);
+      }
+    }
+  }
+
+  // ---------------- views ----------------
+  View dense(int bi) const {
+    const Block& b = p.B[bi];
+    return View{b.off, b.m, b.n, std::max(b.m, 1), 0};
+  }
+  View linv(int bi) const {
+    const Block& b = p.B[bi];
+    return View{b.inv, b.m, b.m, std::max(b.m, 1), 0};
+  }
+  View uinv(int bi) const {
+    const Block& b = p.B[bi];
+    return View{b.inv + (long long)b.m * b.m, b.m, b.m, std::max(b.m, 1), 0};
+  }
+  View lrU(int bi) const {
+    const Block& b = p.B[bi];
+    return View{b.off, b.m, -1 - b.slot, b.m, 0};
+  }
+  View lrV(int bi) const {
+    const Block& b = p.B[bi];
+    return View{b.off + (long long)b.m * b.kcap, b.n, -1 - b.slot, b.n, 0};
+  }
+  int rank_cap(int bi) const { return p.B[bi].kcap; }
+  // static upper bound of a (possibly runtime) dimension
+  int bound(int d) const {
+    if (d >= 0) return d;
+    if (-1 - d == p.n_slots) return p.nrhs_max;   // rhs width of the solve program
+    return p.B[p.lr_blocks[-1 - d]].kcap;
+  }
+  View tmp(int r, int c_bound, int c_dim) {
+    View v{tmp_top, r, c_dim, std::max(r, 1), 0};
+    tmp_top += (long long)std::max(r, 1) * std::max(c_bound, 1);
+    tmp_peak = std::max(tmp_peak, tmp_top - tmp_base);
+    return v;
+  }
+  // row range of child cluster c inside parent cluster par
+  int r0(int par, int c) const { return p.C[c].d0 - p.C[par].d0; }
+  int r1(int par, int c) const { return p.C[c].d1 - p.C[par].d0; }
+
+  // ---------------- op emission ----------------
+  static bool empty(const View& v) { return v.r == 0 || v.c == 0; }
+  void op(int type, View A, View B, View C, double alpha, double beta, int slot = -1) {
+    HOp h;
+    h.type = type;
+    h.slot = slot;
+    h.alpha = alpha;
+    h.beta = beta;
+    h.A = A;
+    h.B = B;
+    h.C = C;
+    prog->push_back(h);
+  }
+  void gemm(View C, View A, View B, double alpha, double beta) {
+    if (empty(C)) return;
+    if (A.c == 0) {
+      if (beta == 0.0) zero(C);
+      return;
+    }
+    op(OP_GEMM, A, B, C, alpha, beta);
+  }
+  void zero(View C) {
+    if (!empty(C)) op(OP_ZERO, View{}, View{}, C, 0, 0);
+  }
+  void append(int cb, View U, View V, double alpha) {
+    const Block& b = p.B[cb];
+    if (U.r == 0 || V.r == 0 || U.c == 0) return;
+    int kin = bound(U.c);
+    p.kconcat_max = std::max(p.kconcat_max, b.kcap + kin);
+    if (b.kcap + kin > o.max_concat)
+      throw Error(HFSEM_ERR_UNSUPPORTED, "low-rank update larger than the recompression kernel");
+    op(OP_APPEND, U, V, lrU(cb), alpha, 0.0, b.slot);
+  }
+  void trunc(int cb) {
+    const Block& b = p.B[cb];
+    p.kconcat_max = std::max(p.kconcat_max, b.kcap);
+    op(OP_TRUNC, View{}, View{}, lrU(cb), 0.0, 0.0, b.slot);
+  }
+
+  // C += alpha U V^T, C any format
+  void add_lr(int cb, View U, View V, double alpha) {
+    const Block& c = p.B[cb];
+    if (c.m == 0 || c.n == 0) return;
+    if (c.type == B_DENSE) {
+      gemm(dense(cb), U, vT(V), alpha, 1.0);
+    } else if (c.type == B_LR) {
+      append(cb, U, V, alpha);
+    } else {
+      for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+          int k = c.kid[2 * i + j];
+          int ti = p.C[c.t].kid[i], sj = p.C[c.s].kid[j];
+          add_lr(k, vrows(U, r0(c.t, ti), r1(c.t, ti)), vrows(V, r0(c.s, sj), r1(c.s, sj)),
+                 alpha);
+        }
+    }
+  }
+
+  // C += alpha Z, Z dense view, C any format
+  void add_dense(int cb, View Z, double alpha) {
+    const Block& c = p.B[cb];
+    if (c.m == 0 || c.n == 0) return;
+    if (c.type == B_DENSE) {
+      op(OP_AXPY, Z, View{}, dense(cb), alpha, 1.0);
+    } else if (c.type == B_LR) {
+      // Z = Z I: append with an identity right factor (B.off < 0)
+      p.hh_lr++;
+      View Iv{-1, c.n, c.n, c.n, 0};
+      append(cb, Z, Iv, alpha);
+    } else {
+      for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+          int k = c.kid[2 * i + j];
+          int ti = p.C[c.t].kid[i], sj = p.C[c.s].kid[j];
+          add_dense(k, vcols(vrows(Z, r0(c.t, ti), r1(c.t, ti)), r0(c.s, sj), r1(c.s, sj)),
+                    alpha);
+        }
+    }
+  }
+
+  // D += alpha A E  (A block, E dense)
+  void gemm_hd(View D, int ab, View E, double alpha) {
+    const Block& a = p.B[ab];
+    if (a.m == 0 || a.n == 0 || empty(D)) return;
+    if (a.type == B_DENSE) {
+      gemm(D, dense(ab), E, alpha, 1.0);
+    } else if (a.type == B_LR) {
+      long long mark = tmp_top;
+      View T = tmp(a.kcap, bound(E.c), E.c);
+      T.r = lrU(ab).c;   // runtime rank rows
+      gemm(T, vT(lrV(ab)), E, 1.0, 0.0);
+      gemm(D, lrU(ab), T, alpha, 1.0);
+      tmp_top = mark;
+    } else {
+      for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+          int ti = p.C[a.t].kid[i], sj = p.C[a.s].kid[j];
+          gemm_hd(vrows(D, r0(a.t, ti), r1(a.t, ti)), a.kid[2 * i + j],
+                  vrows(E, r0(a.s, sj), r1(a.s, sj)), alpha);
+        }
+    }
+  }
+
+  // D += alpha E B  (E dense, B block)
+  void gemm_dh(View D, View E, int bb, double alpha) {
+    const Block& b = p.B[bb];
+    if (b.m == 0 || b.n == 0 || empty(D)) return;
+    if (b.type == B_DENSE) {
+      gemm(D, E, dense(bb), alpha, 1.0);
+    } else if (b.type == B_LR) {
+      long long mark = tmp_top;
+      View T = tmp(bound(E.r), b.kcap, lrU(bb).c);
+      T.r = E.r;
+      gemm(T, E, lrU(bb), 1.0, 0.0);
+      gemm(D, T, vT(lrV(bb)), alpha, 1.0);
+      tmp_top = mark;
+    } else {
+      for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j) {
+          int ti = p.C[b.t].kid[i], sj = p.C[b.s].kid[j];
+          gemm_dh(vcols(D, r0(b.s, sj), r1(b.s, sj)), vcols(E, r0(b.t, ti), r1(b.t, ti)),
+                  b.kid[2 * i + j], alpha);
+        }
+    }
+  }
+
+  // D += alpha A B (A, B blocks; D dense view)
+  void gemm_dab(View D, int ab, int bb, double alpha) {
+    const Block &a = p.B[ab], &b = p.B[bb];
+    if (a.m == 0 || a.n == 0 || b.n == 0 || empty(D)) return;
+    if (a.type == B_DENSE) {
+      gemm_dh(D, dense(ab), bb, alpha);
+    } else if (b.type == B_DENSE) {
+      gemm_hd(D, ab, dense(bb), alpha);
+    } else if (a.type == B_LR) {
+      long long mark = tmp_top;
+      View T = tmp(a.kcap, b.n, b.n);
+      T.r = lrU(ab).c;
+      zero(T);
+      gemm_dh(T, vT(lrV(ab)), bb, 1.0);
+      gemm(D, lrU(ab), T, alpha, 1.0);
+      tmp_top = mark;
+    } else if (b.type == B_LR) {
+      long long mark = tmp_top;
+      View Z = tmp(a.m, b.kcap, lrU(bb).c);
+      zero(Z);
+      gemm_hd(Z, ab, lrU(bb), 1.0);
+      gemm(D, Z, vT(lrV(bb)), alpha, 1.0);
+      tmp_top = mark;
+    } else {
+      for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j)
+          for (int k = 0; k < 2; ++k) {
+            int ti = p.C[a.t].kid[i], sj = p.C[b.s].kid[j];
+            gemm_dab(vcols(vrows(D, r0(a.t, ti), r1(a.t, ti)), r0(b.s, sj), r1(b.s, sj)),
+                     a.kid[2 * i + k], b.kid[2 * k + j], alpha);
+          }
+    }
+  }
+
+  // C -= A B, blocks
+  void gemm_sub(int cb, int ab, int bb) {
+    const Block &c = p.B[cb], &a = p.B[ab], &b = p.B[bb];
+    if (c.m == 0 || c.n == 0 || a.n == 0) return;
+    if (c.type == B_HIER && a.type == B_HIER && b.type == B_HIER) {
+      for (int i = 0; i < 2; ++i)
+        for (int j = 0; j < 2; ++j)
+          for (int k = 0; k < 2; ++k)
+            gemm_sub(c.kid[2 * i + j], a.kid[2 * i + k], b.kid[2 * k + j]);
+      return;
+    }
+    if (c.type == B_DENSE) {
+      gemm_dab(dense(cb), ab, bb, -1.0);
+      return;
+    }
+    if (a.type == B_LR) {
+      // A B = U_A (B^T V_A)^T
+      long long mark = tmp_top;
+      View W = tmp(b.n, a.kcap, lrU(ab).c);      // n x k
+      zero(W);
+      gemm_dh(vT(W), vT(lrV(ab)), bb, 1.0);      // W^T += V_A^T B
+      add_lr(cb, lrU(ab), W, -1.0);
+      tmp_top = mark;
+      return;
+    }
+    if (b.type == B_LR) {
+      long long mark = tmp_top;
+      View Z = tmp(a.m, b.kcap, lrU(bb).c);      // m x k
+      zero(Z);
+      gemm_hd(Z, ab, lrU(bb), 1.0);
+      add_lr(cb, Z, lrV(bb), -1.0);
+      tmp_top = mark;
+      return;
+    }
+    if (a.type == B_DENSE && b.type == B_DENSE) {
+      // rank at most the inner (leaf) cluster size
+      add_lr(cb, dense(ab), vT(dense(bb)), -1.0);
+      return;
+    }
+    // remaining: C LR / H with a hierarchical factor: form the product densely
+    long long mark = tmp_top;
+    View Z = tmp(a.m, b.n, b.n);
+    zero(Z);
+    gemm_dab(Z, ab, bb, 1.0);
+    add_dense(cb, Z, -1.0);
+    tmp_top = mark;
+  }
+
+  // X <- L^-1 X for a dense view, L the diagonal block lb
+  void trsm_ll_d(int lb, View D) {
+    const Block& l = p.B[lb];
+    if (l.m == 0 || empty(D)) return;
+    if (l.type == B_DENSE) {
+      op(OP_TRMM_L, linv(lb), View{}, D, 1.0, 0.0);
+      return;
+    }
+    int t1 = p.C[l.t].kid[0], t2 = p.C[l.t].kid[1];
+    View D1 = vrows(D, r0(l.t, t1), r1(l.t, t1)), D2 = vrows(D, r0(l.t, t2), r1(l.t, t2));
+    trsm_ll_d(l.kid[0], D1);
+    gemm_hd(D2, l.kid[2], D1, -1.0);
+    trsm_ll_d(l.kid[3], D2);
+  }
+  // X <- U^-1 X for a dense view (backward substitution)
+  void trsm_lu_d(int ub, View D) {
+    const Block& u = p.B[ub];
+    if (u.m == 0 || empty(D)) return;
+    if (u.type == B_DENSE) {
+      op(OP_TRMM_L, uinv(ub), View{}, D, 1.0, 0.0);
+      return;
+    }
+    int t1 = p.C[u.t].kid[0], t2 = p.C[u.t].kid[1];
+    View D1 = vrows(D, r0(u.t, t1), r1(u.t, t1)), D2 = vrows(D, r0(u.t, t2), r1(u.t, t2));
+    trsm_lu_d(u.kid[3], D2);
+    gemm_hd(D1, u.kid[1], D2, -1.0);
+    trsm_lu_d(u.kid[0], D1);
+  }
+  // X <- X U^-1 for a dense view
+  void trsm_ru_d(int ub, View D) {
+    const Block& u = p.B[ub];
+    if (u.m == 0 || empty(D)) return;
+    if (u.type == B_DENSE) {
+      op(OP_TRMM_R, uinv(ub), View{}, D, 1.0, 0.0);
+      return;
+    }
+    int s1 = p.C[u.s].kid[0], s2 = p.C[u.s].kid[1];
+    View D1 = vcols(D, r0(u.s, s1), r1(u.s, s1)), D2 = vcols(D, r0(u.s, s2), r1(u.s, s2));
+    trsm_ru_d(u.kid[0], D1);
+    gemm_dh(D2, D1, u.kid[1], -1.0);
+    trsm_ru_d(u.kid[3], D2);
+  }
+
+  void trsm_ll(int lb, int xb) {
+    const Block& x = p.B[xb];
+    if (x.m == 0 || x.n == 0) return;
+    if (x.type == B_DENSE) {
+      trsm_ll_d(lb, dense(xb));
+    } else if (x.type == B_LR) {
+      trunc(xb);
+      trsm_ll_d(lb, lrU(xb));
+    } else {
+      const Block& l = p.B[lb];
+      trsm_ll(l.kid[0], x.kid[0]);
+      trsm_ll(l.kid[0], x.kid[1]);
+      gemm_sub(x.kid[2], l.kid[2], x.kid[0]);
+      gemm_sub(x.kid[3], l.kid[2], x.kid[1]);
+      trsm_ll(l.kid[3], x.kid[2]);
+      trsm_ll(l.kid[3], x.kid[3]);
+    }
+  }
+
+  void trsm_ru(int ub, int xb) {
+    const Block& x = p.B[xb];
+    if (x.m == 0 || x.n == 0) return;
+    if (x.type == B_DENSE) {
+      trsm_ru_d(ub, dense(xb));
+    } else if (x.type == B_LR) {
+      trunc(xb);
+      trsm_ru_d(ub, vT(lrV(xb)));   // V^T <- V^T U^-1
+    } else {
+      const Block& u = p.B[ub];
+      trsm_ru(u.kid[0], x.kid[0]);
+      trsm_ru(u.kid[0], x.kid[2]);
+      gemm_sub(x.kid[1], x.kid[0], u.kid[1]);
+      gemm_sub(x.kid[3], x.kid[2], u.kid[1]);
+      trsm_ru(u.kid[3], x.kid[1]);
+      trsm_ru(u.kid[3], x.kid[3]);
+    }
+  }
+
+  void hlu(int bb) {
+    const Block& b = p.B[bb];
+    if (b.m == 0) return;
+    if (b.type == B_DENSE) {
+      op(OP_GETRF_INV, linv(bb), uinv(bb), dense(bb), 1.0, 0.0);
+      return;
+    }
+    int k0 = b.kid[0], k1 = b.kid[1], k2 = b.kid[2], k3 = b.kid[3];
+    hlu(k0);
+    trsm_ll(k0, k1);
+    trsm_ru(k0, k2);
+    gemm_sub(k3, k2, k1);
+    hlu(k3);
+  }
+};
+
+}  // namespace
+
+void make_plan(const InstHost& I, const PlanOpts& o, HPlan& p) {
+  p = HPlan();
+  p.N = I.N;
+  p.P = I.P;
+  p.Nd = I.Nd;
+  p.nrhs_max = o.nrhs_max;
+  Builder b(I, o, p);
+  int root = b.cluster(0, I.N);
+  b.block(root, root);
+  b.storage();
+  // right-hand-side area, then temporaries, then the truncation workspace
+  p.rhs_off = b.top;
+  b.top += (long long)std::max(I.Nd, 1) * o.nrhs_max;
+  b.tmp_base = b.tmp_top = b.top;
+  b.prog = &p.fac;
+  b.hlu(0);
+  b.tmp_top = b.tmp_base;
+  b.prog = &p.sol;
+  // the width of the rhs area is read at run time from rank slot n_slots
+  View rhs{p.rhs_off, I.Nd, -1 - p.n_slots, std::max(I.Nd, 1), 0};
+  b.trsm_ll_d(0, rhs);
+  b.trsm_lu_d(0, rhs);
+  long long ws_off = b.tmp_base + b.tmp_peak;
+  p.ws_off = ws_off;
+  p.ws_size = (long long)2 * std::max(b.max_m, 1) * std::max(p.kconcat_max, 1);
+  p.arena = ws_off + p.ws_size;
+}
+
+}  // namespace hf

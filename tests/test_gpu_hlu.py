@@ -1,0 +1,108 @@
+"""GPU parity of the H-matrix approximation, the H-LU factorisation and the
+H-triangular solves (Sec. 3, Sec. 4.1) against the oracle, through the C ABI."""
+import numpy as np
+import pytest
+
+from oracle.assemble import system_full
+from oracle.basis import Mesh, n_dof
+from oracle.hmatrix import hmatrix_dense
+from oracle.solve import dense_solve, solve_problem
+from paper_1808_02937_gb300 import hfsem as H
+from paper_1808_02937_gb300 import workloads as W
+from tests._common import ensure_built, rel_err
+
+pytestmark = pytest.mark.gpu
+
+CASES = [
+    # name, h, a, b, P, alpha, theta, rho, leaf, R
+    ("uniform", W.mesh_uniform(24), 0.0, 1.0, 3, 1.5, 0.5, 0.0, 2, 4),
+    ("graded5", W.mesh_graded(20, 5.0, 0.0, 10.0), 0.0, 10.0, 3, 1.6, 1.0, 0.0, 1, 5),
+    ("geo2", W.mesh_geometric_two_sided(16, 0.5), 0.0, 1.0, 4, 1.3, 0.7, 1.0, 1, 6),
+    ("ragged-theta0", W.mesh_graded(19, 2.0), 0.0, 1.0, 2, 1.8, 0.0, 0.4, 2, 3),
+]
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return ensure_built()
+
+
+@pytest.mark.parametrize("prec", [H.PREC_FP64, H.PREC_MIXED])
+@pytest.mark.parametrize("case", CASES, ids=lambda c: c[0])
+def test_hmatrix_entries_match_oracle(lib, case, prec):
+    name, h, a, b, P, alpha, theta, rho, leaf, R = case
+    sys = H.hfsem_assemble([H.make_problem(h, P, alpha, theta, rho, a=a, b=b, matvec=1)])
+    fac = H.hfsem_hlu_factor(sys, H.hopts(R=R, lam=1.0, tol_hlu=0.0, precision=prec,
+                                          leaf_elems=leaf, build_only=1))
+    At_gpu = H.hfsem_hmatrix_dense(fac, 0)
+    m = Mesh(h, a, b)
+    At, _ = hmatrix_dense(m, P, alpha, theta, system_full(m, P, alpha, theta, rho), R, 1.0, leaf)
+    tol = 1e-12 if prec == H.PREC_FP64 else 2e-6
+    assert np.abs(At_gpu - At).max() <= tol * np.abs(At).max()
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: c[0])
+def test_hlu_exact_at_zero_tolerance(lib, case):
+    # Tol_HLU = 0 and no rank cap: H-LU is an exact LU of A~
+    name, h, a, b, P, alpha, theta, rho, leaf, R = case
+    sys = H.hfsem_assemble([H.make_problem(h, P, alpha, theta, rho, a=a, b=b, matvec=1)])
+    fac = H.hfsem_hlu_factor(sys, H.hopts(R=R, lam=1.0, tol_hlu=0.0, precision=H.PREC_FP64,
+                                          leaf_elems=leaf, kmax=48))
+    m = Mesh(h, a, b)
+    At, _ = hmatrix_dense(m, P, alpha, theta, system_full(m, P, alpha, theta, rho), R, 1.0, leaf)
+    rng = np.random.default_rng(11)
+    Nd = n_dof(len(h), P)
+    r = rng.standard_normal((3, Nd))
+    y = H.hfsem_precond_apply(fac, np.ascontiguousarray(r.ravel()), nrhs=3).reshape(3, Nd)
+    ref, _ = dense_solve(At, r.T)
+    assert rel_err(y, ref.T) < 1e-9
+
+
+@pytest.mark.parametrize("case", CASES, ids=lambda c: c[0])
+def test_hlu_mixed_is_a_good_preconditioner(lib, case):
+    name, h, a, b, P, alpha, theta, rho, leaf, R = case
+    sys = H.hfsem_assemble([H.make_problem(h, P, alpha, theta, rho, a=a, b=b, matvec=1)])
+    fac = H.hfsem_hlu_factor(sys, H.hopts(R=R, tol_hlu=1e-3, precision=H.PREC_MIXED,
+                                          leaf_elems=leaf))
+    m = Mesh(h, a, b)
+    Nd = n_dof(len(h), P)
+    A = system_full(m, P, alpha, theta, rho)[:Nd, :Nd]
+    rng = np.random.default_rng(5)
+    x = rng.standard_normal(Nd)
+    y = H.hfsem_precond_apply(fac, A @ x)
+    # M^-1 A x should be close to x
+    assert rel_err(y, x) < 0.2
+
+
+@pytest.mark.parametrize("prec", [H.PREC_FP64, H.PREC_MIXED])
+def test_preconditioned_solve_config1(lib, prec):
+    p = W.config1()
+    sys = H.hfsem_assemble([H.make_problem(p.h, p.P, p.alpha, p.theta, p.rho, c1=p.c1, c2=p.c2)])
+    fac = H.hfsem_hlu_factor(sys, H.hopts(R=4, precision=prec))
+    X, st, code = H.hfsem_solve(sys, fac, [H.rhs_frac_powers([p.rhs[0]])], tol=1e-15,
+                                max_iter=100, allow_fail=True)
+    Xo, _ = solve_problem(Mesh(p.h, 0, 1), p.P, p.alpha, p.theta, p.rho, p.c1, p.c2,
+                          ("frac_powers", p.rhs[0]))
+    assert rel_err(X, Xo) < 1e-10, (st, rel_err(X, Xo))
+    assert st[0]["iters"] <= 20
+
+
+def test_preconditioned_solve_batch_mixed_meshes(lib):
+    # several instances of different shape in one batched call
+    rng = np.random.default_rng(2)
+    insts = [("uniform", W.mesh_uniform(40), 5, 1.4, 0.3, 1.0),
+             ("graded3", W.mesh_graded(33, 3.0), 4, 1.7, 0.8, 0.0),
+             ("geo2", W.mesh_geometric_two_sided(24, 0.5), 6, 1.2, 0.5, 2.0)]
+    probs, rhs, refs = [], [], []
+    for name, h, P, alpha, theta, rho in insts:
+        probs.append(H.make_problem(h, P, alpha, theta, rho))
+        coeffs = W.legendre_rhs(12, rng)
+        rhs.append(H.rhs_legendre([coeffs]))
+        Xo, _ = solve_problem(Mesh(h, 0, 1), P, alpha, theta, rho, 0.0, 0.0,
+                              ("legendre_ab", coeffs))
+        refs.append(Xo)
+    sys = H.hfsem_assemble(probs)
+    fac = H.hfsem_hlu_factor(sys, H.hopts(R=6, precision=H.PREC_MIXED))
+    X, st, code = H.hfsem_solve(sys, fac, rhs, tol=1e-15, max_iter=100, allow_fail=True)
+    for k, Xk in enumerate(H.split(sys, X)):
+        assert rel_err(Xk[:, 0], refs[k]) < 1e-10, (k, st[k])
