@@ -161,6 +161,20 @@ int hfsem_solve(hfsem_system *sys, hfsem_factor *fac, const hfsem_rhs *rhs,
 void hfsem_factor_free(hfsem_factor *fac);
 void hfsem_system_free(hfsem_system *sys);
 
+/* ---- kernel timing (measurement support; the paper has no counterpart) --
+ * When enabled, the library brackets its main kernels with CUDA events on
+ * the stream they are launched on (tags: "pairs", "symbol", "toeplitz_mv",
+ * "dense_mv", "hlu_factor", "hlu_solve", "krylov_vec").  hfsem_timing_read
+ * waits for the recorded events and returns, for one tag, the summed device
+ * time, the number of launches and the summed algorithmic work (flops for
+ * hlu_factor / hlu_solve, counted on the device from the executed shapes;
+ * bytes for the operator kernels; 0 where not counted).  The tag
+ * "launches" returns in *launches the number of kernels this library has
+ * launched so far.  Process-wide. */
+int hfsem_timing_enable(int32_t on);
+int hfsem_timing_reset(void);
+int hfsem_timing_read(const char *tag, double *total_ms, int64_t *launches, double *work);
+
 /* Static string for a status code. */
 const char *hfsem_status_str(int status);
 

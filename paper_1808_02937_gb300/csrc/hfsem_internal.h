@@ -27,7 +27,12 @@ inline void cuda_check(cudaError_t e, const char* what) {
     throw Error(HFSEM_ERR_DEVICE, std::string(what) + ": " + cudaGetErrorString(e));
 }
 #define HF_CHECK(x) ::hf::cuda_check((x), #x)
-#define HF_LAUNCH_CHECK() ::hf::cuda_check(cudaGetLastError(), "kernel launch")
+extern long long g_launches;   // kernels launched by this library (process-wide)
+#define HF_LAUNCH_CHECK() \
+  do {                    \
+    ++::hf::g_launches;   \
+    ::hf::cuda_check(cudaGetLastError(), "kernel launch"); \
+  } while (0)
 
 void set_last_error(const std::string& m);
 
@@ -155,6 +160,15 @@ void perm_to_elem(hfsem_system* s, int nrhs, const double* x_paper, double* x_em
 void perm_to_paper(hfsem_system* s, int nrhs, const double* x_em, double* x_paper);
 void load_vector_em(hfsem_system* s, const hfsem_rhs* rhs, int lifted, double* G_em);
 bool is_device_ptr(const void* p);
+// kernel timing: Tick t(stream, "tag", work) ... ~Tick records the end event
+bool timing_on();
+struct Tick {
+  int id = -1;
+  cudaStream_t st;
+  Tick(cudaStream_t s, const char* tag, double work = 0.0);
+  ~Tick();
+};
+void timing_add_work(const char* tag, double work);
 hf::Precond* precond_of(hfsem_system* s, hfsem_factor* f);
 void bicgstab(hfsem_system* s, Precond* M, int nrhs, const double* b_em, double* x_em,
               double tol, int max_iter, std::vector<KCol>& out);

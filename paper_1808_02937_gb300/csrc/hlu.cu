@@ -15,6 +15,7 @@
 //    compiled from the recursive H-LU (or the forward/backward substitution).
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <array>
 #include <map>
@@ -186,7 +187,6 @@ __global__ void k_lowrank(const HInstDev* __restrict__ hi, const InstDev* __rest
                           const LRPairDev* __restrict__ pairs, const SlotDev* __restrict__ slots,
                           const double* D, T* har, int* ranks) {
   __shared__ double sQ[kMaxP * 32];     // moments of the current element, P x R
-  __shared__ double sQn[32];            // moments L_0 of the next element
   __shared__ double sX[64], sW[64];
   const HInstDev H = hi[blockIdx.y];
   const InstDev I = inst[H.sys_inst];
@@ -215,73 +215,87 @@ __global__ void k_lowrank(const HInstDev* __restrict__ hi, const InstDev* __rest
   const SlotDev up = slots[H.slot0 + pr.upper_slot];
   T* ar = har + H.arena;
   const double* Dv = D + H.d_off;
-  // f(side, element, nu, point) of the expansion
-  // side 0 (tau, variable t), side 1 (sigma, variable s)
-  auto fval = [&](int side, int e, int nu, double xq) -> double {
-    double loc = 0.5 * h[e] * (1.0 + xq);
-    if (sexp) {
-      if (side == 0) {   // h_nu(t) = c_nu (-1)^nu r_s^nu (t - s0)^(1-alpha-nu)
-        double d = ndiff(e, pr.shi) + loc + r_s;
-        double c = 1.0;
-        for (int l = 1; l <= nu; ++l) c *= -(2.0 - I.alpha - l) / l * r_s;
-        return c * pow(d, ex - nu);
+  // expansion functions at the Gauss points of element e, one pow per point:
+  // sF[q*R + nu] = f_nu(x_q); side 0 varies t (tau), side 1 varies s (sigma)
+  __shared__ double sF[64 * 32];
+  __shared__ double sL[64 * kMaxP];
+  __shared__ double sPrev[32];
+  auto fill = [&](int side, int e) {
+    for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+      double xq = sX[q];
+      double loc = 0.5 * h[e] * (1.0 + xq);
+      double* F = sF + q * R;
+      bool singular = (side == 0) == sexp;
+      if (singular) {
+        double d, rr, sg;
+        if (sexp) {            // h_nu(t) = (-1)^nu c_nu r_s^nu (t - s0)^(1-alpha-nu)
+          d = ndiff(e, pr.shi) + loc + r_s;
+          rr = r_s;
+          sg = -1.0;
+        } else {               // h~_nu(s) = c_nu r_t^nu (t0 - s)^(1-alpha-nu)
+          d = r_t + ndiff(pr.tlo, e + 1) + 0.5 * h[e] * (1.0 - xq);
+          rr = r_t;
+          sg = 1.0;
+        }
+        double f = pow(d, ex);
+        F[0] = f;
+        for (int nu = 1; nu < R; ++nu) {
+          f *= sg * (2.0 - I.alpha - nu) / nu * rr / d;
+          F[nu] = f;
+        }
+      } else {
+        double y = sexp ? (ndiff(e, pr.slo) + loc - r_s) / r_s     // (s - s0)/r_s
+                        : (ndiff(e, pr.tlo) + loc - r_t) / r_t;    // (t - t0)/r_t
+        double f = 1.0;
+        for (int nu = 0; nu < R; ++nu) {
+          F[nu] = f;
+          f *= y;
+        }
       }
-      double y = (ndiff(e, pr.slo) + loc - r_s) / r_s;   // g_nu(s) = ((s - s0)/r_s)^nu
-      double c = 1.0;
-      for (int l = 0; l < nu; ++l) c *= y;
-      return c;
+      double* Lq = sL + q * kMaxP;
+      double l0 = 1.0, l1 = xq;
+      Lq[0] = 1.0;
+      if (P > 1) Lq[1] = xq;
+      for (int k = 1; k + 1 < P; ++k) {
+        double l2 = ((2 * k + 1) * xq * l1 - k * l0) / (k + 1);
+        Lq[k + 1] = l2;
+        l0 = l1;
+        l1 = l2;
+      }
     }
-    if (side == 0) {   // g~_nu(t) = ((t - t0)/r_t)^nu
-      double y = (ndiff(e, pr.tlo) + loc - r_t) / r_t;
-      double c = 1.0;
-      for (int l = 0; l < nu; ++l) c *= y;
-      return c;
-    }
-    // h~_nu(s) = c_nu r_t^nu (t0 - s)^(1-alpha-nu)
-    double d = r_t + ndiff(pr.tlo, e + 1) + 0.5 * h[e] * (1.0 - xq);
-    double c = 1.0;
-    for (int l = 1; l <= nu; ++l) c *= (2.0 - I.alpha - l) / l * r_t;
-    return c * pow(d, ex - nu);
-  };
-  // moments int_{I_e} f_nu(x) L_m(xi_e(x)) dx into sQ (all m) or sQn (m = 0)
-  auto moments = [&](int side, int e, double* dst, int mcount) {
-    for (int t = threadIdx.x; t < mcount * R; t += blockDim.x) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < P * R; t += blockDim.x) {
       int m = t / R, nu = t % R;
       double acc = 0.0;
-      for (int q = 0; q < nq; ++q) {
-        double xq = sX[q];
-        double l0 = 1.0, l1 = xq, lm = (m == 0) ? 1.0 : xq;
-        for (int k = 1; k < m; ++k) {
-          double l2 = ((2 * k + 1) * xq * l1 - k * l0) / (k + 1);
-          l0 = l1;
-          l1 = l2;
-          lm = l2;
-        }
-        acc += sW[q] * lm * fval(side, e, nu, xq);
-      }
-      dst[m * R + nu] = 0.5 * h[e] * acc;
+      for (int q = 0; q < nq; ++q) acc += sW[q] * sL[q * kMaxP + m] * sF[q * R + nu];
+      sQ[m * R + nu] = 0.5 * h[e] * acc;
     }
+    __syncthreads();
   };
   for (int side = 0; side < 2; ++side) {
     int e0 = side == 0 ? pr.te0 : pr.se0, e1 = side == 0 ? pr.te1 : pr.se1;
     int d0 = side == 0 ? pr.td0 : pr.sd0;
     double scale_side = (side == 0) ? I.g0 : 1.0;   // gamma0 sits with Q
-    for (int e = e0; e < e1; ++e) {
-      moments(side, e, sQ, P);
-      bool hat = (e + 1 < I.N);
-      if (hat) moments(side, e + 1, sQn, 1);
-      __syncthreads();
-      // rows of this element: bubbles p = 1..P-1, then the hat at node e+1
-      int nrow = P - 1 + (hat ? 1 : 0);
-      for (int t = threadIdx.x; t < nrow * R; t += blockDim.x) {
-        int p = t / R + 1, nu = t % R;
+    int elast = (e1 < I.N) ? e1 : e1 - 1;            // element e1 only feeds the hat at node e1
+    for (int e = e0; e <= elast; ++e) {
+      fill(side, e);
+      // rows: the hat at node e (from elements e-1 and e) when e > e0, the
+      // bubbles of e when e < e1
+      int nb = (e < e1) ? P - 1 : 0;
+      int nh = (e > e0) ? 1 : 0;
+      for (int t = threadIdx.x; t < (nb + nh) * R; t += blockDim.x) {
+        int k = t / R, nu = t % R;
         double v;
-        if (p < P)
+        int dof;
+        if (k < nh) {
+          v = sPrev[nu] / h[e - 1] - sQ[nu] / h[e];
+          dof = e * P - 1;
+        } else {
+          int p = k - nh + 1;
           v = -(2.0 * p + 1.0) * (2.0 / h[e]) * sQ[p * R + nu];
-        else
-          v = sQ[nu] / h[e] - sQn[nu] / h[e + 1];
+          dof = e * P + p - 1;
+        }
         v *= scale_side;
-        int dof = e * P + p - 1;
         int row = dof - d0;
         double dsc = Dv[dof];
         if (side == 0) {
@@ -295,6 +309,8 @@ __global__ void k_lowrank(const HInstDev* __restrict__ hi, const InstDev* __rest
           ar[up.off + row + (long long)nu * up.m] = (T)(dsc * v);
         }
       }
+      __syncthreads();
+      for (int nu = threadIdx.x; nu < R; nu += blockDim.x) sPrev[nu] = sQ[nu];
       __syncthreads();
     }
   }
@@ -347,6 +363,21 @@ __device__ void op_gemm(const HOp& o, HCtx<T>& c) {
     for (int t = tid; t < m * n; t += nt) {
       long long ci = vidx(o.C, t % m, t / m);
       ar[ci] = (beta == (T)0) ? (T)0 : beta * ar[ci];
+    }
+    return;
+  }
+  if ((long long)m * n <= 2048 && k >= 32) {
+    // small output, long inner dimension: one warp per output, lanes split k
+    const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+    for (int oi = warp; oi < m * n; oi += nw) {
+      int i = oi % m, j = oi / m;
+      T acc = 0;
+      for (int kk = lane; kk < k; kk += 32) acc += ar[vidx(o.A, i, kk)] * ar[vidx(o.B, kk, j)];
+      for (int off = 16; off > 0; off >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, off);
+      if (lane == 0) {
+        long long ci = vidx(o.C, i, j);
+        ar[ci] = (beta == (T)0 ? (T)0 : beta * ar[ci]) + alpha * acc;
+      }
     }
     return;
   }
@@ -614,11 +645,13 @@ __device__ void trunc_core(HCtx<T>& c, int slot, T* Ut, T* Vt, int K) {
   for (int t = threadIdx.x; t < kv * kv; t += blockDim.x) J[(t % kv) + (t / kv) * K] = (t % kv == t / kv) ? (T)1 : (T)0;
   __syncthreads();
   // one-sided Jacobi on the kv columns of M (length ku)
-  const T eps = (sizeof(T) == 4) ? (T)1e-7 : (T)1e-15;
+  // rotate only while columns are far from orthogonal: the kept singular
+  // pairs need a few digits beyond Tol_HLU, not orthogonality to roundoff
+  const T eps = (sizeof(T) == 4) ? (T)2e-5 : (T)1e-12;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int kp = kv + (kv & 1);
   __shared__ int rotated;
-  for (int sweep = 0; sweep < 30 && kv > 1; ++sweep) {
+  for (int sweep = 0; sweep < 12 && kv > 1; ++sweep) {
     if (threadIdx.x == 0) rotated = 0;
     __syncthreads();
     for (int round = 0; round < kp - 1; ++round) {
@@ -778,7 +811,37 @@ struct HProgArgs {
   int* ranks;
   int* err;
   double tol;
+  unsigned long long* prof;   // optional: per instance, 16 op types x (cycles, count)
+  double* flops;              // per instance: algorithmic flops of the executed ops
 };
+
+// algorithmic flops of one op with its run-time shapes
+__device__ double op_flops(const HOp& o, const int* rk, const SlotDev* sl) {
+  switch (o.type) {
+    case OP_GEMM: {
+      double m = dimv(o.C.r, rk), n = dimv(o.C.c, rk), k = dimv(o.A.c, rk);
+      return 2.0 * m * n * k;
+    }
+    case OP_GETRF_INV: {
+      double n = o.C.r;
+      return (2.0 / 3.0) * n * n * n + (2.0 / 3.0) * n * n * n;
+    }
+    case OP_TRMM_L: {
+      double n = dimv(o.C.r, rk), c = dimv(o.C.c, rk);
+      return 2.0 * n * n * c;
+    }
+    case OP_TRMM_R: {
+      double m = dimv(o.C.r, rk), n = dimv(o.C.c, rk);
+      return 2.0 * m * n * n;
+    }
+    case OP_TRUNC: {
+      double K = rk[o.slot], m = sl[o.slot].m, n = sl[o.slot].n;
+      return 4.0 * (m + n) * K * K + 2.0 * K * K * K;
+    }
+    default:
+      return 0.0;
+  }
+}
 
 template <class T>
 __global__ void __launch_bounds__(kHThreads) k_hprog(HProgArgs a, T* har, int which) {
@@ -794,8 +857,12 @@ __global__ void __launch_bounds__(kHThreads) k_hprog(HProgArgs a, T* har, int wh
   c.err = a.err + blockIdx.x;
   const HOp* ops = a.ops + (which ? H.sops0 : H.ops0);
   const int nops = which ? H.nsops : H.nops;
+  double fl = 0.0;
   for (int i = 0; i < nops; ++i) {
     const HOp o = ops[i];
+    if (threadIdx.x == 0) fl += op_flops(o, c.rk, c.sl);
+    unsigned long long t0 = 0;
+    if (a.prof && threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
     switch (o.type) {
       case OP_GEMM: op_gemm(o, c); break;
       case OP_GETRF_INV: op_getrf_inv(o, c); break;
@@ -819,7 +886,15 @@ __global__ void __launch_bounds__(kHThreads) k_hprog(HProgArgs a, T* har, int wh
       default: break;
     }
     __syncthreads();
+    if (a.prof && threadIdx.x == 0) {
+      unsigned long long* pr = a.prof + (size_t)blockIdx.x * 32 + 2 * (o.type & 15);
+      unsigned long long t1;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+      pr[0] += t1 - t0;
+      pr[1] += 1ULL;
+    }
   }
+  if (threadIdx.x == 0) a.flops[blockIdx.x * 2 + which] += fl;
 }
 
 // rhs area <- D r (element-major FP64 -> T); rank slot n_slots <- nrhs
@@ -931,7 +1006,11 @@ struct hfsem_factor_s : public hf::Precond {
   hf::DevBuf<unsigned char> d_arena;
   size_t smem = 0;
   long long total_ops = 0, total_sops = 0;
+  hf::DevBuf<unsigned long long> d_prof;   // HFSEM_PROFILE=1: time per op type
+  hf::DevBuf<double> d_flops;               // per instance: factor / solve flops
+  void report(const char* what);
   void apply(int nrhs, const double* r_em, double* y_em) override;
+  void collect_flops();
   void run_prog(int which);
 };
 
@@ -1103,6 +1182,11 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
       maxdense = std::max(maxdense, H.ndense);
       maxpairs = std::max(maxpairs, H.npairs);
     }
+    const bool prof = getenv("HFSEM_PROFILE") != nullptr;
+    cudaEvent_t ev[5];
+    if (prof)
+      for (auto& e : ev) cudaEventCreate(&e);
+    if (prof) cudaEventRecord(ev[0], s->st);
     dim3 gd((maxnd + 255) / 256, ni);
     k_diag<<<gd, 256, 0, s->st>>>(f->d_hi.p, s->d_inst.p, s->arena.p, f->d_D.p);
     HF_LAUNCH_CHECK();
@@ -1112,6 +1196,7 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
       float* ar = reinterpret_cast<float*>(f->d_arena.p);
       k_nearfield<float><<<gn, 256, 0, s->st>>>(f->d_hi.p, s->d_inst.p, s->arena.p, f->d_dense.p, f->d_D.p, ar);
       HF_LAUNCH_CHECK();
+      if (prof) cudaEventRecord(ev[1], s->st);
       k_lowrank<float><<<gp, 128, 0, s->st>>>(f->d_hi.p, s->d_inst.p, s->arena.p, s->gl.p, f->d_pairs.p,
                                               f->d_slots.p, f->d_D.p, ar, f->d_ranks.p);
       HF_LAUNCH_CHECK();
@@ -1120,13 +1205,32 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
       double* ar = reinterpret_cast<double*>(f->d_arena.p);
       k_nearfield<double><<<gn, 256, 0, s->st>>>(f->d_hi.p, s->d_inst.p, s->arena.p, f->d_dense.p, f->d_D.p, ar);
       HF_LAUNCH_CHECK();
+      if (prof) cudaEventRecord(ev[1], s->st);
       k_lowrank<double><<<gp, 128, 0, s->st>>>(f->d_hi.p, s->d_inst.p, s->arena.p, s->gl.p, f->d_pairs.p,
                                                f->d_slots.p, f->d_D.p, ar, f->d_ranks.p);
       HF_LAUNCH_CHECK();
       set_prog_smem<double>(smem);
     }
+    if (prof) cudaEventRecord(ev[2], s->st);
     if (!f->build_only) f->run_prog(0);
+    if (prof) cudaEventRecord(ev[3], s->st);
     HF_CHECK(cudaStreamSynchronize(s->st));
+    if (prof) {
+      float a = 0, b = 0, c = 0;
+      cudaEventElapsedTime(&a, ev[0], ev[1]);
+      cudaEventElapsedTime(&b, ev[1], ev[2]);
+      cudaEventElapsedTime(&c, ev[2], ev[3]);
+      fprintf(stderr, "[hfsem phases] diag+nearfield %.3f ms  lowrank %.3f ms  hlu %.3f ms\n", a, b, c);
+      for (auto& e : ev) cudaEventDestroy(e);
+    }
+    if (getenv("HFSEM_PROFILE")) {
+      const HPlan& p0 = f->plans[0]->plan;
+      fprintf(stderr, "[hfsem plan] N=%d P=%d blocks=%zu dense=%zu lr=%zu fac_ops=%zu sol_ops=%zu "
+              "leaf_max=%d kconcat_max=%d hh_lr=%d arena=%lld\n", p0.N, p0.P, p0.B.size(),
+              p0.dense_blocks.size(), p0.lr_blocks.size(), p0.fac.size(), p0.sol.size(), p0.leaf_max,
+              p0.kconcat_max, p0.hh_lr, p0.arena);
+      f->report("factorisation");
+    }
     std::vector<int> err(ni);
     HF_CHECK(cudaMemcpy(err.data(), f->d_err.p, ni * sizeof(int), cudaMemcpyDeviceToHost));
     for (int e : err)
@@ -1140,8 +1244,46 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
 
 }  // namespace hf
 
+void hfsem_factor_s::collect_flops() {
+  // move the device flop counters into the timing registry
+  if (!d_flops.p || !hf::timing_on()) return;
+  std::vector<double> h(d_flops.n);
+  cudaMemcpy(h.data(), d_flops.p, h.size() * sizeof(double), cudaMemcpyDeviceToHost);
+  double f0 = 0, f1 = 0;
+  for (size_t i = 0; i < h.size(); i += 2) {
+    f0 += h[i];
+    f1 += h[i + 1];
+  }
+  hf::timing_add_work("hlu_factor", f0);
+  hf::timing_add_work("hlu_solve", f1);
+  cudaMemset(d_flops.p, 0, d_flops.n * sizeof(double));
+}
+
+void hfsem_factor_s::report(const char* what) {
+  if (!d_prof.p) return;
+  std::vector<unsigned long long> h(d_prof.n);
+  cudaMemcpy(h.data(), d_prof.p, h.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+  static const char* names[16] = {"?", "GEMM", "GETRF_INV", "TRMM_L", "TRMM_R", "APPEND",
+                                  "TRUNC", "ZERO", "AXPY", "?", "?", "?", "?", "?", "?", "?"};
+  fprintf(stderr, "[hfsem profile] %s (instance 0; ns, ops)\n", what);
+  for (int t = 0; t < 16; ++t)
+    if (h[2 * t + 1])
+      fprintf(stderr, "  %-10s %14llu ns %8llu ops %10.0f ns/op\n", names[t], h[2 * t], h[2 * t + 1],
+              (double)h[2 * t] / h[2 * t + 1]);
+  cudaMemset(d_prof.p, 0, d_prof.n * sizeof(unsigned long long));
+}
+
 void hfsem_factor_s::run_prog(int which) {
-  hf::HProgArgs a{d_hi.p, d_ops.p, d_slots.p, d_ranks.p, d_err.p, tol};
+  if (!d_prof.p && getenv("HFSEM_PROFILE")) {
+    d_prof.alloc((size_t)sys->n_inst * 32);
+    cudaMemset(d_prof.p, 0, d_prof.n * sizeof(unsigned long long));
+  }
+  if (!d_flops.p) {
+    d_flops.alloc((size_t)sys->n_inst * 2);
+    cudaMemsetAsync(d_flops.p, 0, d_flops.n * sizeof(double), sys->st);
+  }
+  hf::HProgArgs a{d_hi.p, d_ops.p, d_slots.p, d_ranks.p, d_err.p, tol, d_prof.p, d_flops.p};
+  hf::Tick tk(sys->st, which ? "hlu_solve" : "hlu_factor");
   if (tsize == sizeof(float))
     hf::k_hprog<float><<<sys->n_inst, hf::kHThreads, smem, sys->st>>>(
         a, reinterpret_cast<float*>(d_arena.p), which);
@@ -1264,6 +1406,7 @@ int hfsem_precond_apply(hfsem_factor* fac, int32_t nrhs, const double* r, double
 void hfsem_factor_free(hfsem_factor* f) {
   if (!f) return;
   cudaStreamSynchronize(f->sys->st);
+  f->collect_flops();
   delete f;
 }
 

@@ -48,6 +48,7 @@ struct Builder {
   long long tmp_base = 0, tmp_top = 0, tmp_peak = 0;
   std::vector<HOp>* prog = nullptr;
   int max_m = 0;
+  std::vector<char> dirty;   // LR block received updates since its last recompression
 
   Builder(const InstHost& i, const PlanOpts& op, HPlan& pl) : I(i), o(op), p(pl) {}
 
@@ -214,8 +215,13 @@ struct Builder {
     if (b.kcap + kin > o.max_concat)
       throw Error(HFSEM_ERR_UNSUPPORTED, "low-rank update larger than the recompression kernel");
     op(OP_APPEND, U, V, lrU(cb), alpha, 0.0, b.slot);
+    dirty[cb] = 1;
   }
   void trunc(int cb) {
+    // blocks that still hold their Taylor factors (rank R <= kmax) are used as
+    // they are; updated blocks are recompressed before they become factors
+    if (!dirty[cb]) return;
+    dirty[cb] = 0;
     const Block& b = p.B[cb];
     p.kconcat_max = std::max(p.kconcat_max, b.kcap);
     op(OP_TRUNC, View{}, View{}, lrU(cb), 0.0, 0.0, b.slot);
@@ -499,6 +505,7 @@ void make_plan(const InstHost& I, const PlanOpts& o, HPlan& p) {
   int root = b.cluster(0, I.N);
   b.block(root, root);
   b.storage();
+  b.dirty.assign(p.B.size(), 0);
   // right-hand-side area, then temporaries, then the truncation workspace
   p.rhs_off = b.top;
   b.top += (long long)std::max(I.Nd, 1) * o.nrhs_max;

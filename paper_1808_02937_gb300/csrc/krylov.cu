@@ -260,8 +260,6 @@ void bicgstab(hfsem_system* s, Precond* M, int nrhs, const double* b_em, double*
   V.s = base + 5 * nv;
   V.sh = base + 6 * nv;
   V.t = base + 7 * nv;
-  double* tmp = base + 8 * nv;
-  (void)tmp;
   if (!M) {
     V.ph = V.p;
     V.sh = V.s;
@@ -269,6 +267,7 @@ void bicgstab(hfsem_system* s, Precond* M, int nrhs, const double* b_em, double*
   dim3 gv(maxchunk, ncols), bv(kDotThreads);
   int sb = (ncols + 127) / 128;
   auto vec = [&](int mode) {
+    Tick tk(s->st, "krylov_vec");
     k_bicg_vec<<<gv, bv, 0, s->st>>>(mode, V, W.coff.p, W.clen.p, W.cols.p, W.partial.p,
                                      maxchunk);
     HF_LAUNCH_CHECK();

@@ -21,13 +21,88 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <map>
 #include <mutex>
 
 namespace hf {
 
+long long g_launches = 0;
 static thread_local std::string g_last_error;
 void set_last_error(const std::string& m) { g_last_error = m; }
 const std::string& last_error() { return g_last_error; }
+
+// ---------------------------------------------------------------------------
+// kernel timing registry
+// ---------------------------------------------------------------------------
+namespace {
+struct TimerRec {
+  double ms = 0.0;
+  long long launches = 0;
+  double work = 0.0;
+};
+struct Pending {
+  cudaEvent_t a, b;
+  std::string tag;
+  double work;
+};
+std::mutex g_tmu;
+bool g_timing = false;
+std::map<std::string, TimerRec> g_tim;
+std::vector<Pending> g_pend;
+std::vector<cudaEvent_t> g_evpool;
+
+cudaEvent_t get_event() {
+  if (!g_evpool.empty()) {
+    cudaEvent_t e = g_evpool.back();
+    g_evpool.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+void flush_pending() {
+  for (auto& p : g_pend) {
+    cudaEventSynchronize(p.b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, p.a, p.b);
+    TimerRec& r = g_tim[p.tag];
+    r.ms += ms;
+    r.launches += 1;
+    r.work += p.work;
+    g_evpool.push_back(p.a);
+    g_evpool.push_back(p.b);
+  }
+  g_pend.clear();
+}
+}  // namespace
+
+bool timing_on() { return g_timing; }
+
+Tick::Tick(cudaStream_t s, const char* tag, double work) : st(s) {
+  if (!g_timing) return;
+  std::lock_guard<std::mutex> lk(g_tmu);
+  Pending p;
+  p.a = get_event();
+  p.b = get_event();
+  p.tag = tag;
+  p.work = work;
+  cudaEventRecord(p.a, s);
+  g_pend.push_back(p);
+  id = (int)g_pend.size() - 1;
+}
+
+Tick::~Tick() {
+  if (id < 0) return;
+  std::lock_guard<std::mutex> lk(g_tmu);
+  cudaEventRecord(g_pend[id].b, st);
+}
+
+void timing_add_work(const char* tag, double work) {
+  std::lock_guard<std::mutex> lk(g_tmu);
+  g_tim[tag].work += work;
+}
 
 bool is_device_ptr(const void* p) {
   if (!p) return false;
@@ -854,6 +929,10 @@ void apply_operator(hfsem_system* s, int nrhs, const double* x, double* y, int l
       di, s->arena.p, x, z, nrhs, lift);
   HF_LAUNCH_CHECK();
   if (s->any_dense) {
+    double bytes = 0.0;
+    for (auto& I : s->ih)
+      if (I.kind == kDense) bytes += 8.0 * I.P * I.P * I.N * (I.N + 1) / 2.0;
+    Tick tk(s->st, "dense_mv", bytes);
     int W = (s->max_P > 16) ? 4 : 8;
     size_t sm = (size_t)(W * 2 * s->max_P * s->max_P + W * s->max_P * nrhs) * sizeof(double);
     set_smem((const void*)k_dense_rows, sm);
@@ -865,6 +944,10 @@ void apply_operator(hfsem_system* s, int nrhs, const double* x, double* y, int l
     HF_LAUNCH_CHECK();
   }
   if (s->any_toep) {
+    double bytes = 0.0;   // symbol read + z in + w out
+    for (auto& D : s->idv)
+      if (D.kind == kToeplitz) bytes += 16.0 * D.L * D.P * D.P + 2.0 * 8.0 * nrhs * D.N * D.P;
+    Tick tk(s->st, "toeplitz_mv", bytes);
     size_t sm = (size_t)s->max_L * sizeof(double2);
     set_smem((const void*)k_toep_fwd, sm);
     set_smem((const void*)k_toep_inv, sm);
@@ -1139,6 +1222,7 @@ static hfsem_system* assemble(int n, const hfsem_problem* probs, void* stream) {
     for (auto& I : s->ih)
       maxpairs = std::max(maxpairs, I.kind == kDense ? (long long)I.N * (I.N + 1) / 2 : (long long)I.N);
     long long gx = std::min<long long>((maxpairs + wpc - 1) / wpc, 65535);
+    Tick tk(s->st, "pairs");
     k_pairs<<<dim3((unsigned)gx, n), wpc * 32, sm, s->st>>>(s->d_inst.p, s->arena.p, s->gl.p,
                                                            wpc, stride);
     HF_LAUNCH_CHECK();
@@ -1263,5 +1347,36 @@ const char* hfsem_status_str(int status) {
 }
 
 const char* hfsem_last_error(void) { return hf::g_last_error.c_str(); }
+
+int hfsem_timing_enable(int32_t on) {
+  std::lock_guard<std::mutex> lk(g_tmu);
+  g_timing = on != 0;
+  return HFSEM_OK;
+}
+
+int hfsem_timing_reset(void) {
+  std::lock_guard<std::mutex> lk(g_tmu);
+  flush_pending();
+  g_tim.clear();
+  return HFSEM_OK;
+}
+
+int hfsem_timing_read(const char* tag, double* total_ms, int64_t* launches, double* work) {
+  if (!tag) return HFSEM_ERR_INVALID_ARG;
+  std::lock_guard<std::mutex> lk(g_tmu);
+  flush_pending();
+  if (std::string(tag) == "launches") {   // kernels launched so far
+    if (total_ms) *total_ms = 0.0;
+    if (launches) *launches = g_launches;
+    if (work) *work = 0.0;
+    return HFSEM_OK;
+  }
+  auto it = g_tim.find(tag);
+  TimerRec r = (it == g_tim.end()) ? TimerRec() : it->second;
+  if (total_ms) *total_ms = r.ms;
+  if (launches) *launches = r.launches;
+  if (work) *work = r.work;
+  return HFSEM_OK;
+}
 
 }  // extern "C"

@@ -31,7 +31,8 @@ RHS_LOAD_VECTOR, RHS_FRAC_POWERS, RHS_LEGENDRE_AB = 0, 1, 2
 EXPORTED = ["hfsem_assemble", "hfsem_ndof", "hfsem_apply", "hfsem_load_vector",
             "hfsem_hlu_factor", "hfsem_hmatrix_dense", "hfsem_precond_apply",
             "hfsem_solve", "hfsem_factor_free", "hfsem_system_free",
-            "hfsem_status_str"]
+            "hfsem_status_str", "hfsem_timing_enable", "hfsem_timing_reset",
+            "hfsem_timing_read"]
 
 
 class HfsemError(RuntimeError):
@@ -91,6 +92,9 @@ def load_library():
     lib.hfsem_status_str.argtypes = [C.c_int]
     lib.hfsem_status_str.restype = C.c_char_p
     lib.hfsem_last_error.restype = C.c_char_p
+    lib.hfsem_timing_enable.argtypes = [C.c_int32]
+    lib.hfsem_timing_read.argtypes = [C.c_char_p, C.POINTER(C.c_double),
+                                      C.POINTER(C.c_int64), C.POINTER(C.c_double)]
     _lib = lib
     return lib
 
@@ -296,3 +300,19 @@ def split(sys: System, v, nrhs: int = 1):
         out.append(v[off: off + nd * nrhs].reshape(nrhs, nd).T)
         off += nd * nrhs
     return out
+
+
+def hfsem_timing_enable(on: bool = True):
+    _check(load_library().hfsem_timing_enable(1 if on else 0), "hfsem_timing_enable")
+
+
+def hfsem_timing_reset():
+    _check(load_library().hfsem_timing_reset(), "hfsem_timing_reset")
+
+
+def hfsem_timing_read(tag: str):
+    """(total device ms, launches, algorithmic work) for one kernel tag."""
+    ms, n, w = C.c_double(), C.c_int64(), C.c_double()
+    _check(load_library().hfsem_timing_read(tag.encode(), C.byref(ms), C.byref(n), C.byref(w)),
+           "hfsem_timing_read")
+    return ms.value, n.value, w.value
