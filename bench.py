@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-fp64-compare", action="store_true")
+    # profiling only: a reduced copy of the workload (fewer instances / elements)
+    ap.add_argument("--instances", type=int, default=9)
+    ap.add_argument("--n-elem", type=int, default=1024)
     return ap.parse_args()
 
 
@@ -74,10 +77,13 @@ def max_over_ranks(x, world):
     return float(t.item())
 
 
-def workload():
+def workload(n_inst=9, n_elem=1024):
     from paper_1808_02937_gb300 import hfsem as H
     from paper_1808_02937_gb300 import workloads as W
-    insts = W.config2()
+    insts = W.config2()[:n_inst]
+    for p in insts:
+        if n_elem != 1024:
+            p.h = W.mesh_uniform(n_elem)
     probs = [H.make_problem(p.h, p.P, p.alpha, p.theta, p.rho) for p in insts]
     rhs = [H.rhs_legendre([p.rhs[0]]) for p in insts]
     return insts, probs, rhs
@@ -217,7 +223,8 @@ def main():
     torch.cuda.set_device(local)
     from paper_1808_02937_gb300 import hfsem as H
     H.load_library()
-    insts, probs, rhs = workload()
+    insts, probs, rhs = workload(args.instances, args.n_elem)
+    reduced = (args.instances, args.n_elem) != (9, 1024)
     n_inst = len(insts)
     nd_total = sum(p.Nd for p in insts)
     prec = H.PREC_MIXED if args.precision == "mixed" else H.PREC_FP64
@@ -326,7 +333,7 @@ def main():
                     "peak_source": peak_src}
 
     cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and not reduced:
         v, dt, Xo = cpu_baseline_oracle(insts[4], os.cpu_count())
         got = _Sys(insts).split(Xd)[4][:, 0]
         cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
@@ -341,7 +348,9 @@ def main():
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
                 "dtype": "f64 Krylov/operator, f32 H-LU" if prec == H.PREC_MIXED else "f64",
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD, "instances_per_gpu": n_inst,
+                "config": {"workload": WORKLOAD if not reduced else
+                           f"REDUCED (profiling only): {n_inst} instances, N={args.n_elem}",
+                           "instances_per_gpu": n_inst,
                            "precision": args.precision, "l2": "flushed between steps (256 MB write)",
                            "krylov_tol": 1e-14},
                 "p50_ms": p50, "p99_ms": p99, "wall_s_timed": wall,
