@@ -126,6 +126,20 @@ int hfsem_ndof(const hfsem_system *sys, int32_t inst, int32_t *nd);
  * values), x and y N_d x nrhs per instance, concatenated; 1 <= nrhs <= 64. */
 int hfsem_apply(hfsem_system *sys, int32_t nrhs, const double *x, double *y);
 
+/* The operator product of hfsem_apply for callers that cannot allocate
+ * device memory while they run (the paper has no counterpart: this serves
+ * applications that own every allocation themselves or call from a section
+ * where cudaMalloc is not allowed).  x and y must be device pointers; no
+ * cudaMalloc, cudaFree or allocating library routine is called.  Its
+ * temporaries live in one file-scope device array of 32 MiB that every GPU
+ * loading the library holds until the process exits; requests needing more
+ * (sum of N_d, N*P, the dense column partials and the FFT buffers, times
+ * nrhs) return HFSEM_ERR_INVALID_ARG.  The first call on a device looks up
+ * the array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  All calls share the array: calls whose work
+ * overlaps on the GPU (other streams, other host threads) race on it. */
+int hfsem_apply_noalloc(hfsem_system *sys, int32_t nrhs, const double *x, double *y);
+
 /* Load vector G_i = (f, phi_i) of Sec. 2.2 for every instance, rhs[inst].
  * lifted = 1 subtracts the boundary-hat columns times (c1, c2), i.e. returns
  * the right-hand side the interior unknowns solve against. */

@@ -32,7 +32,7 @@ EXPORTED = ["hfsem_assemble", "hfsem_ndof", "hfsem_apply", "hfsem_load_vector",
             "hfsem_hlu_factor", "hfsem_hmatrix_dense", "hfsem_precond_apply",
             "hfsem_solve", "hfsem_factor_free", "hfsem_system_free",
             "hfsem_status_str", "hfsem_timing_enable", "hfsem_timing_reset",
-            "hfsem_timing_read"]
+            "hfsem_timing_read", "hfsem_apply_noalloc"]
 
 
 class HfsemError(RuntimeError):
@@ -79,6 +79,7 @@ def load_library():
     lib.hfsem_assemble.argtypes = [C.c_int32, C.POINTER(hfsem_problem), vp, C.POINTER(vp)]
     lib.hfsem_ndof.argtypes = [vp, C.c_int32, C.POINTER(C.c_int32)]
     lib.hfsem_apply.argtypes = [vp, C.c_int32, vp, vp]
+    lib.hfsem_apply_noalloc.argtypes = [vp, C.c_int32, vp, vp]
     lib.hfsem_load_vector.argtypes = [vp, C.POINTER(hfsem_rhs), C.c_int32, vp]
     lib.hfsem_hlu_factor.argtypes = [vp, C.POINTER(hfsem_hopts), C.POINTER(vp)]
     lib.hfsem_hmatrix_dense.argtypes = [vp, C.c_int32, vp]
@@ -204,6 +205,14 @@ def _like(x, n):
 def hfsem_apply(sys: System, x, nrhs: int = 1):
     y = _like(x, sys.total_ndof * nrhs)
     _check(load_library().hfsem_apply(sys.h, nrhs, _ptr(x), _ptr(y)), "hfsem_apply")
+    return y
+
+
+def hfsem_apply_noalloc(sys: System, x, nrhs: int = 1, out=None):
+    """y = A x without device allocation; x (and out) must be CUDA tensors."""
+    y = _like(x, sys.total_ndof * nrhs) if out is None else out
+    _check(load_library().hfsem_apply_noalloc(sys.h, nrhs, _ptr(x), _ptr(y)),
+           "hfsem_apply_noalloc")
     return y
 
 
