@@ -617,8 +617,10 @@ __device__ void apply_q(const T* A, int m, int K, const T* tau, T* Y, int ldy, i
 }
 
 // Recompress U V^T given as Ut (m x K) and Vt (n x K) in the workspace into
-// LR slot `slot`: SVD of R_U R_V^T by one-sided Jacobi, keep sigma_i >
-// tol sigma_1, at most kmax.
+// LR slot `slot`.  U = Q_U R_U, V = Q_V R_V (Householder), then a column-
+// pivoted QR of the small core M = R_U R_V^T, M Pi = Q_M R_M, stopped at the
+// first pivot below tol |R_M(0,0)| (or at kmax):
+//   U V^T ~ (Q_U Q_M[:, :r]) (Q_V Pi R_M[:r, :]^T)^T.
 template <class T>
 __device__ void trunc_core(HCtx<T>& c, int slot, T* Ut, T* Vt, int K) {
   const SlotDev s = c.sl[slot];
@@ -627,118 +629,129 @@ __device__ void trunc_core(HCtx<T>& c, int slot, T* Ut, T* Vt, int K) {
   T* tauV = tauU + K;
   T* red = tauV + K;                 // 32
   T* M = red + 32;                   // ku x kv, ld K
-  T* J = M + K * K;                  // kv x kv, ld K
+  T* tauM = M + K * K;               // K
+  T* cn = tauM + K;                  // K column norms^2
+  T* Z = cn + K;                     // K x K work (ld K)
+  int* piv = reinterpret_cast<int*>(Z + K * K);   // K
+  __shared__ int s_p, s_stop;
+  __shared__ T s_r0;
   house_qr(Ut, m, K, tauU, red);
   house_qr(Vt, n, K, tauV, red);
   const int ku = min(m, K), kv = min(n, K);
-  // M = R_U R_V^T
   for (int t = threadIdx.x; t < ku * kv; t += blockDim.x) {
     int i = t % ku, j = t / ku;
     T acc = 0;
-    for (int l = max(i, j); l < K; ++l) {
-      T ru = (i <= l) ? Ut[i + (long long)l * m] : (T)0;
-      T rv = (j <= l) ? Vt[j + (long long)l * n] : (T)0;
-      acc += ru * rv;
-    }
+    for (int l = max(i, j); l < K; ++l) acc += Ut[i + (long long)l * m] * Vt[j + (long long)l * n];
     M[i + j * K] = acc;
   }
-  for (int t = threadIdx.x; t < kv * kv; t += blockDim.x) J[(t % kv) + (t / kv) * K] = (t % kv == t / kv) ? (T)1 : (T)0;
+  for (int j = threadIdx.x; j < kv; j += blockDim.x) piv[j] = j;
   __syncthreads();
-  // one-sided Jacobi on the kv columns of M (length ku)
-  // rotate only while columns are far from orthogonal: the kept singular
-  // pairs need a few digits beyond Tol_HLU, not orthogonality to roundoff
-  const T eps = (sizeof(T) == 4) ? (T)2e-5 : (T)1e-12;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const int kp = kv + (kv & 1);
-  __shared__ int rotated;
-  for (int sweep = 0; sweep < 12 && kv > 1; ++sweep) {
-    if (threadIdx.x == 0) rotated = 0;
-    __syncthreads();
-    for (int round = 0; round < kp - 1; ++round) {
-      for (int pi = warp; pi < kp / 2; pi += nw) {
-        int p, q;
-        if (pi == 0) {
-          p = round;
-          q = kp - 1;
-        } else {
-          p = (round + pi) % (kp - 1);
-          q = (round - pi + kp - 1) % (kp - 1);
-        }
-        if (p >= kv || q >= kv) continue;
-        T a = 0, b = 0, g = 0;
-        for (int i = lane; i < ku; i += 32) {
-          T mp = M[i + p * K], mq = M[i + q * K];
-          a += mp * mp;
-          b += mq * mq;
-          g += mp * mq;
-        }
-        for (int o = 16; o > 0; o >>= 1) {
-          a += __shfl_xor_sync(0xffffffffu, a, o);
-          b += __shfl_xor_sync(0xffffffffu, b, o);
-          g += __shfl_xor_sync(0xffffffffu, g, o);
-        }
-        if (g != (T)0 && fabs((double)g) > (double)eps * sqrt((double)a * (double)b)) {
-          T zeta = (b - a) / (2 * g);
-          T t = (zeta >= (T)0 ? (T)1 : (T)-1) / (fabs(zeta) + sqrt((T)1 + zeta * zeta));
-          T cs = (T)1 / sqrt((T)1 + t * t), sn = cs * t;
-          for (int i = lane; i < ku; i += 32) {
-            T mp = M[i + p * K], mq = M[i + q * K];
-            M[i + p * K] = cs * mp - sn * mq;
-            M[i + q * K] = sn * mp + cs * mq;
-          }
-          for (int i = lane; i < kv; i += 32) {
-            T jp = J[i + p * K], jq = J[i + q * K];
-            J[i + p * K] = cs * jp - sn * jq;
-            J[i + q * K] = sn * jp + cs * jq;
-          }
-          if (lane == 0) rotated = 1;
-        }
-      }
-      __syncthreads();
+  const int rmax = min(min(ku, kv), s.kmax);
+  int r = 0;
+  for (int st = 0; st < rmax; ++st) {
+    // exact norms of the remaining parts of the columns
+    for (int j = st + threadIdx.x; j < kv; j += blockDim.x) {
+      T a = 0;
+      for (int i = st; i < ku; ++i) a += M[i + j * K] * M[i + j * K];
+      cn[j] = a;
     }
-    if (!rotated) break;
     __syncthreads();
+    if (threadIdx.x == 0) {
+      int p = st;
+      for (int j = st + 1; j < kv; ++j)
+        if (cn[j] > cn[p]) p = j;
+      T nrm = sqrt(cn[p]);
+      if (st == 0) s_r0 = nrm;
+      s_stop = (nrm == (T)0 || (st > 0 && nrm <= (T)c.tol * s_r0)) ? 1 : 0;
+      s_p = p;
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const int p = s_p;
+    if (p != st) {
+      for (int i = threadIdx.x; i < ku; i += blockDim.x) {
+        T a = M[i + st * K];
+        M[i + st * K] = M[i + p * K];
+        M[i + p * K] = a;
+      }
+      if (threadIdx.x == 0) {
+        int a = piv[st];
+        piv[st] = piv[p];
+        piv[p] = a;
+      }
+    }
+    __syncthreads();
+    // Householder on M[st:ku, st] (one warp), stored as in house_qr
+    if (warp == 0) {
+      T a = 0;
+      for (int i = st + lane; i < ku; i += 32) a += M[i + st * K] * M[i + st * K];
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      T x0 = M[st + st * K];
+      T sn = sqrt(a);
+      T alpha = (x0 >= (T)0) ? -sn : sn;
+      T v0 = x0 - alpha;
+      bool trivial = (sn == (T)0) || (v0 == (T)0);
+      __syncwarp();
+      if (!trivial)
+        for (int i = st + 1 + lane; i < ku; i += 32) M[i + st * K] /= v0;
+      __syncwarp();
+      if (lane == 0) {
+        tauM[st] = trivial ? (T)0 : (alpha - x0) / alpha;
+        if (!trivial) M[st + st * K] = alpha;
+      }
+    }
+    __syncthreads();
+    const T tj = tauM[st];
+    if (tj != (T)0)
+      for (int l = st + 1 + warp; l < kv; l += nw) {
+        T w = 0;
+        for (int i = st + 1 + lane; i < ku; i += 32) w += M[i + st * K] * M[i + l * K];
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        w = (w + M[st + l * K]) * tj;
+        if (lane == 0) M[st + l * K] -= w;
+        for (int i = st + 1 + lane; i < ku; i += 32) M[i + l * K] -= w * M[i + st * K];
+      }
+    __syncthreads();
+    r = st + 1;
   }
-  // singular values and their order
-  T* sig = J + K * K;          // kv
-  int* pos = (int*)(sig + K);  // kv
-  for (int j = threadIdx.x; j < kv; j += blockDim.x) {
-    T a = 0;
-    for (int i = 0; i < ku; ++i) a += M[i + j * K] * M[i + j * K];
-    sig[j] = sqrt(a);
-  }
-  __syncthreads();
-  T smax = 0;
-  for (int j = 0; j < kv; ++j) smax = fmax(smax, sig[j]);
-  T thr = (T)c.tol * smax;
-  int keep = 0;
-  for (int j = 0; j < kv; ++j)
-    if (sig[j] > thr && sig[j] > (T)0) ++keep;
-  keep = min(keep, s.kmax);
-  for (int j = threadIdx.x; j < kv; j += blockDim.x) {
-    int r = 0;
-    for (int l = 0; l < kv; ++l)
-      if (sig[l] > sig[j] || (sig[l] == sig[j] && l < j)) ++r;
-    pos[j] = r;
-  }
-  __syncthreads();
-  // new factors: U = Q_U [M_j; 0], V = Q_V [J_j; 0] for the kept columns
+  // (all threads agree on r: every exit is uniform)
   T* Ud = c.ar + s.off;
   T* Vd = c.ar + s.off + (long long)m * s.kcap;
-  for (int t = threadIdx.x; t < m * keep; t += blockDim.x) Ud[t] = 0;
-  for (int t = threadIdx.x; t < n * keep; t += blockDim.x) Vd[t] = 0;
+  // Z = Q_M [I_r; 0] (ku x r): apply the r reflectors of M in reverse
+  for (int t = threadIdx.x; t < ku * r; t += blockDim.x) Z[(t % ku) + (t / ku) * K] = (t % ku == t / ku) ? (T)1 : (T)0;
   __syncthreads();
-  for (int t = threadIdx.x; t < kv * max(ku, kv); t += blockDim.x) {
-    int j = t / max(ku, kv), i = t % max(ku, kv);
-    int pj = pos[j];
-    if (pj >= keep) continue;
-    if (i < ku) Ud[i + (long long)pj * m] = M[i + j * K];
-    if (i < kv) Vd[i + (long long)pj * n] = J[i + j * K];
+  for (int j = r - 1; j >= 0; --j) {
+    T tj = tauM[j];
+    if (tj != (T)0)
+      for (int col = warp; col < r; col += nw) {
+        T w = 0;
+        for (int i = j + 1 + lane; i < ku; i += 32) w += M[i + j * K] * Z[i + col * K];
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        w = (w + Z[j + col * K]) * tj;
+        if (lane == 0) Z[j + col * K] -= w;
+        for (int i = j + 1 + lane; i < ku; i += 32) Z[i + col * K] -= w * M[i + j * K];
+      }
+    __syncthreads();
+  }
+  // U_new = Q_U [Z; 0]
+  for (int t = threadIdx.x; t < m * r; t += blockDim.x) {
+    int i = t % m, j = t / m;
+    Ud[t] = (i < ku) ? Z[i + j * K] : (T)0;
+  }
+  // V_new = Q_V [Pi R_M[:r,:]^T; 0]: row piv[j] of the core factor is R_M[:, j]
+  for (int t = threadIdx.x; t < n * r; t += blockDim.x) Vd[t] = 0;
+  __syncthreads();
+  for (int t = threadIdx.x; t < kv * r; t += blockDim.x) {
+    int j = t % kv, i = t / kv;   // R_M[i][j], j >= i
+    Vd[piv[j] + (long long)i * n] = (j >= i) ? M[i + j * K] : (T)0;
   }
   __syncthreads();
-  apply_q(Ut, m, K, tauU, Ud, m, keep);
-  apply_q(Vt, n, K, tauV, Vd, n, keep);
-  if (threadIdx.x == 0) c.rk[slot] = keep;
+  apply_q(Ut, m, K, tauU, Ud, m, r);
+  apply_q(Vt, n, K, tauV, Vd, n, r);
+  if (threadIdx.x == 0) c.rk[slot] = r;
   __syncthreads();
 }
 
@@ -1025,7 +1038,7 @@ static void set_prog_smem(size_t bytes) {
 static size_t prog_smem(const HPlan& p, size_t ts) {
   size_t leaf = (size_t)2 * p.leaf_max * p.leaf_max;
   size_t K = (size_t)std::max(p.kconcat_max, 1);
-  size_t trunc = 2 * K + 32 + 2 * K * K + 2 * K + 8;
+  size_t trunc = 2 * K + 32 + 2 * K * K + 3 * K + 8;
   size_t trmm = (size_t)std::max(p.leaf_max, 1) * 32;
   size_t gemm = 2 * 16 * 64;
   return std::max(std::max(leaf, trunc), std::max(trmm, gemm)) * ts + 64;
@@ -1064,11 +1077,11 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
       const InstHost& I = s->ih[i];
       PlanOpts o;
       o.lambda = opt.lambda;
-      int leaf = opt.leaf_elems ? opt.leaf_elems : std::max(1, 64 / I.P);
+      int leaf = opt.leaf_elems ? opt.leaf_elems : std::max(1, max_leaf / I.P);
       leaf = std::min(leaf, std::max(1, max_leaf / I.P));
       o.leaf_elems = leaf;
       o.R = opt.R;
-      o.kmax = opt.kmax ? opt.kmax : std::max(2 * opt.R, 8);
+      o.kmax = opt.kmax ? opt.kmax : opt.R;
       o.nrhs_max = 64;
       o.max_concat = fp32 ? 128 : 96;
       o.max_leaf = max_leaf;

@@ -17,6 +17,7 @@
 // truncate), which the device interpreter runs in order.
 #include <algorithm>
 #include <cmath>
+#include <map>
 #include <string>
 
 #include "hplan.h"
@@ -173,6 +174,9 @@ struct Builder {
     if (-1 - d == p.n_slots) return p.nrhs_max;   // rhs width of the solve program
     return p.B[p.lr_blocks[-1 - d]].kcap;
   }
+  void release(long long mark) {
+    if (!o.unique_tmp) tmp_top = mark;
+  }
   View tmp(int r, int c_bound, int c_dim) {
     View v{tmp_top, r, c_dim, std::max(r, 1), 0};
     tmp_top += (long long)std::max(r, 1) * std::max(c_bound, 1);
@@ -280,7 +284,7 @@ struct Builder {
       T.r = lrU(ab).c;   // runtime rank rows
       gemm(T, vT(lrV(ab)), E, 1.0, 0.0);
       gemm(D, lrU(ab), T, alpha, 1.0);
-      tmp_top = mark;
+      release(mark);
     } else {
       for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 2; ++j) {
@@ -303,7 +307,7 @@ struct Builder {
       T.r = E.r;
       gemm(T, E, lrU(bb), 1.0, 0.0);
       gemm(D, T, vT(lrV(bb)), alpha, 1.0);
-      tmp_top = mark;
+      release(mark);
     } else {
       for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 2; ++j) {
@@ -329,14 +333,14 @@ struct Builder {
       zero(T);
       gemm_dh(T, vT(lrV(ab)), bb, 1.0);
       gemm(D, lrU(ab), T, alpha, 1.0);
-      tmp_top = mark;
+      release(mark);
     } else if (b.type == B_LR) {
       long long mark = tmp_top;
       View Z = tmp(a.m, b.kcap, lrU(bb).c);
       zero(Z);
       gemm_hd(Z, ab, lrU(bb), 1.0);
       gemm(D, Z, vT(lrV(bb)), alpha, 1.0);
-      tmp_top = mark;
+      release(mark);
     } else {
       for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 2; ++j)
@@ -370,7 +374,7 @@ struct Builder {
       zero(W);
       gemm_dh(vT(W), vT(lrV(ab)), bb, 1.0);      // W^T += V_A^T B
       add_lr(cb, lrU(ab), W, -1.0);
-      tmp_top = mark;
+      release(mark);
       return;
     }
     if (b.type == B_LR) {
@@ -379,7 +383,7 @@ struct Builder {
       zero(Z);
       gemm_hd(Z, ab, lrU(bb), 1.0);
       add_lr(cb, Z, lrV(bb), -1.0);
-      tmp_top = mark;
+      release(mark);
       return;
     }
     if (a.type == B_DENSE && b.type == B_DENSE) {
@@ -393,7 +397,7 @@ struct Builder {
     zero(Z);
     gemm_dab(Z, ab, bb, 1.0);
     add_dense(cb, Z, -1.0);
-    tmp_top = mark;
+    release(mark);
   }
 
   // X <- L^-1 X for a dense view, L the diagonal block lb
@@ -512,16 +516,192 @@ void make_plan(const InstHost& I, const PlanOpts& o, HPlan& p) {
   b.tmp_base = b.tmp_top = b.top;
   b.prog = &p.fac;
   b.hlu(0);
-  b.tmp_top = b.tmp_base;
+  if (!o.unique_tmp) b.tmp_top = b.tmp_base;
   b.prog = &p.sol;
   // the width of the rhs area is read at run time from rank slot n_slots
   View rhs{p.rhs_off, I.Nd, -1 - p.n_slots, std::max(I.Nd, 1), 0};
   b.trsm_ll_d(0, rhs);
   b.trsm_lu_d(0, rhs);
   long long ws_off = b.tmp_base + b.tmp_peak;
+  p.tmp_base = b.tmp_base;
+  p.tmp_size = b.tmp_peak;
   p.ws_off = ws_off;
   p.ws_size = (long long)2 * std::max(b.max_m, 1) * std::max(p.kconcat_max, 1);
   p.arena = ws_off + p.ws_size;
+}
+
+}  // namespace hf
+
+namespace hf {
+namespace {
+
+// storage rectangle touched by a view: [r0, r1) x [c0, c1) of the column-major
+// matrix starting at `base` with leading dimension ld (rank dims -> capacity)
+struct Rect {
+  long long base;
+  int ld;
+  long long r0, r1, c0, c1;
+  int slot;   // LR slot whose rank is read (-1 none)
+};
+
+struct Access {
+  Rect rc;
+  bool write;
+};
+
+}  // namespace
+
+int program_levels(const HPlan& p, const std::vector<HOp>& prog, std::vector<int>& level) {
+  // map storage offsets to the allocation that holds them
+  struct Alloc {
+    long long off, size;
+    int ld;
+    int slot;
+  };
+  std::vector<Alloc> al;
+  for (const Block& b : p.B) {
+    if (b.type == B_DENSE) {
+      al.push_back({b.off, (long long)b.m * b.n, std::max(b.m, 1), -1});
+      if (b.inv >= 0) {
+        al.push_back({b.inv, (long long)b.m * b.m, std::max(b.m, 1), -1});
+        al.push_back({b.inv + (long long)b.m * b.m, (long long)b.m * b.m, std::max(b.m, 1), -1});
+      }
+    } else if (b.type == B_LR) {
+      al.push_back({b.off, (long long)b.m * b.kcap, b.m, b.slot});
+      al.push_back({b.off + (long long)b.m * b.kcap, (long long)b.n * b.kcap, b.n, b.slot});
+    }
+  }
+  std::sort(al.begin(), al.end(), [](const Alloc& a, const Alloc& b) { return a.off < b.off; });
+  auto find = [&](long long off) -> const Alloc* {
+    size_t lo = 0, hi = al.size();
+    while (lo < hi) {
+      size_t mid = (lo + hi) / 2;
+      if (al[mid].off <= off) lo = mid + 1; else hi = mid;
+    }
+    if (lo == 0) return nullptr;
+    const Alloc& a = al[lo - 1];
+    return (off < a.off + a.size) ? &a : nullptr;
+  };
+  auto rect_of = [&](const View& v, int ncol_cap) -> Rect {
+    // rows/cols in storage coordinates
+    int sr = v.tr ? v.c : v.r, sc = v.tr ? v.r : v.c;
+    Rect r;
+    const Alloc* a = find(v.off);
+    int slot = -1;
+    if (sr < 0) slot = -1 - sr;
+    if (sc < 0) slot = -1 - sc;
+    if (a && a->slot >= 0) {   // LR factor: whole factor, rank read
+      r.base = a->off;
+      r.ld = a->ld;
+      r.r0 = 0;
+      r.r1 = a->ld;
+      r.c0 = 0;
+      r.c1 = a->size / a->ld;
+      r.slot = a->slot;
+      return r;
+    }
+    long long rows = sr < 0 ? ncol_cap : sr, cols = sc < 0 ? ncol_cap : sc;
+    if (a) {
+      long long rel = v.off - a->off;
+      r.base = a->off;
+      r.ld = a->ld;
+      r.r0 = rel % a->ld;
+      r.c0 = rel / a->ld;
+    } else if (v.off >= p.rhs_off && v.off < p.rhs_off + (long long)std::max(p.Nd, 1) * p.nrhs_max) {
+      long long rel = v.off - p.rhs_off;
+      int ldr = std::max(p.Nd, 1);
+      r.base = p.rhs_off;
+      r.ld = ldr;
+      r.r0 = rel % ldr;
+      r.c0 = rel / ldr;
+    } else {   // temporaries: by raw address
+      r.base = -1;
+      r.ld = v.ld;
+      r.r0 = v.off % std::max(v.ld, 1);
+      r.c0 = v.off / std::max(v.ld, 1);
+      // treat as an interval [off, off + ld*cols)
+      r.r0 = v.off;
+      r.r1 = v.off + (long long)std::max(v.ld, 1) * (cols - 1) + rows;
+      r.c0 = 0;
+      r.c1 = 1;
+      r.slot = slot;
+      return r;
+    }
+    r.r1 = r.r0 + rows;
+    r.c1 = r.c0 + cols;
+    r.slot = slot;
+    return r;
+  };
+  auto overlap = [](const Rect& a, const Rect& b) {
+    if (a.base != b.base) return false;
+    return a.r0 < b.r1 && b.r0 < a.r1 && a.c0 < b.c1 && b.c0 < a.c1;
+  };
+  const int cap = 64;
+  level.assign(prog.size(), 0);
+  // last writer / readers per storage region are tracked by scanning a window
+  // of recent accesses per allocation base
+  struct Rec {
+    Rect rc;
+    bool write;
+    int lvl;
+  };
+  std::map<long long, std::vector<Rec>> hist;   // base (or -1 for raw) -> accesses
+  std::map<int, std::pair<int, int>> slot_state; // slot -> (last write level, max read level)
+  int nlev = 0;
+  for (size_t i = 0; i < prog.size(); ++i) {
+    const HOp& o = prog[i];
+    std::vector<Access> acc;
+    auto add = [&](const View& v, bool w) {
+      if (v.r == 0 || v.c == 0) return;
+      acc.push_back({rect_of(v, cap), w});
+    };
+    int slot_w = -1;
+    switch (o.type) {
+      case OP_GEMM: add(o.A, false); add(o.B, false); add(o.C, true); break;
+      case OP_GETRF_INV: add(o.C, true); add(o.A, true); add(o.B, true); break;
+      case OP_TRMM_L: case OP_TRMM_R: add(o.A, false); add(o.C, true); break;
+      case OP_APPEND: add(o.A, false); if (o.B.off >= 0) add(o.B, false); add(o.C, true); slot_w = o.slot; break;
+      case OP_TRUNC: add(o.C, true); slot_w = o.slot; break;
+      case OP_ZERO: add(o.C, true); break;
+      case OP_AXPY: add(o.A, false); add(o.C, true); break;
+    }
+    int lv = 0;
+    for (auto& a : acc) {
+      auto& h = hist[a.rc.base];
+      for (auto& r : h)
+        if ((a.write || r.write) && overlap(a.rc, r.rc)) lv = std::max(lv, r.lvl);
+      if (a.rc.slot >= 0) {
+        auto it = slot_state.find(a.rc.slot);
+        if (it != slot_state.end()) {
+          lv = std::max(lv, it->second.first);
+          if (a.write) lv = std::max(lv, it->second.second);
+        }
+      }
+    }
+    if (slot_w >= 0) {
+      auto it = slot_state.find(slot_w);
+      if (it != slot_state.end()) lv = std::max(lv, std::max(it->second.first, it->second.second));
+    }
+    lv += 1;
+    level[i] = lv;
+    nlev = std::max(nlev, lv);
+    for (auto& a : acc) {
+      auto& h = hist[a.rc.base];
+      // drop records fully covered by this write at a lower level
+      h.push_back({a.rc, a.write, lv});
+      if (h.size() > 256) h.erase(h.begin(), h.begin() + 128);
+      if (a.rc.slot >= 0) {
+        auto& st = slot_state[a.rc.slot];
+        if (a.write) st.first = std::max(st.first, lv);
+        else st.second = std::max(st.second, lv);
+      }
+    }
+    if (slot_w >= 0) {
+      auto& st = slot_state[slot_w];
+      st.first = std::max(st.first, lv);
+    }
+  }
+  return nlev;
 }
 
 }  // namespace hf

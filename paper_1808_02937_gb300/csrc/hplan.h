@@ -76,6 +76,7 @@ struct HPlan {
   int leaf_max = 0;                    // largest diagonal leaf
   int n_slots = 0;
   int hh_lr = 0;                       // H x H products into LR blocks seen
+  long long tmp_base = 0, tmp_size = 0;  // temporaries region
 };
 
 struct PlanOpts {
@@ -86,9 +87,18 @@ struct PlanOpts {
   int nrhs_max;
   int max_concat;    // limit on K in a truncation (shared memory)
   int max_leaf;      // limit on diagonal leaf size
+  int unique_tmp = 0;  // 1: never reuse temporary storage (independent ops stay independent)
 };
 
 // Build clusters, blocks, storage and the two programs.
 void make_plan(const InstHost& I, const PlanOpts& o, HPlan& out);
 
+}  // namespace hf
+
+namespace hf {
+// Dependency levels of an op program: op i may run concurrently with every
+// op of the same level; level(i) = 1 + max level of the earlier ops it
+// conflicts with (read/write or write/write on overlapping storage, or on the
+// same low-rank slot / rank).  Returns the number of levels.
+int program_levels(const HPlan& p, const std::vector<HOp>& prog, std::vector<int>& level);
 }  // namespace hf
