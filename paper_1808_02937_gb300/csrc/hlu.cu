@@ -44,6 +44,8 @@ struct LRPairDev {  // an admissible pair: tau (rows of the lower block) right o
   int td0, tm, sd0, sn;         // unknown ranges
 };
 
+constexpr int kCluster = 8;   // CTAs (one thread-block cluster) per instance
+
 struct HInstDev {
   long long arena;   // offset of the instance arena (elements)
   long long rk0;     // offset into the rank array
@@ -52,7 +54,9 @@ struct HInstDev {
   long long pair0;   // offset into the pair table
   long long ops0, sops0;
   int nops, nsops, ndense, npairs, n_slots;
-  long long ws_off, rhs_off;
+  long long ws_off, rhs_off, ws_size;
+  long long fw0, sw0;   // offsets into the wave table (factor, solve)
+  int nfw, nsw;         // number of waves
   long long d_off;   // scaling D (FP64) offset
   int sys_inst;      // index into the system's instances
   int R;
@@ -452,107 +456,166 @@ __device__ void op_gemm(const HOp& o, HCtx<T>& c) {
     }
 }
 
-// C <- A C (A n x n), column panels staged in shared memory
+// C <- A C (A n x n, n <= 128): A (column-major) and a 32-column panel of C
+// (row-major, ld 33) staged in shared memory; thread (ty, tx) computes rows
+// 4ty..4ty+3 and columns tx, tx+8, tx+16, tx+24 of the panel.  Every shared
+// load is a broadcast or hits 8 distinct banks.
 template <class T>
 __device__ void op_trmm_l(const HOp& o, HCtx<T>& c) {
   const int n = dimv(o.C.r, c.rk), cc = dimv(o.C.c, c.rk);
   if (n <= 0 || cc <= 0) return;
   T* ar = c.ar;
-  const int CP = 32;
-  T* S = c.sm;
-  for (int c0 = 0; c0 < cc; c0 += CP) {
-    int cp = min(CP, cc - c0);
-    for (int t = threadIdx.x; t < n * cp; t += blockDim.x) {
-      int i = t % n, j = t / n;
-      S[j * n + i] = ar[vidx(o.C, i, c0 + j)];
+  if (cc <= 4) {
+    // a few right-hand sides (the H-solves): rows in parallel, A read from
+    // L2 column by column (consecutive threads, consecutive rows)
+    T* Pv = c.sm;   // n x cc
+    for (int t = threadIdx.x; t < n * cc; t += blockDim.x) Pv[t] = ar[vidx(o.C, t % n, t / n)];
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      T acc[4] = {0, 0, 0, 0};
+      for (int k = 0; k < n; ++k) {
+        T a = ar[vidx(o.A, i, k)];
+        for (int j = 0; j < cc; ++j) acc[j] += a * Pv[k + j * n];
+      }
+      for (int j = 0; j < cc; ++j) ar[vidx(o.C, i, j)] = acc[j];
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < n * cp; t += blockDim.x) {
-      int i = t % n, j = t / n;
-      T acc = 0;
-      for (int k = 0; k < n; ++k) acc += ar[vidx(o.A, i, k)] * S[j * n + k];
-      ar[vidx(o.C, i, c0 + j)] = acc;
-    }
-    __syncthreads();
+    return;
   }
+  T* As = c.sm;            // n x n, [i + k n]
+  T* Pn = c.sm + n * n;    // n x 32, [k * 33 + j]
+  const int tid = threadIdx.x;
+  for (int t = tid; t < n * n; t += blockDim.x) As[t] = ar[vidx(o.A, t % n, t / n)];
+  const int tx = tid & 7, ty = tid >> 3;
+  for (int c0 = 0; c0 < cc; c0 += 32) {
+    const int cp = min(32, cc - c0);
+    __syncthreads();
+    for (int t = tid; t < n * cp; t += blockDim.x) {
+      int i = t % n, j = t / n;
+      Pn[i * 33 + j] = ar[vidx(o.C, i, c0 + j)];
+    }
+    __syncthreads();
+    for (int rb = ty * 4; rb < n; rb += 128) {
+      T acc[4][4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = 0;
+      for (int k = 0; k < n; ++k) {
+        T a[4], b[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) a[p] = (rb + p < n) ? As[rb + p + k * n] : (T)0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) b[q] = Pn[k * 33 + tx + 8 * q];
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[p][q] += a[p] * b[q];
+      }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (rb + p < n && tx + 8 * q < cp) ar[vidx(o.C, rb + p, c0 + tx + 8 * q)] = acc[p][q];
+    }
+  }
+  __syncthreads();
 }
 
-// C <- C A (A n x n), row panels staged in shared memory
+// C <- C A (A n x n, n <= 128): A (row-major) and a 32-row panel of C
+// (column-major) in shared memory; thread (ty, tx) computes rows
+// 4ty..4ty+3 and columns tx, tx+32, tx+64, tx+96.
 template <class T>
 __device__ void op_trmm_r(const HOp& o, HCtx<T>& c) {
   const int m = dimv(o.C.r, c.rk), n = dimv(o.C.c, c.rk);
   if (m <= 0 || n <= 0) return;
   T* ar = c.ar;
-  const int RP = 32;
-  T* S = c.sm;
-  for (int r0 = 0; r0 < m; r0 += RP) {
-    int rp = min(RP, m - r0);
-    for (int t = threadIdx.x; t < rp * n; t += blockDim.x) {
-      int i = t % rp, k = t / rp;
-      S[k * RP + i] = ar[vidx(o.C, r0 + i, k)];
-    }
+  T* As = c.sm;            // n x n, [k n + j]
+  T* Pn = c.sm + n * n;    // 32 x n, [i + k * 32]
+  const int tid = threadIdx.x;
+  for (int t = tid; t < n * n; t += blockDim.x) As[(t % n) * n + t / n] = ar[vidx(o.A, t % n, t / n)];
+  const int tx = tid & 31, ty = tid >> 5;
+  for (int r0 = 0; r0 < m; r0 += 32) {
+    const int rp = min(32, m - r0);
     __syncthreads();
-    for (int t = threadIdx.x; t < rp * n; t += blockDim.x) {
-      int i = t % rp, j = t / rp;
-      T acc = 0;
-      for (int k = 0; k < n; ++k) acc += S[k * RP + i] * ar[vidx(o.A, k, j)];
-      ar[vidx(o.C, r0 + i, j)] = acc;
-    }
+    for (int t = tid; t < rp * n; t += blockDim.x) Pn[(t % rp) + (t / rp) * 32] = ar[vidx(o.C, r0 + t % rp, t / rp)];
     __syncthreads();
+    T acc[4][4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[p][q] = 0;
+    for (int k = 0; k < n; ++k) {
+      T a[4], b[4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) a[p] = Pn[ty * 4 + p + k * 32];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) b[q] = (tx + 32 * q < n) ? As[k * n + tx + 32 * q] : (T)0;
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] += a[p] * b[q];
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (ty * 4 + p < rp && tx + 32 * q < n) ar[vidx(o.C, r0 + ty * 4 + p, tx + 32 * q)] = acc[p][q];
   }
+  __syncthreads();
 }
 
-// unpivoted LU of C (n x n) and the inverses of both factors
+// Unpivoted LU of C (n x n, n <= 128) in shared memory and the inverses of
+// both factors; 16 x 16 thread grid, no index divisions in the loops.
 template <class T>
 __device__ void op_getrf_inv(const HOp& o, HCtx<T>& c) {
   const int n = o.C.r;
   if (n <= 0) return;
   T* ar = c.ar;
-  T* S = c.sm;          // LU, column-major n x n
-  T* X = c.sm + n * n;  // inverse being built
-  const int tid = threadIdx.x, nt = blockDim.x;
-  for (int t = tid; t < n * n; t += nt) S[t] = ar[vidx(o.C, t % n, t / n)];
+  T* S = c.sm;             // n x n, [i + j n]
+  T* X = c.sm + n * n;     // n x n
+  const int tid = threadIdx.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  for (int t = tid; t < n * n; t += blockDim.x) S[t] = ar[vidx(o.C, t % n, t / n)];
   __syncthreads();
   for (int k = 0; k < n; ++k) {
-    T piv = S[k + k * n];
+    const T piv = S[k + k * n];
     if (tid == 0 && (piv == (T)0 || !isfinite((double)piv))) atomicExch(c.err, 1);
-    for (int i = k + 1 + tid; i < n; i += nt) S[i + k * n] /= piv;
+    const T inv = (T)1 / piv;
+    for (int i = k + 1 + tid; i < n; i += blockDim.x) S[i + k * n] *= inv;
     __syncthreads();
-    int w = n - k - 1;
-    for (int t = tid; t < w * w; t += nt) {
-      int i = k + 1 + t % w, j = k + 1 + t / w;
-      S[i + j * n] -= S[i + k * n] * S[k + j * n];
+    for (int j = k + 1 + ty; j < n; j += 16) {
+      const T ukj = S[k + j * n];
+      for (int i = k + 1 + tx; i < n; i += 16) S[i + j * n] -= S[i + k * n] * ukj;
     }
     __syncthreads();
   }
-  // L^-1 (unit lower): X = I, eliminate below the diagonal column by column
-  for (int t = tid; t < n * n; t += nt) X[t] = (t % n == t / n) ? (T)1 : (T)0;
+  // L^-1: X = I; for k: X[i][j] -= L[i][k] X[k][j] for i > k, j <= k
+  for (int t = tid; t < n * n; t += blockDim.x) X[t] = (t % n == t / n) ? (T)1 : (T)0;
   __syncthreads();
   for (int k = 0; k + 1 < n; ++k) {
-    int w = n - k - 1;
-    for (int t = tid; t < w * (k + 1); t += nt) {
-      int i = k + 1 + t % w, j = t / w;
-      X[i + j * n] -= S[i + k * n] * X[k + j * n];
+    for (int j = ty; j <= k; j += 16) {
+      const T xkj = X[k + j * n];
+      for (int i = k + 1 + tx; i < n; i += 16) X[i + j * n] -= S[i + k * n] * xkj;
     }
     __syncthreads();
   }
-  for (int t = tid; t < n * n; t += nt) ar[vidx(o.A, t % n, t / n)] = X[t];
+  for (int t = tid; t < n * n; t += blockDim.x) ar[vidx(o.A, t % n, t / n)] = X[t];
   __syncthreads();
-  // U^-1: X = I, rows from the bottom: X[k,:] /= U_kk; X[i,:] -= U_ik X[k,:]
-  for (int t = tid; t < n * n; t += nt) X[t] = (t % n == t / n) ? (T)1 : (T)0;
+  // U^-1: X = I; k = n-1..0: X[k][j] /= U_kk (j >= k); X[i][j] -= U_ik X[k][j] (i < k, j >= k)
+  for (int t = tid; t < n * n; t += blockDim.x) X[t] = (t % n == t / n) ? (T)1 : (T)0;
   __syncthreads();
   for (int k = n - 1; k >= 0; --k) {
-    T ukk = S[k + k * n];
-    for (int j = k + tid; j < n; j += nt) X[k + j * n] /= ukk;
+    const T ukk = S[k + k * n];
+    for (int j = k + tid; j < n; j += blockDim.x) X[k + j * n] /= ukk;
     __syncthreads();
-    int w = n - k;
-    for (int t = tid; t < k * w; t += nt) {
-      int i = t % k, j = k + t / k;
-      X[i + j * n] -= S[i + k * n] * X[k + j * n];
+    for (int j = k + ty; j < n; j += 16) {
+      const T xkj = X[k + j * n];
+      for (int i = tx; i < k; i += 16) X[i + j * n] -= S[i + k * n] * xkj;
     }
     __syncthreads();
   }
-  for (int t = tid; t < n * n; t += nt) ar[vidx(o.B, t % n, t / n)] = X[t];
+  for (int t = tid; t < n * n; t += blockDim.x) ar[vidx(o.B, t % n, t / n)] = X[t];
 }
 
 // Householder QR of A (m x K, ld m) in place: R in the upper trapezoid,
@@ -819,6 +882,7 @@ __device__ void op_trunc(const HOp& o, HCtx<T>& c) {
 
 struct HProgArgs {
   const HInstDev* inst;
+  const int* waves;
   const HOp* ops;
   const SlotDev* slots;
   int* ranks;
@@ -856,58 +920,85 @@ __device__ double op_flops(const HOp& o, const int* rk, const SlotDev* sl) {
   }
 }
 
+__device__ __forceinline__ unsigned cluster_rank() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ unsigned cluster_id() {
+  unsigned r;
+  asm volatile("mov.u32 %0, %%clusterid.x;" : "=r"(r));
+  return r;
+}
+// hardware barrier of all threads of the cluster; release/acquire at cluster
+// scope makes every global write before it visible to every CTA after it
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\t"
+               "barrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// One thread-block cluster of kCluster CTAs per instance runs the instance's
+// op program wave by wave: the ops of a wave are independent and spread
+// round-robin over the CTAs, a cluster barrier separates consecutive waves.
 template <class T>
 __global__ void __launch_bounds__(kHThreads) k_hprog(HProgArgs a, T* har, int which) {
   extern __shared__ __align__(16) unsigned char smraw[];
-  const HInstDev H = a.inst[blockIdx.x];
+  const unsigned crank = cluster_rank();
+  const unsigned cid = cluster_id();
+  const HInstDev H = a.inst[cid];
   HCtx<T> c;
   c.ar = har + H.arena;
   c.rk = a.ranks + H.rk0;
   c.sl = a.slots + H.slot0;
-  c.ws = c.ar + H.ws_off;
+  c.ws = c.ar + H.ws_off + (long long)crank * H.ws_size;
   c.sm = reinterpret_cast<T*>(smraw);
   c.tol = a.tol;
-  c.err = a.err + blockIdx.x;
+  c.err = a.err + cid;
   const HOp* ops = a.ops + (which ? H.sops0 : H.ops0);
-  const int nops = which ? H.nsops : H.nops;
+  const int* waves = a.waves + (which ? H.sw0 : H.fw0);
+  const int nw = which ? H.nsw : H.nfw;
   double fl = 0.0;
-  for (int i = 0; i < nops; ++i) {
-    const HOp o = ops[i];
-    if (threadIdx.x == 0) fl += op_flops(o, c.rk, c.sl);
-    unsigned long long t0 = 0;
-    if (a.prof && threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
-    switch (o.type) {
-      case OP_GEMM: op_gemm(o, c); break;
-      case OP_GETRF_INV: op_getrf_inv(o, c); break;
-      case OP_TRMM_L: op_trmm_l(o, c); break;
-      case OP_TRMM_R: op_trmm_r(o, c); break;
-      case OP_APPEND: op_append(o, c); break;
-      case OP_TRUNC: op_trunc(o, c); break;
-      case OP_ZERO: {
-        int m = dimv(o.C.r, c.rk), n = dimv(o.C.c, c.rk);
-        for (int t = threadIdx.x; t < m * n; t += blockDim.x) c.ar[vidx(o.C, t % m, t / m)] = 0;
-        break;
-      }
-      case OP_AXPY: {
-        int m = dimv(o.C.r, c.rk), n = dimv(o.C.c, c.rk);
-        for (int t = threadIdx.x; t < m * n; t += blockDim.x) {
-          int i = t % m, j = t / m;
-          c.ar[vidx(o.C, i, j)] += (T)o.alpha * c.ar[vidx(o.A, i, j)];
+  for (int w = 0; w < nw; ++w) {
+    const int i1 = waves[w + 1];
+    for (int i = waves[w] + (int)crank; i < i1; i += kCluster) {
+      const HOp o = ops[i];
+      if (threadIdx.x == 0) fl += op_flops(o, c.rk, c.sl);
+      unsigned long long t0 = 0;
+      if (a.prof && crank == 0 && threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+      switch (o.type) {
+        case OP_GEMM: op_gemm(o, c); break;
+        case OP_GETRF_INV: op_getrf_inv(o, c); break;
+        case OP_TRMM_L: op_trmm_l(o, c); break;
+        case OP_TRMM_R: op_trmm_r(o, c); break;
+        case OP_APPEND: op_append(o, c); break;
+        case OP_TRUNC: op_trunc(o, c); break;
+        case OP_ZERO: {
+          int m = dimv(o.C.r, c.rk), n = dimv(o.C.c, c.rk);
+          for (int t = threadIdx.x; t < m * n; t += blockDim.x) c.ar[vidx(o.C, t % m, t / m)] = 0;
+          break;
         }
-        break;
+        case OP_AXPY: {
+          int m = dimv(o.C.r, c.rk), n = dimv(o.C.c, c.rk);
+          for (int t = threadIdx.x; t < m * n; t += blockDim.x) {
+            int ii = t % m, j = t / m;
+            c.ar[vidx(o.C, ii, j)] += (T)o.alpha * c.ar[vidx(o.A, ii, j)];
+          }
+          break;
+        }
+        default: break;
       }
-      default: break;
+      __syncthreads();
+      if (a.prof && crank == 0 && threadIdx.x == 0) {
+        unsigned long long t1;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+        unsigned long long* pr = a.prof + (size_t)cid * 32 + 2 * (o.type & 15);
+        pr[0] += t1 - t0;
+        pr[1] += 1ULL;
+      }
     }
-    __syncthreads();
-    if (a.prof && threadIdx.x == 0) {
-      unsigned long long* pr = a.prof + (size_t)blockIdx.x * 32 + 2 * (o.type & 15);
-      unsigned long long t1;
-      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
-      pr[0] += t1 - t0;
-      pr[1] += 1ULL;
-    }
+    cluster_barrier();
   }
-  if (threadIdx.x == 0) a.flops[blockIdx.x * 2 + which] += fl;
+  if (threadIdx.x == 0) a.flops[((size_t)cid * kCluster + crank) * 2 + which] += fl;
 }
 
 // rhs area <- D r (element-major FP64 -> T); rank slot n_slots <- nrhs
@@ -1010,6 +1101,7 @@ struct hfsem_factor_s : public hf::Precond {
   std::vector<std::shared_ptr<hf::PlanBundle>> plans;   // per instance (shared)
   std::vector<hf::HInstDev> hidev;
   hf::DevBuf<hf::HInstDev> d_hi;
+  hf::DevBuf<int> d_waves;
   hf::DevBuf<hf::HOp> d_ops;
   hf::DevBuf<hf::SlotDev> d_slots;
   hf::DevBuf<hf::DenseDev> d_dense;
@@ -1039,7 +1131,7 @@ static size_t prog_smem(const HPlan& p, size_t ts) {
   size_t leaf = (size_t)2 * p.leaf_max * p.leaf_max;
   size_t K = (size_t)std::max(p.kconcat_max, 1);
   size_t trunc = 2 * K + 32 + 2 * K * K + 3 * K + 8;
-  size_t trmm = (size_t)std::max(p.leaf_max, 1) * 32;
+  size_t trmm = (size_t)p.leaf_max * p.leaf_max + (size_t)std::max(p.leaf_max, 1) * 33;
   size_t gemm = 2 * 16 * 64;
   return std::max(std::max(leaf, trunc), std::max(trmm, gemm)) * ts + 64;
 }
@@ -1085,6 +1177,8 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
       o.nrhs_max = 64;
       o.max_concat = fp32 ? 128 : 96;
       o.max_leaf = max_leaf;
+      o.unique_tmp = 1;
+      o.ncta = kCluster;
       std::string key = plan_key(I, o);
       auto it = cache.find(key);
       if (it == cache.end()) {
@@ -1117,19 +1211,23 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
     }
     // concatenate tables
     std::vector<HOp> ops;
+    std::vector<int> waves;
     std::vector<SlotDev> slots;
     std::vector<DenseDev> dense;
     std::vector<LRPairDev> pairs;
-    std::map<const PlanBundle*, std::array<long long, 5>> placed;
+    std::map<const PlanBundle*, std::array<long long, 7>> placed;
     long long arena = 0, rk = 0, doff = 0;
     size_t smem = 0;
     for (int i = 0; i < ni; ++i) {
       const PlanBundle* pb = f->plans[i].get();
       auto pi = placed.find(pb);
       if (pi == placed.end()) {
-        std::array<long long, 5> a{(long long)ops.size(), (long long)(ops.size() + pb->plan.fac.size()),
+        std::array<long long, 7> a{(long long)ops.size(), (long long)(ops.size() + pb->plan.fac.size()),
                                    (long long)slots.size(), (long long)dense.size(),
-                                   (long long)pairs.size()};
+                                   (long long)pairs.size(), (long long)waves.size(),
+                                   (long long)(waves.size() + pb->plan.fac_waves.size())};
+        waves.insert(waves.end(), pb->plan.fac_waves.begin(), pb->plan.fac_waves.end());
+        waves.insert(waves.end(), pb->plan.sol_waves.begin(), pb->plan.sol_waves.end());
         ops.insert(ops.end(), pb->plan.fac.begin(), pb->plan.fac.end());
         ops.insert(ops.end(), pb->plan.sol.begin(), pb->plan.sol.end());
         slots.insert(slots.end(), pb->slots.begin(), pb->slots.end());
@@ -1157,7 +1255,12 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
       H.npairs = (int)pb->pairs.size();
       H.n_slots = p.n_slots;
       H.ws_off = p.ws_off;
+      H.ws_size = p.ws_size;
       H.rhs_off = p.rhs_off;
+      H.fw0 = pi->second[5];
+      H.sw0 = pi->second[6];
+      H.nfw = (int)p.fac_waves.size() - 1;
+      H.nsw = (int)p.sol_waves.size() - 1;
       H.d_off = doff;
       doff += s->ih[i].Nd;
       H.sys_inst = i;
@@ -1169,6 +1272,9 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
     f->smem = smem;
     f->d_hi.alloc(ni);
     HF_CHECK(cudaMemcpyAsync(f->d_hi.p, f->hidev.data(), ni * sizeof(HInstDev), cudaMemcpyHostToDevice, s->st));
+    f->d_waves.alloc(std::max<size_t>(waves.size(), 1));
+    if (!waves.empty())
+      HF_CHECK(cudaMemcpyAsync(f->d_waves.p, waves.data(), waves.size() * sizeof(int), cudaMemcpyHostToDevice, s->st));
     f->d_ops.alloc(std::max<size_t>(ops.size(), 1));
     if (!ops.empty())
       HF_CHECK(cudaMemcpyAsync(f->d_ops.p, ops.data(), ops.size() * sizeof(HOp), cudaMemcpyHostToDevice, s->st));
@@ -1292,17 +1398,27 @@ void hfsem_factor_s::run_prog(int which) {
     cudaMemset(d_prof.p, 0, d_prof.n * sizeof(unsigned long long));
   }
   if (!d_flops.p) {
-    d_flops.alloc((size_t)sys->n_inst * 2);
+    d_flops.alloc((size_t)sys->n_inst * hf::kCluster * 2);
     cudaMemsetAsync(d_flops.p, 0, d_flops.n * sizeof(double), sys->st);
   }
-  hf::HProgArgs a{d_hi.p, d_ops.p, d_slots.p, d_ranks.p, d_err.p, tol, d_prof.p, d_flops.p};
+  hf::HProgArgs a{d_hi.p, d_waves.p, d_ops.p, d_slots.p, d_ranks.p, d_err.p, tol, d_prof.p, d_flops.p};
   hf::Tick tk(sys->st, which ? "hlu_solve" : "hlu_factor");
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(sys->n_inst * hf::kCluster));
+  cfg.blockDim = dim3(hf::kHThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = sys->st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = hf::kCluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
   if (tsize == sizeof(float))
-    hf::k_hprog<float><<<sys->n_inst, hf::kHThreads, smem, sys->st>>>(
-        a, reinterpret_cast<float*>(d_arena.p), which);
+    HF_CHECK(cudaLaunchKernelEx(&cfg, hf::k_hprog<float>, a, reinterpret_cast<float*>(d_arena.p), which));
   else
-    hf::k_hprog<double><<<sys->n_inst, hf::kHThreads, smem, sys->st>>>(
-        a, reinterpret_cast<double*>(d_arena.p), which);
+    HF_CHECK(cudaLaunchKernelEx(&cfg, hf::k_hprog<double>, a, reinterpret_cast<double*>(d_arena.p), which));
   HF_LAUNCH_CHECK();
 }
 

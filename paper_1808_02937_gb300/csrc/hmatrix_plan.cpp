@@ -179,6 +179,7 @@ struct Builder {
   }
   View tmp(int r, int c_bound, int c_dim) {
     View v{tmp_top, r, c_dim, std::max(r, 1), 0};
+    p.tmps.push_back({tmp_top, (long long)std::max(r, 1) * std::max(c_bound, 1), std::max(r, 1)});
     tmp_top += (long long)std::max(r, 1) * std::max(c_bound, 1);
     tmp_peak = std::max(tmp_peak, tmp_top - tmp_base);
     return v;
@@ -527,7 +528,10 @@ void make_plan(const InstHost& I, const PlanOpts& o, HPlan& p) {
   p.tmp_size = b.tmp_peak;
   p.ws_off = ws_off;
   p.ws_size = (long long)2 * std::max(b.max_m, 1) * std::max(p.kconcat_max, 1);
-  p.arena = ws_off + p.ws_size;
+  p.ncta = std::max(o.ncta, 1);
+  p.arena = ws_off + p.ws_size * p.ncta;
+  schedule_program(p, p.fac, p.fac_waves);
+  schedule_program(p, p.sol, p.sol_waves);
 }
 
 }  // namespace hf
@@ -571,6 +575,7 @@ int program_levels(const HPlan& p, const std::vector<HOp>& prog, std::vector<int
       al.push_back({b.off + (long long)b.m * b.kcap, (long long)b.n * b.kcap, b.n, b.slot});
     }
   }
+  for (const auto& t : p.tmps) al.push_back({t.off, t.size, t.ld, -1});
   std::sort(al.begin(), al.end(), [](const Alloc& a, const Alloc& b) { return a.off < b.off; });
   auto find = [&](long long off) -> const Alloc* {
     size_t lo = 0, hi = al.size();
@@ -670,12 +675,9 @@ int program_levels(const HPlan& p, const std::vector<HOp>& prog, std::vector<int
       auto& h = hist[a.rc.base];
       for (auto& r : h)
         if ((a.write || r.write) && overlap(a.rc, r.rc)) lv = std::max(lv, r.lvl);
-      if (a.rc.slot >= 0) {
+      if (a.rc.slot >= 0) {   // the view's shape reads the rank of this slot
         auto it = slot_state.find(a.rc.slot);
-        if (it != slot_state.end()) {
-          lv = std::max(lv, it->second.first);
-          if (a.write) lv = std::max(lv, it->second.second);
-        }
+        if (it != slot_state.end()) lv = std::max(lv, it->second.first);
       }
     }
     if (slot_w >= 0) {
@@ -688,12 +690,10 @@ int program_levels(const HPlan& p, const std::vector<HOp>& prog, std::vector<int
     for (auto& a : acc) {
       auto& h = hist[a.rc.base];
       // drop records fully covered by this write at a lower level
-      h.push_back({a.rc, a.write, lv});
-      if (h.size() > 256) h.erase(h.begin(), h.begin() + 128);
-      if (a.rc.slot >= 0) {
+      h.push_back({a.rc, a.write, lv});   // full history: a dropped record could hide a dependency
+      if (a.rc.slot >= 0) {   // only APPEND / TRUNC change a rank (slot_w below)
         auto& st = slot_state[a.rc.slot];
-        if (a.write) st.first = std::max(st.first, lv);
-        else st.second = std::max(st.second, lv);
+        st.second = std::max(st.second, lv);
       }
     }
     if (slot_w >= 0) {
@@ -702,6 +702,51 @@ int program_levels(const HPlan& p, const std::vector<HOp>& prog, std::vector<int
     }
   }
   return nlev;
+}
+
+}  // namespace hf
+
+namespace hf {
+
+void schedule_program(const HPlan& p, std::vector<HOp>& prog, std::vector<int>& waves) {
+  // 1. split big ops into independent pieces
+  std::vector<HOp> out;
+  out.reserve(prog.size() * 2);
+  for (const HOp& o : prog) {
+    if (o.type == OP_GEMM && o.C.r > 128) {
+      for (int r0 = 0; r0 < o.C.r; r0 += 128) {
+        int r1 = std::min(o.C.r, r0 + 128);
+        HOp q = o;
+        q.C = vrows(o.C, r0, r1);
+        q.A = vrows(o.A, r0, r1);
+        out.push_back(q);
+      }
+    } else if (o.type == OP_TRMM_L && o.C.c > 32) {
+      for (int c0 = 0; c0 < o.C.c; c0 += 32) {
+        HOp q = o;
+        q.C = vcols(o.C, c0, std::min(o.C.c, c0 + 32));
+        out.push_back(q);
+      }
+    } else if (o.type == OP_TRMM_R && o.C.r > 32) {
+      for (int r0 = 0; r0 < o.C.r; r0 += 32) {
+        HOp q = o;
+        q.C = vrows(o.C, r0, std::min(o.C.r, r0 + 32));
+        out.push_back(q);
+      }
+    } else {
+      out.push_back(o);
+    }
+  }
+  // 2. dependency levels, 3. stable order by level
+  std::vector<int> lv;
+  int nl = program_levels(p, out, lv);
+  std::vector<int> cnt(nl + 2, 0);
+  for (int l : lv) cnt[l]++;
+  waves.assign(nl + 1, 0);
+  for (int l = 1; l <= nl; ++l) waves[l] = waves[l - 1] + cnt[l];
+  std::vector<int> pos(waves.begin(), waves.end());
+  prog.assign(out.size(), HOp());
+  for (size_t i = 0; i < out.size(); ++i) prog[pos[lv[i] - 1]++] = out[i];
 }
 
 }  // namespace hf

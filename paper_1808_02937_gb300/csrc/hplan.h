@@ -77,6 +77,13 @@ struct HPlan {
   int n_slots = 0;
   int hh_lr = 0;                       // H x H products into LR blocks seen
   long long tmp_base = 0, tmp_size = 0;  // temporaries region
+  struct TmpAlloc {
+    long long off, size;
+    int ld;
+  };
+  std::vector<TmpAlloc> tmps;          // every temporary handed out
+  std::vector<int> fac_waves, sol_waves;   // op offsets of the dependency waves
+  int ncta = 1;                        // CTAs that execute one instance
 };
 
 struct PlanOpts {
@@ -88,6 +95,7 @@ struct PlanOpts {
   int max_concat;    // limit on K in a truncation (shared memory)
   int max_leaf;      // limit on diagonal leaf size
   int unique_tmp = 0;  // 1: never reuse temporary storage (independent ops stay independent)
+  int ncta = 1;        // CTAs per instance (one truncation workspace each)
 };
 
 // Build clusters, blocks, storage and the two programs.
@@ -101,4 +109,8 @@ namespace hf {
 // conflicts with (read/write or write/write on overlapping storage, or on the
 // same low-rank slot / rank).  Returns the number of levels.
 int program_levels(const HPlan& p, const std::vector<HOp>& prog, std::vector<int>& level);
+
+// Split large ops into independent tile ops, then order the program by
+// dependency level; waves[w] .. waves[w+1] are the ops of wave w.
+void schedule_program(const HPlan& p, std::vector<HOp>& prog, std::vector<int>& waves);
 }  // namespace hf
