@@ -386,16 +386,48 @@ __device__ void op_gemm(const HOp& o, HCtx<T>& c) {
     return;
   }
   if (n <= 8) {
-    for (int i = tid; i < m; i += nt) {
+    // tall and narrow: rows in parallel; idle threads split k (partials
+    // combined in shared memory); four independent loads in flight
+    const int rows_per = (m >= nt) ? nt : m;
+    const int S = (m >= nt) ? 1 : min(nt / m, 16);
+    T* red = c.sm;   // S x rows_per x 8
+    for (int i0 = 0; i0 < m; i0 += rows_per) {
+      const int r = tid % rows_per, part = tid / rows_per, i = i0 + r;
+      const int kc = (k + S - 1) / S, k0 = part * kc, k1 = min(k, k0 + kc);
       T acc[8];
+#pragma unroll
       for (int j = 0; j < 8; ++j) acc[j] = 0;
-      for (int kk = 0; kk < k; ++kk) {
-        T a = ar[vidx(o.A, i, kk)];
-        for (int j = 0; j < n; ++j) acc[j] += a * ar[vidx(o.B, kk, j)];
+      if (part < S && i < m) {
+        int kk = k0;
+        for (; kk + 4 <= k1; kk += 4) {
+          T a0 = ar[vidx(o.A, i, kk)], a1 = ar[vidx(o.A, i, kk + 1)];
+          T a2 = ar[vidx(o.A, i, kk + 2)], a3 = ar[vidx(o.A, i, kk + 3)];
+          for (int j = 0; j < n; ++j)
+            acc[j] += a0 * ar[vidx(o.B, kk, j)] + a1 * ar[vidx(o.B, kk + 1, j)] +
+                      a2 * ar[vidx(o.B, kk + 2, j)] + a3 * ar[vidx(o.B, kk + 3, j)];
+        }
+        for (; kk < k1; ++kk) {
+          T a = ar[vidx(o.A, i, kk)];
+          for (int j = 0; j < n; ++j) acc[j] += a * ar[vidx(o.B, kk, j)];
+        }
       }
-      for (int j = 0; j < n; ++j) {
-        long long ci = vidx(o.C, i, j);
-        ar[ci] = (beta == (T)0 ? (T)0 : beta * ar[ci]) + alpha * acc[j];
+      if (S > 1) {
+        if (part < S)
+          for (int j = 0; j < n; ++j) red[(part * rows_per + r) * 8 + j] = acc[j];
+        __syncthreads();
+        if (part == 0 && i < m)
+          for (int j = 0; j < n; ++j) {
+            T v = 0;
+            for (int q = 0; q < S; ++q) v += red[(q * rows_per + r) * 8 + j];
+            long long ci = vidx(o.C, i, j);
+            ar[ci] = (beta == (T)0 ? (T)0 : beta * ar[ci]) + alpha * v;
+          }
+        __syncthreads();
+      } else if (i < m) {
+        for (int j = 0; j < n; ++j) {
+          long long ci = vidx(o.C, i, j);
+          ar[ci] = (beta == (T)0 ? (T)0 : beta * ar[ci]) + alpha * acc[j];
+        }
       }
     }
     return;
@@ -465,20 +497,37 @@ __device__ void op_trmm_l(const HOp& o, HCtx<T>& c) {
   const int n = dimv(o.C.r, c.rk), cc = dimv(o.C.c, c.rk);
   if (n <= 0 || cc <= 0) return;
   T* ar = c.ar;
-  if (cc <= 4) {
-    // a few right-hand sides (the H-solves): rows in parallel, A read from
-    // L2 column by column (consecutive threads, consecutive rows)
-    T* Pv = c.sm;   // n x cc
+  if (cc <= 4 && !o.A.tr) {
+    // a few right-hand sides (the H-solves): 2 threads per row split k, four
+    // independent loads in flight per thread, A read from L2 (consecutive
+    // threads, consecutive rows), partial sums combined in shared memory
+    T* Pv = c.sm;            // n x cc
+    T* red = c.sm + n * cc;  // 128 x cc partials of the second half
     for (int t = threadIdx.x; t < n * cc; t += blockDim.x) Pv[t] = ar[vidx(o.C, t % n, t / n)];
     __syncthreads();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-      T acc[4] = {0, 0, 0, 0};
-      for (int k = 0; k < n; ++k) {
-        T a = ar[vidx(o.A, i, k)];
+    const int r = threadIdx.x & 127, part = threadIdx.x >> 7;
+    const int kh = (n + 1) / 2, k0 = part * kh, k1 = min(n, k0 + kh);
+    const T* Ac = ar + o.A.off + r;
+    const long long ld = o.A.ld;
+    T acc[4] = {0, 0, 0, 0};
+    if (r < n) {
+      int k = k0;
+      for (; k + 4 <= k1; k += 4) {
+        T a0 = Ac[k * ld], a1 = Ac[(k + 1) * ld], a2 = Ac[(k + 2) * ld], a3 = Ac[(k + 3) * ld];
+        for (int j = 0; j < cc; ++j)
+          acc[j] += a0 * Pv[k + j * n] + a1 * Pv[k + 1 + j * n] + a2 * Pv[k + 2 + j * n] +
+                    a3 * Pv[k + 3 + j * n];
+      }
+      for (; k < k1; ++k) {
+        T a = Ac[k * ld];
         for (int j = 0; j < cc; ++j) acc[j] += a * Pv[k + j * n];
       }
-      for (int j = 0; j < cc; ++j) ar[vidx(o.C, i, j)] = acc[j];
     }
+    if (part == 1 && r < n)
+      for (int j = 0; j < cc; ++j) red[r + j * 128] = acc[j];
+    __syncthreads();
+    if (part == 0 && r < n)
+      for (int j = 0; j < cc; ++j) ar[vidx(o.C, r, j)] = acc[j] + red[r + j * 128];
     __syncthreads();
     return;
   }
@@ -565,8 +614,12 @@ __device__ void op_trmm_r(const HOp& o, HCtx<T>& c) {
   __syncthreads();
 }
 
-// Unpivoted LU of C (n x n, n <= 128) in shared memory and the inverses of
-// both factors; 16 x 16 thread grid, no index divisions in the loops.
+// Unpivoted LU of C (n x n, n <= 128) in shared memory, returning L^-1 and
+// U^-1 (L itself is never needed).  Step k of the elimination updates the
+// trailing block and, in the same pass, X <- E_k X with E_k the k-th
+// elimination matrix, so X ends as L^-1; every value a step reads is left
+// untouched by that step, hence one barrier per step.  U^-1 = (D^-1 U)^-1 D^-1
+// with D = diag(U), again one barrier per step.
 template <class T>
 __device__ void op_getrf_inv(const HOp& o, HCtx<T>& c) {
   const int n = o.C.r;
@@ -576,46 +629,40 @@ __device__ void op_getrf_inv(const HOp& o, HCtx<T>& c) {
   T* X = c.sm + n * n;     // n x n
   const int tid = threadIdx.x;
   const int tx = tid & 15, ty = tid >> 4;
-  for (int t = tid; t < n * n; t += blockDim.x) S[t] = ar[vidx(o.C, t % n, t / n)];
+  for (int t = tid; t < n * n; t += blockDim.x) {
+    S[t] = ar[vidx(o.C, t % n, t / n)];
+    X[t] = (t % n == t / n) ? (T)1 : (T)0;
+  }
   __syncthreads();
   for (int k = 0; k < n; ++k) {
     const T piv = S[k + k * n];
     if (tid == 0 && (piv == (T)0 || !isfinite((double)piv))) atomicExch(c.err, 1);
     const T inv = (T)1 / piv;
-    for (int i = k + 1 + tid; i < n; i += blockDim.x) S[i + k * n] *= inv;
-    __syncthreads();
-    for (int j = k + 1 + ty; j < n; j += 16) {
-      const T ukj = S[k + j * n];
-      for (int i = k + 1 + tx; i < n; i += 16) S[i + j * n] -= S[i + k * n] * ukj;
-    }
-    __syncthreads();
-  }
-  // L^-1: X = I; for k: X[i][j] -= L[i][k] X[k][j] for i > k, j <= k
-  for (int t = tid; t < n * n; t += blockDim.x) X[t] = (t % n == t / n) ? (T)1 : (T)0;
-  __syncthreads();
-  for (int k = 0; k + 1 < n; ++k) {
-    for (int j = ty; j <= k; j += 16) {
-      const T xkj = X[k + j * n];
-      for (int i = k + 1 + tx; i < n; i += 16) X[i + j * n] -= S[i + k * n] * xkj;
+    // row i > k: columns j > k of S, columns j <= k of X (n columns in all)
+    for (int j = ty; j < n; j += 16) {
+      const bool lu = j > k;
+      const T rk = lu ? S[k + j * n] : X[k + j * n];
+      T* dst = lu ? S : X;
+      for (int i = k + 1 + tx; i < n; i += 16) dst[i + j * n] -= (S[i + k * n] * inv) * rk;
     }
     __syncthreads();
   }
   for (int t = tid; t < n * n; t += blockDim.x) ar[vidx(o.A, t % n, t / n)] = X[t];
   __syncthreads();
-  // U^-1: X = I; k = n-1..0: X[k][j] /= U_kk (j >= k); X[i][j] -= U_ik X[k][j] (i < k, j >= k)
+  // (D^-1 U)^-1 by backward elimination of the unit upper factor
   for (int t = tid; t < n * n; t += blockDim.x) X[t] = (t % n == t / n) ? (T)1 : (T)0;
   __syncthreads();
-  for (int k = n - 1; k >= 0; --k) {
-    const T ukk = S[k + k * n];
-    for (int j = k + tid; j < n; j += blockDim.x) X[k + j * n] /= ukk;
-    __syncthreads();
+  for (int k = n - 1; k > 0; --k) {
     for (int j = k + ty; j < n; j += 16) {
       const T xkj = X[k + j * n];
-      for (int i = tx; i < k; i += 16) X[i + j * n] -= S[i + k * n] * xkj;
+      for (int i = tx; i < k; i += 16) X[i + j * n] -= (S[i + k * n] / S[i + i * n]) * xkj;
     }
     __syncthreads();
   }
-  for (int t = tid; t < n * n; t += blockDim.x) ar[vidx(o.B, t % n, t / n)] = X[t];
+  for (int t = tid; t < n * n; t += blockDim.x) {
+    int i = t % n, j = t / n;
+    ar[vidx(o.B, i, j)] = X[t] / S[j + j * n];
+  }
 }
 
 // Householder QR of A (m x K, ld m) in place: R in the upper trapezoid,
@@ -1433,6 +1480,10 @@ void hfsem_factor_s::apply(int nrhs, const double* r_em, double* y_em) {
     hf::k_hsolve_in<float><<<g, 256, 0, sys->st>>>(d_hi.p, sys->d_inst.p, r_em, d_D.p, ar, d_ranks.p, nrhs);
     HF_LAUNCH_CHECK();
     run_prog(1);
+    if (d_prof.p) {
+      cudaStreamSynchronize(sys->st);
+      report("H-solve apply");
+    }
     hf::k_hsolve_out<float><<<g, 256, 0, sys->st>>>(d_hi.p, sys->d_inst.p, d_D.p, ar, y_em, nrhs);
   } else {
     double* ar = reinterpret_cast<double*>(d_arena.p);
