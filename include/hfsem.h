@@ -57,7 +57,9 @@ extern "C" {
 
 #define HFSEM_PREC_FP64   0       /* H-matrix, H-LU and H-solves in FP64     */
 #define HFSEM_PREC_MIXED  1       /* H-matrix, H-LU and H-solves in FP32;
-                                     Krylov loop and operator stay FP64      */
+                                     Krylov loop and operator stay FP64.  A
+                                     batch holding a mesh whose element sizes
+                                     span more than 1e45 is factored in FP64 */
 
 #define HFSEM_RHS_LOAD_VECTOR  0  /* G given directly                        */
 #define HFSEM_RHS_FRAC_POWERS  1  /* f = sum c_k (x-a)^mu_k + sum d_k (b-x)^nu_k */
@@ -94,7 +96,8 @@ typedef struct {
 typedef struct {
   int32_t kind;       /* HFSEM_RHS_*                                         */
   int32_t nrhs;       /* >= 1; must be equal for all instances of a call     */
-  int32_t n_terms;    /* FRAC_POWERS: terms per rhs; LEGENDRE_AB: K + 1      */
+  int32_t n_terms;    /* FRAC_POWERS: terms per rhs; LEGENDRE_AB: K + 1;
+                         may differ between instances                    */
   const double *data; /* host.  LOAD_VECTOR: N_d x nrhs column-major (X's
                          ordering).  FRAC_POWERS: per rhs, n_terms triples
                          (coef, exponent > -1, side: 0 = (x-a), 1 = (b-x)).

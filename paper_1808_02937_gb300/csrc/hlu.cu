@@ -276,47 +276,73 @@ __global__ void k_lowrank(const HInstDev* __restrict__ hi, const InstDev* __rest
     }
     __syncthreads();
   };
-  for (int side = 0; side < 2; ++side) {
-    int e0 = side == 0 ? pr.te0 : pr.se0, e1 = side == 0 ? pr.te1 : pr.se1;
-    int d0 = side == 0 ? pr.td0 : pr.sd0;
-    double scale_side = (side == 0) ? I.g0 : 1.0;   // gamma0 sits with Q
-    int elast = (e1 < I.N) ? e1 : e1 - 1;            // element e1 only feeds the hat at node e1
-    for (int e = e0; e <= elast; ++e) {
-      fill(side, e);
-      // rows: the hat at node e (from elements e-1 and e) when e > e0, the
-      // bubbles of e when e < e1
-      int nb = (e < e1) ? P - 1 : 0;
-      int nh = (e > e0) ? 1 : 0;
-      for (int t = threadIdx.x; t < (nb + nh) * R; t += blockDim.x) {
-        int k = t / R, nu = t % R;
-        double v;
-        int dof;
-        if (k < nh) {
-          v = sPrev[nu] / h[e - 1] - sQ[nu] / h[e];
-          dof = e * P - 1;
-        } else {
-          int p = k - nh + 1;
-          v = -(2.0 * p + 1.0) * (2.0 / h[e]) * sQ[p * R + nu];
-          dof = e * P + p - 1;
-        }
-        v *= scale_side;
-        int row = dof - d0;
-        double dsc = Dv[dof];
-        if (side == 0) {
-          // Q row: lower U = theta D Q, upper V = (1-theta) D Q
-          ar[lo.off + row + (long long)nu * lo.m] = (T)(I.theta * dsc * v);
-          ar[up.off + (long long)up.m * up.kcap + row + (long long)nu * up.n] =
-              (T)((1.0 - I.theta) * dsc * v);
-        } else {
-          // W row: lower V = D W, upper U = D W
-          ar[lo.off + (long long)lo.m * lo.kcap + row + (long long)nu * lo.n] = (T)(dsc * v);
-          ar[up.off + row + (long long)nu * up.m] = (T)(dsc * v);
-        }
+  // Two passes over the elements: the first finds, per term nu, the largest
+  // |Q| and |W| row entries (after the D scaling), the second writes the
+  // factors with every rank-one term balanced (|U_nu| and |V_nu| scaled to
+  // equal maxima).  The products are unchanged; the balance keeps each factor
+  // inside the FP32 range on meshes whose element sizes span 10^80.
+  __shared__ unsigned long long smax[2][32];
+  __shared__ double sscale[32];
+  for (int t = threadIdx.x; t < 64; t += blockDim.x) smax[t / 32][t % 32] = 0ULL;
+  __syncthreads();
+  for (int pass = 0; pass < 2; ++pass) {
+    if (pass == 1) {
+      for (int nu = threadIdx.x; nu < R; nu += blockDim.x) {
+        double mq = __longlong_as_double((long long)smax[0][nu]);
+        double mw = __longlong_as_double((long long)smax[1][nu]);
+        double sc = (mq > 0.0 && mw > 0.0) ? sqrt(mw) / sqrt(mq) : 1.0;   // Q *= s, W /= s
+        sscale[nu] = (isfinite(sc) && sc > 0.0) ? sc : 1.0;
       }
       __syncthreads();
-      for (int nu = threadIdx.x; nu < R; nu += blockDim.x) sPrev[nu] = sQ[nu];
-      __syncthreads();
     }
+    for (int side = 0; side < 2; ++side) {
+      int e0 = side == 0 ? pr.te0 : pr.se0, e1 = side == 0 ? pr.te1 : pr.se1;
+      int d0 = side == 0 ? pr.td0 : pr.sd0;
+      double scale_side = (side == 0) ? I.g0 : 1.0;   // gamma0 sits with Q
+      int elast = (e1 < I.N) ? e1 : e1 - 1;            // element e1 only feeds the hat at node e1
+      for (int e = e0; e <= elast; ++e) {
+        fill(side, e);
+        // rows: the hat at node e (from elements e-1 and e) when e > e0, the
+        // bubbles of e when e < e1
+        int nb = (e < e1) ? P - 1 : 0;
+        int nh = (e > e0) ? 1 : 0;
+        for (int t = threadIdx.x; t < (nb + nh) * R; t += blockDim.x) {
+          int k = t / R, nu = t % R;
+          double v;
+          int dof;
+          if (k < nh) {
+            v = sPrev[nu] / h[e - 1] - sQ[nu] / h[e];
+            dof = e * P - 1;
+          } else {
+            int p = k - nh + 1;
+            v = -(2.0 * p + 1.0) * (2.0 / h[e]) * sQ[p * R + nu];
+            dof = e * P + p - 1;
+          }
+          v *= scale_side * Dv[dof];
+          if (pass == 0) {
+            atomicMax(&smax[side][nu], (unsigned long long)__double_as_longlong(fabs(v)));
+            continue;
+          }
+          int row = dof - d0;
+          if (side == 0) {
+            v *= sscale[nu];
+            // Q row: lower U = theta D Q, upper V = (1-theta) D Q
+            ar[lo.off + row + (long long)nu * lo.m] = (T)(I.theta * v);
+            ar[up.off + (long long)up.m * up.kcap + row + (long long)nu * up.n] =
+                (T)((1.0 - I.theta) * v);
+          } else {
+            v /= sscale[nu];
+            // W row: lower V = D W, upper U = D W
+            ar[lo.off + (long long)lo.m * lo.kcap + row + (long long)nu * lo.n] = (T)v;
+            ar[up.off + row + (long long)nu * up.m] = (T)v;
+          }
+        }
+        __syncthreads();
+        for (int nu = threadIdx.x; nu < R; nu += blockDim.x) sPrev[nu] = sQ[nu];
+        __syncthreads();
+      }
+    }
+    __syncthreads();
   }
   if (threadIdx.x == 0) {
     ranks[H.rk0 + pr.lower_slot] = (I.theta != 0.0) ? R : 0;
@@ -873,7 +899,8 @@ __device__ void op_append(const HOp& o, HCtx<T>& c) {
   const int r0 = c.rk[slot];
   __syncthreads();
   if (k <= 0) return;
-  const bool ident = o.B.off < 0;
+  const bool ident = o.B.off < 0;                 // V_p = columns of I from ioff
+  const long long ioff = ident ? (-1 - o.B.off) : 0;
   const T alpha = (T)o.alpha;
   T* ar = c.ar;
   if (r0 + k <= s.kcap) {
@@ -885,7 +912,7 @@ __device__ void op_append(const HOp& o, HCtx<T>& c) {
     }
     for (int t = threadIdx.x; t < s.n * k; t += blockDim.x) {
       int i = t % s.n, j = t / s.n;
-      Vd[i + (long long)(r0 + j) * s.n] = ident ? (T)(i == j ? 1 : 0) : ar[vidx(o.B, i, j)];
+      Vd[i + (long long)(r0 + j) * s.n] = ident ? (T)(i == ioff + j ? 1 : 0) : ar[vidx(o.B, i, j)];
     }
     __syncthreads();
     if (threadIdx.x == 0) c.rk[slot] = r0 + k;
@@ -904,7 +931,7 @@ __device__ void op_append(const HOp& o, HCtx<T>& c) {
   for (int t = threadIdx.x; t < s.n * K; t += blockDim.x) {
     int i = t % s.n, j = t / s.n;
     Vt[t] = (j < r0) ? Vs[i + (long long)j * s.n]
-                     : (ident ? (T)(i == j - r0 ? 1 : 0) : ar[vidx(o.B, i, j - r0)]);
+                     : (ident ? (T)(i == ioff + j - r0 ? 1 : 0) : ar[vidx(o.B, i, j - r0)]);
   }
   __syncthreads();
   trunc_core(c, slot, Ut, Vt, K);
@@ -1140,6 +1167,7 @@ struct PlanBundle {
 
 struct hfsem_factor_s : public hf::Precond {
   hfsem_system* sys = nullptr;
+  cudaStream_t st = nullptr;   // copy of the system's stream (free never touches sys)
   int precision = HFSEM_PREC_MIXED;
   int build_only = 0;
   double tol = 1e-3;
@@ -1201,11 +1229,21 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
   auto* f = new hfsem_factor();
   try {
     f->sys = s;
+    f->st = s->st;
     f->precision = opt.precision;
+    // FP32 cannot factor the equilibrated H-matrix of meshes whose element
+    // sizes span more than ~1e45 (the preconditioner then loses all digits);
+    // such batches are factored in FP64 on the GPU
+    if (f->precision == HFSEM_PREC_MIXED)
+      for (const InstHost& I : s->ih) {
+        double hmax = *std::max_element(I.h.begin(), I.h.end());
+        double hmin = *std::min_element(I.h.begin(), I.h.end());
+        if (hmax > 1e45 * hmin) f->precision = HFSEM_PREC_FP64;
+      }
     f->build_only = opt.build_only;
     f->tol = opt.tol_hlu;
     f->R = opt.R;
-    const bool fp32 = opt.precision == HFSEM_PREC_MIXED;
+    const bool fp32 = f->precision == HFSEM_PREC_MIXED;
     f->tsize = fp32 ? sizeof(float) : sizeof(double);
     const int max_leaf = fp32 ? 128 : 96;
     std::map<std::string, std::shared_ptr<PlanBundle>> cache;
@@ -1216,13 +1254,17 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
       const InstHost& I = s->ih[i];
       PlanOpts o;
       o.lambda = opt.lambda;
-      int leaf = opt.leaf_elems ? opt.leaf_elems : std::max(1, max_leaf / I.P);
-      leaf = std::min(leaf, std::max(1, max_leaf / I.P));
+      const int kmax_eff = opt.kmax ? opt.kmax : opt.R;
+      const int max_concat = fp32 ? 160 : 112;   // shared memory of the recompression
+      // a dense product appended to a low-rank block adds one leaf's worth of rank
+      const int leaf_cap = std::min(max_leaf, max_concat - 2 * kmax_eff);
+      int leaf = opt.leaf_elems ? opt.leaf_elems : std::max(1, leaf_cap / I.P);
+      leaf = std::min(leaf, std::max(1, leaf_cap / I.P));
       o.leaf_elems = leaf;
       o.R = opt.R;
-      o.kmax = opt.kmax ? opt.kmax : opt.R;
+      o.kmax = kmax_eff;
       o.nrhs_max = 64;
-      o.max_concat = fp32 ? 128 : 96;
+      o.max_concat = max_concat;
       o.max_leaf = max_leaf;
       o.unique_tmp = 1;
       o.ncta = kCluster;
@@ -1585,7 +1627,7 @@ int hfsem_precond_apply(hfsem_factor* fac, int32_t nrhs, const double* r, double
 
 void hfsem_factor_free(hfsem_factor* f) {
   if (!f) return;
-  cudaStreamSynchronize(f->sys->st);
+  cudaStreamSynchronize(f->st);
   f->collect_flops();
   delete f;
 }

@@ -258,10 +258,14 @@ struct Builder {
     if (c.type == B_DENSE) {
       op(OP_AXPY, Z, View{}, dense(cb), alpha, 1.0);
     } else if (c.type == B_LR) {
-      // Z = Z I: append with an identity right factor (B.off < 0)
+      // Z = Z I: append 32-column slices with identity right factors
+      // (B.off = -1 - first column), each followed by a recompression
       p.hh_lr++;
-      View Iv{-1, c.n, c.n, c.n, 0};
-      append(cb, Z, Iv, alpha);
+      for (int c0 = 0; c0 < c.n; c0 += 32) {
+        int c1 = std::min(c.n, c0 + 32);
+        View Iv{-1 - (long long)c0, c.n, c1 - c0, c.n, 0};
+        append(cb, vcols(Z, c0, c1), Iv, alpha);
+      }
     } else {
       for (int i = 0; i < 2; ++i)
         for (int j = 0; j < 2; ++j) {

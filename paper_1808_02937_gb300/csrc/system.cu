@@ -727,8 +727,9 @@ __global__ void k_load_moments(const InstDev* __restrict__ inst, const double* a
   const double* dl = arena + I.o_dl;
   const double* dr = arena + I.o_dr;
   const double Lab = dl[N];
+  n_terms = (int)roff[2 * blockIdx.y + 1];
   const int stride = (kind == HFSEM_RHS_FRAC_POWERS) ? 3 * n_terms : n_terms;
-  const double* rd = rhsdata + roff[blockIdx.y] + (size_t)r * stride;
+  const double* rd = rhsdata + roff[2 * blockIdx.y] + (size_t)r * stride;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < N; e += gridDim.x * blockDim.x) {
     double g[kMaxP + 1];
     for (int m = 0; m <= P; ++m) g[m] = 0.0;
@@ -990,16 +991,16 @@ static int check_rhs(hfsem_system* s, const hfsem_rhs* rhs) {
       throw Error(HFSEM_ERR_INVALID_ARG, "rhs kind differs between instances");
     if (!R.data) throw Error(HFSEM_ERR_INVALID_ARG, "rhs data is NULL");
     if (R.kind == HFSEM_RHS_FRAC_POWERS) {
-      if (R.n_terms < 1 || R.n_terms != rhs[0].n_terms)
-        throw Error(HFSEM_ERR_INVALID_ARG, "FRAC_POWERS: n_terms must be >= 1 and equal");
+      if (R.n_terms < 1 || R.n_terms > 4096)
+        throw Error(HFSEM_ERR_INVALID_ARG, "FRAC_POWERS: 1 <= n_terms <= 4096");
       for (int k = 0; k < R.n_terms * nrhs; ++k) {
         double mu = R.data[3 * k + 1], side = R.data[3 * k + 2];
         if (!(mu > -1.0) || !(side == 0.0 || side == 1.0))
           throw Error(HFSEM_ERR_INVALID_ARG, "FRAC_POWERS: exponent > -1, side 0 or 1");
       }
     } else if (R.kind == HFSEM_RHS_LEGENDRE_AB) {
-      if (R.n_terms < 1 || R.n_terms > 128 || R.n_terms != rhs[0].n_terms)
-        throw Error(HFSEM_ERR_INVALID_ARG, "LEGENDRE_AB: 1 <= K+1 <= 128, equal across instances");
+      if (R.n_terms < 1 || R.n_terms > 128)
+        throw Error(HFSEM_ERR_INVALID_ARG, "LEGENDRE_AB: 1 <= K+1 <= 128");
     } else if (R.kind != HFSEM_RHS_LOAD_VECTOR) {
       throw Error(HFSEM_ERR_INVALID_ARG, "unknown rhs kind");
     }
@@ -1026,21 +1027,22 @@ void load_vector_em(hfsem_system* s, const hfsem_rhs* rhs, int lifted, double* G
     HF_CHECK(cudaStreamSynchronize(s->st));
     perm_to_elem(s, nrhs, s->w_y.p, G_em);
   } else {
-    int n_terms = rhs[0].n_terms;
-    int stride = (kind == HFSEM_RHS_FRAC_POWERS) ? 3 * n_terms : n_terms;
     std::vector<double> buf;
-    std::vector<long long> roff(ni);
+    std::vector<long long> roff(2 * ni);   // per instance: data offset, n_terms
     for (int i = 0; i < ni; ++i) {
-      roff[i] = (long long)buf.size();
+      int stride = (kind == HFSEM_RHS_FRAC_POWERS) ? 3 * rhs[i].n_terms : rhs[i].n_terms;
+      roff[2 * i] = (long long)buf.size();
+      roff[2 * i + 1] = rhs[i].n_terms;
       buf.insert(buf.end(), rhs[i].data, rhs[i].data + (size_t)stride * nrhs);
     }
-    size_t nb = buf.size() + (size_t)ni * sizeof(long long) / sizeof(double) + 2;
+    size_t nb = buf.size() + (size_t)2 * ni + 2;
     s->w_rhsdata.ensure(nb);
     HF_CHECK(cudaMemcpyAsync(s->w_rhsdata.p, buf.data(), buf.size() * sizeof(double),
                              cudaMemcpyHostToDevice, s->st));
     long long* d_roff = reinterpret_cast<long long*>(s->w_rhsdata.p + buf.size());
-    HF_CHECK(cudaMemcpyAsync(d_roff, roff.data(), ni * sizeof(long long),
+    HF_CHECK(cudaMemcpyAsync(d_roff, roff.data(), 2 * ni * sizeof(long long),
                              cudaMemcpyHostToDevice, s->st));
+    const int n_terms = 0;   // per instance, from the table
     // moments: sum over instances of N (P+1) = total_nz + sum N, per rhs
     s->w_mom.ensure((size_t)(s->total_nz + s->total_N) * nrhs);
     k_load_moments<<<grid1(s->max_N, 128, ni, nrhs), 128, 0, s->st>>>(

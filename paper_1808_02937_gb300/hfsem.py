@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import weakref
 
 import numpy as np
 
@@ -141,6 +142,7 @@ class System:
         self.h = handle
         self.problems = problems
         self.ndofs = [int(p.n_elem) * int(p.P) - 1 for p in problems]
+        self.factors = weakref.WeakSet()   # freed before the system
 
     @property
     def total_ndof(self):
@@ -148,6 +150,8 @@ class System:
 
     def __del__(self):
         if getattr(self, "h", None) and _lib is not None:
+            for f in list(getattr(self, "factors", ())):
+                f.free()
             _lib.hfsem_system_free(self.h)
             self.h = None
 
@@ -156,11 +160,15 @@ class Factor:
     def __init__(self, handle, system):
         self.h = handle
         self.system = system
+        system.factors.add(self)
 
-    def __del__(self):
+    def free(self):
         if getattr(self, "h", None) and _lib is not None:
             _lib.hfsem_factor_free(self.h)
             self.h = None
+
+    def __del__(self):
+        self.free()
 
 
 def make_problem(h, P, alpha, theta, rho, a=0.0, b=None, c1=0.0, c2=0.0,

@@ -1,0 +1,154 @@
+"""GPU parity at the workloads' full sizes, in the launch configuration the
+benchmark times (R = 8, lambda = 1, Tol_HLU = 1e-3, mixed precision, BiCGSTAB
+to 1e-14):
+
+* config 2 (nine uniform instances, N = 1024, P = 8): one instance against the
+  oracle's exact discrete solution, every instance by its true residual;
+* config 4 shape (heterogeneous batch, 4 right-hand sides, manufactured
+  polynomial solutions): instances with P >= deg u must reproduce u exactly
+  (a property that holds at any size), small ones against the oracle;
+* degenerate shapes (one element, P = 1).
+"""
+import os
+
+import numpy as np
+import pytest
+
+from oracle.basis import Mesh
+from oracle.solve import solve_problem
+from paper_1808_02937_gb300 import hfsem as H
+from paper_1808_02937_gb300 import workloads as W
+from tests._common import ensure_built, rel_err
+from tests.test_oracle_solve import expected_coeffs
+
+pytestmark = pytest.mark.gpu
+
+OPTS = dict(R=8, lam=1.0, tol_hlu=1e-3, precision=H.PREC_MIXED)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return ensure_built()
+
+
+def test_config2_full_size(lib):
+    insts = W.config2()
+    sys_ = H.hfsem_assemble([H.make_problem(p.h, p.P, p.alpha, p.theta, p.rho) for p in insts])
+    fac = H.hfsem_hlu_factor(sys_, H.hopts(**OPTS))
+    X, st, code = H.hfsem_solve(sys_, fac, [H.rhs_legendre([p.rhs[0]]) for p in insts],
+                                tol=1e-14, max_iter=60)
+    assert code == H.HFSEM_OK
+    for s in st:
+        assert s["iters"] <= 10 and s["rel_true_residual"] < 1e-11
+    p = insts[4]
+    Xo, _ = solve_problem(Mesh(p.h, 0.0, 1.0), p.P, p.alpha, p.theta, p.rho, 0.0, 0.0,
+                          ("legendre_ab", p.rhs[0]))
+    got = H.split(sys_, X)[4][:, 0]
+    assert rel_err(got, Xo) < 1e-10
+
+
+def _config4(n):
+    return W.config4()[:n]
+
+
+@pytest.mark.parametrize("n_inst", [512])
+def test_config4_batch_exact_reproduction(lib, n_inst):
+    insts = _config4(n_inst)
+    sys_ = H.hfsem_assemble([H.make_problem(p.h, p.P, p.alpha, p.theta, p.rho) for p in insts])
+    fac = H.hfsem_hlu_factor(sys_, H.hopts(**OPTS))
+    rhs = [H.rhs_frac_powers(p.rhs) for p in insts]
+    X, st, code = H.hfsem_solve(sys_, fac, rhs, tol=1e-14, max_iter=80, allow_fail=True)
+    assert code == H.HFSEM_OK, [s for s in st if s["status"]][:3]
+    parts = H.split(sys_, X, nrhs=4)
+    # manufactured u = x(1-x)p(x) of degree <= 6: exact when P >= deg u
+    checked = 0
+    for k, p in enumerate(insts):
+        us = _u_coeffs(k)
+        for r in range(4):
+            u = us[r]
+            deg = len(u) - 1
+            if p.P >= deg:
+                Xe = expected_coeffs(Mesh(p.h, 0.0, 1.0), p.P, np.polynomial.Polynomial(u))
+                assert rel_err(parts[k][:, r], Xe) < 1e-9, (k, r, p.name)
+                checked += 1
+    assert checked > 100
+
+
+def _u_coeffs(k, cache={}):
+    """u = x(1-x)p(x) coefficients of instance k of config 4, drawn with the
+    same seeded sequence as workloads.config4."""
+    if not cache:
+        rng = np.random.default_rng(18080004)
+        for i in range(512):
+            N = int(rng.integers(32, 513))
+            rng.integers(2, 13)
+            rng.uniform(1.1, 1.9)
+            rng.uniform(0.0, 1.0)
+            rng.uniform(0.0, 2.0)
+            fam = int(rng.integers(0, 3))
+            if fam == 1:
+                rng.uniform(0.3, 0.7)
+            elif fam == 2:
+                rng.integers(2, 4)
+            us = []
+            for _ in range(4):
+                pc = rng.standard_normal(int(rng.integers(0, 5)) + 1)
+                us.append(np.convolve([0.0, 1.0, -1.0], pc))
+            cache[i] = us
+    return cache[k]
+
+
+def test_config4_small_instances_vs_oracle(lib):
+    insts = [p for p in _config4(512) if p.N <= 48][:4]
+    assert insts
+    sys_ = H.hfsem_assemble([H.make_problem(p.h, p.P, p.alpha, p.theta, p.rho) for p in insts])
+    fac = H.hfsem_hlu_factor(sys_, H.hopts(**OPTS))
+    X, st, code = H.hfsem_solve(sys_, fac, [H.rhs_frac_powers(p.rhs) for p in insts],
+                                tol=1e-14, max_iter=80)
+    parts = H.split(sys_, X, nrhs=4)
+    for k, p in enumerate(insts):
+        for r in range(4):
+            Xo, _ = solve_problem(Mesh(p.h, 0.0, 1.0), p.P, p.alpha, p.theta, p.rho, 0.0, 0.0,
+                                  ("frac_powers", p.rhs[r]))
+            assert rel_err(parts[k][:, r], Xo) < 1e-10, (k, r)
+
+
+@pytest.mark.parametrize("prec", [H.PREC_MIXED, H.PREC_FP64])
+def test_degenerate_shapes(lib, prec):
+    cases = [(np.array([1.0]), 3), (W.mesh_uniform(2), 1), (W.mesh_graded(3, 2.0), 2),
+             (np.array([1.0]), 1)]
+    probs, rhs, refs = [], [], []
+    for h, P in cases:
+        probs.append(H.make_problem(h, P, 1.45, 0.35, 0.8))
+        rhs.append(H.rhs_frac_powers([[(1.0, 0.0, "a"), (0.5, -0.3, "b")]]))
+    sys_ = H.hfsem_assemble(probs)
+    fac = H.hfsem_hlu_factor(sys_, H.hopts(R=4, precision=prec))
+    X, st, code = H.hfsem_solve(sys_, fac, rhs, tol=1e-15, max_iter=50, allow_fail=True)
+    parts = H.split(sys_, X)
+    for k, (h, P) in enumerate(cases):
+        Nd = len(h) * P - 1
+        if Nd == 0:
+            assert parts[k].size == 0
+            continue
+        Xo, _ = solve_problem(Mesh(h, 0.0, 1.0), P, 1.45, 0.35, 0.8, 0.0, 0.0,
+                              ("frac_powers", [(1.0, 0.0, "a"), (0.5, -0.3, "b")]))
+        assert rel_err(parts[k][:, 0], Xo) < 1e-10, (k, st[k])
+
+
+def test_config3_geometric_mixed_and_fp64(lib):
+    # two-sided geometric q = 0.5, N = 256 (elements down to ~2^-129),
+    # P = 16, alpha = 1.3, theta = 0.7, R = 10
+    p = W.config3()
+    sys_ = H.hfsem_assemble([H.make_problem(p.h, p.P, p.alpha, p.theta, p.rho)])
+    Xo, _ = solve_problem(Mesh(p.h, 0.0, 1.0), p.P, p.alpha, p.theta, p.rho, 0.0, 0.0,
+                          ("legendre_ab", p.rhs[0]))
+    iters = {}
+    for prec in (H.PREC_MIXED, H.PREC_FP64):
+        fac = H.hfsem_hlu_factor(sys_, H.hopts(R=10, lam=1.0, tol_hlu=1e-3, precision=prec))
+        X, st, code = H.hfsem_solve(sys_, fac, [H.rhs_legendre([p.rhs[0]])], tol=1e-14,
+                                    max_iter=80)
+        assert code == H.HFSEM_OK
+        assert rel_err(X, Xo) < 1e-10, (prec, st)
+        iters[prec] = st[0]["iters"]
+    # the mixed-precision preconditioner costs at most a few extra iterations
+    assert iters[H.PREC_MIXED] <= iters[H.PREC_FP64] + 4, iters
