@@ -473,6 +473,72 @@ __device__ void op_gemm(const HOp& o, HCtx<T>& c) {
     }
     return;
   }
+  if (m >= 96 && n >= 96) {
+    // 128 x 128 C tiles, 8 x 8 outputs per thread, k in chunks of 8; the
+    // next chunk is loaded into registers while the current one is used
+    T* As = c.sm;             // [8][128]
+    T* Bs = c.sm + 8 * 128;   // [8][128]
+    const int tx = tid & 15, ty = tid >> 4;
+    for (int m0 = 0; m0 < m; m0 += 128)
+      for (int n0 = 0; n0 < n; n0 += 128) {
+        T acc[8][8];
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+#pragma unroll
+          for (int b = 0; b < 8; ++b) acc[a][b] = 0;
+        T ra[4], rb[4];
+        auto fetch = [&](int k0) {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            int t = tid + q * 256;
+            int kk = t >> 7, ii = t & 127;
+            int gi = m0 + ii, gj = n0 + ii, gk = k0 + kk;
+            ra[q] = (gi < m && gk < k) ? ar[vidx(o.A, gi, gk)] : (T)0;
+            rb[q] = (gj < n && gk < k) ? ar[vidx(o.B, gk, gj)] : (T)0;
+          }
+        };
+        fetch(0);
+        for (int k0 = 0; k0 < k; k0 += 8) {
+          __syncthreads();
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            int t = tid + q * 256;
+            As[t] = ra[q];
+            Bs[t] = rb[q];
+          }
+          __syncthreads();
+          if (k0 + 8 < k) fetch(k0 + 8);
+#pragma unroll
+          for (int kk = 0; kk < 8; ++kk) {
+            T a[8], b[8];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              a[q] = As[kk * 128 + ty * 4 + q];
+              a[q + 4] = As[kk * 128 + 64 + ty * 4 + q];
+              b[q] = Bs[kk * 128 + tx * 4 + q];
+              b[q + 4] = Bs[kk * 128 + 64 + tx * 4 + q];
+            }
+#pragma unroll
+            for (int p = 0; p < 8; ++p)
+#pragma unroll
+              for (int q = 0; q < 8; ++q) acc[p][q] += a[p] * b[q];
+          }
+        }
+#pragma unroll
+        for (int p = 0; p < 8; ++p)
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            int gi = m0 + (p < 4 ? ty * 4 + p : 64 + ty * 4 + p - 4);
+            int gj = n0 + (q < 4 ? tx * 4 + q : 64 + tx * 4 + q - 4);
+            if (gi < m && gj < n) {
+              long long ci = vidx(o.C, gi, gj);
+              ar[ci] = (beta == (T)0 ? (T)0 : beta * ar[ci]) + alpha * acc[p][q];
+            }
+          }
+      }
+    __syncthreads();
+    return;
+  }
   // tiled: 64 x 64 C tiles, k in chunks of 16, 4 x 4 per thread
   T* As = c.sm;            // [16][64]
   T* Bs = c.sm + 16 * 64;  // [16][64]
@@ -654,7 +720,7 @@ __device__ void op_getrf_inv(const HOp& o, HCtx<T>& c) {
   T* S = c.sm;             // n x n, [i + j n]
   T* X = c.sm + n * n;     // n x n
   const int tid = threadIdx.x;
-  const int tx = tid & 15, ty = tid >> 4;
+  const int tx = tid & 31, ty = tid >> 5;   // a warp covers 32 consecutive rows of one column
   for (int t = tid; t < n * n; t += blockDim.x) {
     S[t] = ar[vidx(o.C, t % n, t / n)];
     X[t] = (t % n == t / n) ? (T)1 : (T)0;
@@ -664,24 +730,51 @@ __device__ void op_getrf_inv(const HOp& o, HCtx<T>& c) {
     const T piv = S[k + k * n];
     if (tid == 0 && (piv == (T)0 || !isfinite((double)piv))) atomicExch(c.err, 1);
     const T inv = (T)1 / piv;
-    // row i > k: columns j > k of S, columns j <= k of X (n columns in all)
-    for (int j = ty; j < n; j += 16) {
+    // this thread's rows i = k+1+tx+32r (n <= 128: at most 4): multipliers
+    // in registers, then columns j > k of S and j <= k of X (n in all)
+    T l[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      int i = k + 1 + tx + 32 * r;
+      l[r] = (i < n) ? S[i + k * n] * inv : (T)0;
+    }
+    for (int j = ty; j < n; j += 8) {
       const bool lu = j > k;
       const T rk = lu ? S[k + j * n] : X[k + j * n];
-      T* dst = lu ? S : X;
-      for (int i = k + 1 + tx; i < n; i += 16) dst[i + j * n] -= (S[i + k * n] * inv) * rk;
+      T* dst = (lu ? S : X) + j * n;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        int i = k + 1 + tx + 32 * r;
+        if (i < n) dst[i] -= l[r] * rk;
+      }
     }
     __syncthreads();
   }
   for (int t = tid; t < n * n; t += blockDim.x) ar[vidx(o.A, t % n, t / n)] = X[t];
+  // (D^-1 U)^-1 by backward elimination of the unit upper factor: first
+  // scale the strict upper part of S row by row (one division per entry)
   __syncthreads();
-  // (D^-1 U)^-1 by backward elimination of the unit upper factor
-  for (int t = tid; t < n * n; t += blockDim.x) X[t] = (t % n == t / n) ? (T)1 : (T)0;
+  for (int t = tid; t < n * n; t += blockDim.x) {
+    int i = t % n, j = t / n;
+    X[t] = (i == j) ? (T)1 : (T)0;
+    if (j > i) S[t] = S[t] / S[i + i * n];
+  }
   __syncthreads();
   for (int k = n - 1; k > 0; --k) {
-    for (int j = k + ty; j < n; j += 16) {
+    T u[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      int i = tx + 32 * r;
+      u[r] = (i < k) ? S[i + k * n] : (T)0;
+    }
+    for (int j = k + ty; j < n; j += 8) {
       const T xkj = X[k + j * n];
-      for (int i = tx; i < k; i += 16) X[i + j * n] -= (S[i + k * n] / S[i + i * n]) * xkj;
+      T* dst = X + j * n;
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        int i = tx + 32 * r;
+        if (i < k) dst[i] -= u[r] * xkj;
+      }
     }
     __syncthreads();
   }
