@@ -60,7 +60,19 @@ struct HInstDev {
   long long d_off;   // scaling D (FP64) offset
   int sys_inst;      // index into the system's instances
   int R;
+  int nd;            // unknowns (leading dimension of the rhs area)
+  long long st0, job0;  // leaf-solve tables: steps, jobs
+  long long pk0;     // this instance's first job in the solve pack
+  int jcap;          // jobs per part of the leaf solve
+  int nst;           // steps (2 x leaves)
+  int njob;          // jobs of the instance's plan
 };
+
+// right-hand sides per pass of the leaf solve
+template <class T>
+__host__ __device__ constexpr int solve_w() {
+  return sizeof(T) == 4 ? 4 : 2;
+}
 
 constexpr int kHThreads = 256;
 
@@ -365,6 +377,7 @@ struct HCtx {
   const SlotDev* sl;
   T* ws;
   T* sm;
+  long long smcap;   // elements of T in the dynamic shared memory
   double tol;
   int* err;
 };
@@ -712,10 +725,154 @@ __device__ void op_trmm_r(const HOp& o, HCtx<T>& c) {
 // elimination matrix, so X ends as L^-1; every value a step reads is left
 // untouched by that step, hence one barrier per step.  U^-1 = (D^-1 U)^-1 D^-1
 // with D = diag(U), again one barrier per step.
+// FP32 leaves (n <= 128), register resident: thread (tx, ty) holds rows
+// tx + 32 r (r < 4) and columns ty + 8 q (q < 16) of the matrix and of the
+// inverse being built.  Step k sends column k (the multipliers) and row k
+// through two double-buffered shared vectors, so a step costs one barrier and
+// the rank-one update itself touches registers only.  The outer loop over
+// column blocks of 8 is unrolled so that every register index is static.
+__device__ void getrf_inv_reg(const HOp& o, HCtx<float>& c) {
+  const int n = o.C.r;
+  float* ar = c.ar;
+  float* colb = c.sm;         // [2][128]
+  float* rowb = c.sm + 256;   // [2][128]
+  float* diag = c.sm + 512;   // [128]
+  const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  float S[4][16], X[4][16];
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int i = tx + 32 * r, j = ty + 8 * q;
+      S[r][q] = (i < n && j < n) ? ar[vidx(o.C, i, j)] : 0.f;
+      X[r][q] = (i == j && i < n) ? 1.f : 0.f;
+    }
+  int buf = 0;
+  // forward: S -> U (upper part), X -> L^-1
+#pragma unroll
+  for (int cb = 0; cb < 16; ++cb) {
+    const int rb = cb >> 2;   // register row block of rows 8 cb .. 8 cb + 7
+    if (8 * cb >= n) break;
+    for (int q = 0; q < 8; ++q) {
+      const int k = 8 * cb + q;
+      if (k >= n) break;
+      float* col = colb + 128 * buf;
+      float* row = rowb + 128 * buf;
+      if (ty == q) {
+#pragma unroll
+        for (int r = rb; r < 4; ++r) col[tx + 32 * r] = S[r][cb];
+      }
+      if (tx == (k & 31)) {
+#pragma unroll
+        for (int c2 = 0; c2 < 16; ++c2) {
+          float v;
+          if (c2 > cb) v = S[rb][c2];
+          else if (c2 < cb) v = X[rb][c2];
+          else v = (ty > q) ? S[rb][c2] : X[rb][c2];
+          row[ty + 8 * c2] = v;
+        }
+      }
+      __syncthreads();
+      const float piv = col[k];
+      if (tid == 0 && (piv == 0.f || !isfinite(piv))) atomicExch(c.err, 1);
+      const float inv = 1.f / piv;
+      float l[4], rv[16];
+#pragma unroll
+      for (int r = rb; r < 4; ++r) {
+        const int i = tx + 32 * r;
+        l[r] = (i > k) ? col[i] * inv : 0.f;
+      }
+#pragma unroll
+      for (int c2 = 0; c2 < 16; ++c2) rv[c2] = row[ty + 8 * c2];
+#pragma unroll
+      for (int r = rb; r < 4; ++r)
+#pragma unroll
+        for (int c2 = 0; c2 < 16; ++c2) {
+          if (c2 > cb) S[r][c2] -= l[r] * rv[c2];
+          else if (c2 < cb) X[r][c2] -= l[r] * rv[c2];
+          else if (ty > q) S[r][c2] -= l[r] * rv[c2];
+          else X[r][c2] -= l[r] * rv[c2];
+        }
+      buf ^= 1;
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      const int i = tx + 32 * r, j = ty + 8 * q;
+      if (i < n && j < n) ar[vidx(o.A, i, j)] = X[r][q];
+      if (i == j && i < n) diag[i] = S[r][q];
+    }
+  __syncthreads();
+  // backward: with D = diag(U), X -> (D^-1 U)^-1, then U^-1 = X D^-1
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int i = tx + 32 * r;
+    const float ri = (i < n) ? 1.f / diag[i] : 0.f;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+      S[r][q] *= ri;
+      X[r][q] = (i == ty + 8 * q && i < n) ? 1.f : 0.f;
+    }
+  }
+#pragma unroll
+  for (int cb = 15; cb >= 0; --cb) {
+    const int rb = cb >> 2;
+    if (8 * cb < n) {
+      for (int q = 7; q >= 0; --q) {
+        const int k = 8 * cb + q;
+        if (k >= n || k == 0) continue;
+        float* col = colb + 128 * buf;
+        float* row = rowb + 128 * buf;
+        if (ty == q) {
+#pragma unroll
+          for (int r = 0; r <= rb; ++r) col[tx + 32 * r] = S[r][cb];
+        }
+        if (tx == (k & 31)) {
+#pragma unroll
+          for (int c2 = cb; c2 < 16; ++c2) row[ty + 8 * c2] = X[rb][c2];
+        }
+        __syncthreads();
+        float u[4], rv[16];
+#pragma unroll
+        for (int r = 0; r <= rb; ++r) {
+          const int i = tx + 32 * r;
+          u[r] = (i < k) ? col[i] : 0.f;
+        }
+#pragma unroll
+        for (int c2 = cb; c2 < 16; ++c2) rv[c2] = row[ty + 8 * c2];
+#pragma unroll
+        for (int r = 0; r <= rb; ++r)
+#pragma unroll
+          for (int c2 = cb; c2 < 16; ++c2) X[r][c2] -= u[r] * rv[c2];
+        buf ^= 1;
+      }
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int j = ty + 8 * q;
+    if (j >= n) continue;
+    const float cj = 1.f / diag[j];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      const int i = tx + 32 * r;
+      if (i < n) ar[vidx(o.B, i, j)] = X[r][q] * cj;
+    }
+  }
+}
+
 template <class T>
 __device__ void op_getrf_inv(const HOp& o, HCtx<T>& c) {
   const int n = o.C.r;
   if (n <= 0) return;
+  if constexpr (sizeof(T) == 4) {
+    if (n <= 128) {
+      getrf_inv_reg(o, c);
+      return;
+    }
+  }
   T* ar = c.ar;
   T* S = c.sm;             // n x n, [i + j n]
   T* X = c.sm + n * n;     // n x n
@@ -845,6 +1002,40 @@ __device__ void apply_q(const T* A, int m, int K, const T* tau, T* Y, int ldy, i
   }
 }
 
+// house_qr of A (m x K, global) run on a shared-memory copy when m K <= cap
+template <class T>
+__device__ void qr_staged(T* A, int m, int K, T* tau, T* red, T* stage, long long cap) {
+  const long long mk = (long long)m * K;
+  if (mk > cap) {
+    house_qr(A, m, K, tau, red);
+    return;
+  }
+  for (long long t = threadIdx.x; t < mk; t += blockDim.x) stage[t] = A[t];
+  __syncthreads();
+  house_qr(stage, m, K, tau, red);
+  for (long long t = threadIdx.x; t < mk; t += blockDim.x) A[t] = stage[t];
+  __syncthreads();
+}
+
+// Y (m x r, ld m, global) <- Q Y, with Q and Y copied to shared memory when
+// m (K + r) <= cap
+template <class T>
+__device__ void apply_q_staged(const T* A, int m, int K, const T* tau, T* Y, int r, T* stage,
+                               long long cap) {
+  const long long mk = (long long)m * K, mr = (long long)m * r;
+  if (mk + mr > cap) {
+    apply_q(A, m, K, tau, Y, m, r);
+    return;
+  }
+  T* Ys = stage + mk;
+  for (long long t = threadIdx.x; t < mk; t += blockDim.x) stage[t] = A[t];
+  for (long long t = threadIdx.x; t < mr; t += blockDim.x) Ys[t] = Y[t];
+  __syncthreads();
+  apply_q(stage, m, K, tau, Ys, m, r);
+  for (long long t = threadIdx.x; t < mr; t += blockDim.x) Y[t] = Ys[t];
+  __syncthreads();
+}
+
 // Recompress U V^T given as Ut (m x K) and Vt (n x K) in the workspace into
 // LR slot `slot`.  U = Q_U R_U, V = Q_V R_V (Householder), then a column-
 // pivoted QR of the small core M = R_U R_V^T, M Pi = Q_M R_M, stopped at the
@@ -862,15 +1053,36 @@ __device__ void trunc_core(HCtx<T>& c, int slot, T* Ut, T* Vt, int K) {
   T* cn = tauM + K;                  // K column norms^2
   T* Z = cn + K;                     // K x K work (ld K)
   int* piv = reinterpret_cast<int*>(Z + K * K);   // K
+  // the rest of the shared memory stages the tall factors (16-byte aligned)
+  const long long small = ((2LL * K + 32 + 2LL * K * K + 3LL * K + K + 8) + 3) & ~3LL;
+  T* stage = c.sm + small;
+  const long long cap = c.smcap - small;
   __shared__ int s_p, s_stop;
   __shared__ T s_r0;
-  house_qr(Ut, m, K, tauU, red);
-  house_qr(Vt, n, K, tauV, red);
+  // Householder QR of the tall factors, in shared memory when they fit (the
+  // reflector loops are latency bound), written back for the final products
+  qr_staged(Ut, m, K, tauU, red, stage, cap);
+  qr_staged(Vt, n, K, tauV, red, stage, cap);
   const int ku = min(m, K), kv = min(n, K);
+  // core M = R_U R_V^T from the two triangles, staged
+  T* RU = Ut;
+  T* RV = Vt;
+  long long ldu = m, ldv = n;
+  if ((long long)2 * K * K <= cap) {
+    RU = stage;
+    RV = stage + (long long)K * K;
+    for (int t = threadIdx.x; t < K * K; t += blockDim.x) {
+      int i = t % K, l = t / K;
+      RU[t] = (i < ku && i <= l) ? Ut[i + (long long)l * m] : (T)0;
+      RV[t] = (i < kv && i <= l) ? Vt[i + (long long)l * n] : (T)0;
+    }
+    ldu = ldv = K;
+    __syncthreads();
+  }
   for (int t = threadIdx.x; t < ku * kv; t += blockDim.x) {
     int i = t % ku, j = t / ku;
     T acc = 0;
-    for (int l = max(i, j); l < K; ++l) acc += Ut[i + (long long)l * m] * Vt[j + (long long)l * n];
+    for (int l = max(i, j); l < K; ++l) acc += RU[i + l * ldu] * RV[j + l * ldv];
     M[i + j * K] = acc;
   }
   for (int j = threadIdx.x; j < kv; j += blockDim.x) piv[j] = j;
@@ -978,8 +1190,8 @@ __device__ void trunc_core(HCtx<T>& c, int slot, T* Ut, T* Vt, int K) {
     Vd[piv[j] + (long long)i * n] = (j >= i) ? M[i + j * K] : (T)0;
   }
   __syncthreads();
-  apply_q(Ut, m, K, tauU, Ud, m, r);
-  apply_q(Vt, n, K, tauV, Vd, n, r);
+  apply_q_staged(Ut, m, K, tauU, Ud, r, stage, cap);
+  apply_q_staged(Vt, n, K, tauV, Vd, r, stage, cap);
   if (threadIdx.x == 0) c.rk[slot] = r;
   __syncthreads();
 }
@@ -1057,6 +1269,10 @@ struct HProgArgs {
   double tol;
   unsigned long long* prof;   // optional: per instance, 16 op types x (cycles, count)
   double* flops;              // per instance: algorithmic flops of the executed ops
+  unsigned long long* wprof;  // optional: per instance and wave, wall ns then per CTA
+                              // (busy ns, longest op ns, longest op index)
+  int wstride;                // waves per instance in wprof
+  long long smem_elems;       // dynamic shared memory, in elements of the factor type
 };
 
 // algorithmic flops of one op with its run-time shapes
@@ -1119,19 +1335,23 @@ __global__ void __launch_bounds__(kHThreads) k_hprog(HProgArgs a, T* har, int wh
   c.sl = a.slots + H.slot0;
   c.ws = c.ar + H.ws_off + (long long)crank * H.ws_size;
   c.sm = reinterpret_cast<T*>(smraw);
+  c.smcap = a.smem_elems;
   c.tol = a.tol;
   c.err = a.err + cid;
   const HOp* ops = a.ops + (which ? H.sops0 : H.ops0);
   const int* waves = a.waves + (which ? H.sw0 : H.fw0);
   const int nw = which ? H.nsw : H.nfw;
   double fl = 0.0;
+  const bool wp = a.wprof && threadIdx.x == 0;
   for (int w = 0; w < nw; ++w) {
     const int i1 = waves[w + 1];
+    unsigned long long tw0 = 0, busy = 0, lmax = 0, ltype = 0;
+    if (wp) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(tw0));
     for (int i = waves[w] + (int)crank; i < i1; i += kCluster) {
       const HOp o = ops[i];
       if (threadIdx.x == 0) fl += op_flops(o, c.rk, c.sl);
       unsigned long long t0 = 0;
-      if (a.prof && crank == 0 && threadIdx.x == 0) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+      if ((a.prof && crank == 0 && threadIdx.x == 0) || wp) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
       switch (o.type) {
         case OP_GEMM: op_gemm(o, c); break;
         case OP_GETRF_INV: op_getrf_inv(o, c); break;
@@ -1162,10 +1382,371 @@ __global__ void __launch_bounds__(kHThreads) k_hprog(HProgArgs a, T* har, int wh
         pr[0] += t1 - t0;
         pr[1] += 1ULL;
       }
+      if (wp) {
+        unsigned long long t1;
+        asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+        busy += t1 - t0;
+        if (t1 - t0 > lmax) {
+          lmax = t1 - t0;
+          ltype = (unsigned long long)i;
+        }
+      }
     }
     cluster_barrier();
+    if (wp) {
+      unsigned long long t1;
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+      unsigned long long* q = a.wprof + ((size_t)cid * a.wstride + w) * (1 + 3 * kCluster);
+      if (crank == 0) q[0] = t1 - tw0;
+      q[1 + 3 * crank] = busy;
+      q[2 + 3 * crank] = lmax;
+      q[3 + 3 * crank] = ltype;
+    }
   }
   if (threadIdx.x == 0) a.flops[((size_t)cid * kCluster + crank) * 2 + which] += fl;
+}
+
+// --- asynchronous bulk copies and distributed shared memory (inline PTX) ---
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// global -> this CTA's shared memory, completion counted on bar (bytes)
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
+                                         unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ float ld_dsmem(const float* p, unsigned rank) {
+  unsigned a;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"(smem_u32(p)), "r"(rank));
+  float v;
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ double ld_dsmem(const double* p, unsigned rank) {
+  unsigned a;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"(smem_u32(p)), "r"(rank));
+  double v;
+  asm volatile("ld.shared::cluster.f64 %0, [%1];" : "=d"(v) : "r"(a) : "memory");
+  return v;
+}
+
+// The solve pack: after the factorisation, every job's column segment is
+// copied to its own slot of slot_elems entries (16-byte aligned) in job
+// order, and its fields to a 16-byte record {x, active | kind << 9 | ldw <<
+// 12} (a low-rank column is active below its block's current rank; the
+// slot of an inactive one is zeroed).  The jobs of one CTA in one step are
+// contiguous, so a step reaches shared memory in two bulk copies.
+template <class T>
+__global__ void k_solve_pack(const HInstDev* __restrict__ hi, const SolJob* __restrict__ jobs,
+                             const T* har, const int* __restrict__ ranks, T* pack, int4* meta,
+                             int slot_elems, int* err) {
+  const HInstDev H = hi[blockIdx.y];
+  const T* ar = har + H.arena;
+  const int* rk = ranks + H.rk0;
+  const int lane = threadIdx.x & 31;
+  const long long nw = (long long)gridDim.x * (blockDim.x >> 5);
+  for (long long j = blockIdx.x * (long long)(blockDim.x >> 5) + (threadIdx.x >> 5); j < H.njob;
+       j += nw) {
+    const SolJob J = jobs[H.job0 + j];
+    const int act = (J.slot < 0 || J.l < rk[J.slot]) ? 1 : 0;
+    // a rank above the columns the solve reads would lose part of the block
+    if (lane == 0 && J.slot >= 0 && rk[J.slot] > J.lmax) atomicExch(err + blockIdx.y, 3);
+    if (lane == 0)
+      meta[H.pk0 + j] = make_int4(J.x, (act << 8) | ((int)J.kind << 9) | (J.ldw << 12), 0, 0);
+    T* dst = pack + (H.pk0 + j) * slot_elems;
+    for (int i = lane; i < J.n; i += 32) dst[i] = act ? ar[J.src + i] : (T)0;
+  }
+}
+
+// one thread issues the two bulk copies of the jobs [a, a + nj)
+template <class T>
+__device__ __forceinline__ void solve_prefetch(int a, int nj, long long pk0, const T* pack,
+                                               const int4* meta, int slot_elems, T* buf,
+                                               int4* mbuf, unsigned long long* bar) {
+  const unsigned bd = (unsigned)((long long)nj * slot_elems * sizeof(T));
+  const unsigned bm = (unsigned)(nj * sizeof(int4));
+  mbar_expect_tx(bar, bd + bm);
+  if (nj > 0) {
+    bulk_g2s(buf, pack + (pk0 + a) * slot_elems, bd, bar);
+    bulk_g2s(mbuf, meta + pk0 + a, bm, bar);
+  }
+}
+
+// Both triangular solves of an instance by its cluster of kCluster CTAs,
+// one leaf step after another.  A CTA's jobs of a step reach shared memory in
+// parts of jcap jobs (bulk copies, two buffers: the next part streams in
+// while the current one is used).  Each CTA owns a fixed share of the
+// low-rank columns and keeps their w in its own shared memory, every CTA
+// keeps the solutions of the last kRing leaves, and the partial sums of the
+// gathers and of the inverse product meet through distributed shared memory:
+// two cluster barriers per step.
+template <class T>
+__global__ void __launch_bounds__(kHThreads) k_hsolve_cl(const HInstDev* __restrict__ hi,
+                                                        const StepInfo* __restrict__ sinfo,
+                                                        const StepCta* __restrict__ scta,
+                                                        const T* __restrict__ pack,
+                                                        const int4* __restrict__ meta, T* har,
+                                                        int nrhs, int jmax, int slot_elems,
+                                                        int wcols, int* err, double* flops,
+                                                        unsigned long long* sprof) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int kSolveW = solve_w<T>();
+  constexpr int V = 128 * kSolveW;
+  unsigned long long* bar = reinterpret_cast<unsigned long long*>(smraw);   // [2]
+  T* colb = reinterpret_cast<T*>(smraw + 16);                              // [2][jmax][slot]
+  T* pr = colb + 2LL * jmax * slot_elems;   // [V] gather partial (read remotely)
+  T* px = pr + V;                           // [V] inverse partial (read remotely)
+  T* tmp = px + V;                          // [V] half sums
+  T* r = tmp + V;                           // [V] leaf right-hand side
+  T* bb = r + V;                            // [V] b of the leaf
+  T* xs = bb + V;                           // [V] x of the leaf
+  T* ring = xs + V;                         // [kRing][V] x of the last leaves
+  T* wl = ring + kRing * V;                 // [wcols][W] w of this CTA's columns
+  T* sx = wl + (long long)wcols * kSolveW;  // [jmax][W] scalars of the gathers
+  int4* mbb = reinterpret_cast<int4*>(sx + (long long)jmax * kSolveW);   // [2][jmax]
+  const unsigned crank = cluster_rank();
+  const unsigned cid = cluster_id();
+  const HInstDev H = hi[cid];
+  T* ar = har + H.arena;
+  const StepInfo* si = sinfo + H.st0;
+  const StepCta* sc = scta + H.st0 * kCluster;
+  const int jcap = H.jcap;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const long long ld = H.nd;
+  const int nst = H.nst;
+  const int nchunk = (nrhs + kSolveW - 1) / kSolveW;
+  const int total = nst * nchunk;
+  double fl = 0.0;
+  bool ok = true;
+  long long qfail = -1;   // part whose copy did not arrive in time
+  // optional phase timer (cluster 0, CTA 0): waits, A, barrier, B, barrier, C
+  const bool tp = sprof && cid == 0 && crank == 0 && tid == 0;
+  unsigned long long tq = 0;
+  auto tmark = [&](int k) {
+    if (!tp) return;
+    unsigned long long t1;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+    if (k >= 0) sprof[k] += t1 - tq;
+    tq = t1;
+  };
+  auto nparts = [&](const StepCta& C) { return max(1, (C.a3 - C.a0 + jcap - 1) / jcap); };
+  auto prefetch = [&](const StepCta& C, int k, int b) {
+    const int a = C.a0 + k * jcap;
+    const int nj = max(0, min(C.a3 - a, jcap));
+    solve_prefetch(a, nj, H.pk0, pack, meta, slot_elems, colb + (long long)b * jmax * slot_elems,
+                   mbb + b * jmax, &bar[b]);
+  };
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (tid == 0 && total > 0) prefetch(sc[crank], 0, 0);
+  // parts are begun in the order (step, k); qn counts them; the part begun
+  // last is resident in buffer cb
+  long long qn = 0;
+  int ck = -1, cb = 0;
+  auto begin = [&](int g, const StepCta& C, int k) {
+    __syncthreads();   // the buffer about to be refilled is no longer read
+    const int b = (int)(qn & 1);
+    if (ok) {
+      long long spins = 0;
+      while (!mbar_try_wait(&bar[b], (unsigned)((qn >> 1) & 1))) {
+        if (++spins > (1LL << 24)) {
+          ok = false;
+          qfail = qn;
+          break;
+        }
+      }
+    }
+    if (tid == 0 && ok) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      if (k + 1 < nparts(C)) prefetch(C, k + 1, b ^ 1);
+      else if (g + 1 < total) prefetch(sc[(long long)((g + 1) % nst) * kCluster + crank], 0, b ^ 1);
+    }
+    ck = k;
+    cb = b;
+    ++qn;
+  };
+  for (int g = 0; g < total; ++g) {
+    const int s = g % nst, c0 = (g / nst) * kSolveW;
+    const int nc = min(kSolveW, nrhs - c0);
+    T* b = ar + H.rhs_off + (long long)c0 * ld;
+    if (s == 0) {   // a new chunk of right-hand sides: clear this CTA's w
+      __syncthreads();
+      for (int t = tid; t < wcols * kSolveW; t += blockDim.x) wl[t] = (T)0;
+    }
+    tmark(-1);
+    const StepInfo S = si[s];
+    const StepCta C = sc[(long long)s * kCluster + crank];
+    const int n = S.n;
+    const int i = tid & 127, h = tid >> 7;
+    // b of the leaf (read now, used after the first barrier)
+    for (int t = tid; t < n * nc; t += blockDim.x) {
+      const int ii = t % n, c = t / n;
+      bb[c * 128 + ii] = b[S.d0 + ii + c * ld];
+    }
+    begin(g, C, 0);
+    tmark(0);
+    // A: gathers, summed over this CTA's columns
+    T acc[kSolveW];
+#pragma unroll
+    for (int c = 0; c < kSolveW; ++c) acc[c] = (T)0;
+    for (int x = C.a0; x < C.a1;) {
+      const int k = (x - C.a0) / jcap;
+      if (k != ck) begin(g, C, k);
+      const int pa = C.a0 + k * jcap, e = min(C.a1, pa + jcap);
+      const T* buf = colb + (long long)cb * jmax * slot_elems;
+      const int4* mb = mbb + cb * jmax;
+      for (int t = tid; t < (e - x) * kSolveW; t += blockDim.x) {
+        const int jl = x - pa + t / kSolveW, c = t % kSolveW;
+        const int4 m = mb[jl];
+        const int f = m.y, kind = (f >> 9) & 7;
+        T v = (T)0;
+        if (c < nc && ((f >> 8) & 1)) {
+          if (kind == 0) v = ring[(m.x >> 7) * V + (m.x & 127) + c * 128];
+          else if (kind == 4) v = b[m.x + c * ld];
+          else v = wl[m.x * kSolveW + c];
+        }
+        sx[t] = v;
+      }
+      __syncthreads();
+      if (i < n)
+        for (int jl = h; jl < e - x; jl += 2) {
+          const T a = buf[(long long)(x - pa + jl) * slot_elems + i];
+#pragma unroll
+          for (int c = 0; c < kSolveW; ++c) acc[c] += a * sx[jl * kSolveW + c];
+        }
+      if (tid == 0) fl += 2.0 * n * nc * (e - x);
+      __syncthreads();
+      x = e;
+    }
+    if (h == 1)
+#pragma unroll
+      for (int c = 0; c < kSolveW; ++c) tmp[c * 128 + i] = acc[c];
+    __syncthreads();
+    if (h == 0)
+#pragma unroll
+      for (int c = 0; c < kSolveW; ++c) pr[c * 128 + i] = acc[c] + tmp[c * 128 + i];
+    tmark(1);
+    cluster_barrier();
+    tmark(2);
+    // B: r = b - sum of the partials; partial product of the inverse columns
+    for (int t = tid; t < n * nc; t += blockDim.x) {
+      const int ii = t % n, c = t / n;
+      T v = bb[c * 128 + ii];
+      for (unsigned qq = 0; qq < kCluster; ++qq) v -= ld_dsmem(&pr[c * 128 + ii], qq);
+      r[c * 128 + ii] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int c = 0; c < kSolveW; ++c) acc[c] = (T)0;
+    for (int x = C.a1; x < C.a2;) {
+      const int k = (x - C.a0) / jcap;
+      if (k != ck) begin(g, C, k);
+      const int pa = C.a0 + k * jcap, e = min(C.a2, pa + jcap);
+      const T* buf = colb + (long long)cb * jmax * slot_elems;
+      const int4* mb = mbb + cb * jmax;
+      if (i < n)
+        for (int jl = x - pa + h; jl < e - pa; jl += 2) {
+          const T a = buf[(long long)jl * slot_elems + i];
+          const int kk = mb[jl].x;
+#pragma unroll
+          for (int c = 0; c < kSolveW; ++c) acc[c] += a * r[c * 128 + kk];
+        }
+      if (tid == 0) fl += 2.0 * n * nc * (e - x);
+      x = e;
+    }
+    if (h == 1)
+#pragma unroll
+      for (int c = 0; c < kSolveW; ++c) tmp[c * 128 + i] = acc[c];
+    __syncthreads();
+    if (h == 0)
+#pragma unroll
+      for (int c = 0; c < kSolveW; ++c) px[c * 128 + i] = acc[c] + tmp[c * 128 + i];
+    tmark(3);
+    cluster_barrier();
+    tmark(4);
+    // C: x = sum of the partials (every CTA); w += V^T x over this CTA's columns
+    T* rg = ring + (long long)S.ring * V;
+    for (int t = tid; t < n * nc; t += blockDim.x) {
+      const int ii = t % n, c = t / n;
+      T v = (T)0;
+      for (unsigned qq = 0; qq < kCluster; ++qq) v += ld_dsmem(&px[c * 128 + ii], qq);
+      xs[c * 128 + ii] = v;
+      rg[c * 128 + ii] = v;
+      if (crank == 0) b[S.d0 + ii + c * ld] = v;
+    }
+    __syncthreads();
+    for (int x = C.a2; x < C.a3;) {
+      const int k = (x - C.a0) / jcap;
+      if (k != ck) begin(g, C, k);
+      const int pa = C.a0 + k * jcap, e = min(C.a3, pa + jcap);
+      const T* buf = colb + (long long)cb * jmax * slot_elems;
+      const int4* mb = mbb + cb * jmax;
+      for (int jl = x - pa + warp; jl < e - pa; jl += (int)(blockDim.x >> 5)) {
+        const int4 m = mb[jl];
+        if (!((m.y >> 8) & 1)) continue;
+        const T* col = buf + (long long)jl * slot_elems;
+        T pa_[kSolveW];
+#pragma unroll
+        for (int c = 0; c < kSolveW; ++c) pa_[c] = (T)0;
+        for (int ii = lane; ii < n; ii += 32) {
+          const T a = col[ii];
+#pragma unroll
+          for (int c = 0; c < kSolveW; ++c) pa_[c] += a * xs[c * 128 + ii];
+        }
+#pragma unroll
+        for (int c = 0; c < kSolveW; ++c)
+          if (c < nc)
+            for (int o = 16; o > 0; o >>= 1) pa_[c] += __shfl_xor_sync(0xffffffffu, pa_[c], o);
+        if (lane == 0)
+          for (int c = 0; c < nc; ++c) wl[m.x * kSolveW + c] += pa_[c];
+      }
+      if (tid == 0) fl += 2.0 * n * nc * (e - x);
+      x = e;
+    }
+    // every part of the step is begun (keeps the prefetch chain in order)
+    for (int k = ck + 1; k < nparts(C); ++k) begin(g, C, k);
+    tmark(5);
+  }
+  // no CTA may leave while another can still read its shared memory
+  cluster_barrier();
+  if (!ok) {
+    // a copy never arrived: flag it and give the copies in flight a bounded
+    // time to land before the shared memory is released
+    if (tid == 0) atomicExch(err + cid, 2);
+    if (qfail >= 0) {
+      long long spins = 0;
+      while (!mbar_try_wait(&bar[qfail & 1], (unsigned)((qfail >> 1) & 1)) && ++spins < (1LL << 20)) {
+      }
+    }
+  }
+  if (tid == 0) flops[((size_t)cid * kCluster + crank) * 2 + 1] += fl;
 }
 
 // rhs area <- D r (element-major FP64 -> T); rank slot n_slots <- nrhs
@@ -1254,7 +1835,9 @@ struct PlanBundle {
   std::vector<DenseDev> dense;
   std::vector<LRPairDev> pairs;
   std::vector<SlotDev> slots;
+  LeafSolve ls;                  // tables of the leaf solves
 };
+
 
 }  // namespace hf
 
@@ -1274,6 +1857,16 @@ struct hfsem_factor_s : public hf::Precond {
   hf::DevBuf<hf::SlotDev> d_slots;
   hf::DevBuf<hf::DenseDev> d_dense;
   hf::DevBuf<hf::LRPairDev> d_pairs;
+  hf::DevBuf<hf::StepInfo> d_steps;   // leaf solve tables
+  hf::DevBuf<hf::StepCta> d_step_cta;
+  hf::DevBuf<hf::SolJob> d_jobs;
+  hf::DevBuf<unsigned char> d_pack;    // solve pack: column segments in job order
+  hf::DevBuf<int4> d_meta;             // and the jobs' records
+  int sol_jmax = 1, sol_slot = 1, sol_wcols = 1;
+  hf::DevBuf<unsigned long long> d_sprof;   // HFSEM_PROFILE=2: leaf-solve phase times
+  size_t sol_smem = 0;
+  void run_leaf_solve(int nrhs);
+  void run_pack();
   hf::DevBuf<int> d_ranks, d_err;
   hf::DevBuf<double> d_D;
   hf::DevBuf<unsigned char> d_arena;
@@ -1281,7 +1874,10 @@ struct hfsem_factor_s : public hf::Precond {
   long long total_ops = 0, total_sops = 0;
   hf::DevBuf<unsigned long long> d_prof;   // HFSEM_PROFILE=1: time per op type
   hf::DevBuf<double> d_flops;               // per instance: factor / solve flops
+  hf::DevBuf<unsigned long long> d_wprof;   // HFSEM_PROFILE=2: per-wave records
+  int wstride = 0;
   void report(const char* what);
+  void report_waves(const char* what, int which);
   void apply(int nrhs, const double* r_em, double* y_em) override;
   void collect_flops();
   void run_prog(int which);
@@ -1338,6 +1934,13 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
     f->R = opt.R;
     const bool fp32 = f->precision == HFSEM_PREC_MIXED;
     f->tsize = fp32 ? sizeof(float) : sizeof(double);
+    size_t sol_budget = 0;   // shared memory the leaf solve may take
+    {
+      int dev = 0, optin = 0;
+      HF_CHECK(cudaGetDevice(&dev));
+      HF_CHECK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+      sol_budget = (size_t)optin - 1024;
+    }
     const int max_leaf = fp32 ? 128 : 96;
     std::map<std::string, std::shared_ptr<PlanBundle>> cache;
     const int ni = s->n_inst;
@@ -1387,9 +1990,26 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
           pb->pairs.push_back(LRPairDev{b.slot, mi->second, ct.e0, ct.e1, cs.e0, cs.e1, ct.lo,
                                         ct.hi, cs.lo, cs.hi, ct.d0, b.m, cs.d0, b.n});
         }
+        build_leaf_solve(pb->plan, kCluster, sol_budget, (int)f->tsize,
+                         fp32 ? solve_w<float>() : solve_w<double>(), pb->ls);
         it = cache.emplace(key, pb).first;
       }
       f->plans[i] = it->second;
+    }
+    // one solve kernel serves every plan: cut the parts of each plan for the
+    // largest leaf and the most owned low-rank columns of all of them
+    {
+      std::vector<PlanBundle*> bs;
+      for (auto& kv : cache) bs.push_back(kv.second.get());
+      int nm = 1, wc = 1;
+      for (PlanBundle* pb : bs) {
+        nm = std::max(nm, pb->ls.nmax);
+        wc = std::max(wc, pb->ls.wcols);
+      }
+      for (PlanBundle* pb : bs)
+        if (pb->ls.nmax < nm || pb->ls.wcols < wc)
+          build_leaf_solve(pb->plan, kCluster, sol_budget, (int)f->tsize,
+                           fp32 ? solve_w<float>() : solve_w<double>(), pb->ls, nm, wc);
     }
     // concatenate tables
     std::vector<HOp> ops;
@@ -1398,7 +2018,12 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
     std::vector<DenseDev> dense;
     std::vector<LRPairDev> pairs;
     std::map<const PlanBundle*, std::array<long long, 7>> placed;
-    long long arena = 0, rk = 0, doff = 0;
+    std::vector<StepInfo> steps;
+    std::vector<StepCta> step_cta;
+    std::vector<SolJob> jobs;
+    std::map<const PlanBundle*, std::array<long long, 2>> placed_leaf;
+    int jmax = 1, nmax = 1, wcols = 1;
+    long long arena = 0, rk = 0, doff = 0, pkoff = 0;
     size_t smem = 0;
     for (int i = 0; i < ni; ++i) {
       const PlanBundle* pb = f->plans[i].get();
@@ -1417,6 +2042,13 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
         pairs.insert(pairs.end(), pb->pairs.begin(), pb->pairs.end());
         pi = placed.emplace(pb, a).first;
         smem = std::max(smem, prog_smem(pb->plan, f->tsize));
+        placed_leaf[pb] = {(long long)steps.size(), (long long)jobs.size()};
+        steps.insert(steps.end(), pb->ls.steps.begin(), pb->ls.steps.end());
+        step_cta.insert(step_cta.end(), pb->ls.step_cta.begin(), pb->ls.step_cta.end());
+        jobs.insert(jobs.end(), pb->ls.jobs.begin(), pb->ls.jobs.end());
+        jmax = std::max(jmax, pb->ls.jcap);
+        wcols = std::max(wcols, pb->ls.wcols);
+        nmax = std::max(nmax, pb->ls.nmax);
       }
       HInstDev& H = f->hidev[i];
       std::memset(&H, 0, sizeof(H));
@@ -1447,10 +2079,33 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
       doff += s->ih[i].Nd;
       H.sys_inst = i;
       H.R = opt.R;
+      H.nd = s->ih[i].Nd;
+      H.st0 = placed_leaf[pb][0];
+      H.job0 = placed_leaf[pb][1];
+      H.jcap = pb->ls.jcap;
+      H.nst = (int)pb->ls.steps.size();
+      H.njob = (int)pb->ls.jobs.size();
+      H.pk0 = pkoff;
+      pkoff += (long long)pb->ls.jobs.size();
       f->total_ops += H.nops;
       f->total_sops += H.nsops;
     }
-    if (smem > 227 * 1024) throw Error(HFSEM_ERR_UNSUPPORTED, "H-LU kernel needs too much shared memory");
+    // every CTA of the cluster sits alone on its SM (register bound), so the
+    // kernel takes all the shared memory it may have: the recompression
+    // stages its tall factors in what the other ops leave free
+    {
+      int dev = 0, optin = 0;
+      HF_CHECK(cudaGetDevice(&dev));
+      HF_CHECK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+      cudaFuncAttributes fa;
+      if (fp32)
+        HF_CHECK(cudaFuncGetAttributes(&fa, k_hprog<float>));
+      else
+        HF_CHECK(cudaFuncGetAttributes(&fa, k_hprog<double>));
+      const size_t avail = (size_t)optin - fa.sharedSizeBytes - 1024;
+      if (smem > avail) throw Error(HFSEM_ERR_UNSUPPORTED, "H-LU kernel needs too much shared memory");
+      smem = avail & ~(size_t)15;
+    }
     f->smem = smem;
     f->d_hi.alloc(ni);
     HF_CHECK(cudaMemcpyAsync(f->d_hi.p, f->hidev.data(), ni * sizeof(HInstDev), cudaMemcpyHostToDevice, s->st));
@@ -1469,6 +2124,35 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
     f->d_pairs.alloc(std::max<size_t>(pairs.size(), 1));
     if (!pairs.empty())
       HF_CHECK(cudaMemcpyAsync(f->d_pairs.p, pairs.data(), pairs.size() * sizeof(LRPairDev), cudaMemcpyHostToDevice, s->st));
+    f->d_steps.alloc(std::max<size_t>(steps.size(), 1));
+    if (!steps.empty())
+      HF_CHECK(cudaMemcpyAsync(f->d_steps.p, steps.data(), steps.size() * sizeof(StepInfo), cudaMemcpyHostToDevice, s->st));
+    f->d_step_cta.alloc(std::max<size_t>(step_cta.size(), 1));
+    if (!step_cta.empty())
+      HF_CHECK(cudaMemcpyAsync(f->d_step_cta.p, step_cta.data(), step_cta.size() * sizeof(StepCta), cudaMemcpyHostToDevice, s->st));
+    f->d_jobs.alloc(std::max<size_t>(jobs.size(), 1));
+    if (!jobs.empty())
+      HF_CHECK(cudaMemcpyAsync(f->d_jobs.p, jobs.data(), jobs.size() * sizeof(SolJob), cudaMemcpyHostToDevice, s->st));
+    // leaf-solve shared memory: two buffers of jmax column slots, seven 128 x W
+    // vectors, the ring, the CTA's w columns, the gather scalars and two
+    // buffers of job records
+    f->sol_jmax = jmax;
+    f->sol_slot = (int)(((size_t)nmax * f->tsize + 15) / 16 * 16 / f->tsize);
+    f->sol_wcols = wcols;
+    const int sw = fp32 ? solve_w<float>() : solve_w<double>();
+    f->sol_smem = solve_smem(jmax, nmax, wcols, (int)f->tsize, sw);
+    f->d_pack.alloc((size_t)std::max<long long>(pkoff, 1) * f->sol_slot * f->tsize);
+    f->d_meta.alloc((size_t)std::max<long long>(pkoff, 1));
+    {
+      if (f->sol_smem > sol_budget)
+        throw Error(HFSEM_ERR_UNSUPPORTED, "leaf solve needs too much shared memory");
+      if (fp32)
+        HF_CHECK(cudaFuncSetAttribute((const void*)k_hsolve_cl<float>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f->sol_smem));
+      else
+        HF_CHECK(cudaFuncSetAttribute((const void*)k_hsolve_cl<double>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f->sol_smem));
+    }
     f->d_ranks.alloc(std::max<long long>(rk, 1));
     HF_CHECK(cudaMemsetAsync(f->d_ranks.p, 0, std::max<long long>(rk, 1) * sizeof(int), s->st));
     f->d_err.alloc(ni);
@@ -1513,7 +2197,10 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
       set_prog_smem<double>(smem);
     }
     if (prof) cudaEventRecord(ev[2], s->st);
-    if (!f->build_only) f->run_prog(0);
+    if (!f->build_only) {
+      f->run_prog(0);
+      f->run_pack();
+    }
     if (prof) cudaEventRecord(ev[3], s->st);
     HF_CHECK(cudaStreamSynchronize(s->st));
     if (prof) {
@@ -1531,11 +2218,14 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
               p0.dense_blocks.size(), p0.lr_blocks.size(), p0.fac.size(), p0.sol.size(), p0.leaf_max,
               p0.kconcat_max, p0.hh_lr, p0.arena);
       f->report("factorisation");
+      f->report_waves("factorisation", 0);
     }
     std::vector<int> err(ni);
     HF_CHECK(cudaMemcpy(err.data(), f->d_err.p, ni * sizeof(int), cudaMemcpyDeviceToHost));
-    for (int e : err)
+    for (int e : err) {
+      if (e == 3) throw Error(HFSEM_ERR_DEVICE, "low-rank block above the rank bound of the solves");
       if (e) throw Error(HFSEM_ERR_BREAKDOWN, "zero or non-finite pivot in an H-LU leaf");
+    }
   } catch (...) {
     delete f;
     throw;
@@ -1574,6 +2264,64 @@ void hfsem_factor_s::report(const char* what) {
   cudaMemset(d_prof.p, 0, d_prof.n * sizeof(unsigned long long));
 }
 
+// Critical-path view of one program run, for the instance whose run took
+// longest: per wave the CTA with the most busy time decides, and the type
+// of its longest op takes the wave's time.
+void hfsem_factor_s::report_waves(const char* what, int which) {
+  if (!d_wprof.p) return;
+  const int rec = 1 + 3 * hf::kCluster;
+  std::vector<unsigned long long> h(d_wprof.n);
+  cudaMemcpy(h.data(), d_wprof.p, h.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
+  int worst = 0;
+  double wworst = -1;
+  for (size_t c = 0; c < hidev.size(); ++c) {
+    const int nw = which ? hidev[c].nsw : hidev[c].nfw;
+    double wall = 0;
+    for (int w = 0; w < nw; ++w) wall += h[((size_t)c * wstride + w) * rec];
+    if (wall > wworst) {
+      wworst = wall;
+      worst = (int)c;
+    }
+  }
+  const hf::HPlan& P = plans[worst]->plan;
+  const std::vector<hf::HOp>& prog = which ? P.sol : P.fac;
+  const int nw = which ? hidev[worst].nsw : hidev[worst].nfw;
+  static const char* names[16] = {"?", "GEMM", "GETRF_INV", "TRMM_L", "TRMM_R", "APPEND",
+                                  "TRUNC", "ZERO", "AXPY", "?", "?", "?", "?", "?", "?", "?"};
+  double wall = 0, crit = 0, sumbusy = 0, bytype[16] = {0}, ntype[16] = {0};
+  std::map<std::string, std::pair<double, int>> shapes;
+  for (int w = 0; w < nw; ++w) {
+    const unsigned long long* q = &h[((size_t)worst * wstride + w) * rec];
+    wall += q[0];
+    int cm = 0;
+    for (int k = 0; k < hf::kCluster; ++k) {
+      sumbusy += q[1 + 3 * k];
+      if (q[1 + 3 * k] > q[1 + 3 * cm]) cm = k;
+    }
+    crit += q[1 + 3 * cm];
+    const size_t oi = (size_t)q[3 + 3 * cm];
+    const hf::HOp& o = prog[std::min(oi, prog.size() - 1)];
+    bytype[o.type & 15] += q[1 + 3 * cm];
+    ntype[o.type & 15] += 1;
+    char key[96];
+    snprintf(key, sizeof(key), "%-9s C %4dx%-4d A.c %4d  wave ops %4d", names[o.type & 15], o.C.r,
+             o.C.c, o.A.c, (which ? P.sol_waves : P.fac_waves)[w + 1] - (which ? P.sol_waves : P.fac_waves)[w]);
+    auto& e = shapes[key];
+    e.first += q[1 + 3 * cm];
+    e.second += 1;
+  }
+  fprintf(stderr, "[hfsem waves] %s (instance %d): %d waves  wall %.3f ms  max-busy %.3f ms  mean CTA busy %.3f ms\n",
+          what, worst, nw, wall * 1e-6, crit * 1e-6, sumbusy * 1e-6 / hf::kCluster);
+  for (int t = 0; t < 16; ++t)
+    if (ntype[t] > 0)
+      fprintf(stderr, "  waves led by %-10s %6.0f  %.3f ms\n", names[t], ntype[t], bytype[t] * 1e-6);
+  std::vector<std::pair<double, std::string>> top;
+  for (auto& kv : shapes) top.push_back({kv.second.first, kv.first + "  x" + std::to_string(kv.second.second)});
+  std::sort(top.rbegin(), top.rend());
+  for (size_t t = 0; t < top.size() && t < 12; ++t)
+    fprintf(stderr, "    %8.3f ms  %s\n", top[t].first * 1e-6, top[t].second.c_str());
+}
+
 void hfsem_factor_s::run_prog(int which) {
   if (!d_prof.p && getenv("HFSEM_PROFILE")) {
     d_prof.alloc((size_t)sys->n_inst * 32);
@@ -1583,7 +2331,16 @@ void hfsem_factor_s::run_prog(int which) {
     d_flops.alloc((size_t)sys->n_inst * hf::kCluster * 2);
     cudaMemsetAsync(d_flops.p, 0, d_flops.n * sizeof(double), sys->st);
   }
-  hf::HProgArgs a{d_hi.p, d_waves.p, d_ops.p, d_slots.p, d_ranks.p, d_err.p, tol, d_prof.p, d_flops.p};
+  const char* pe = getenv("HFSEM_PROFILE");
+  if (!d_wprof.p && pe && atoi(pe) >= 2) {
+    int nwmax = 1;
+    for (auto& H : hidev) nwmax = std::max(nwmax, std::max(H.nfw, H.nsw));
+    wstride = nwmax;
+    d_wprof.alloc((size_t)nwmax * hidev.size() * (1 + 3 * hf::kCluster));
+  }
+  if (d_wprof.p) cudaMemsetAsync(d_wprof.p, 0, d_wprof.n * sizeof(unsigned long long), sys->st);
+  hf::HProgArgs a{d_hi.p, d_waves.p, d_ops.p, d_slots.p, d_ranks.p, d_err.p, tol, d_prof.p, d_flops.p,
+                  d_wprof.p, wstride, (long long)(smem / tsize) - 8};
   hf::Tick tk(sys->st, which ? "hlu_solve" : "hlu_factor");
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(sys->n_inst * hf::kCluster));
@@ -1604,9 +2361,70 @@ void hfsem_factor_s::run_prog(int which) {
   HF_LAUNCH_CHECK();
 }
 
+void hfsem_factor_s::run_pack() {
+  hf::Tick tk(sys->st, "solve_pack");
+  dim3 g(128, sys->n_inst);
+  if (tsize == sizeof(float))
+    hf::k_solve_pack<float><<<g, 256, 0, sys->st>>>(d_hi.p, d_jobs.p, reinterpret_cast<const float*>(d_arena.p),
+                                                    d_ranks.p, reinterpret_cast<float*>(d_pack.p), d_meta.p, sol_slot,
+                                                    d_err.p);
+  else
+    hf::k_solve_pack<double><<<g, 256, 0, sys->st>>>(d_hi.p, d_jobs.p, reinterpret_cast<const double*>(d_arena.p),
+                                                     d_ranks.p, reinterpret_cast<double*>(d_pack.p), d_meta.p, sol_slot,
+                                                     d_err.p);
+  HF_LAUNCH_CHECK();
+}
+
+void hfsem_factor_s::run_leaf_solve(int nrhs) {
+  const char* pe = getenv("HFSEM_PROFILE");
+  if (!d_sprof.p && pe && atoi(pe) >= 2) {
+    d_sprof.alloc(8);
+    cudaMemset(d_sprof.p, 0, 8 * sizeof(unsigned long long));
+  }
+  hf::Tick tk(sys->st, "hlu_solve");
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(sys->n_inst * hf::kCluster));
+  cfg.blockDim = dim3(hf::kHThreads);
+  cfg.dynamicSmemBytes = sol_smem;
+  cfg.stream = sys->st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = hf::kCluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (tsize == sizeof(float))
+    HF_CHECK(cudaLaunchKernelEx(&cfg, hf::k_hsolve_cl<float>, (const hf::HInstDev*)d_hi.p,
+                                (const hf::StepInfo*)d_steps.p, (const hf::StepCta*)d_step_cta.p,
+                                (const float*)d_pack.p, (const int4*)d_meta.p,
+                                reinterpret_cast<float*>(d_arena.p), nrhs, sol_jmax, sol_slot, sol_wcols,
+                                d_err.p, d_flops.p, d_sprof.p));
+  else
+    HF_CHECK(cudaLaunchKernelEx(&cfg, hf::k_hsolve_cl<double>, (const hf::HInstDev*)d_hi.p,
+                                (const hf::StepInfo*)d_steps.p, (const hf::StepCta*)d_step_cta.p,
+                                (const double*)d_pack.p, (const int4*)d_meta.p,
+                                reinterpret_cast<double*>(d_arena.p), nrhs, sol_jmax, sol_slot, sol_wcols,
+                                d_err.p, d_flops.p, d_sprof.p));
+  HF_LAUNCH_CHECK();
+  if (d_sprof.p) {
+    unsigned long long h[8];
+    cudaMemcpy(h, d_sprof.p, sizeof(h), cudaMemcpyDeviceToHost);
+    static const char* nm[7] = {"wait", "gather", "barrier1", "inverse", "barrier2", "scatter", "barrier3"};
+    fprintf(stderr, "[hfsem leaf solve] instance 0, CTA 0 (ms):");
+    for (int k = 0; k < 7; ++k) fprintf(stderr, " %s %.3f", nm[k], h[k] * 1e-6);
+    fprintf(stderr, "\n");
+    cudaMemset(d_sprof.p, 0, sizeof(h));
+  }
+}
+
 void hfsem_factor_s::apply(int nrhs, const double* r_em, double* y_em) {
   if (build_only) throw hf::Error(HFSEM_ERR_INVALID_ARG, "factor was built with build_only");
   if (nrhs > 64) throw hf::Error(HFSEM_ERR_INVALID_ARG, "nrhs > 64");
+  if (!d_flops.p) {
+    d_flops.alloc((size_t)sys->n_inst * hf::kCluster * 2);
+    cudaMemsetAsync(d_flops.p, 0, d_flops.n * sizeof(double), sys->st);
+  }
   int maxnd = 1;
   for (auto& I : sys->ih) maxnd = std::max(maxnd, I.Nd);
   dim3 g(std::min(1024, (maxnd * nrhs + 255) / 256), sys->n_inst);
@@ -1614,17 +2432,13 @@ void hfsem_factor_s::apply(int nrhs, const double* r_em, double* y_em) {
     float* ar = reinterpret_cast<float*>(d_arena.p);
     hf::k_hsolve_in<float><<<g, 256, 0, sys->st>>>(d_hi.p, sys->d_inst.p, r_em, d_D.p, ar, d_ranks.p, nrhs);
     HF_LAUNCH_CHECK();
-    run_prog(1);
-    if (d_prof.p) {
-      cudaStreamSynchronize(sys->st);
-      report("H-solve apply");
-    }
+    run_leaf_solve(nrhs);
     hf::k_hsolve_out<float><<<g, 256, 0, sys->st>>>(d_hi.p, sys->d_inst.p, d_D.p, ar, y_em, nrhs);
   } else {
     double* ar = reinterpret_cast<double*>(d_arena.p);
     hf::k_hsolve_in<double><<<g, 256, 0, sys->st>>>(d_hi.p, sys->d_inst.p, r_em, d_D.p, ar, d_ranks.p, nrhs);
     HF_LAUNCH_CHECK();
-    run_prog(1);
+    run_leaf_solve(nrhs);
     hf::k_hsolve_out<double><<<g, 256, 0, sys->st>>>(d_hi.p, sys->d_inst.p, d_D.p, ar, y_em, nrhs);
   }
   HF_LAUNCH_CHECK();

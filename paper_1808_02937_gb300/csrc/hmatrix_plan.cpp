@@ -16,6 +16,7 @@
 // triangular multiplies with the inverted diagonal leaves, append and
 // truncate), which the device interpreter runs in order.
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <map>
 #include <string>
@@ -510,6 +511,7 @@ void make_plan(const InstHost& I, const PlanOpts& o, HPlan& p) {
   p.P = I.P;
   p.Nd = I.Nd;
   p.nrhs_max = o.nrhs_max;
+  p.R = o.R;
   Builder b(I, o, p);
   int root = b.cluster(0, I.N);
   b.block(root, root);
@@ -753,4 +755,170 @@ void schedule_program(const HPlan& p, std::vector<HOp>& prog, std::vector<int>& 
   for (size_t i = 0; i < out.size(); ++i) prog[pos[lv[i] - 1]++] = out[i];
 }
 
+}  // namespace hf
+
+namespace hf {
+// Tables of the leaf solves: the leaf clusters in the order of their
+// unknowns; for each leaf and direction the column jobs of the blocks in its
+// block row (left of the diagonal forward, right of it backward), of its
+// inverse diagonal block, and of the low-rank blocks whose column cluster
+// holds it (the leaf's rows of V).  Column l of low-rank slot k belongs to
+// CTA (k + l) mod ncta for both its gathers and its scatters; dense and
+// inverse columns go to the CTA with the fewest jobs in the step so far.
+size_t solve_smem(int jmax, int nmax, int wcols, int ts, int sw) {
+  // mbarriers, two buffers of jmax column slots (nmax entries rounded to 16
+  // bytes), six 128 x sw vectors and the ring, the CTA's w columns, the
+  // gather scalars, two buffers of 16-byte job records
+  const size_t slot = ((size_t)nmax * ts + 15) / 16 * 16;
+  return 16 + 2 * (size_t)jmax * slot + (size_t)(6 + kRing) * 128 * sw * ts +
+         (size_t)wcols * sw * ts + (size_t)jmax * sw * ts + 2 * (size_t)jmax * 16;
+}
+
+void build_leaf_solve(const HPlan& p, int ncta, size_t budget, int ts, int sw, LeafSolve& pb,
+                      int nmax_min, int wcols_min) {
+  std::vector<int> lf;
+  for (size_t c = 0; c < p.C.size(); ++c)
+    if (p.C[c].kid[0] < 0 && p.C[c].d1 > p.C[c].d0) lf.push_back((int)c);
+  std::sort(lf.begin(), lf.end(), [&](int a, int b) { return p.C[a].d0 < p.C[b].d0; });
+  const int nl = (int)lf.size();
+  std::vector<long long> inv(p.C.size(), -1);
+  for (const Block& b : p.B)
+    if (b.type == B_DENSE && b.t == b.s) inv[b.t] = b.inv;
+  // a factored low-rank block holds its Taylor rank R or a rank <= kmax after
+  // recompression (every updated block is recompressed before it is used),
+  // so columns from max(R, kmax) on are never active in the solves
+  auto lmax = [&](const Block& b) { return std::min(b.kcap, std::max(p.R, b.kmax)); };
+  // owner CTA and local w column of every low-rank column
+  std::vector<std::vector<int>> wloc(p.n_slots);
+  std::vector<int> wcnt(ncta, 0);
+  for (int sl = 0; sl < p.n_slots; ++sl) {
+    const Block& b = p.B[p.lr_blocks[sl]];
+    wloc[sl].resize(lmax(b));
+    for (int l = 0; l < lmax(b); ++l) wloc[sl][l] = wcnt[(sl + l) % ncta]++;
+  }
+  pb.wcols = 1;
+  for (int c = 0; c < ncta; ++c) pb.wcols = std::max(pb.wcols, wcnt[c]);
+  auto leaves_in = [&](int c, int& q0, int& q1) {
+    const int d0 = p.C[c].d0, d1 = p.C[c].d1;
+    q0 = (int)(std::lower_bound(lf.begin(), lf.end(), d0,
+                                [&](int a, int v) { return p.C[a].d0 < v; }) - lf.begin());
+    q1 = q0;
+    while (q1 < nl && p.C[lf[q1]].d1 <= d1) ++q1;
+  };
+  auto leaf_of = [&](int d) {   // leaf holding unknown d
+    int q = (int)(std::upper_bound(lf.begin(), lf.end(), d,
+                                   [&](int v, int a) { return v < p.C[a].d0; }) - lf.begin()) - 1;
+    return q;
+  };
+  // per leaf and direction: gather and scatter jobs, with their owner (-1: free)
+  struct OJ {
+    SolJob j;
+    int owner;
+  };
+  std::vector<std::vector<OJ>> gat[2], sca[2];
+  for (int d = 0; d < 2; ++d) {
+    gat[d].assign(nl, {});
+    sca[d].assign(nl, {});
+  }
+  for (const Block& b : p.B) {
+    if (b.m == 0 || b.n == 0 || b.t == b.s) continue;
+    if (b.type != B_DENSE && b.type != B_LR) continue;
+    const Cluster &ct = p.C[b.t], &cs = p.C[b.s];
+    const int d = (cs.d1 <= ct.d0) ? 0 : 1;   // block of L (forward) or of U (backward)
+    int q0, q1;
+    leaves_in(b.t, q0, q1);
+    for (int q = q0; q < q1; ++q) {
+      const long long ro = p.C[lf[q]].d0 - ct.d0;
+      const int nq = p.C[lf[q]].d1 - p.C[lf[q]].d0;
+      if (b.type == B_DENSE) {
+        for (int k = 0; k < b.n; ++k) {
+          const int row = cs.d0 + k, qs = leaf_of(row);
+          const int dist = d == 0 ? q - qs : qs - q;
+          SolJob J{b.off + ro + (long long)k * b.m, row, -1, 0, 4, 0, nq, 0};
+          if (dist >= 1 && dist <= kRing) {
+            J.kind = 0;
+            J.x = (qs % kRing) * 128 + (row - p.C[lf[qs]].d0);
+          }
+          gat[d][q].push_back({J, -1});
+        }
+      } else {
+        for (int l = 0; l < lmax(b); ++l)
+          gat[d][q].push_back({SolJob{b.off + ro + (long long)l * b.m, wloc[b.slot][l], b.slot,
+                                      (short)l, 1, 0, nq, lmax(b)},
+                               (b.slot + l) % ncta});
+      }
+    }
+    if (b.type == B_LR) {
+      leaves_in(b.s, q0, q1);
+      const long long v0 = b.off + (long long)b.m * b.kcap;
+      for (int q = q0; q < q1; ++q) {
+        const long long ro = p.C[lf[q]].d0 - cs.d0;
+        const int nq = p.C[lf[q]].d1 - p.C[lf[q]].d0;
+        for (int l = 0; l < lmax(b); ++l)
+          sca[d][q].push_back({SolJob{v0 + ro + (long long)l * b.n, wloc[b.slot][l], b.slot,
+                                      (short)l, 3, 0, nq, lmax(b)},
+                               (b.slot + l) % ncta});
+      }
+    }
+  }
+  pb.steps.clear();
+  pb.step_cta.clear();
+  pb.jobs.clear();
+  pb.nmax = 1;
+  for (int q = 0; q < nl; ++q) pb.nmax = std::max(pb.nmax, p.C[lf[q]].d1 - p.C[lf[q]].d0);
+  // the largest part that fits the budget
+  const int nm = std::max(pb.nmax, nmax_min), wc = std::max(pb.wcols, wcols_min);
+  int jcap = 1;
+  while (jcap < 4096 && solve_smem(jcap + 1, nm, wc, ts, sw) <= budget) ++jcap;
+  if (solve_smem(jcap, nm, wc, ts, sw) > budget)
+    throw Error(HFSEM_ERR_UNSUPPORTED, "leaf solve does not fit in shared memory");
+  pb.jcap = jcap;
+  for (int st = 0; st < 2 * nl; ++st) {
+    const int d = st < nl ? 0 : 1;
+    const int q = d == 0 ? st : 2 * nl - 1 - st;
+    const Cluster& c = p.C[lf[q]];
+    const int n = c.d1 - c.d0;
+    if (inv[lf[q]] < 0) throw Error(HFSEM_ERR_DEVICE, "leaf without a dense diagonal block");
+    if (n > 128) throw Error(HFSEM_ERR_UNSUPPORTED, "leaf larger than the solve kernel supports");
+    pb.steps.push_back(StepInfo{c.d0, n, q % kRing});
+    const long long dinv = inv[lf[q]] + (d ? (long long)n * n : 0LL);
+    std::vector<std::array<std::vector<SolJob>, 3>> per(ncta);
+    std::vector<int> load(ncta, 0);
+    for (const OJ& o : gat[d][q])
+      if (o.owner >= 0) {
+        per[o.owner][0].push_back(o.j);
+        load[o.owner]++;
+      }
+    for (const OJ& o : sca[d][q]) load[o.owner]++;
+    auto least = [&]() {
+      int c0 = 0;
+      for (int k = 1; k < ncta; ++k)
+        if (load[k] < load[c0]) c0 = k;
+      return c0;
+    };
+    for (const OJ& o : gat[d][q])
+      if (o.owner < 0) {
+        const int c0 = least();
+        per[c0][0].push_back(o.j);
+        load[c0]++;
+      }
+    for (int k = 0; k < n; ++k) {
+      const int c0 = least();
+      per[c0][1].push_back(SolJob{dinv + (long long)k * n, k, -1, 0, 2, 0, n, 0});
+      load[c0]++;
+    }
+    for (const OJ& o : sca[d][q]) per[o.owner][2].push_back(o.j);
+    for (int cr = 0; cr < ncta; ++cr) {
+      StepCta sc{};
+      sc.a0 = (int)pb.jobs.size();
+      pb.jobs.insert(pb.jobs.end(), per[cr][0].begin(), per[cr][0].end());
+      sc.a1 = (int)pb.jobs.size();
+      pb.jobs.insert(pb.jobs.end(), per[cr][1].begin(), per[cr][1].end());
+      sc.a2 = (int)pb.jobs.size();
+      pb.jobs.insert(pb.jobs.end(), per[cr][2].begin(), per[cr][2].end());
+      sc.a3 = (int)pb.jobs.size();
+      pb.step_cta.push_back(sc);
+    }
+  }
+}
 }  // namespace hf

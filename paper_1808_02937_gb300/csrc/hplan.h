@@ -84,6 +84,7 @@ struct HPlan {
   std::vector<TmpAlloc> tmps;          // every temporary handed out
   std::vector<int> fac_waves, sol_waves;   // op offsets of the dependency waves
   int ncta = 1;                        // CTAs that execute one instance
+  int R = 0;                           // rank of the Taylor factors
 };
 
 struct PlanOpts {
@@ -104,6 +105,63 @@ void make_plan(const InstHost& I, const PlanOpts& o, HPlan& out);
 }  // namespace hf
 
 namespace hf {
+// Triangular solves by leaf clusters (gather form).  Forward, for the leaves
+// i in order: x_i = L_ii^-1 (b_i - sum_{j<i} L_ij x_j), where a dense block
+// contributes A x_s directly and a low-rank block U V^T contributes U w with
+// w = V^T x_s accumulated leaf by leaf as x_s is produced; backward the same
+// with U and the leaves in reverse order.  A step (one leaf, one direction)
+// is cut into column jobs, each one column segment of a factor restricted to
+// the leaf's rows, spread over the CTAs of the instance's cluster:
+//   kind 0: r_part += A(:, k) x_s[k]        (dense block column, x_s[k] in
+//                                            the ring of recent leaves)
+//   kind 4: the same with x_s[k] read from the rhs area
+//   kind 1: r_part += U(:, l) w[l]          (low-rank block column, l < rank)
+//   kind 2: x_part += D^-1(:, k) r[k]       (inverse diagonal block column)
+//   kind 3: w[l]  += V(:, l)^T x            (low-rank column, l < rank)
+// The gather and scatter jobs of a low-rank column always go to the same CTA,
+// which keeps its w.
+struct SolJob {
+  long long src;      // first entry of the segment (instance arena offset)
+  int x;              // kind 0: ring offset; 4: unknown index; 1, 3: w column of
+                      // the owning CTA; 2: k
+  int slot;           // kinds 1, 3: LR slot whose rank bounds l; else -1
+  short l, kind;
+  int ldw;            // kinds 1, 3: leading dimension of w
+  int n;              // segment length (the leaf's unknowns)
+  int lmax;           // kinds 1, 3: columns the solve reads of the block
+};
+
+struct StepInfo {
+  int d0, n;          // unknowns of the leaf
+  int ring;           // slot of the leaf's solution in the ring of recent leaves
+};
+
+struct StepCta {      // jobs of one CTA in one step: [a0, a1) gathers,
+  int a0, a1, a2, a3; // [a1, a2) inverse columns, [a2, a3) scatters; they reach
+};                    // shared memory in parts of jcap jobs from a0 on
+
+constexpr int kRing = 4;     // leaves whose solutions every CTA keeps
+
+struct LeafSolve {
+  std::vector<StepInfo> steps;   // 2 x leaves steps: forward, then backward
+  std::vector<StepCta> step_cta; // [step][ncta]
+  std::vector<SolJob> jobs;
+  int wcols = 1;                 // most low-rank columns one CTA owns
+  int jcap = 1;                  // jobs per part
+  int nmax = 0;                  // largest leaf
+};
+
+// Tables of the leaf solves of a factored plan, for ncta CTAs per instance,
+// entries of ts bytes and sw right-hand sides per pass; parts are cut so that
+// the solve kernel's shared memory (solve_smem) stays within budget bytes.
+// The budget is checked for leaves of at least nmax_min entries and at least
+// wcols_min low-rank columns per CTA (when one kernel serves several plans).
+void build_leaf_solve(const HPlan& p, int ncta, size_t budget, int ts, int sw, LeafSolve& out,
+                      int nmax_min = 1, int wcols_min = 1);
+
+// Shared memory of the leaf-solve kernel for parts of jmax jobs.
+size_t solve_smem(int jmax, int nmax, int wcols, int ts, int sw);
+
 // Dependency levels of an op program: op i may run concurrently with every
 // op of the same level; level(i) = 1 + max level of the earlier ops it
 // conflicts with (read/write or write/write on overlapping storage, or on the
