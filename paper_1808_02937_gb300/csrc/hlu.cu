@@ -18,7 +18,9 @@
 #include <cstdlib>
 #include <cstring>
 #include <array>
+#include <list>
 #include <map>
+#include <mutex>
 #include <memory>
 #include <string>
 
@@ -61,6 +63,8 @@ struct HInstDev {
   int sys_inst;      // index into the system's instances
   int R;
   int nd;            // unknowns (leading dimension of the rhs area)
+  long long ptask0;  // low-rank build: task offsets of the pairs (npairs + 1)
+  long long gmax0;   // low-rank build: this instance's first pair in the maxima
   long long st0, job0;  // leaf-solve tables: steps, jobs
   long long pk0;     // this instance's first job in the solve pack
   int jcap;          // jobs per part of the leaf solve
@@ -178,187 +182,287 @@ __global__ void k_diag(const HInstDev* __restrict__ hi, const InstDev* __restric
   }
 }
 
+// Near-field dense blocks of D A D.  One CTA per block and 128 x 128 tile:
+// the derivative terms of the tile's rows and columns (z = Pi x, at most two
+// per unknown) are formed once, so an entry costs only its moment products.
 template <class T>
-__global__ void k_nearfield(const HInstDev* __restrict__ hi, const InstDev* __restrict__ inst,
-                            const double* arena, const DenseDev* __restrict__ dens,
-                            const double* D, T* har) {
+__global__ void __launch_bounds__(256) k_nearfield(const HInstDev* __restrict__ hi,
+                                                   const InstDev* __restrict__ inst,
+                                                   const double* arena,
+                                                   const DenseDev* __restrict__ dens,
+                                                   const double* D, T* har) {
+  __shared__ Term rt[128][2], ct[128][2];
+  __shared__ int rn[128], cn[128];
   const HInstDev H = hi[blockIdx.y];
   const InstDev I = inst[H.sys_inst];
   T* ar = har + H.arena;
   const double* Dv = D + H.d_off;
+  const double* h = arena + I.o_h;
   for (int b = blockIdx.x; b < H.ndense; b += gridDim.x) {
     const DenseDev d = dens[H.dense0 + b];
-    for (int t = threadIdx.x; t < d.m * d.n; t += blockDim.x) {
-      int i = t % d.m, j = t / d.m;
-      int r = d.d0r + i, c = d.d0c + j;
-      ar[d.off + t] = (T)(Dv[r] * a_entry(I, arena, r, c) * Dv[c]);
-    }
+    for (int i0 = 0; i0 < d.m; i0 += 128)
+      for (int j0 = 0; j0 < d.n; j0 += 128) {
+        const int mi = min(128, d.m - i0), nj = min(128, d.n - j0);
+        __syncthreads();
+        for (int t = threadIdx.x; t < 256; t += blockDim.x) {
+          if (t < 128) {
+            if (t < mi) rn[t] = terms_of(I, h, d.d0r + i0 + t, rt[t]);
+          } else if (t - 128 < nj) {
+            cn[t - 128] = terms_of(I, h, d.d0c + j0 + t - 128, ct[t - 128]);
+          }
+        }
+        __syncthreads();
+        for (int t = threadIdx.x; t < mi * nj; t += blockDim.x) {
+          const int i = t % mi, j = t / mi;
+          const int r = d.d0r + i0 + i, c = d.d0c + j0 + j;
+          double sl = 0.0, su = 0.0;   // S_l[r][c] and S_l[c][r]
+          for (int a = 0; a < rn[i]; ++a)
+            for (int q = 0; q < cn[j]; ++q) {
+              const Term A = rt[i][a], B = ct[j][q];
+              if (A.e < 0 || A.e >= I.N || B.e < 0 || B.e >= I.N) continue;
+              const double ab = A.a * B.a;
+              if (B.e <= A.e) sl += ab * mb_entry(I, arena, A.e, B.e, A.m, B.m);
+              if (A.e <= B.e) su += ab * mb_entry(I, arena, B.e, A.e, B.m, A.m);
+            }
+          double v = I.theta * sl + (1.0 - I.theta) * su;
+          if (I.rho != 0.0) v += I.rho * mass_entry(I, h, r, c);
+          ar[d.off + (long long)(j0 + j) * d.m + i0 + i] = (T)(Dv[r] * v * Dv[c]);
+        }
+      }
   }
 }
 
-// Taylor low-rank factors of every admissible pair.  CTA per pair.
+// shared memory of k_lowrank: per CTA the quadrature (points, weights,
+// Legendre values) and the recurrence coefficients, per warp the expansion
+// functions and the moment block (16-byte multiples)
+__host__ __device__ inline size_t lowrank_cta_bytes(int nq, int P, int R, size_t csize) {
+  return ((size_t)(nq * (2 + P) + R) * csize + 15) & ~(size_t)15;
+}
+__host__ __device__ inline size_t lowrank_warp_bytes(int nq, int P, int R, size_t csize) {
+  return ((size_t)(nq * R + P * R + R) * csize + 15) & ~(size_t)15;
+}
+
+// Taylor low-rank factors of every admissible pair (tau right of sigma).
+// One warp per task: a task is one element e of one side of one pair; it
+// forms the element's moment block (the Legendre modes of the element against
+// the R expansion functions of the side, by Gauss-Legendre quadrature) and
+// writes the factor rows of the bubbles of e and of the hat at its left node
+// (which also needs mode 0 of element e-1).  Tasks of pair k are [ptask[k],
+// ptask[k+1]): the elements te0..elast of side 0, then of side 1; a warp
+// takes a contiguous run of tasks.
+// The per-point work runs in the precision of the factors (C = T): the
+// geometry is formed in FP64 once per element, and the singular side is
+// written as rr^(1-alpha) [u^(1-alpha) c_nu (sg / u)^nu] with d = rr u
+// (u >= 1 on an admissible pair), the FP64 scale rr^(1-alpha) joining the
+// row scales.  With the moments of the bubble p, 0.5 h_e acc, the h_e of the
+// quadrature cancels the 2 / h_e of the derivative, and the hat row is
+// 0.5 (acc_{e-1} - acc_e).
+// Pass 0 finds, per term nu, the largest |Q| and |W| entries (after the D
+// scaling); pass 1 writes the factors with every rank-one term balanced
+// (|U_nu| and |V_nu| scaled to equal maxima): the products are unchanged and
+// each factor stays inside the FP32 range on meshes whose element sizes span
+// 10^80.
 template <class T>
-__global__ void k_lowrank(const HInstDev* __restrict__ hi, const InstDev* __restrict__ inst,
-                          const double* arena, const double* __restrict__ gl,
-                          const LRPairDev* __restrict__ pairs, const SlotDev* __restrict__ slots,
-                          const double* D, T* har, int* ranks) {
-  __shared__ double sQ[kMaxP * 32];     // moments of the current element, P x R
-  __shared__ double sX[64], sW[64];
+__global__ void __launch_bounds__(256) k_lowrank(const HInstDev* __restrict__ hi,
+                                                 const InstDev* __restrict__ inst,
+                                                 const double* arena, const double* __restrict__ gl,
+                                                 const LRPairDev* __restrict__ pairs,
+                                                 const SlotDev* __restrict__ slots,
+                                                 const int* __restrict__ ptask, const double* D,
+                                                 T* har, unsigned long long* gmax, int pass,
+                                                 int* ranks) {
+  using C = T;
+  extern __shared__ __align__(16) unsigned char lsm_raw[];
   const HInstDev H = hi[blockIdx.y];
   const InstDev I = inst[H.sys_inst];
-  if ((int)blockIdx.x >= H.npairs) return;
-  const LRPairDev pr = pairs[H.pair0 + blockIdx.x];
   const int P = I.P, R = H.R;
+  const int nq = min((P + R) / 2 + 13, kMaxGL);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  C* sX = reinterpret_cast<C*>(lsm_raw);   // [nq] Gauss-Legendre points
+  C* sW = sX + nq;                         // [nq] weights
+  C* sL = sW + nq;                         // [nq][P] Legendre polynomials
+  C* sCo = sL + nq * P;                    // [R] (2 - alpha - nu) / nu
+  unsigned char* wb = lsm_raw + lowrank_cta_bytes(nq, P, R, sizeof(C)) +
+                      (size_t)warp * lowrank_warp_bytes(nq, P, R, sizeof(C));
+  C* sF = reinterpret_cast<C*>(wb);        // [nq][R] expansion functions (scaled)
+  C* sQ = sF + nq * R;                     // [P][R] quadrature sums of the element
+  C* sQ0 = sQ + P * R;                     // [R] mode-0 sums of element e-1
+  const double* X = gl + gl_off(nq);
+  for (int q = threadIdx.x; q < nq; q += blockDim.x) {
+    const double xq = X[q];
+    sX[q] = (C)xq;
+    sW[q] = (C)X[nq + q];
+    double l0 = 1.0, l1 = xq;
+    sL[q * P] = (C)1;
+    if (P > 1) sL[q * P + 1] = (C)xq;
+    for (int k = 1; k + 1 < P; ++k) {
+      const double l2 = ((2 * k + 1) * xq * l1 - k * l0) / (k + 1);
+      sL[q * P + k + 1] = (C)l2;
+      l0 = l1;
+      l1 = l2;
+    }
+  }
+  for (int nu = threadIdx.x; nu < R; nu += blockDim.x)
+    sCo[nu] = nu ? (C)((2.0 - I.alpha - nu) / nu) : (C)0;
+  __syncthreads();
   const double* h = arena + I.o_h;
   const double* dl = arena + I.o_dl;
   const double* dr = arena + I.o_dr;
   auto ndiff = [&](int a, int b) {   // x_a - x_b, a >= b
     return (dl[a] <= dr[b]) ? dl[a] - dl[b] : dr[b] - dr[a];
   };
-  const double r_s = 0.5 * ndiff(pr.shi, pr.slo);
-  const double r_t = 0.5 * ndiff(pr.thi, pr.tlo);
-  const bool sexp = (r_s <= r_t);
-  const double ex = 1.0 - I.alpha;
-  const int nq = min((P + R) / 2 + 13, kMaxGL);
-  const double* X = gl + gl_off(nq);
-  const double* Wt = X + nq;
-  for (int q = threadIdx.x; q < nq; q += blockDim.x) {
-    sX[q] = X[q];
-    sW[q] = Wt[q];
-  }
-  __syncthreads();
-  const SlotDev lo = slots[H.slot0 + pr.lower_slot];
-  const SlotDev up = slots[H.slot0 + pr.upper_slot];
+  const int* pt = ptask + H.ptask0;   // npairs + 1 task offsets
+  const int ntask = pt[H.npairs];
   T* ar = har + H.arena;
   const double* Dv = D + H.d_off;
-  // expansion functions at the Gauss points of element e, one pow per point:
-  // sF[q*R + nu] = f_nu(x_q); side 0 varies t (tau), side 1 varies s (sigma)
-  __shared__ double sF[64 * 32];
-  __shared__ double sL[64 * kMaxP];
-  __shared__ double sPrev[32];
-  auto fill = [&](int side, int e) {
-    for (int q = threadIdx.x; q < nq; q += blockDim.x) {
-      double xq = sX[q];
-      double loc = 0.5 * h[e] * (1.0 + xq);
-      double* F = sF + q * R;
-      bool singular = (side == 0) == sexp;
-      if (singular) {
-        double d, rr, sg;
-        if (sexp) {            // h_nu(t) = (-1)^nu c_nu r_s^nu (t - s0)^(1-alpha-nu)
-          d = ndiff(e, pr.shi) + loc + r_s;
-          rr = r_s;
-          sg = -1.0;
-        } else {               // h~_nu(s) = c_nu r_t^nu (t0 - s)^(1-alpha-nu)
-          d = r_t + ndiff(pr.tlo, e + 1) + 0.5 * h[e] * (1.0 - xq);
-          rr = r_t;
-          sg = 1.0;
-        }
-        double f = pow(d, ex);
-        F[0] = f;
-        for (int nu = 1; nu < R; ++nu) {
-          f *= sg * (2.0 - I.alpha - nu) / nu * rr / d;
-          F[nu] = f;
-        }
-      } else {
-        double y = sexp ? (ndiff(e, pr.slo) + loc - r_s) / r_s     // (s - s0)/r_s
-                        : (ndiff(e, pr.tlo) + loc - r_t) / r_t;    // (t - t0)/r_t
-        double f = 1.0;
-        for (int nu = 0; nu < R; ++nu) {
-          F[nu] = f;
-          f *= y;
-        }
-      }
-      double* Lq = sL + q * kMaxP;
-      double l0 = 1.0, l1 = xq;
-      Lq[0] = 1.0;
-      if (P > 1) Lq[1] = xq;
-      for (int k = 1; k + 1 < P; ++k) {
-        double l2 = ((2 * k + 1) * xq * l1 - k * l0) / (k + 1);
-        Lq[k + 1] = l2;
-        l0 = l1;
-        l1 = l2;
-      }
+  const double ex = 1.0 - I.alpha;
+  const C exc = (C)ex;
+  // each warp takes a contiguous run of tasks: one search for the first
+  // pair, then the pairs follow in order
+  const int gw = blockIdx.x * nw + warp, nwarps = gridDim.x * nw;
+  const int chunk = (ntask + nwarps - 1) / nwarps;
+  const int t_begin = gw * chunk, t_end = min(ntask, t_begin + chunk);
+  int lo = 0;
+  if (t_begin < t_end) {
+    int hi_ = H.npairs;
+    while (hi_ - lo > 1) {
+      const int mid = (lo + hi_) >> 1;
+      if (pt[mid] <= t_begin) lo = mid; else hi_ = mid;
     }
-    __syncthreads();
-    for (int t = threadIdx.x; t < P * R; t += blockDim.x) {
-      int m = t / R, nu = t % R;
-      double acc = 0.0;
-      for (int q = 0; q < nq; ++q) acc += sW[q] * sL[q * kMaxP + m] * sF[q * R + nu];
-      sQ[m * R + nu] = 0.5 * h[e] * acc;
-    }
-    __syncthreads();
-  };
-  // Two passes over the elements: the first finds, per term nu, the largest
-  // |Q| and |W| row entries (after the D scaling), the second writes the
-  // factors with every rank-one term balanced (|U_nu| and |V_nu| scaled to
-  // equal maxima).  The products are unchanged; the balance keeps each factor
-  // inside the FP32 range on meshes whose element sizes span 10^80.
-  __shared__ unsigned long long smax[2][32];
-  __shared__ double sscale[32];
-  for (int t = threadIdx.x; t < 64; t += blockDim.x) smax[t / 32][t % 32] = 0ULL;
-  __syncthreads();
-  for (int pass = 0; pass < 2; ++pass) {
-    if (pass == 1) {
-      for (int nu = threadIdx.x; nu < R; nu += blockDim.x) {
-        double mq = __longlong_as_double((long long)smax[0][nu]);
-        double mw = __longlong_as_double((long long)smax[1][nu]);
-        double sc = (mq > 0.0 && mw > 0.0) ? sqrt(mw) / sqrt(mq) : 1.0;   // Q *= s, W /= s
-        sscale[nu] = (isfinite(sc) && sc > 0.0) ? sc : 1.0;
-      }
-      __syncthreads();
-    }
-    for (int side = 0; side < 2; ++side) {
-      int e0 = side == 0 ? pr.te0 : pr.se0, e1 = side == 0 ? pr.te1 : pr.se1;
-      int d0 = side == 0 ? pr.td0 : pr.sd0;
-      double scale_side = (side == 0) ? I.g0 : 1.0;   // gamma0 sits with Q
-      int elast = (e1 < I.N) ? e1 : e1 - 1;            // element e1 only feeds the hat at node e1
-      for (int e = e0; e <= elast; ++e) {
-        fill(side, e);
-        // rows: the hat at node e (from elements e-1 and e) when e > e0, the
-        // bubbles of e when e < e1
-        int nb = (e < e1) ? P - 1 : 0;
-        int nh = (e > e0) ? 1 : 0;
-        for (int t = threadIdx.x; t < (nb + nh) * R; t += blockDim.x) {
-          int k = t / R, nu = t % R;
-          double v;
-          int dof;
-          if (k < nh) {
-            v = sPrev[nu] / h[e - 1] - sQ[nu] / h[e];
-            dof = e * P - 1;
-          } else {
-            int p = k - nh + 1;
-            v = -(2.0 * p + 1.0) * (2.0 / h[e]) * sQ[p * R + nu];
-            dof = e * P + p - 1;
-          }
-          v *= scale_side * Dv[dof];
-          if (pass == 0) {
-            atomicMax(&smax[side][nu], (unsigned long long)__double_as_longlong(fabs(v)));
-            continue;
-          }
-          int row = dof - d0;
-          if (side == 0) {
-            v *= sscale[nu];
-            // Q row: lower U = theta D Q, upper V = (1-theta) D Q
-            ar[lo.off + row + (long long)nu * lo.m] = (T)(I.theta * v);
-            ar[up.off + (long long)up.m * up.kcap + row + (long long)nu * up.n] =
-                (T)((1.0 - I.theta) * v);
-          } else {
-            v /= sscale[nu];
-            // W row: lower V = D W, upper U = D W
-            ar[lo.off + (long long)lo.m * lo.kcap + row + (long long)nu * lo.n] = (T)v;
-            ar[up.off + row + (long long)nu * up.m] = (T)v;
-          }
-        }
-        __syncthreads();
-        for (int nu = threadIdx.x; nu < R; nu += blockDim.x) sPrev[nu] = sQ[nu];
-        __syncthreads();
-      }
-    }
-    __syncthreads();
   }
-  if (threadIdx.x == 0) {
-    ranks[H.rk0 + pr.lower_slot] = (I.theta != 0.0) ? R : 0;
-    ranks[H.rk0 + pr.upper_slot] = (I.theta != 1.0) ? R : 0;
+  int next_start = (t_begin < t_end) ? pt[lo + 1] : 0;
+  for (int task = t_begin; task < t_end; ++task) {
+    while (task >= next_start) {
+      ++lo;
+      next_start = pt[lo + 1];
+    }
+    const LRPairDev pr = pairs[H.pair0 + lo];
+    const int tl = task - pt[lo];
+    const int elast_t = (pr.te1 < I.N) ? pr.te1 : pr.te1 - 1;   // element e1 only feeds the hat at node e1
+    const int nt = elast_t - pr.te0 + 1;
+    const int side = tl < nt ? 0 : 1;
+    const int e0 = side == 0 ? pr.te0 : pr.se0, e1 = side == 0 ? pr.te1 : pr.se1;
+    const int e = e0 + (side == 0 ? tl : tl - nt);
+    const int d0 = side == 0 ? pr.td0 : pr.sd0;
+    const double r_s = 0.5 * ndiff(pr.shi, pr.slo);
+    const double r_t = 0.5 * ndiff(pr.thi, pr.tlo);
+    const bool sexp = (r_s <= r_t);
+    const bool singular = (side == 0) == sexp;
+    const double rr = sexp ? r_s : r_t;
+    const double inv_rr = 1.0 / rr;
+    const double fsc = singular ? pow(rr, ex) : 1.0;
+    // expansion functions of element ee at the Gauss points: the argument is
+    // A + B (1 +- x) with A, B from the FP64 geometry of the element
+    auto fill_f = [&](int ee) {
+      double A, B;
+      const C sg = sexp ? (C)-1 : (C)1;
+      if (singular) {
+        if (sexp) A = (ndiff(ee, pr.shi) + r_s) * inv_rr;        // (t - s0) / r_s, t = left end
+        else A = (r_t + ndiff(pr.tlo, ee + 1)) * inv_rr;         // (t0 - s) / r_t, s = right end
+      } else {
+        A = sexp ? (ndiff(ee, pr.slo) - r_s) * inv_rr             // (s - s0) / r_s
+                 : (ndiff(ee, pr.tlo) - r_t) * inv_rr;            // (t - t0) / r_t
+      }
+      B = 0.5 * h[ee] * inv_rr;
+      const C Ac = (C)A, Bc = (C)B;
+      const bool rev = singular && !sexp;   // the argument falls as x rises
+      for (int q = lane; q < nq; q += 32) {
+        const C xq = sX[q];
+        const C u = Ac + Bc * (rev ? ((C)1 - xq) : ((C)1 + xq));
+        C* F = sF + q * R;
+        if (singular) {
+          const C iu = sg / u;
+          C f = pow(u, exc);
+          F[0] = f;
+          for (int nu = 1; nu < R; ++nu) {
+            f *= sCo[nu] * iu;
+            F[nu] = f;
+          }
+        } else {
+          C f = (C)1;
+          for (int nu = 0; nu < R; ++nu) {
+            F[nu] = f;
+            f *= u;
+          }
+        }
+      }
+      __syncwarp();
+    };
+    const bool hat = e > e0, bub = e < e1;
+    if (hat) {   // mode 0 of element e-1 (the Legendre mode 0 is 1)
+      fill_f(e - 1);
+      for (int nu = lane; nu < R; nu += 32) {
+        C acc = (C)0;
+        for (int q = 0; q < nq; ++q) acc += sW[q] * sF[q * R + nu];
+        sQ0[nu] = acc;
+      }
+      __syncwarp();
+    }
+    fill_f(e);
+    for (int t = lane; t < P * R; t += 32) {
+      const int m = t / R, nu = t % R;
+      C acc = (C)0;
+      for (int q = 0; q < nq; ++q) acc += sW[q] * sL[q * P + m] * sF[q * R + nu];
+      sQ[m * R + nu] = acc;
+    }
+    __syncwarp();
+    // rows: the hat at node e (elements e-1 and e) when e > e0, the bubbles
+    // of e when e < e1
+    const double scale_side = ((side == 0) ? I.g0 : 1.0) * fsc;   // gamma0 sits with Q
+    const int nb = bub ? P - 1 : 0, nh = hat ? 1 : 0;
+    const SlotDev slo = slots[H.slot0 + pr.lower_slot];
+    const SlotDev sup = slots[H.slot0 + pr.upper_slot];
+    unsigned long long* gm = gmax + ((size_t)H.gmax0 + lo) * 64;
+    // lane k holds row k (P <= 32 rows per element)
+    const int k = lane;
+    const bool has = k < nb + nh;
+    int row = 0, pp = 0;
+    double rs = 0.0;
+    if (has) {
+      int dof;
+      if (k < nh) {
+        dof = e * P - 1;
+        rs = 0.5 * scale_side * Dv[dof];
+      } else {
+        pp = k - nh + 1;
+        dof = e * P + pp - 1;
+        rs = -(2.0 * pp + 1.0) * scale_side * Dv[dof];
+      }
+      row = dof - d0;
+    }
+    for (int nu = 0; nu < R; ++nu) {
+      double v = 0.0;
+      if (has) v = rs * (double)((k < nh) ? (sQ0[nu] - sQ[nu]) : sQ[pp * R + nu]);
+      if (pass == 0) {
+        double vmax = fabs(v);
+        for (int o = 16; o > 0; o >>= 1) vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+        if (lane == 0 && vmax > 0.0)
+          atomicMax(&gm[side * 32 + nu], (unsigned long long)__double_as_longlong(vmax));
+        continue;
+      }
+      if (!has) continue;
+      const double mq = __longlong_as_double((long long)gm[nu]);
+      const double mw = __longlong_as_double((long long)gm[32 + nu]);
+      double sc = (mq > 0.0 && mw > 0.0) ? sqrt(mw) / sqrt(mq) : 1.0;   // Q *= sc, W /= sc
+      sc = (isfinite(sc) && sc > 0.0) ? sc : 1.0;
+      if (side == 0) {
+        v *= sc;
+        // Q row: lower U = theta D Q, upper V = (1-theta) D Q
+        ar[slo.off + row + (long long)nu * slo.m] = (T)(I.theta * v);
+        ar[sup.off + (long long)sup.m * sup.kcap + row + (long long)nu * sup.n] =
+            (T)((1.0 - I.theta) * v);
+      } else {
+        v /= sc;
+        // W row: lower V = D W, upper U = D W
+        ar[slo.off + (long long)slo.m * slo.kcap + row + (long long)nu * slo.n] = (T)v;
+        ar[sup.off + row + (long long)nu * sup.m] = (T)v;
+      }
+    }
+    if (pass == 1 && tl == 0 && lane == 0) {
+      ranks[H.rk0 + pr.lower_slot] = (I.theta != 0.0) ? R : 0;
+      ranks[H.rk0 + pr.upper_slot] = (I.theta != 1.0) ? R : 0;
+    }
+    __syncwarp();
   }
 }
 
@@ -1834,6 +1938,7 @@ struct PlanBundle {
   HPlan plan;
   std::vector<DenseDev> dense;
   std::vector<LRPairDev> pairs;
+  std::vector<int> ptask;        // low-rank build tasks per pair (prefix sums)
   std::vector<SlotDev> slots;
   LeafSolve ls;                  // tables of the leaf solves
 };
@@ -1857,6 +1962,8 @@ struct hfsem_factor_s : public hf::Precond {
   hf::DevBuf<hf::SlotDev> d_slots;
   hf::DevBuf<hf::DenseDev> d_dense;
   hf::DevBuf<hf::LRPairDev> d_pairs;
+  hf::DevBuf<int> d_ptask;                  // low-rank build tasks
+  hf::DevBuf<unsigned long long> d_gmax;    // low-rank build: per pair and term, the largest entries
   hf::DevBuf<hf::StepInfo> d_steps;   // leaf solve tables
   hf::DevBuf<hf::StepCta> d_step_cta;
   hf::DevBuf<hf::SolJob> d_jobs;
@@ -1898,6 +2005,29 @@ static size_t prog_smem(const HPlan& p, size_t ts) {
   size_t trmm = (size_t)p.leaf_max * p.leaf_max + (size_t)std::max(p.leaf_max, 1) * 33;
   size_t gemm = 2 * 16 * 64;
   return std::max(std::max(leaf, trunc), std::max(trmm, gemm)) * ts + 64;
+}
+
+// Plans depend on the mesh and the options only, so they are kept across
+// factorisations (least recently used first out): refactoring the same
+// meshes with new alpha, theta or rho skips the host planning.
+constexpr size_t kPlanCacheMax = 64;
+static std::mutex g_plan_mu;
+static std::list<std::pair<std::string, std::shared_ptr<PlanBundle>>> g_plan_lru;
+
+static std::shared_ptr<PlanBundle> plan_cache_get(const std::string& key) {
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  for (auto it = g_plan_lru.begin(); it != g_plan_lru.end(); ++it)
+    if (it->first == key) {
+      g_plan_lru.splice(g_plan_lru.begin(), g_plan_lru, it);
+      return g_plan_lru.front().second;
+    }
+  return nullptr;
+}
+
+static void plan_cache_put(const std::string& key, std::shared_ptr<PlanBundle> pb) {
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  g_plan_lru.emplace_front(key, std::move(pb));
+  while (g_plan_lru.size() > kPlanCacheMax) g_plan_lru.pop_back();
 }
 
 static std::string plan_key(const InstHost& I, const PlanOpts& o) {
@@ -1944,6 +2074,7 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
     const int max_leaf = fp32 ? 128 : 96;
     std::map<std::string, std::shared_ptr<PlanBundle>> cache;
     const int ni = s->n_inst;
+    std::vector<std::string> keys(ni);
     f->plans.resize(ni);
     f->hidev.resize(ni);
     for (int i = 0; i < ni; ++i) {
@@ -1964,8 +2095,12 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
       o.max_leaf = max_leaf;
       o.unique_tmp = 1;
       o.ncta = kCluster;
-      std::string key = plan_key(I, o);
+      std::string key = plan_key(I, o) + (fp32 ? "|f32|" : "|f64|") + std::to_string(sol_budget);
+      keys[i] = key;
       auto it = cache.find(key);
+      if (it == cache.end()) {
+        if (auto hit = plan_cache_get(key)) it = cache.emplace(key, hit).first;
+      }
       if (it == cache.end()) {
         auto pb = std::make_shared<PlanBundle>();
         make_plan(I, o, pb->plan);
@@ -1990,8 +2125,17 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
           pb->pairs.push_back(LRPairDev{b.slot, mi->second, ct.e0, ct.e1, cs.e0, cs.e1, ct.lo,
                                         ct.hi, cs.lo, cs.hi, ct.d0, b.m, cs.d0, b.n});
         }
+        // one task per element of each side (element e1 only feeds the hat at
+        // node e1 and is left out when it is past the last element)
+        pb->ptask.assign(1, 0);
+        for (const LRPairDev& q : pb->pairs) {
+          const int nt = ((q.te1 < I.N) ? q.te1 : q.te1 - 1) - q.te0 + 1;
+          const int ns = ((q.se1 < I.N) ? q.se1 : q.se1 - 1) - q.se0 + 1;
+          pb->ptask.push_back(pb->ptask.back() + nt + ns);
+        }
         build_leaf_solve(pb->plan, kCluster, sol_budget, (int)f->tsize,
                          fp32 ? solve_w<float>() : solve_w<double>(), pb->ls);
+        plan_cache_put(key, pb);
         it = cache.emplace(key, pb).first;
       }
       f->plans[i] = it->second;
@@ -1999,17 +2143,20 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
     // one solve kernel serves every plan: cut the parts of each plan for the
     // largest leaf and the most owned low-rank columns of all of them
     {
-      std::vector<PlanBundle*> bs;
-      for (auto& kv : cache) bs.push_back(kv.second.get());
       int nm = 1, wc = 1;
-      for (PlanBundle* pb : bs) {
-        nm = std::max(nm, pb->ls.nmax);
-        wc = std::max(wc, pb->ls.wcols);
+      for (auto& kv : cache) {
+        nm = std::max(nm, kv.second->ls.nmax);
+        wc = std::max(wc, kv.second->ls.wcols);
       }
-      for (PlanBundle* pb : bs)
-        if (pb->ls.nmax < nm || pb->ls.wcols < wc)
-          build_leaf_solve(pb->plan, kCluster, sol_budget, (int)f->tsize,
-                           fp32 ? solve_w<float>() : solve_w<double>(), pb->ls, nm, wc);
+      for (auto& kv : cache) {
+        if (kv.second->ls.nmax >= nm && kv.second->ls.wcols >= wc) continue;
+        // a private copy: the shared plan keeps the tables cut for itself
+        auto cp = std::make_shared<PlanBundle>(*kv.second);
+        build_leaf_solve(cp->plan, kCluster, sol_budget, (int)f->tsize,
+                         fp32 ? solve_w<float>() : solve_w<double>(), cp->ls, nm, wc);
+        kv.second = cp;
+      }
+      for (int i = 0; i < ni; ++i) f->plans[i] = cache[keys[i]];
     }
     // concatenate tables
     std::vector<HOp> ops;
@@ -2022,6 +2169,9 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
     std::vector<StepCta> step_cta;
     std::vector<SolJob> jobs;
     std::map<const PlanBundle*, std::array<long long, 2>> placed_leaf;
+    std::map<const PlanBundle*, long long> placed_task;
+    std::vector<int> ptask;
+    long long gmax_n = 0, max_tasks = 0;
     int jmax = 1, nmax = 1, wcols = 1;
     long long arena = 0, rk = 0, doff = 0, pkoff = 0;
     size_t smem = 0;
@@ -2040,6 +2190,8 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
         slots.insert(slots.end(), pb->slots.begin(), pb->slots.end());
         dense.insert(dense.end(), pb->dense.begin(), pb->dense.end());
         pairs.insert(pairs.end(), pb->pairs.begin(), pb->pairs.end());
+        placed_task[pb] = (long long)ptask.size();
+        ptask.insert(ptask.end(), pb->ptask.begin(), pb->ptask.end());
         pi = placed.emplace(pb, a).first;
         smem = std::max(smem, prog_smem(pb->plan, f->tsize));
         placed_leaf[pb] = {(long long)steps.size(), (long long)jobs.size()};
@@ -2061,6 +2213,10 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
       H.slot0 = pi->second[2];
       H.dense0 = pi->second[3];
       H.pair0 = pi->second[4];
+      H.ptask0 = placed_task[pb];
+      H.gmax0 = gmax_n;
+      gmax_n += (long long)pb->pairs.size();
+      max_tasks = std::max<long long>(max_tasks, pb->ptask.back());
       H.ops0 = pi->second[0];
       H.sops0 = pi->second[1];
       H.nops = (int)p.fac.size();
@@ -2124,6 +2280,11 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
     f->d_pairs.alloc(std::max<size_t>(pairs.size(), 1));
     if (!pairs.empty())
       HF_CHECK(cudaMemcpyAsync(f->d_pairs.p, pairs.data(), pairs.size() * sizeof(LRPairDev), cudaMemcpyHostToDevice, s->st));
+    f->d_ptask.alloc(std::max<size_t>(ptask.size(), 1));
+    if (!ptask.empty())
+      HF_CHECK(cudaMemcpyAsync(f->d_ptask.p, ptask.data(), ptask.size() * sizeof(int), cudaMemcpyHostToDevice, s->st));
+    f->d_gmax.alloc((size_t)std::max<long long>(gmax_n, 1) * 64);
+    HF_CHECK(cudaMemsetAsync(f->d_gmax.p, 0, f->d_gmax.n * sizeof(unsigned long long), s->st));
     f->d_steps.alloc(std::max<size_t>(steps.size(), 1));
     if (!steps.empty())
       HF_CHECK(cudaMemcpyAsync(f->d_steps.p, steps.data(), steps.size() * sizeof(StepInfo), cudaMemcpyHostToDevice, s->st));
@@ -2161,11 +2322,10 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
     f->d_arena.alloc((size_t)std::max<long long>(arena, 1) * f->tsize);
     HF_CHECK(cudaMemsetAsync(f->d_arena.p, 0, (size_t)std::max<long long>(arena, 1) * f->tsize, s->st));
     // build A~
-    int maxnd = 1, maxdense = 1, maxpairs = 1;
+    int maxnd = 1, maxdense = 1;
     for (auto& H : f->hidev) {
       maxnd = std::max(maxnd, s->ih[H.sys_inst].Nd);
       maxdense = std::max(maxdense, H.ndense);
-      maxpairs = std::max(maxpairs, H.npairs);
     }
     const bool prof = getenv("HFSEM_PROFILE") != nullptr;
     cudaEvent_t ev[5];
@@ -2176,24 +2336,43 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
     k_diag<<<gd, 256, 0, s->st>>>(f->d_hi.p, s->d_inst.p, s->arena.p, f->d_D.p);
     HF_LAUNCH_CHECK();
     dim3 gn(std::min(maxdense, 1024), ni);
-    dim3 gp(maxpairs, ni);
+    // low-rank build: warps per CTA as the per-warp quadrature tables allow
+    const int Pm = s->max_P, Rr = opt.R;
+    const int nqm = std::min((Pm + Rr) / 2 + 13, kMaxGL);
+    const size_t per_warp = lowrank_warp_bytes(nqm, Pm, Rr, f->tsize);
+    const size_t per_cta = lowrank_cta_bytes(nqm, Pm, Rr, f->tsize);
+    const int lr_warps = (int)std::max<size_t>(1, std::min<size_t>(8, (160 * 1024 - per_cta) / per_warp));
+    const size_t lr_smem = per_cta + lr_warps * per_warp;
+    dim3 gp((unsigned)std::max<long long>(1, std::min<long long>((max_tasks + lr_warps - 1) / lr_warps, 2048)), ni);
     if (fp32) {
       float* ar = reinterpret_cast<float*>(f->d_arena.p);
       k_nearfield<float><<<gn, 256, 0, s->st>>>(f->d_hi.p, s->d_inst.p, s->arena.p, f->d_dense.p, f->d_D.p, ar);
       HF_LAUNCH_CHECK();
       if (prof) cudaEventRecord(ev[1], s->st);
-      k_lowrank<float><<<gp, 128, 0, s->st>>>(f->d_hi.p, s->d_inst.p, s->arena.p, s->gl.p, f->d_pairs.p,
-                                              f->d_slots.p, f->d_D.p, ar, f->d_ranks.p);
-      HF_LAUNCH_CHECK();
+      if (lr_smem > 48 * 1024)
+        HF_CHECK(cudaFuncSetAttribute((const void*)k_lowrank<float>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lr_smem));
+      for (int pass = 0; pass < 2; ++pass) {
+        k_lowrank<float><<<gp, lr_warps * 32, lr_smem, s->st>>>(f->d_hi.p, s->d_inst.p, s->arena.p, s->gl.p,
+                                                            f->d_pairs.p, f->d_slots.p, f->d_ptask.p,
+                                                            f->d_D.p, ar, f->d_gmax.p, pass, f->d_ranks.p);
+        HF_LAUNCH_CHECK();
+      }
       set_prog_smem<float>(smem);
     } else {
       double* ar = reinterpret_cast<double*>(f->d_arena.p);
       k_nearfield<double><<<gn, 256, 0, s->st>>>(f->d_hi.p, s->d_inst.p, s->arena.p, f->d_dense.p, f->d_D.p, ar);
       HF_LAUNCH_CHECK();
       if (prof) cudaEventRecord(ev[1], s->st);
-      k_lowrank<double><<<gp, 128, 0, s->st>>>(f->d_hi.p, s->d_inst.p, s->arena.p, s->gl.p, f->d_pairs.p,
-                                               f->d_slots.p, f->d_D.p, ar, f->d_ranks.p);
-      HF_LAUNCH_CHECK();
+      if (lr_smem > 48 * 1024)
+        HF_CHECK(cudaFuncSetAttribute((const void*)k_lowrank<double>,
+                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lr_smem));
+      for (int pass = 0; pass < 2; ++pass) {
+        k_lowrank<double><<<gp, lr_warps * 32, lr_smem, s->st>>>(f->d_hi.p, s->d_inst.p, s->arena.p, s->gl.p,
+                                                            f->d_pairs.p, f->d_slots.p, f->d_ptask.p,
+                                                            f->d_D.p, ar, f->d_gmax.p, pass, f->d_ranks.p);
+        HF_LAUNCH_CHECK();
+      }
       set_prog_smem<double>(smem);
     }
     if (prof) cudaEventRecord(ev[2], s->st);
@@ -2354,6 +2533,27 @@ void hfsem_factor_s::run_prog(int which) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
+  if (getenv("HFSEM_PROFILE") && which == 0) {
+    // diagnostic: how many clusters of 8 and of 16 CTAs fit at once
+    const void* fn = tsize == sizeof(float) ? (const void*)hf::k_hprog<float> : (const void*)hf::k_hprog<double>;
+    cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
+    for (int cs : {8, 16}) {
+      cudaLaunchConfig_t c2 = cfg;
+      cudaLaunchAttribute a2[1];
+      a2[0].id = cudaLaunchAttributeClusterDimension;
+      a2[0].val.clusterDim.x = cs;
+      a2[0].val.clusterDim.y = 1;
+      a2[0].val.clusterDim.z = 1;
+      c2.attrs = a2;
+      c2.numAttrs = 1;
+      c2.gridDim = dim3(cs * 16);
+      int nc = -1;
+      cudaError_t e = cudaOccupancyMaxActiveClusters(&nc, fn, &c2);
+      fprintf(stderr, "[hfsem] max active clusters of %d CTAs (smem %zu): %d (%s)\n", cs, smem, nc,
+              cudaGetErrorString(e));
+    }
+    cudaGetLastError();
+  }
   if (tsize == sizeof(float))
     HF_CHECK(cudaLaunchKernelEx(&cfg, hf::k_hprog<float>, a, reinterpret_cast<float*>(d_arena.p), which));
   else
