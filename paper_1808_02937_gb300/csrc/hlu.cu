@@ -54,11 +54,11 @@ struct HInstDev {
   long long slot0;   // offset into the slot table
   long long dense0;  // offset into the dense-block table
   long long pair0;   // offset into the pair table
-  long long ops0, sops0;
-  int nops, nsops, ndense, npairs, n_slots;
+  long long ops0;
+  int nops, ndense, npairs, n_slots;
   long long ws_off, rhs_off, ws_size;
-  long long fw0, sw0;   // offsets into the wave table (factor, solve)
-  int nfw, nsw;         // number of waves
+  long long wc0;     // offset into the table of the CTAs' op ranges per wave
+  int nfw;           // number of waves
   long long d_off;   // scaling D (FP64) offset
   int sys_inst;      // index into the system's instances
   int R;
@@ -474,6 +474,31 @@ __device__ __forceinline__ long long vidx(const View& v, int i, int j) {
   return v.tr ? v.off + j + (long long)i * v.ld : v.off + i + (long long)j * v.ld;
 }
 
+// --- asynchronous element copies, global -> shared (cp.async): every
+// thread issues its copies without waiting, so a whole operand is in flight
+// at once; cp_async_wait_all + a barrier make it visible ---
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+template <class T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
+  if constexpr (sizeof(T) == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
+// dst[i + j ldd] <- view(i, j), i < m, j < n
+template <class T>
+__device__ __forceinline__ void stage_view(T* dst, int ldd, const T* ar, const View& v, int m, int n) {
+  const int total = m * n;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int i = t % m, j = t / m;
+    cp_async_elem(dst + i + j * ldd, ar + vidx(v, i, j));
+  }
+}
+
 template <class T>
 struct HCtx {
   T* ar;
@@ -512,6 +537,54 @@ __device__ void op_gemm(const HOp& o, HCtx<T>& c) {
       ar[ci] = (beta == (T)0) ? (T)0 : beta * ar[ci];
     }
     return;
+  }
+  {
+    // staged: A, B and C reach shared memory in one pass of asynchronous
+    // copies; outputs in column-major order (coalesced C), the inner
+    // dimension split over idle threads when the output is small
+    const long long mn = (long long)m * n;
+    const long long need = (long long)m * k + (long long)k * n + mn;
+    if ((mn <= 4096 || k <= 32) && need + 16 * 256 <= c.smcap) {
+      T* As = c.sm;                 // [i + kk m]
+      T* Bs = As + (long long)m * k;   // [kk + j k]
+      T* Cs = Bs + (long long)k * n;   // [i + j m]
+      T* red = Cs + mn;             // partials of the split inner dimension
+      stage_view(As, m, ar, o.A, m, k);
+      stage_view(Bs, k, ar, o.B, k, n);
+      if (beta != (T)0) stage_view(Cs, m, ar, o.C, m, n);
+      cp_async_wait_all();
+      __syncthreads();
+      const int imn = (int)mn;
+      const int S = (imn >= nt) ? 1 : min(nt / imn, 16);
+      if (S == 1) {
+        for (int t = tid; t < imn; t += nt) {
+          const int i = t % m, j = t / m;
+          const T* a = As + i;
+          const T* b = Bs + (long long)j * k;
+          T acc = 0;
+          for (int kk = 0; kk < k; ++kk) acc += a[(long long)kk * m] * b[kk];
+          ar[vidx(o.C, i, j)] = (beta == (T)0 ? (T)0 : beta * Cs[t]) + alpha * acc;
+        }
+      } else {
+        const int t = tid % imn, sl = tid / imn;
+        if (sl < S) {
+          const int i = t % m, j = t / m;
+          const int kc = (k + S - 1) / S, k0 = sl * kc, k1 = min(k, k0 + kc);
+          T acc = 0;
+          for (int kk = k0; kk < k1; ++kk) acc += As[i + (long long)kk * m] * Bs[kk + (long long)j * k];
+          red[sl * imn + t] = acc;
+        }
+        __syncthreads();
+        for (int t2 = tid; t2 < imn; t2 += nt) {
+          T acc = 0;
+          for (int q = 0; q < S; ++q) acc += red[q * imn + t2];
+          const int i = t2 % m, j = t2 / m;
+          ar[vidx(o.C, i, j)] = (beta == (T)0 ? (T)0 : beta * Cs[t2]) + alpha * acc;
+        }
+      }
+      __syncthreads();
+      return;
+    }
   }
   if ((long long)m * n <= 2048 && k >= 32) {
     // small output, long inner dimension: one warp per output, lanes split k
@@ -743,15 +816,16 @@ __device__ void op_trmm_l(const HOp& o, HCtx<T>& c) {
   T* As = c.sm;            // n x n, [i + k n]
   T* Pn = c.sm + n * n;    // n x 32, [k * 33 + j]
   const int tid = threadIdx.x;
-  for (int t = tid; t < n * n; t += blockDim.x) As[t] = ar[vidx(o.A, t % n, t / n)];
+  stage_view(As, n, ar, o.A, n, n);
   const int tx = tid & 7, ty = tid >> 3;
   for (int c0 = 0; c0 < cc; c0 += 32) {
     const int cp = min(32, cc - c0);
     __syncthreads();
     for (int t = tid; t < n * cp; t += blockDim.x) {
       int i = t % n, j = t / n;
-      Pn[i * 33 + j] = ar[vidx(o.C, i, c0 + j)];
+      cp_async_elem(Pn + i * 33 + j, ar + vidx(o.C, i, c0 + j));
     }
+    cp_async_wait_all();
     __syncthreads();
     for (int rb = ty * 4; rb < n; rb += 128) {
       T acc[4][4];
@@ -791,12 +865,15 @@ __device__ void op_trmm_r(const HOp& o, HCtx<T>& c) {
   T* As = c.sm;            // n x n, [k n + j]
   T* Pn = c.sm + n * n;    // 32 x n, [i + k * 32]
   const int tid = threadIdx.x;
-  for (int t = tid; t < n * n; t += blockDim.x) As[(t % n) * n + t / n] = ar[vidx(o.A, t % n, t / n)];
+  for (int t = tid; t < n * n; t += blockDim.x)
+    cp_async_elem(As + (t % n) * n + t / n, ar + vidx(o.A, t % n, t / n));
   const int tx = tid & 31, ty = tid >> 5;
   for (int r0 = 0; r0 < m; r0 += 32) {
     const int rp = min(32, m - r0);
     __syncthreads();
-    for (int t = tid; t < rp * n; t += blockDim.x) Pn[(t % rp) + (t / rp) * 32] = ar[vidx(o.C, r0 + t % rp, t / rp)];
+    for (int t = tid; t < rp * n; t += blockDim.x)
+      cp_async_elem(Pn + (t % rp) + (t / rp) * 32, ar + vidx(o.C, r0 + t % rp, t / rp));
+    cp_async_wait_all();
     __syncthreads();
     T acc[4][4];
 #pragma unroll
@@ -1365,7 +1442,7 @@ __device__ void op_trunc(const HOp& o, HCtx<T>& c) {
 
 struct HProgArgs {
   const HInstDev* inst;
-  const int* waves;
+  const int* wcta;   // per wave, the CTAs' op ranges
   const HOp* ops;
   const SlotDev* slots;
   int* ranks;
@@ -1425,10 +1502,11 @@ __device__ __forceinline__ void cluster_barrier() {
 }
 
 // One thread-block cluster of kCluster CTAs per instance runs the instance's
-// op program wave by wave: the ops of a wave are independent and spread
-// round-robin over the CTAs, a cluster barrier separates consecutive waves.
+// H-LU program wave by wave: the ops of a wave are independent and dealt to
+// the CTAs by the planner (longest first, to the least loaded CTA), a
+// cluster barrier separates consecutive waves.
 template <class T>
-__global__ void __launch_bounds__(kHThreads) k_hprog(HProgArgs a, T* har, int which) {
+__global__ void __launch_bounds__(kHThreads) k_hprog(HProgArgs a, T* har) {
   extern __shared__ __align__(16) unsigned char smraw[];
   const unsigned crank = cluster_rank();
   const unsigned cid = cluster_id();
@@ -1442,16 +1520,16 @@ __global__ void __launch_bounds__(kHThreads) k_hprog(HProgArgs a, T* har, int wh
   c.smcap = a.smem_elems;
   c.tol = a.tol;
   c.err = a.err + cid;
-  const HOp* ops = a.ops + (which ? H.sops0 : H.ops0);
-  const int* waves = a.waves + (which ? H.sw0 : H.fw0);
-  const int nw = which ? H.nsw : H.nfw;
+  const HOp* ops = a.ops + H.ops0;
+  const int* wc = a.wcta + H.wc0;
+  const int nw = H.nfw;
   double fl = 0.0;
   const bool wp = a.wprof && threadIdx.x == 0;
   for (int w = 0; w < nw; ++w) {
-    const int i1 = waves[w + 1];
+    const int i0 = wc[w * (kCluster + 1) + crank], i1 = wc[w * (kCluster + 1) + crank + 1];
     unsigned long long tw0 = 0, busy = 0, lmax = 0, ltype = 0;
     if (wp) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(tw0));
-    for (int i = waves[w] + (int)crank; i < i1; i += kCluster) {
+    for (int i = i0; i < i1; ++i) {
       const HOp o = ops[i];
       if (threadIdx.x == 0) fl += op_flops(o, c.rk, c.sl);
       unsigned long long t0 = 0;
@@ -1507,13 +1585,10 @@ __global__ void __launch_bounds__(kHThreads) k_hprog(HProgArgs a, T* har, int wh
       q[3 + 3 * crank] = ltype;
     }
   }
-  if (threadIdx.x == 0) a.flops[((size_t)cid * kCluster + crank) * 2 + which] += fl;
+  if (threadIdx.x == 0) a.flops[((size_t)cid * kCluster + crank) * 2] += fl;
 }
 
 // --- asynchronous bulk copies and distributed shared memory (inline PTX) ---
-__device__ __forceinline__ unsigned smem_u32(const void* p) {
-  return (unsigned)__cvta_generic_to_shared(p);
-}
 __device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
   asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
 }
@@ -1978,16 +2053,16 @@ struct hfsem_factor_s : public hf::Precond {
   hf::DevBuf<double> d_D;
   hf::DevBuf<unsigned char> d_arena;
   size_t smem = 0;
-  long long total_ops = 0, total_sops = 0;
+  long long total_ops = 0;
   hf::DevBuf<unsigned long long> d_prof;   // HFSEM_PROFILE=1: time per op type
   hf::DevBuf<double> d_flops;               // per instance: factor / solve flops
   hf::DevBuf<unsigned long long> d_wprof;   // HFSEM_PROFILE=2: per-wave records
   int wstride = 0;
   void report(const char* what);
-  void report_waves(const char* what, int which);
+  void report_waves(const char* what);
   void apply(int nrhs, const double* r_em, double* y_em) override;
   void collect_flops();
-  void run_prog(int which);
+  void run_prog();
 };
 
 namespace hf {
@@ -2179,14 +2254,11 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
       const PlanBundle* pb = f->plans[i].get();
       auto pi = placed.find(pb);
       if (pi == placed.end()) {
-        std::array<long long, 7> a{(long long)ops.size(), (long long)(ops.size() + pb->plan.fac.size()),
-                                   (long long)slots.size(), (long long)dense.size(),
-                                   (long long)pairs.size(), (long long)waves.size(),
-                                   (long long)(waves.size() + pb->plan.fac_waves.size())};
-        waves.insert(waves.end(), pb->plan.fac_waves.begin(), pb->plan.fac_waves.end());
-        waves.insert(waves.end(), pb->plan.sol_waves.begin(), pb->plan.sol_waves.end());
+        std::array<long long, 7> a{(long long)ops.size(), 0, (long long)slots.size(),
+                                   (long long)dense.size(), (long long)pairs.size(),
+                                   (long long)waves.size(), 0};
+        waves.insert(waves.end(), pb->plan.fac_cta.begin(), pb->plan.fac_cta.end());
         ops.insert(ops.end(), pb->plan.fac.begin(), pb->plan.fac.end());
-        ops.insert(ops.end(), pb->plan.sol.begin(), pb->plan.sol.end());
         slots.insert(slots.end(), pb->slots.begin(), pb->slots.end());
         dense.insert(dense.end(), pb->dense.begin(), pb->dense.end());
         pairs.insert(pairs.end(), pb->pairs.begin(), pb->pairs.end());
@@ -2218,19 +2290,19 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
       gmax_n += (long long)pb->pairs.size();
       max_tasks = std::max<long long>(max_tasks, pb->ptask.back());
       H.ops0 = pi->second[0];
-      H.sops0 = pi->second[1];
+
       H.nops = (int)p.fac.size();
-      H.nsops = (int)p.sol.size();
+
       H.ndense = (int)pb->dense.size();
       H.npairs = (int)pb->pairs.size();
       H.n_slots = p.n_slots;
       H.ws_off = p.ws_off;
       H.ws_size = p.ws_size;
       H.rhs_off = p.rhs_off;
-      H.fw0 = pi->second[5];
-      H.sw0 = pi->second[6];
+      H.wc0 = pi->second[5];
+
       H.nfw = (int)p.fac_waves.size() - 1;
-      H.nsw = (int)p.sol_waves.size() - 1;
+
       H.d_off = doff;
       doff += s->ih[i].Nd;
       H.sys_inst = i;
@@ -2244,7 +2316,7 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
       H.pk0 = pkoff;
       pkoff += (long long)pb->ls.jobs.size();
       f->total_ops += H.nops;
-      f->total_sops += H.nsops;
+
     }
     // every CTA of the cluster sits alone on its SM (register bound), so the
     // kernel takes all the shared memory it may have: the recompression
@@ -2377,7 +2449,7 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
     }
     if (prof) cudaEventRecord(ev[2], s->st);
     if (!f->build_only) {
-      f->run_prog(0);
+      f->run_prog();
       f->run_pack();
     }
     if (prof) cudaEventRecord(ev[3], s->st);
@@ -2392,12 +2464,12 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
     }
     if (getenv("HFSEM_PROFILE")) {
       const HPlan& p0 = f->plans[0]->plan;
-      fprintf(stderr, "[hfsem plan] N=%d P=%d blocks=%zu dense=%zu lr=%zu fac_ops=%zu sol_ops=%zu "
+      fprintf(stderr, "[hfsem plan] N=%d P=%d blocks=%zu dense=%zu lr=%zu fac_ops=%zu waves=%zu "
               "leaf_max=%d kconcat_max=%d hh_lr=%d arena=%lld\n", p0.N, p0.P, p0.B.size(),
-              p0.dense_blocks.size(), p0.lr_blocks.size(), p0.fac.size(), p0.sol.size(), p0.leaf_max,
+              p0.dense_blocks.size(), p0.lr_blocks.size(), p0.fac.size(), (size_t)p0.fac_waves.size() - 1, p0.leaf_max,
               p0.kconcat_max, p0.hh_lr, p0.arena);
       f->report("factorisation");
-      f->report_waves("factorisation", 0);
+      f->report_waves("factorisation");
     }
     std::vector<int> err(ni);
     HF_CHECK(cudaMemcpy(err.data(), f->d_err.p, ni * sizeof(int), cudaMemcpyDeviceToHost));
@@ -2446,7 +2518,7 @@ void hfsem_factor_s::report(const char* what) {
 // Critical-path view of one program run, for the instance whose run took
 // longest: per wave the CTA with the most busy time decides, and the type
 // of its longest op takes the wave's time.
-void hfsem_factor_s::report_waves(const char* what, int which) {
+void hfsem_factor_s::report_waves(const char* what) {
   if (!d_wprof.p) return;
   const int rec = 1 + 3 * hf::kCluster;
   std::vector<unsigned long long> h(d_wprof.n);
@@ -2454,7 +2526,7 @@ void hfsem_factor_s::report_waves(const char* what, int which) {
   int worst = 0;
   double wworst = -1;
   for (size_t c = 0; c < hidev.size(); ++c) {
-    const int nw = which ? hidev[c].nsw : hidev[c].nfw;
+    const int nw = hidev[c].nfw;
     double wall = 0;
     for (int w = 0; w < nw; ++w) wall += h[((size_t)c * wstride + w) * rec];
     if (wall > wworst) {
@@ -2463,8 +2535,8 @@ void hfsem_factor_s::report_waves(const char* what, int which) {
     }
   }
   const hf::HPlan& P = plans[worst]->plan;
-  const std::vector<hf::HOp>& prog = which ? P.sol : P.fac;
-  const int nw = which ? hidev[worst].nsw : hidev[worst].nfw;
+  const std::vector<hf::HOp>& prog = P.fac;
+  const int nw = hidev[worst].nfw;
   static const char* names[16] = {"?", "GEMM", "GETRF_INV", "TRMM_L", "TRMM_R", "APPEND",
                                   "TRUNC", "ZERO", "AXPY", "?", "?", "?", "?", "?", "?", "?"};
   double wall = 0, crit = 0, sumbusy = 0, bytype[16] = {0}, ntype[16] = {0};
@@ -2484,7 +2556,7 @@ void hfsem_factor_s::report_waves(const char* what, int which) {
     ntype[o.type & 15] += 1;
     char key[96];
     snprintf(key, sizeof(key), "%-9s C %4dx%-4d A.c %4d  wave ops %4d", names[o.type & 15], o.C.r,
-             o.C.c, o.A.c, (which ? P.sol_waves : P.fac_waves)[w + 1] - (which ? P.sol_waves : P.fac_waves)[w]);
+             o.C.c, o.A.c, P.fac_waves[w + 1] - P.fac_waves[w]);
     auto& e = shapes[key];
     e.first += q[1 + 3 * cm];
     e.second += 1;
@@ -2501,7 +2573,7 @@ void hfsem_factor_s::report_waves(const char* what, int which) {
     fprintf(stderr, "    %8.3f ms  %s\n", top[t].first * 1e-6, top[t].second.c_str());
 }
 
-void hfsem_factor_s::run_prog(int which) {
+void hfsem_factor_s::run_prog() {
   if (!d_prof.p && getenv("HFSEM_PROFILE")) {
     d_prof.alloc((size_t)sys->n_inst * 32);
     cudaMemset(d_prof.p, 0, d_prof.n * sizeof(unsigned long long));
@@ -2513,14 +2585,14 @@ void hfsem_factor_s::run_prog(int which) {
   const char* pe = getenv("HFSEM_PROFILE");
   if (!d_wprof.p && pe && atoi(pe) >= 2) {
     int nwmax = 1;
-    for (auto& H : hidev) nwmax = std::max(nwmax, std::max(H.nfw, H.nsw));
+    for (auto& H : hidev) nwmax = std::max(nwmax, H.nfw);
     wstride = nwmax;
     d_wprof.alloc((size_t)nwmax * hidev.size() * (1 + 3 * hf::kCluster));
   }
   if (d_wprof.p) cudaMemsetAsync(d_wprof.p, 0, d_wprof.n * sizeof(unsigned long long), sys->st);
   hf::HProgArgs a{d_hi.p, d_waves.p, d_ops.p, d_slots.p, d_ranks.p, d_err.p, tol, d_prof.p, d_flops.p,
                   d_wprof.p, wstride, (long long)(smem / tsize) - 8};
-  hf::Tick tk(sys->st, which ? "hlu_solve" : "hlu_factor");
+  hf::Tick tk(sys->st, "hlu_factor");
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(sys->n_inst * hf::kCluster));
   cfg.blockDim = dim3(hf::kHThreads);
@@ -2533,7 +2605,7 @@ void hfsem_factor_s::run_prog(int which) {
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  if (getenv("HFSEM_PROFILE") && which == 0) {
+  if (getenv("HFSEM_PROFILE")) {
     // diagnostic: how many clusters of 8 and of 16 CTAs fit at once
     const void* fn = tsize == sizeof(float) ? (const void*)hf::k_hprog<float> : (const void*)hf::k_hprog<double>;
     cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
@@ -2555,9 +2627,9 @@ void hfsem_factor_s::run_prog(int which) {
     cudaGetLastError();
   }
   if (tsize == sizeof(float))
-    HF_CHECK(cudaLaunchKernelEx(&cfg, hf::k_hprog<float>, a, reinterpret_cast<float*>(d_arena.p), which));
+    HF_CHECK(cudaLaunchKernelEx(&cfg, hf::k_hprog<float>, a, reinterpret_cast<float*>(d_arena.p)));
   else
-    HF_CHECK(cudaLaunchKernelEx(&cfg, hf::k_hprog<double>, a, reinterpret_cast<double*>(d_arena.p), which));
+    HF_CHECK(cudaLaunchKernelEx(&cfg, hf::k_hprog<double>, a, reinterpret_cast<double*>(d_arena.p)));
   HF_LAUNCH_CHECK();
 }
 

@@ -420,20 +420,6 @@ struct Builder {
     gemm_hd(D2, l.kid[2], D1, -1.0);
     trsm_ll_d(l.kid[3], D2);
   }
-  // X <- U^-1 X for a dense view (backward substitution)
-  void trsm_lu_d(int ub, View D) {
-    const Block& u = p.B[ub];
-    if (u.m == 0 || empty(D)) return;
-    if (u.type == B_DENSE) {
-      op(OP_TRMM_L, uinv(ub), View{}, D, 1.0, 0.0);
-      return;
-    }
-    int t1 = p.C[u.t].kid[0], t2 = p.C[u.t].kid[1];
-    View D1 = vrows(D, r0(u.t, t1), r1(u.t, t1)), D2 = vrows(D, r0(u.t, t2), r1(u.t, t2));
-    trsm_lu_d(u.kid[3], D2);
-    gemm_hd(D1, u.kid[1], D2, -1.0);
-    trsm_lu_d(u.kid[0], D1);
-  }
   // X <- X U^-1 for a dense view
   void trsm_ru_d(int ub, View D) {
     const Block& u = p.B[ub];
@@ -523,12 +509,6 @@ void make_plan(const InstHost& I, const PlanOpts& o, HPlan& p) {
   b.tmp_base = b.tmp_top = b.top;
   b.prog = &p.fac;
   b.hlu(0);
-  if (!o.unique_tmp) b.tmp_top = b.tmp_base;
-  b.prog = &p.sol;
-  // the width of the rhs area is read at run time from rank slot n_slots
-  View rhs{p.rhs_off, I.Nd, -1 - p.n_slots, std::max(I.Nd, 1), 0};
-  b.trsm_ll_d(0, rhs);
-  b.trsm_lu_d(0, rhs);
   long long ws_off = b.tmp_base + b.tmp_peak;
   p.tmp_base = b.tmp_base;
   p.tmp_size = b.tmp_peak;
@@ -536,8 +516,7 @@ void make_plan(const InstHost& I, const PlanOpts& o, HPlan& p) {
   p.ws_size = (long long)2 * std::max(b.max_m, 1) * std::max(p.kconcat_max, 1);
   p.ncta = std::max(o.ncta, 1);
   p.arena = ws_off + p.ws_size * p.ncta;
-  schedule_program(p, p.fac, p.fac_waves);
-  schedule_program(p, p.sol, p.sol_waves);
+  schedule_program(p, p.fac, p.fac_waves, p.fac_cta);
 }
 
 }  // namespace hf
@@ -714,7 +693,39 @@ int program_levels(const HPlan& p, const std::vector<HOp>& prog, std::vector<int
 
 namespace hf {
 
-void schedule_program(const HPlan& p, std::vector<HOp>& prog, std::vector<int>& waves) {
+// Estimated run time (microseconds) of an op on one CTA, runtime ranks taken
+// as the Taylor rank: a fixed cost for the op's latencies plus its flops at
+// the rates the interpreter's kernels reach.
+static double op_cost(const HPlan& p, const HOp& o) {
+  auto dim = [&](int d) -> double {
+    if (d >= 0) return d;
+    const int sl = -1 - d;
+    if (sl >= p.n_slots) return p.nrhs_max;
+    return std::min(p.B[p.lr_blocks[sl]].kcap, std::max(p.R, 1));
+  };
+  switch (o.type) {
+    case OP_GEMM: return 2.0 + 2.0 * dim(o.C.r) * dim(o.C.c) * dim(o.A.c) / 3e5;
+    case OP_TRMM_L: return 2.0 + 2.0 * dim(o.C.r) * dim(o.C.r) * dim(o.C.c) / 2e5;
+    case OP_TRMM_R: return 2.0 + 2.0 * dim(o.C.r) * dim(o.C.c) * dim(o.C.c) / 2e5;
+    case OP_GETRF_INV: {
+      const double n = dim(o.C.r) / 128.0;
+      return 5.0 + 100.0 * n * n * n;
+    }
+    case OP_TRUNC: {
+      const Block& b = p.B[p.lr_blocks[o.slot]];
+      const double K = b.kcap;
+      return 8.0 + 4.0 * (b.m + b.n) * K * K / 5e4;
+    }
+    case OP_APPEND: {
+      const Block& b = p.B[p.lr_blocks[o.slot]];
+      return 2.0 + (b.m + b.n) * dim(o.A.c) / 2e4;
+    }
+    default: return 0.5 + dim(o.C.r) * dim(o.C.c) / 1e5;
+  }
+}
+
+void schedule_program(const HPlan& p, std::vector<HOp>& prog, std::vector<int>& waves,
+                      std::vector<int>& wcta) {
   // 1. split big ops into independent pieces
   std::vector<HOp> out;
   out.reserve(prog.size() * 2);
@@ -753,6 +764,35 @@ void schedule_program(const HPlan& p, std::vector<HOp>& prog, std::vector<int>& 
   std::vector<int> pos(waves.begin(), waves.end());
   prog.assign(out.size(), HOp());
   for (size_t i = 0; i < out.size(); ++i) prog[pos[lv[i] - 1]++] = out[i];
+  // 4. each wave's ops dealt to the CTAs longest first, each to the least
+  // loaded CTA; a CTA's ops of a wave are contiguous:
+  // wcta[w (ncta + 1) + c] .. wcta[w (ncta + 1) + c + 1]
+  const int nc = std::max(p.ncta, 1);
+  wcta.assign((size_t)nl * (nc + 1), 0);
+  std::vector<HOp> tmp;
+  for (int w = 0; w < nl; ++w) {
+    const int a = waves[w], b = waves[w + 1];
+    std::vector<std::pair<double, int>> ord;
+    for (int i = a; i < b; ++i) ord.push_back({-op_cost(p, prog[i]), i});
+    std::stable_sort(ord.begin(), ord.end());
+    std::vector<double> load(nc, 0.0);
+    std::vector<std::vector<int>> to(nc);
+    for (auto& q : ord) {
+      int c = 0;
+      for (int k = 1; k < nc; ++k)
+        if (load[k] < load[c]) c = k;
+      load[c] -= q.first;
+      to[c].push_back(q.second);
+    }
+    tmp.clear();
+    for (int c = 0; c < nc; ++c) {
+      wcta[(size_t)w * (nc + 1) + c] = a + (int)tmp.size();
+      std::sort(to[c].begin(), to[c].end());   // program order within the CTA
+      for (int i : to[c]) tmp.push_back(prog[i]);
+    }
+    wcta[(size_t)w * (nc + 1) + nc] = b;
+    std::copy(tmp.begin(), tmp.end(), prog.begin() + a);
+  }
 }
 
 }  // namespace hf

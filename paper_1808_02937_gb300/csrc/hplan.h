@@ -67,7 +67,6 @@ struct HPlan {
   std::vector<int> lr_blocks;      // block ids of LR blocks, by slot
   std::vector<int> dense_blocks;   // block ids of dense blocks
   std::vector<HOp> fac;            // H-LU program
-  std::vector<HOp> sol;            // forward + backward substitution on the rhs area
   long long arena = 0;             // elements (T) per instance
   long long rhs_off = 0;           // rhs area: Nd x nrhs_max
   int nrhs_max = 0;
@@ -82,7 +81,8 @@ struct HPlan {
     int ld;
   };
   std::vector<TmpAlloc> tmps;          // every temporary handed out
-  std::vector<int> fac_waves, sol_waves;   // op offsets of the dependency waves
+  std::vector<int> fac_waves;          // op offsets of the dependency waves
+  std::vector<int> fac_cta;            // per wave, the CTAs' op ranges (ncta + 1 offsets)
   int ncta = 1;                        // CTAs that execute one instance
   int R = 0;                           // rank of the Taylor factors
 };
@@ -169,6 +169,8 @@ size_t solve_smem(int jmax, int nmax, int wcols, int ts, int sw);
 int program_levels(const HPlan& p, const std::vector<HOp>& prog, std::vector<int>& level);
 
 // Split large ops into independent tile ops, then order the program by
-// dependency level; waves[w] .. waves[w+1] are the ops of wave w.
-void schedule_program(const HPlan& p, std::vector<HOp>& prog, std::vector<int>& waves);
+// dependency level; waves[w] .. waves[w+1] are the ops of wave w, dealt to
+// p.ncta CTAs (wcta: per wave ncta + 1 offsets).
+void schedule_program(const HPlan& p, std::vector<HOp>& prog, std::vector<int>& waves,
+                      std::vector<int>& wcta);
 }  // namespace hf
