@@ -57,7 +57,7 @@ struct HInstDev {
   long long ops0;
   int nops, ndense, npairs, n_slots;
   long long ws_off, rhs_off, ws_size;
-  long long wc0;     // offset into the table of the CTAs' op ranges per wave
+  long long fw0;     // offset into the wave table
   int nfw;           // number of waves
   long long d_off;   // scaling D (FP64) offset
   int sys_inst;      // index into the system's instances
@@ -507,6 +507,7 @@ struct HCtx {
   T* ws;
   T* sm;
   long long smcap;   // elements of T in the dynamic shared memory
+  unsigned long long* tprof;   // optional: recompression phase times (profiling)
   double tol;
   int* err;
 };
@@ -1124,41 +1125,63 @@ __device__ void op_getrf_inv(const HOp& o, HCtx<T>& c) {
 
 // Householder QR of A (m x K, ld m) in place: R in the upper trapezoid,
 // reflectors v (v_0 = 1 implied) below, tau[j]; kr = min(m, K) reflectors.
+// Warp w owns the columns l = w mod (warps).  Step j: every warp forms the
+// reflector of column j itself (x0 = A[j][j], sigma = sum_{i>j} A[i][j]^2),
+// then applies it to its own columns l > j (w_l = A[j][l] + d_l / v0 with
+// d_l = sum_{i>j} A[i][j] A[i][l]); the owner of column j scales its
+// reflector at the start of step j + 1, when no warp reads it any more.  One
+// barrier per step.
 template <class T>
 __device__ void house_qr(T* A, int m, int K, T* tau, T* red) {
+  (void)red;
   const int kr = min(m, K);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  T pv0 = (T)0;   // v0 of the previous step (used by the owner of its column)
   for (int j = 0; j < kr; ++j) {
-    T part = 0;
-    for (int i = j + threadIdx.x; i < m; i += blockDim.x) part += A[i + (long long)j * m] * A[i + (long long)j * m];
-    T s2 = block_sum<T>(part, red);
-    T x0 = A[j + (long long)j * m];
-    T s = sqrt(s2);
-    T alpha = (x0 >= (T)0) ? -s : s;
-    T v0 = x0 - alpha;
-    bool trivial = (s == (T)0) || (v0 == (T)0);
-    if (!trivial)
-      for (int i = j + 1 + threadIdx.x; i < m; i += blockDim.x) A[i + (long long)j * m] /= v0;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      tau[j] = trivial ? (T)0 : (alpha - x0) / alpha;
-      if (!trivial) A[j + (long long)j * m] = alpha;
+    // the owner of column j - 1 turns it into its reflector
+    if (j > 0 && ((j - 1) % nw) == warp && pv0 != (T)0) {
+      T* col = A + (long long)(j - 1) * m;
+      const T inv = (T)1 / pv0;
+      for (int i = j + lane; i < m; i += 32) col[i] *= inv;
     }
-    __syncthreads();
-    T tj = tau[j];
-    if (tj != (T)0) {
-      for (int l = j + 1 + warp; l < K; l += nw) {
-        T w = 0;
-        for (int i = j + 1 + lane; i < m; i += 32) w += A[i + (long long)j * m] * A[i + (long long)l * m];
-        for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
-        w = __shfl_sync(0xffffffffu, w, 0);
-        w = (w + A[j + (long long)l * m]) * tj;
-        if (lane == 0) A[j + (long long)l * m] -= w;
-        for (int i = j + 1 + lane; i < m; i += 32) A[i + (long long)l * m] -= w * A[i + (long long)j * m];
+    const T* cj = A + (long long)j * m;
+    T sg = (T)0;
+    for (int i = j + 1 + lane; i < m; i += 32) sg += cj[i] * cj[i];
+    for (int o = 16; o > 0; o >>= 1) sg += __shfl_xor_sync(0xffffffffu, sg, o);
+    const T x0 = cj[j];
+    const T sn = sqrt(x0 * x0 + sg);
+    const T alpha = (x0 >= (T)0) ? -sn : sn;
+    const T v0 = x0 - alpha;
+    const bool trivial = (sn == (T)0) || (v0 == (T)0) || sg == (T)0;
+    const T tj = trivial ? (T)0 : (alpha - x0) / alpha;
+    if (!trivial) {
+      const T iv0 = (T)1 / v0;
+      for (int l = j + 1 + ((warp - (j + 1)) % nw + nw) % nw; l < K; l += nw) {
+        T* cl = A + (long long)l * m;
+        T d = (T)0;
+        for (int i = j + 1 + lane; i < m; i += 32) d += cj[i] * cl[i];
+        for (int o = 16; o > 0; o >>= 1) d += __shfl_xor_sync(0xffffffffu, d, o);
+        const T w = (cl[j] + d * iv0) * tj;
+        __syncwarp();
+        if (lane == 0) cl[j] -= w;
+        const T wv = w * iv0;
+        for (int i = j + 1 + lane; i < m; i += 32) cl[i] -= wv * cj[i];
       }
     }
     __syncthreads();
+    if ((j % nw) == warp && lane == 0) {
+      tau[j] = tj;
+      if (!trivial) A[j + (long long)j * m] = alpha;
+    }
+    pv0 = trivial ? (T)0 : v0;
   }
+  // the last reflector
+  if (kr > 0 && ((kr - 1) % nw) == warp && pv0 != (T)0) {
+    T* col = A + (long long)(kr - 1) * m;
+    const T inv = (T)1 / pv0;
+    for (int i = kr + lane; i < m; i += 32) col[i] *= inv;
+  }
+  __syncthreads();
 }
 
 // Y (m x r, ld ldy) <- Q Y with Q = H_0 ... H_{kr-1} stored in A (m x K)
@@ -1238,12 +1261,23 @@ __device__ void trunc_core(HCtx<T>& c, int slot, T* Ut, T* Vt, int K) {
   const long long small = ((2LL * K + 32 + 2LL * K * K + 3LL * K + K + 8) + 3) & ~3LL;
   T* stage = c.sm + small;
   const long long cap = c.smcap - small;
-  __shared__ int s_p, s_stop;
+  __shared__ int s_stop;
   __shared__ T s_r0;
   // Householder QR of the tall factors, in shared memory when they fit (the
   // reflector loops are latency bound), written back for the final products
+  unsigned long long tq = 0;
+  auto tmk = [&](int k) {
+    if (!c.tprof || threadIdx.x != 0) return;
+    unsigned long long t1;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+    if (k >= 0) atomicAdd(c.tprof + k, t1 - tq);
+    tq = t1;
+  };
+  tmk(-1);
   qr_staged(Ut, m, K, tauU, red, stage, cap);
+  tmk(0);
   qr_staged(Vt, n, K, tauV, red, stage, cap);
+  tmk(1);
   const int ku = min(m, K), kv = min(n, K);
   // core M = R_U R_V^T from the two triangles, staged
   T* RU = Ut;
@@ -1271,67 +1305,82 @@ __device__ void trunc_core(HCtx<T>& c, int slot, T* Ut, T* Vt, int K) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int rmax = min(min(ku, kv), s.kmax);
   int r = 0;
+  tmk(2);
   for (int st = 0; st < rmax; ++st) {
-    // exact norms of the remaining parts of the columns
-    for (int j = st + threadIdx.x; j < kv; j += blockDim.x) {
+    // exact norms of the remaining parts of the columns (a warp per column)
+    for (int j = st + warp; j < kv; j += nw) {
       T a = 0;
-      for (int i = st; i < ku; ++i) a += M[i + j * K] * M[i + j * K];
-      cn[j] = a;
+      for (int i = st + lane; i < ku; i += 32) a += M[i + j * K] * M[i + j * K];
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      if (lane == 0) cn[j] = a;
     }
     __syncthreads();
-    if (threadIdx.x == 0) {
+    // warp 0: pivot (largest remaining norm), stop test, swap, reflector
+    if (warp == 0) {
+      T best = (T)-1;
       int p = st;
-      for (int j = st + 1; j < kv; ++j)
-        if (cn[j] > cn[p]) p = j;
-      T nrm = sqrt(cn[p]);
-      if (st == 0) s_r0 = nrm;
-      s_stop = (nrm == (T)0 || (st > 0 && nrm <= (T)c.tol * s_r0)) ? 1 : 0;
-      s_p = p;
+      for (int j = st + lane; j < kv; j += 32)
+        if (cn[j] > best) {
+          best = cn[j];
+          p = j;
+        }
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int op = __shfl_xor_sync(0xffffffffu, p, o);
+        if (ob > best || (ob == best && op < p)) {
+          best = ob;
+          p = op;
+        }
+      }
+      const T nrm = sqrt(fmax(best, (T)0));
+      if (st == 0 && lane == 0) s_r0 = nrm;
+      __syncwarp();
+      const int stop = (nrm == (T)0 || (st > 0 && nrm <= (T)c.tol * s_r0)) ? 1 : 0;
+      if (lane == 0) s_stop = stop;
+      if (!stop) {
+        if (p != st) {
+          for (int i = lane; i < ku; i += 32) {
+            const T a = M[i + st * K];
+            M[i + st * K] = M[i + p * K];
+            M[i + p * K] = a;
+          }
+          if (lane == 0) {
+            const int a = piv[st];
+            piv[st] = piv[p];
+            piv[p] = a;
+          }
+        }
+        __syncwarp();
+        T a = 0;
+        for (int i = st + 1 + lane; i < ku; i += 32) a += M[i + st * K] * M[i + st * K];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        const T x0 = M[st + st * K];
+        const T sn = sqrt(x0 * x0 + a);
+        const T alpha = (x0 >= (T)0) ? -sn : sn;
+        const T v0 = x0 - alpha;
+        const bool trivial = (sn == (T)0) || (v0 == (T)0) || a == (T)0;
+        __syncwarp();
+        if (!trivial) {
+          const T iv = (T)1 / v0;
+          for (int i = st + 1 + lane; i < ku; i += 32) M[i + st * K] *= iv;
+        }
+        __syncwarp();
+        if (lane == 0) {
+          tauM[st] = trivial ? (T)0 : (alpha - x0) / alpha;
+          if (!trivial) M[st + st * K] = alpha;
+        }
+      }
     }
     __syncthreads();
     if (s_stop) break;
-    const int p = s_p;
-    if (p != st) {
-      for (int i = threadIdx.x; i < ku; i += blockDim.x) {
-        T a = M[i + st * K];
-        M[i + st * K] = M[i + p * K];
-        M[i + p * K] = a;
-      }
-      if (threadIdx.x == 0) {
-        int a = piv[st];
-        piv[st] = piv[p];
-        piv[p] = a;
-      }
-    }
-    __syncthreads();
-    // Householder on M[st:ku, st] (one warp), stored as in house_qr
-    if (warp == 0) {
-      T a = 0;
-      for (int i = st + lane; i < ku; i += 32) a += M[i + st * K] * M[i + st * K];
-      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-      T x0 = M[st + st * K];
-      T sn = sqrt(a);
-      T alpha = (x0 >= (T)0) ? -sn : sn;
-      T v0 = x0 - alpha;
-      bool trivial = (sn == (T)0) || (v0 == (T)0);
-      __syncwarp();
-      if (!trivial)
-        for (int i = st + 1 + lane; i < ku; i += 32) M[i + st * K] /= v0;
-      __syncwarp();
-      if (lane == 0) {
-        tauM[st] = trivial ? (T)0 : (alpha - x0) / alpha;
-        if (!trivial) M[st + st * K] = alpha;
-      }
-    }
-    __syncthreads();
     const T tj = tauM[st];
     if (tj != (T)0)
       for (int l = st + 1 + warp; l < kv; l += nw) {
         T w = 0;
         for (int i = st + 1 + lane; i < ku; i += 32) w += M[i + st * K] * M[i + l * K];
-        for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
-        w = __shfl_sync(0xffffffffu, w, 0);
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
         w = (w + M[st + l * K]) * tj;
+        __syncwarp();
         if (lane == 0) M[st + l * K] -= w;
         for (int i = st + 1 + lane; i < ku; i += 32) M[i + l * K] -= w * M[i + st * K];
       }
@@ -1341,6 +1390,7 @@ __device__ void trunc_core(HCtx<T>& c, int slot, T* Ut, T* Vt, int K) {
   // (all threads agree on r: every exit is uniform)
   T* Ud = c.ar + s.off;
   T* Vd = c.ar + s.off + (long long)m * s.kcap;
+  tmk(3);
   // Z = Q_M [I_r; 0] (ku x r): apply the r reflectors of M in reverse
   for (int t = threadIdx.x; t < ku * r; t += blockDim.x) Z[(t % ku) + (t / ku) * K] = (t % ku == t / ku) ? (T)1 : (T)0;
   __syncthreads();
@@ -1371,20 +1421,29 @@ __device__ void trunc_core(HCtx<T>& c, int slot, T* Ut, T* Vt, int K) {
     Vd[piv[j] + (long long)i * n] = (j >= i) ? M[i + j * K] : (T)0;
   }
   __syncthreads();
+  tmk(4);
   apply_q_staged(Ut, m, K, tauU, Ud, r, stage, cap);
+  tmk(5);
   apply_q_staged(Vt, n, K, tauV, Vd, r, stage, cap);
+  tmk(6);
+  if (c.tprof && threadIdx.x == 0) {
+    atomicAdd(c.tprof + 8, 1ULL);
+    atomicAdd(c.tprof + 9, (unsigned long long)K);
+    atomicAdd(c.tprof + 10, (unsigned long long)(m + n));
+  }
   if (threadIdx.x == 0) c.rk[slot] = r;
   __syncthreads();
 }
 
 template <class T>
-__device__ void op_append(const HOp& o, HCtx<T>& c) {
+// returns true when the append overflowed the capacity and recompressed
+__device__ bool op_append(const HOp& o, HCtx<T>& c) {
   const int slot = o.slot;
   const SlotDev s = c.sl[slot];
   const int k = dimv(o.A.c, c.rk);
   const int r0 = c.rk[slot];
   __syncthreads();
-  if (k <= 0) return;
+  if (k <= 0) return false;
   const bool ident = o.B.off < 0;                 // V_p = columns of I from ioff
   const long long ioff = ident ? (-1 - o.B.off) : 0;
   const T alpha = (T)o.alpha;
@@ -1403,7 +1462,7 @@ __device__ void op_append(const HOp& o, HCtx<T>& c) {
     __syncthreads();
     if (threadIdx.x == 0) c.rk[slot] = r0 + k;
     __syncthreads();
-    return;
+    return false;
   }
   const int K = r0 + k;
   T* Ut = c.ws;
@@ -1421,6 +1480,7 @@ __device__ void op_append(const HOp& o, HCtx<T>& c) {
   }
   __syncthreads();
   trunc_core(c, slot, Ut, Vt, K);
+  return true;
 }
 
 template <class T>
@@ -1442,7 +1502,7 @@ __device__ void op_trunc(const HOp& o, HCtx<T>& c) {
 
 struct HProgArgs {
   const HInstDev* inst;
-  const int* wcta;   // per wave, the CTAs' op ranges
+  const int* waves;  // op offsets of the waves
   const HOp* ops;
   const SlotDev* slots;
   int* ranks;
@@ -1454,6 +1514,7 @@ struct HProgArgs {
                               // (busy ns, longest op ns, longest op index)
   int wstride;                // waves per instance in wprof
   long long smem_elems;       // dynamic shared memory, in elements of the factor type
+  int n_inst_prof;            // instances in prof (the recompression phases follow them)
 };
 
 // algorithmic flops of one op with its run-time shapes
@@ -1502,9 +1563,11 @@ __device__ __forceinline__ void cluster_barrier() {
 }
 
 // One thread-block cluster of kCluster CTAs per instance runs the instance's
-// H-LU program wave by wave: the ops of a wave are independent and dealt to
-// the CTAs by the planner (longest first, to the least loaded CTA), a
-// cluster barrier separates consecutive waves.
+// H-LU program wave by wave: the ops of a wave are independent; a CTA that
+// becomes free takes the next op of the wave from a counter in the shared
+// memory of CTA 0 (distributed shared memory atomics; the planner orders a
+// wave's ops longest first), and a cluster barrier separates consecutive
+// waves.
 template <class T>
 __global__ void __launch_bounds__(kHThreads) k_hprog(HProgArgs a, T* har) {
   extern __shared__ __align__(16) unsigned char smraw[];
@@ -1518,28 +1581,55 @@ __global__ void __launch_bounds__(kHThreads) k_hprog(HProgArgs a, T* har) {
   c.ws = c.ar + H.ws_off + (long long)crank * H.ws_size;
   c.sm = reinterpret_cast<T*>(smraw);
   c.smcap = a.smem_elems;
+  c.tprof = a.prof ? a.prof + (size_t)a.n_inst_prof * 32 : nullptr;
   c.tol = a.tol;
   c.err = a.err + cid;
   const HOp* ops = a.ops + H.ops0;
-  const int* wc = a.wcta + H.wc0;
+  const int* waves = a.waves + H.fw0;
   const int nw = H.nfw;
+  // per-wave op counters (two, alternating), used in CTA 0
+  __shared__ unsigned s_ctr[2];
+  __shared__ int s_next;
+  if (threadIdx.x == 0) s_ctr[0] = s_ctr[1] = 0u;
+  const unsigned ctr_base = smem_u32(&s_ctr[0]);
+  unsigned ctr0;   // the counters of CTA 0 in the cluster's shared window
+  asm volatile("mapa.shared::cluster.u32 %0, %1, 0;" : "=r"(ctr0) : "r"(ctr_base));
+  cluster_barrier();
   double fl = 0.0;
   const bool wp = a.wprof && threadIdx.x == 0;
   for (int w = 0; w < nw; ++w) {
-    const int i0 = wc[w * (kCluster + 1) + crank], i1 = wc[w * (kCluster + 1) + crank + 1];
+    const int i0 = waves[w], n_w = waves[w + 1] - i0;
+    // the other counter is idle (every CTA passed the barrier after wave
+    // w - 1): reset it for wave w + 1
+    if (crank == 0 && threadIdx.x == 0) s_ctr[(w + 1) & 1] = 0u;
     unsigned long long tw0 = 0, busy = 0, lmax = 0, ltype = 0;
     if (wp) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(tw0));
-    for (int i = i0; i < i1; ++i) {
+    for (;;) {
+      if (threadIdx.x == 0) {
+        unsigned k;
+        asm volatile("atom.shared::cluster.add.u32 %0, [%1], 1;"
+                     : "=r"(k)
+                     : "r"(ctr0 + 4u * (unsigned)(w & 1))
+                     : "memory");
+        s_next = (int)k;
+      }
+      __syncthreads();
+      const int kk = s_next;
+      if (kk >= n_w) break;
+      const int i = i0 + kk;
       const HOp o = ops[i];
       if (threadIdx.x == 0) fl += op_flops(o, c.rk, c.sl);
       unsigned long long t0 = 0;
-      if ((a.prof && crank == 0 && threadIdx.x == 0) || wp) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+      if ((a.prof && threadIdx.x == 0) || wp) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+      int ptype = o.type;
       switch (o.type) {
         case OP_GEMM: op_gemm(o, c); break;
         case OP_GETRF_INV: op_getrf_inv(o, c); break;
         case OP_TRMM_L: op_trmm_l(o, c); break;
         case OP_TRMM_R: op_trmm_r(o, c); break;
-        case OP_APPEND: op_append(o, c); break;
+        case OP_APPEND:
+          if (op_append(o, c)) ptype = 9;   // the append recompressed (profile bucket)
+          break;
         case OP_TRUNC: op_trunc(o, c); break;
         case OP_ZERO: {
           int m = dimv(o.C.r, c.rk), n = dimv(o.C.c, c.rk);
@@ -1557,12 +1647,12 @@ __global__ void __launch_bounds__(kHThreads) k_hprog(HProgArgs a, T* har) {
         default: break;
       }
       __syncthreads();
-      if (a.prof && crank == 0 && threadIdx.x == 0) {
+      if (a.prof && threadIdx.x == 0) {   // all CTAs of the instance, summed
         unsigned long long t1;
         asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
-        unsigned long long* pr = a.prof + (size_t)cid * 32 + 2 * (o.type & 15);
-        pr[0] += t1 - t0;
-        pr[1] += 1ULL;
+        unsigned long long* pr = a.prof + (size_t)cid * 32 + 2 * (ptype & 15);
+        atomicAdd(pr, t1 - t0);
+        atomicAdd(pr + 1, 1ULL);
       }
       if (wp) {
         unsigned long long t1;
@@ -2159,7 +2249,8 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
       const int kmax_eff = opt.kmax ? opt.kmax : opt.R;
       const int max_concat = fp32 ? 160 : 112;   // shared memory of the recompression
       // a dense product appended to a low-rank block adds one leaf's worth of rank
-      const int leaf_cap = std::min(max_leaf, max_concat - 2 * kmax_eff);
+      // (in slices of 32 columns) to a block holding up to kKcapMult kmax
+      const int leaf_cap = std::min(max_leaf, max_concat - kKcapMult * kmax_eff);
       int leaf = opt.leaf_elems ? opt.leaf_elems : std::max(1, leaf_cap / I.P);
       leaf = std::min(leaf, std::max(1, leaf_cap / I.P));
       o.leaf_elems = leaf;
@@ -2257,7 +2348,7 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
         std::array<long long, 7> a{(long long)ops.size(), 0, (long long)slots.size(),
                                    (long long)dense.size(), (long long)pairs.size(),
                                    (long long)waves.size(), 0};
-        waves.insert(waves.end(), pb->plan.fac_cta.begin(), pb->plan.fac_cta.end());
+        waves.insert(waves.end(), pb->plan.fac_waves.begin(), pb->plan.fac_waves.end());
         ops.insert(ops.end(), pb->plan.fac.begin(), pb->plan.fac.end());
         slots.insert(slots.end(), pb->slots.begin(), pb->slots.end());
         dense.insert(dense.end(), pb->dense.begin(), pb->dense.end());
@@ -2299,7 +2390,7 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
       H.ws_off = p.ws_off;
       H.ws_size = p.ws_size;
       H.rhs_off = p.rhs_off;
-      H.wc0 = pi->second[5];
+      H.fw0 = pi->second[5];
 
       H.nfw = (int)p.fac_waves.size() - 1;
 
@@ -2506,12 +2597,33 @@ void hfsem_factor_s::report(const char* what) {
   std::vector<unsigned long long> h(d_prof.n);
   cudaMemcpy(h.data(), d_prof.p, h.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
   static const char* names[16] = {"?", "GEMM", "GETRF_INV", "TRMM_L", "TRMM_R", "APPEND",
-                                  "TRUNC", "ZERO", "AXPY", "?", "?", "?", "?", "?", "?", "?"};
-  fprintf(stderr, "[hfsem profile] %s (instance 0; ns, ops)\n", what);
-  for (int t = 0; t < 16; ++t)
-    if (h[2 * t + 1])
-      fprintf(stderr, "  %-10s %14llu ns %8llu ops %10.0f ns/op\n", names[t], h[2 * t], h[2 * t + 1],
-              (double)h[2 * t] / h[2 * t + 1]);
+                                  "TRUNC", "ZERO", "AXPY", "APPEND+TR", "?", "?", "?", "?", "?", "?"};
+  // the instance with the most op time
+  int worst = 0;
+  unsigned long long wt = 0;
+  for (size_t c = 0; c < (h.size() - 16) / 32; ++c) {
+    unsigned long long t = 0;
+    for (int k = 0; k < 16; ++k) t += h[c * 32 + 2 * k];
+    if (t > wt) {
+      wt = t;
+      worst = (int)c;
+    }
+  }
+  fprintf(stderr, "[hfsem profile] %s (instance %d, all CTAs; ns, ops)\n", what, worst);
+  for (int t = 0; t < 16; ++t) {
+    const unsigned long long ns = h[worst * 32 + 2 * t], n = h[worst * 32 + 2 * t + 1];
+    if (n) fprintf(stderr, "  %-10s %14llu ns %8llu ops %10.0f ns/op\n", names[t], ns, n, (double)ns / n);
+  }
+  {
+    const unsigned long long* q = &h[h.size() - 16];
+    if (q[8]) {
+      static const char* ph[7] = {"qr U", "qr V", "core", "rrqr", "Z+rows", "apply U", "apply V"};
+      fprintf(stderr, "[hfsem recompression] %llu calls (all instances), mean K %.1f, mean m+n %.0f; us/call:",
+              q[8], (double)q[9] / q[8], (double)q[10] / q[8]);
+      for (int k = 0; k < 7; ++k) fprintf(stderr, " %s %.1f", ph[k], q[k] * 1e-3 / q[8]);
+      fprintf(stderr, "\n");
+    }
+  }
   cudaMemset(d_prof.p, 0, d_prof.n * sizeof(unsigned long long));
 }
 
@@ -2575,7 +2687,7 @@ void hfsem_factor_s::report_waves(const char* what) {
 
 void hfsem_factor_s::run_prog() {
   if (!d_prof.p && getenv("HFSEM_PROFILE")) {
-    d_prof.alloc((size_t)sys->n_inst * 32);
+    d_prof.alloc((size_t)sys->n_inst * 32 + 16);
     cudaMemset(d_prof.p, 0, d_prof.n * sizeof(unsigned long long));
   }
   if (!d_flops.p) {
@@ -2591,7 +2703,7 @@ void hfsem_factor_s::run_prog() {
   }
   if (d_wprof.p) cudaMemsetAsync(d_wprof.p, 0, d_wprof.n * sizeof(unsigned long long), sys->st);
   hf::HProgArgs a{d_hi.p, d_waves.p, d_ops.p, d_slots.p, d_ranks.p, d_err.p, tol, d_prof.p, d_flops.p,
-                  d_wprof.p, wstride, (long long)(smem / tsize) - 8};
+                  d_wprof.p, wstride, (long long)(smem / tsize) - 8, sys->n_inst};
   hf::Tick tk(sys->st, "hlu_factor");
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(sys->n_inst * hf::kCluster));

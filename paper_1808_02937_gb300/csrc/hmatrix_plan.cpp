@@ -51,6 +51,7 @@ struct Builder {
   std::vector<HOp>* prog = nullptr;
   int max_m = 0;
   std::vector<char> dirty;   // LR block received updates since its last recompression
+  std::vector<int> rank_est; // per LR slot: estimated current rank (Taylor rank R at first)
 
   Builder(const InstHost& i, const PlanOpts& op, HPlan& pl) : I(i), o(op), p(pl) {}
 
@@ -138,7 +139,7 @@ struct Builder {
       } else if (b.type == B_LR) {
         int mn = std::min(b.m, b.n);
         b.kmax = std::min(o.kmax, mn);
-        b.kcap = std::max(o.R, std::min(mn, 2 * o.kmax));
+        b.kcap = std::max(o.R, std::min(mn, kKcapMult * o.kmax));
         b.off = top;
         top += (long long)(b.m + b.n) * b.kcap;
         b.slot = p.n_slots++;
@@ -191,7 +192,7 @@ struct Builder {
 
   // ---------------- op emission ----------------
   static bool empty(const View& v) { return v.r == 0 || v.c == 0; }
-  void op(int type, View A, View B, View C, double alpha, double beta, int slot = -1) {
+  void op(int type, View A, View B, View C, double alpha, double beta, int slot = -1, int kest = 0) {
     HOp h;
     h.type = type;
     h.slot = slot;
@@ -200,7 +201,16 @@ struct Builder {
     h.A = A;
     h.B = B;
     h.C = C;
+    h.kest = kest;
+    h.pad = 0;
     prog->push_back(h);
+  }
+  // estimated run-time value of a (possibly runtime) dimension: a rank is
+  // taken at the estimate the planner keeps for its slot
+  int est(int d) const {
+    if (d >= 0) return d;
+    if (-1 - d == p.n_slots) return p.nrhs_max;
+    return rank_est[-1 - d];
   }
   void gemm(View C, View A, View B, double alpha, double beta) {
     if (empty(C)) return;
@@ -220,7 +230,10 @@ struct Builder {
     p.kconcat_max = std::max(p.kconcat_max, b.kcap + kin);
     if (b.kcap + kin > o.max_concat)
       throw Error(HFSEM_ERR_UNSUPPORTED, "low-rank update larger than the recompression kernel");
-    op(OP_APPEND, U, V, lrU(cb), alpha, 0.0, b.slot);
+    // the append overflows (and recompresses) when the estimate passes kcap
+    const int kest = rank_est[b.slot] + est(U.c);
+    op(OP_APPEND, U, V, lrU(cb), alpha, 0.0, b.slot, kest);
+    rank_est[b.slot] = (kest > b.kcap) ? b.kmax : kest;
     dirty[cb] = 1;
   }
   void trunc(int cb) {
@@ -230,7 +243,8 @@ struct Builder {
     dirty[cb] = 0;
     const Block& b = p.B[cb];
     p.kconcat_max = std::max(p.kconcat_max, b.kcap);
-    op(OP_TRUNC, View{}, View{}, lrU(cb), 0.0, 0.0, b.slot);
+    op(OP_TRUNC, View{}, View{}, lrU(cb), 0.0, 0.0, b.slot, rank_est[b.slot]);
+    rank_est[b.slot] = std::min(rank_est[b.slot], b.kmax);
   }
 
   // C += alpha U V^T, C any format
@@ -503,6 +517,7 @@ void make_plan(const InstHost& I, const PlanOpts& o, HPlan& p) {
   b.block(root, root);
   b.storage();
   b.dirty.assign(p.B.size(), 0);
+  b.rank_est.assign(p.n_slots, o.R);
   // right-hand-side area, then temporaries, then the truncation workspace
   p.rhs_off = b.top;
   b.top += (long long)std::max(I.Nd, 1) * o.nrhs_max;
@@ -516,7 +531,7 @@ void make_plan(const InstHost& I, const PlanOpts& o, HPlan& p) {
   p.ws_size = (long long)2 * std::max(b.max_m, 1) * std::max(p.kconcat_max, 1);
   p.ncta = std::max(o.ncta, 1);
   p.arena = ws_off + p.ws_size * p.ncta;
-  schedule_program(p, p.fac, p.fac_waves, p.fac_cta);
+  schedule_program(p, p.fac, p.fac_waves);
 }
 
 }  // namespace hf
@@ -693,9 +708,14 @@ int program_levels(const HPlan& p, const std::vector<HOp>& prog, std::vector<int
 
 namespace hf {
 
+// recompression of an m x K and an n x K factor: K Householder steps on each,
+// a pivoted QR of the K x K core and two applications of the reflectors
+static double trunc_cost(int m, int n, int K) { return 8.0 + K * (1.5 + (m + n) / 400.0); }
+
 // Estimated run time (microseconds) of an op on one CTA, runtime ranks taken
-// as the Taylor rank: a fixed cost for the op's latencies plus its flops at
-// the rates the interpreter's kernels reach.
+// as the Taylor rank (or the planner's estimate for appends and
+// recompressions): a fixed cost for the op's latencies plus its work at the
+// rates the interpreter's kernels reach.
 static double op_cost(const HPlan& p, const HOp& o) {
   auto dim = [&](int d) -> double {
     if (d >= 0) return d;
@@ -713,19 +733,18 @@ static double op_cost(const HPlan& p, const HOp& o) {
     }
     case OP_TRUNC: {
       const Block& b = p.B[p.lr_blocks[o.slot]];
-      const double K = b.kcap;
-      return 8.0 + 4.0 * (b.m + b.n) * K * K / 5e4;
+      return trunc_cost(b.m, b.n, std::max(o.kest, 1));
     }
     case OP_APPEND: {
       const Block& b = p.B[p.lr_blocks[o.slot]];
+      if (o.kest > b.kcap) return trunc_cost(b.m, b.n, o.kest);   // overflow: recompression
       return 2.0 + (b.m + b.n) * dim(o.A.c) / 2e4;
     }
     default: return 0.5 + dim(o.C.r) * dim(o.C.c) / 1e5;
   }
 }
 
-void schedule_program(const HPlan& p, std::vector<HOp>& prog, std::vector<int>& waves,
-                      std::vector<int>& wcta) {
+void schedule_program(const HPlan& p, std::vector<HOp>& prog, std::vector<int>& waves) {
   // 1. split big ops into independent pieces
   std::vector<HOp> out;
   out.reserve(prog.size() * 2);
@@ -764,33 +783,16 @@ void schedule_program(const HPlan& p, std::vector<HOp>& prog, std::vector<int>& 
   std::vector<int> pos(waves.begin(), waves.end());
   prog.assign(out.size(), HOp());
   for (size_t i = 0; i < out.size(); ++i) prog[pos[lv[i] - 1]++] = out[i];
-  // 4. each wave's ops dealt to the CTAs longest first, each to the least
-  // loaded CTA; a CTA's ops of a wave are contiguous:
-  // wcta[w (ncta + 1) + c] .. wcta[w (ncta + 1) + c + 1]
-  const int nc = std::max(p.ncta, 1);
-  wcta.assign((size_t)nl * (nc + 1), 0);
+  // 4. within a wave, the longest ops first: the CTAs take ops in this order
+  // as they become free (a counter per wave), longest-processing-time first
   std::vector<HOp> tmp;
   for (int w = 0; w < nl; ++w) {
     const int a = waves[w], b = waves[w + 1];
     std::vector<std::pair<double, int>> ord;
     for (int i = a; i < b; ++i) ord.push_back({-op_cost(p, prog[i]), i});
     std::stable_sort(ord.begin(), ord.end());
-    std::vector<double> load(nc, 0.0);
-    std::vector<std::vector<int>> to(nc);
-    for (auto& q : ord) {
-      int c = 0;
-      for (int k = 1; k < nc; ++k)
-        if (load[k] < load[c]) c = k;
-      load[c] -= q.first;
-      to[c].push_back(q.second);
-    }
     tmp.clear();
-    for (int c = 0; c < nc; ++c) {
-      wcta[(size_t)w * (nc + 1) + c] = a + (int)tmp.size();
-      std::sort(to[c].begin(), to[c].end());   // program order within the CTA
-      for (int i : to[c]) tmp.push_back(prog[i]);
-    }
-    wcta[(size_t)w * (nc + 1) + nc] = b;
+    for (auto& q : ord) tmp.push_back(prog[q.second]);
     std::copy(tmp.begin(), tmp.end(), prog.begin() + a);
   }
 }

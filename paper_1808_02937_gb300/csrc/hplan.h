@@ -36,6 +36,9 @@ struct HOp {
   int slot;            // LR slot (APPEND / TRUNC)
   double alpha, beta;
   View A, B, C;
+  int kest;            // APPEND / TRUNC: the planner's estimate of the rank the slot
+                       // reaches (scheduling only; the device reads ranks at run time)
+  int pad;
 };
 
 enum BlkType : int { B_DENSE = 0, B_LR = 1, B_HIER = 2 };
@@ -82,10 +85,14 @@ struct HPlan {
   };
   std::vector<TmpAlloc> tmps;          // every temporary handed out
   std::vector<int> fac_waves;          // op offsets of the dependency waves
-  std::vector<int> fac_cta;            // per wave, the CTAs' op ranges (ncta + 1 offsets)
   int ncta = 1;                        // CTAs that execute one instance
   int R = 0;                           // rank of the Taylor factors
 };
+
+// Capacity of a low-rank block in multiples of kmax: updates are appended
+// until the capacity is reached, then the block is recompressed (fewer,
+// larger recompressions for a larger multiple).
+constexpr int kKcapMult = 2;
 
 struct PlanOpts {
   double lambda;
@@ -169,8 +176,7 @@ size_t solve_smem(int jmax, int nmax, int wcols, int ts, int sw);
 int program_levels(const HPlan& p, const std::vector<HOp>& prog, std::vector<int>& level);
 
 // Split large ops into independent tile ops, then order the program by
-// dependency level; waves[w] .. waves[w+1] are the ops of wave w, dealt to
-// p.ncta CTAs (wcta: per wave ncta + 1 offsets).
-void schedule_program(const HPlan& p, std::vector<HOp>& prog, std::vector<int>& waves,
-                      std::vector<int>& wcta);
+// dependency level; waves[w] .. waves[w+1] are the ops of wave w, longest
+// (by a cost model) first.
+void schedule_program(const HPlan& p, std::vector<HOp>& prog, std::vector<int>& waves);
 }  // namespace hf
