@@ -539,32 +539,99 @@ __device__ void op_gemm(const HOp& o, HCtx<T>& c) {
     }
     return;
   }
-  {
-    // staged: A, B and C reach shared memory in one pass of asynchronous
-    // copies; outputs in column-major order (coalesced C), the inner
-    // dimension split over idle threads when the output is small
-    const long long mn = (long long)m * n;
-    const long long need = (long long)m * k + (long long)k * n + mn;
-    if ((mn <= 4096 || k <= 32) && need + 16 * 256 <= c.smcap) {
-      T* As = c.sm;                 // [i + kk m]
-      T* Bs = As + (long long)m * k;   // [kk + j k]
-      T* Cs = Bs + (long long)k * n;   // [i + j m]
-      T* red = Cs + mn;             // partials of the split inner dimension
+  if constexpr (sizeof(T) == 4) {
+    // rank-k update of an aligned column-major C (k <= 16): A and B staged,
+    // C moved with 16-byte accesses, eight in flight per thread
+    if (k <= 16 && m >= 64 && n >= 32 && !o.C.tr && (m & 3) == 0 && (o.C.off & 3) == 0 &&
+        (o.C.ld & 3) == 0 && (long long)m * k + (long long)k * n + 64 <= c.smcap) {
+      float* As = c.sm;                    // [i + kk m]
+      float* Bs = As + (long long)m * k;   // [kk + j k]
       stage_view(As, m, ar, o.A, m, k);
       stage_view(Bs, k, ar, o.B, k, n);
-      if (beta != (T)0) stage_view(Cs, m, ar, o.C, m, n);
+      cp_async_wait_all();
+      __syncthreads();
+      const int m4 = m >> 2, items = m4 * n;
+      const long long ldc = o.C.ld;
+      for (int u0 = tid; u0 < items; u0 += 8 * nt) {
+        float4 cv[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int u = u0 + q * nt;
+          if (u < items && beta != 0.f)
+            cv[q] = *reinterpret_cast<const float4*>(ar + o.C.off + 4LL * (u % m4) + (long long)(u / m4) * ldc);
+          else
+            cv[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int u = u0 + q * nt;
+          if (u < items) {
+            const int i4 = u % m4, j = u / m4;
+            float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int kk = 0; kk < k; ++kk) {
+              const float4 a4 = *reinterpret_cast<const float4*>(As + 4 * i4 + (long long)kk * m);
+              const float b = Bs[kk + (long long)j * k];
+              acc.x += a4.x * b;
+              acc.y += a4.y * b;
+              acc.z += a4.z * b;
+              acc.w += a4.w * b;
+            }
+            float4 out;
+            out.x = beta * cv[q].x + alpha * acc.x;
+            out.y = beta * cv[q].y + alpha * acc.y;
+            out.z = beta * cv[q].z + alpha * acc.z;
+            out.w = beta * cv[q].w + alpha * acc.w;
+            *reinterpret_cast<float4*>(ar + o.C.off + 4LL * i4 + (long long)j * ldc) = out;
+          }
+        }
+      }
+      __syncthreads();
+      return;
+    }
+  }
+  {
+    // staged: A and B reach shared memory in one pass of asynchronous copies;
+    // the outputs run in column-major order (coalesced C, four loads of C in
+    // flight per thread), the inner dimension split over idle threads when
+    // the output is small
+    const long long mn = (long long)m * n;
+    const long long need = (long long)m * k + (long long)k * n;
+    if ((mn <= 4096 || k <= 32) && need + 16 * 256 <= c.smcap) {
+      T* As = c.sm;                    // [i + kk m]
+      T* Bs = As + (long long)m * k;   // [kk + j k]
+      T* red = Bs + (long long)k * n;  // partials of the split inner dimension
+      stage_view(As, m, ar, o.A, m, k);
+      stage_view(Bs, k, ar, o.B, k, n);
       cp_async_wait_all();
       __syncthreads();
       const int imn = (int)mn;
       const int S = (imn >= nt) ? 1 : min(nt / imn, 16);
       if (S == 1) {
-        for (int t = tid; t < imn; t += nt) {
-          const int i = t % m, j = t / m;
-          const T* a = As + i;
-          const T* b = Bs + (long long)j * k;
-          T acc = 0;
-          for (int kk = 0; kk < k; ++kk) acc += a[(long long)kk * m] * b[kk];
-          ar[vidx(o.C, i, j)] = (beta == (T)0 ? (T)0 : beta * Cs[t]) + alpha * acc;
+        for (int t0 = tid; t0 < imn; t0 += 4 * nt) {
+          long long ci[4];
+          T cv[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int t = t0 + u * nt;
+            ci[u] = -1;
+            cv[u] = (T)0;
+            if (t < imn) {
+              ci[u] = vidx(o.C, t % m, t / m);
+              if (beta != (T)0) cv[u] = ar[ci[u]];
+            }
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int t = t0 + u * nt;
+            if (t < imn) {
+              const int i = t % m, j = t / m;
+              const T* a = As + i;
+              const T* b = Bs + (long long)j * k;
+              T acc = 0;
+              for (int kk = 0; kk < k; ++kk) acc += a[(long long)kk * m] * b[kk];
+              ar[ci[u]] = beta * cv[u] + alpha * acc;
+            }
+          }
         }
       } else {
         const int t = tid % imn, sl = tid / imn;
@@ -580,7 +647,8 @@ __device__ void op_gemm(const HOp& o, HCtx<T>& c) {
           T acc = 0;
           for (int q = 0; q < S; ++q) acc += red[q * imn + t2];
           const int i = t2 % m, j = t2 / m;
-          ar[vidx(o.C, i, j)] = (beta == (T)0 ? (T)0 : beta * Cs[t2]) + alpha * acc;
+          const long long ci = vidx(o.C, i, j);
+          ar[ci] = (beta == (T)0 ? (T)0 : beta * ar[ci]) + alpha * acc;
         }
       }
       __syncthreads();
@@ -682,10 +750,14 @@ __device__ void op_gemm(const HOp& o, HCtx<T>& c) {
 #pragma unroll
           for (int q = 0; q < 4; ++q) {
             int t = tid + q * 256;
+            // A by rows (consecutive threads, consecutive rows), B by k
+            // (eight threads read the eight k of one column)
             int kk = t >> 7, ii = t & 127;
-            int gi = m0 + ii, gj = n0 + ii, gk = k0 + kk;
+            int gi = m0 + ii, gk = k0 + kk;
             ra[q] = (gi < m && gk < k) ? ar[vidx(o.A, gi, gk)] : (T)0;
-            rb[q] = (gj < n && gk < k) ? ar[vidx(o.B, gk, gj)] : (T)0;
+            int kb = t & 7, jb = t >> 3;
+            int gj = n0 + jb, gkb = k0 + kb;
+            rb[q] = (gj < n && gkb < k) ? ar[vidx(o.B, gkb, gj)] : (T)0;
           }
         };
         fetch(0);
@@ -695,7 +767,7 @@ __device__ void op_gemm(const HOp& o, HCtx<T>& c) {
           for (int q = 0; q < 4; ++q) {
             int t = tid + q * 256;
             As[t] = ra[q];
-            Bs[t] = rb[q];
+            Bs[(t & 7) * 128 + (t >> 3)] = rb[q];
           }
           __syncthreads();
           if (k0 + 8 < k) fetch(k0 + 8);
@@ -715,17 +787,25 @@ __device__ void op_gemm(const HOp& o, HCtx<T>& c) {
               for (int q = 0; q < 8; ++q) acc[p][q] += a[p] * b[q];
           }
         }
+        // the tile goes through shared memory so that C is read and written
+        // in column-major order (coalesced)
+        T* Ct = c.sm + 2 * 8 * 128;   // [128][129]
+        __syncthreads();
 #pragma unroll
         for (int p = 0; p < 8; ++p)
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
-            int gi = m0 + (p < 4 ? ty * 4 + p : 64 + ty * 4 + p - 4);
-            int gj = n0 + (q < 4 ? tx * 4 + q : 64 + tx * 4 + q - 4);
-            if (gi < m && gj < n) {
-              long long ci = vidx(o.C, gi, gj);
-              ar[ci] = (beta == (T)0 ? (T)0 : beta * ar[ci]) + alpha * acc[p][q];
-            }
+            const int li = p < 4 ? ty * 4 + p : 64 + ty * 4 + p - 4;
+            const int lj = q < 4 ? tx * 4 + q : 64 + tx * 4 + q - 4;
+            Ct[li + lj * 129] = acc[p][q];
           }
+        __syncthreads();
+        const int mt = min(128, m - m0), ntl = min(128, n - n0);
+        for (int t = tid; t < mt * ntl; t += nt) {
+          const int li = t % mt, lj = t / mt;
+          const long long ci = vidx(o.C, m0 + li, n0 + lj);
+          ar[ci] = (beta == (T)0 ? (T)0 : beta * ar[ci]) + alpha * Ct[li + lj * 129];
+        }
       }
     __syncthreads();
     return;
@@ -1131,11 +1211,20 @@ __device__ void op_getrf_inv(const HOp& o, HCtx<T>& c) {
 // d_l = sum_{i>j} A[i][j] A[i][l]); the owner of column j scales its
 // reflector at the start of step j + 1, when no warp reads it any more.  One
 // barrier per step.
+// barrier of the warps [w0, w0 + nw) (the whole CTA when nw covers it)
+__device__ __forceinline__ void group_sync(int nw, int bar_id) {
+  if (nw * 32 == (int)blockDim.x) {
+    __syncthreads();
+  } else {
+    asm volatile("bar.sync %0, %1;" ::"r"(bar_id), "r"(nw * 32) : "memory");
+  }
+}
+
 template <class T>
-__device__ void house_qr(T* A, int m, int K, T* tau, T* red) {
-  (void)red;
+__device__ void house_qr(T* A, int m, int K, T* tau, int w0 = 0, int nw_ = 0, int bar_id = 0) {
   const int kr = min(m, K);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nw = nw_ ? nw_ : (int)(blockDim.x >> 5);
+  const int lane = threadIdx.x & 31, warp = (int)(threadIdx.x >> 5) - w0;
   T pv0 = (T)0;   // v0 of the previous step (used by the owner of its column)
   for (int j = 0; j < kr; ++j) {
     // the owner of column j - 1 turns it into its reflector
@@ -1168,7 +1257,7 @@ __device__ void house_qr(T* A, int m, int K, T* tau, T* red) {
         for (int i = j + 1 + lane; i < m; i += 32) cl[i] -= wv * cj[i];
       }
     }
-    __syncthreads();
+    group_sync(nw, bar_id);
     if ((j % nw) == warp && lane == 0) {
       tau[j] = tj;
       if (!trivial) A[j + (long long)j * m] = alpha;
@@ -1181,14 +1270,16 @@ __device__ void house_qr(T* A, int m, int K, T* tau, T* red) {
     const T inv = (T)1 / pv0;
     for (int i = kr + lane; i < m; i += 32) col[i] *= inv;
   }
-  __syncthreads();
+  group_sync(nw, bar_id);
 }
 
 // Y (m x r, ld ldy) <- Q Y with Q = H_0 ... H_{kr-1} stored in A (m x K)
 template <class T>
-__device__ void apply_q(const T* A, int m, int K, const T* tau, T* Y, int ldy, int r) {
+__device__ void apply_q(const T* A, int m, int K, const T* tau, T* Y, int ldy, int r, int w0 = 0,
+                        int nw_ = 0, int bar_id = 0) {
   const int kr = min(m, K);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int nw = nw_ ? nw_ : (int)(blockDim.x >> 5);
+  const int lane = threadIdx.x & 31, warp = (int)(threadIdx.x >> 5) - w0;
   for (int j = kr - 1; j >= 0; --j) {
     T tj = tau[j];
     if (tj != (T)0) {
@@ -1202,7 +1293,7 @@ __device__ void apply_q(const T* A, int m, int K, const T* tau, T* Y, int ldy, i
         for (int i = j + 1 + lane; i < m; i += 32) Y[i + (long long)col * ldy] -= w * A[i + (long long)j * m];
       }
     }
-    __syncthreads();
+    group_sync(nw, bar_id);
   }
 }
 
@@ -1211,12 +1302,12 @@ template <class T>
 __device__ void qr_staged(T* A, int m, int K, T* tau, T* red, T* stage, long long cap) {
   const long long mk = (long long)m * K;
   if (mk > cap) {
-    house_qr(A, m, K, tau, red);
+    house_qr(A, m, K, tau);
     return;
   }
   for (long long t = threadIdx.x; t < mk; t += blockDim.x) stage[t] = A[t];
   __syncthreads();
-  house_qr(stage, m, K, tau, red);
+  house_qr(stage, m, K, tau);
   for (long long t = threadIdx.x; t < mk; t += blockDim.x) A[t] = stage[t];
   __syncthreads();
 }
@@ -1274,16 +1365,36 @@ __device__ void trunc_core(HCtx<T>& c, int slot, T* Ut, T* Vt, int K) {
     tq = t1;
   };
   tmk(-1);
-  qr_staged(Ut, m, K, tauU, red, stage, cap);
-  tmk(0);
-  qr_staged(Vt, n, K, tauV, red, stage, cap);
+  const int nwt = (int)(blockDim.x >> 5), nwh = nwt / 2;
+  const int wid = (int)(threadIdx.x >> 5);
+  // both factors and their outputs fit: the two halves of the CTA factor U
+  // and V at the same time (named barriers 1 and 2) and keep the reflectors
+  const bool both = (long long)(m + n) * K * 2 <= cap && nwh > 0;
+  T* SU = stage;
+  T* SV = stage + (long long)m * K;
+  if (both) {
+    for (long long t = threadIdx.x; t < (long long)m * K; t += blockDim.x) SU[t] = Ut[t];
+    for (long long t = threadIdx.x; t < (long long)n * K; t += blockDim.x) SV[t] = Vt[t];
+    __syncthreads();
+    if (wid < nwh) house_qr(SU, m, K, tauU, 0, nwh, 1);
+    else if (wid < 2 * nwh) house_qr(SV, n, K, tauV, nwh, nwh, 2);
+    __syncthreads();
+    tmk(0);
+  } else {
+    qr_staged(Ut, m, K, tauU, red, stage, cap);
+    tmk(0);
+    qr_staged(Vt, n, K, tauV, red, stage, cap);
+  }
   tmk(1);
   const int ku = min(m, K), kv = min(n, K);
   // core M = R_U R_V^T from the two triangles, staged
   T* RU = Ut;
   T* RV = Vt;
   long long ldu = m, ldv = n;
-  if ((long long)2 * K * K <= cap) {
+  if (both) {
+    RU = SU;
+    RV = SV;
+  } else if ((long long)2 * K * K <= cap) {
     RU = stage;
     RV = stage + (long long)K * K;
     for (int t = threadIdx.x; t < K * K; t += blockDim.x) {
@@ -1408,23 +1519,35 @@ __device__ void trunc_core(HCtx<T>& c, int slot, T* Ut, T* Vt, int K) {
       }
     __syncthreads();
   }
-  // U_new = Q_U [Z; 0]
+  // U_new = Q_U [Z; 0], V_new = Q_V [Pi R_M[:r,:]^T; 0] (row piv[j] of the
+  // core factor is R_M[:, j]); built in shared memory when both fit
+  T* YU = both ? SV + (long long)n * K : Ud;
+  T* YV = both ? YU + (long long)m * r : Vd;
   for (int t = threadIdx.x; t < m * r; t += blockDim.x) {
     int i = t % m, j = t / m;
-    Ud[t] = (i < ku) ? Z[i + j * K] : (T)0;
+    YU[t] = (i < ku) ? Z[i + j * K] : (T)0;
   }
-  // V_new = Q_V [Pi R_M[:r,:]^T; 0]: row piv[j] of the core factor is R_M[:, j]
-  for (int t = threadIdx.x; t < n * r; t += blockDim.x) Vd[t] = 0;
+  for (int t = threadIdx.x; t < n * r; t += blockDim.x) YV[t] = 0;
   __syncthreads();
   for (int t = threadIdx.x; t < kv * r; t += blockDim.x) {
     int j = t % kv, i = t / kv;   // R_M[i][j], j >= i
-    Vd[piv[j] + (long long)i * n] = (j >= i) ? M[i + j * K] : (T)0;
+    YV[piv[j] + (long long)i * n] = (j >= i) ? M[i + j * K] : (T)0;
   }
   __syncthreads();
   tmk(4);
-  apply_q_staged(Ut, m, K, tauU, Ud, r, stage, cap);
-  tmk(5);
-  apply_q_staged(Vt, n, K, tauV, Vd, r, stage, cap);
+  if (both) {
+    if (wid < nwh) apply_q(SU, m, K, tauU, YU, m, r, 0, nwh, 1);
+    else if (wid < 2 * nwh) apply_q(SV, n, K, tauV, YV, n, r, nwh, nwh, 2);
+    __syncthreads();
+    tmk(5);
+    for (int t = threadIdx.x; t < m * r; t += blockDim.x) Ud[t] = YU[t];
+    for (int t = threadIdx.x; t < n * r; t += blockDim.x) Vd[t] = YV[t];
+    __syncthreads();
+  } else {
+    apply_q_staged(Ut, m, K, tauU, Ud, r, stage, cap);
+    tmk(5);
+    apply_q_staged(Vt, n, K, tauV, Vd, r, stage, cap);
+  }
   tmk(6);
   if (c.tprof && threadIdx.x == 0) {
     atomicAdd(c.tprof + 8, 1ULL);
@@ -1653,6 +1776,13 @@ __global__ void __launch_bounds__(kHThreads) k_hprog(HProgArgs a, T* har) {
         unsigned long long* pr = a.prof + (size_t)cid * 32 + 2 * (ptype & 15);
         atomicAdd(pr, t1 - t0);
         atomicAdd(pr + 1, 1ULL);
+        if (o.type == OP_GEMM) {   // GEMM time by shape class (m, n, k: <=8, <=64, >64)
+          auto cls = [](int d) { return d <= 8 ? 0 : (d <= 64 ? 1 : 2); };
+          const int key = cls(dimv(o.C.r, c.rk)) * 9 + cls(dimv(o.C.c, c.rk)) * 3 + cls(dimv(o.A.c, c.rk));
+          unsigned long long* g = a.prof + (size_t)a.n_inst_prof * 32 + 16 + 2 * key;
+          atomicAdd(g, t1 - t0);
+          atomicAdd(g + 1, 1ULL);
+        }
       }
       if (wp) {
         unsigned long long t1;
@@ -2168,7 +2298,7 @@ static size_t prog_smem(const HPlan& p, size_t ts) {
   size_t K = (size_t)std::max(p.kconcat_max, 1);
   size_t trunc = 2 * K + 32 + 2 * K * K + 3 * K + 8;
   size_t trmm = (size_t)p.leaf_max * p.leaf_max + (size_t)std::max(p.leaf_max, 1) * 33;
-  size_t gemm = 2 * 16 * 64;
+  size_t gemm = 2 * 8 * 128 + 128 * 129;   // tiled GEMM: k chunks and the C tile
   return std::max(std::max(leaf, trunc), std::max(trmm, gemm)) * ts + 64;
 }
 
@@ -2601,7 +2731,8 @@ void hfsem_factor_s::report(const char* what) {
   // the instance with the most op time
   int worst = 0;
   unsigned long long wt = 0;
-  for (size_t c = 0; c < (h.size() - 16) / 32; ++c) {
+  const size_t ninst = (h.size() - 16 - 64) / 32;
+  for (size_t c = 0; c < ninst; ++c) {
     unsigned long long t = 0;
     for (int k = 0; k < 16; ++k) t += h[c * 32 + 2 * k];
     if (t > wt) {
@@ -2615,7 +2746,7 @@ void hfsem_factor_s::report(const char* what) {
     if (n) fprintf(stderr, "  %-10s %14llu ns %8llu ops %10.0f ns/op\n", names[t], ns, n, (double)ns / n);
   }
   {
-    const unsigned long long* q = &h[h.size() - 16];
+    const unsigned long long* q = &h[ninst * 32];
     if (q[8]) {
       static const char* ph[7] = {"qr U", "qr V", "core", "rrqr", "Z+rows", "apply U", "apply V"};
       fprintf(stderr, "[hfsem recompression] %llu calls (all instances), mean K %.1f, mean m+n %.0f; us/call:",
@@ -2623,6 +2754,15 @@ void hfsem_factor_s::report(const char* what) {
       for (int k = 0; k < 7; ++k) fprintf(stderr, " %s %.1f", ph[k], q[k] * 1e-3 / q[8]);
       fprintf(stderr, "\n");
     }
+  }
+  {
+    const unsigned long long* g = &h[ninst * 32 + 16];
+    static const char* cl[3] = {"<=8", "<=64", ">64"};
+    fprintf(stderr, "[hfsem gemm shapes] (all instances; m x n x k classes)\n");
+    for (int key = 0; key < 27; ++key)
+      if (g[2 * key + 1])
+        fprintf(stderr, "  m%-4s n%-4s k%-4s %10.3f ms %7llu ops %8.0f ns/op\n", cl[key / 9], cl[(key / 3) % 3],
+                cl[key % 3], g[2 * key] * 1e-6, g[2 * key + 1], (double)g[2 * key] / g[2 * key + 1]);
   }
   cudaMemset(d_prof.p, 0, d_prof.n * sizeof(unsigned long long));
 }
@@ -2687,7 +2827,7 @@ void hfsem_factor_s::report_waves(const char* what) {
 
 void hfsem_factor_s::run_prog() {
   if (!d_prof.p && getenv("HFSEM_PROFILE")) {
-    d_prof.alloc((size_t)sys->n_inst * 32 + 16);
+    d_prof.alloc((size_t)sys->n_inst * 32 + 16 + 64);
     cudaMemset(d_prof.p, 0, d_prof.n * sizeof(unsigned long long));
   }
   if (!d_flops.p) {

@@ -26,6 +26,11 @@
 namespace hf {
 namespace {
 
+// every allocation of the arena starts on a multiple of 4 entries (16 bytes
+// in FP32), so columns of blocks whose leading dimension is a multiple of 4
+// can be moved with 16-byte accesses
+inline long long align4(long long x) { return (x + 3) & ~3LL; }
+
 View vT(View v) {
   std::swap(v.r, v.c);
   v.tr ^= 1;
@@ -127,21 +132,21 @@ struct Builder {
       max_m = std::max(max_m, std::max(b.m, b.n));
       if (b.type == B_DENSE) {
         b.off = top;
-        top += (long long)b.m * b.n;
+        top = align4(top + (long long)b.m * b.n);
         p.dense_blocks.push_back((int)i);
         if (b.t == b.s) {
           if (b.m > o.max_leaf)
             throw Error(HFSEM_ERR_UNSUPPORTED, "diagonal leaf larger than the kernel supports");
           p.leaf_max = std::max(p.leaf_max, b.m);
           b.inv = top;
-          top += 2LL * b.m * b.m;
+          top = align4(top + 2LL * b.m * b.m);
         }
       } else if (b.type == B_LR) {
         int mn = std::min(b.m, b.n);
         b.kmax = std::min(o.kmax, mn);
         b.kcap = std::max(o.R, std::min(mn, kKcapMult * o.kmax));
         b.off = top;
-        top += (long long)(b.m + b.n) * b.kcap;
+        top = align4(top + (long long)(b.m + b.n) * b.kcap);
         b.slot = p.n_slots++;
         p.lr_blocks.push_back((int)i);
       }
@@ -182,7 +187,7 @@ struct Builder {
   View tmp(int r, int c_bound, int c_dim) {
     View v{tmp_top, r, c_dim, std::max(r, 1), 0};
     p.tmps.push_back({tmp_top, (long long)std::max(r, 1) * std::max(c_bound, 1), std::max(r, 1)});
-    tmp_top += (long long)std::max(r, 1) * std::max(c_bound, 1);
+    tmp_top = align4(tmp_top + (long long)std::max(r, 1) * std::max(c_bound, 1));
     tmp_peak = std::max(tmp_peak, tmp_top - tmp_base);
     return v;
   }
@@ -520,7 +525,7 @@ void make_plan(const InstHost& I, const PlanOpts& o, HPlan& p) {
   b.rank_est.assign(p.n_slots, o.R);
   // right-hand-side area, then temporaries, then the truncation workspace
   p.rhs_off = b.top;
-  b.top += (long long)std::max(I.Nd, 1) * o.nrhs_max;
+  b.top = align4(b.top + (long long)std::max(I.Nd, 1) * o.nrhs_max);
   b.tmp_base = b.tmp_top = b.top;
   b.prog = &p.fac;
   b.hlu(0);
