@@ -489,9 +489,25 @@ __device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
-// dst[i + j ldd] <- view(i, j), i < m, j < n
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+
+// dst[i + j ldd] <- view(i, j), i < m, j < n; 16-byte copies when the view is
+// column-major and every column run starts on a 16-byte boundary on both sides
 template <class T>
 __device__ __forceinline__ void stage_view(T* dst, int ldd, const T* ar, const View& v, int m, int n) {
+  if constexpr (sizeof(T) == 4) {
+    if (!v.tr && (m & 3) == 0 && (ldd & 3) == 0 && (v.off & 3) == 0 && (v.ld & 3) == 0 &&
+        ((smem_u32(dst) & 15u) == 0) && ((reinterpret_cast<unsigned long long>(ar) & 15ULL) == 0)) {
+      const int m4 = m >> 2, total4 = m4 * n;
+      for (int t = threadIdx.x; t < total4; t += blockDim.x) {
+        const int i4 = t % m4, j = t / m4;
+        cp_async16(dst + 4 * i4 + (long long)j * ldd, ar + v.off + 4LL * i4 + (long long)j * v.ld);
+      }
+      return;
+    }
+  }
   const int total = m * n;
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
     const int i = t % m, j = t / m;
@@ -943,17 +959,54 @@ __device__ void op_trmm_r(const HOp& o, HCtx<T>& c) {
   const int m = dimv(o.C.r, c.rk), n = dimv(o.C.c, c.rk);
   if (m <= 0 || n <= 0) return;
   T* ar = c.ar;
-  T* As = c.sm;            // n x n, [k n + j]
-  T* Pn = c.sm + n * n;    // 32 x n, [i + k * 32]
+  // A row-major with a padded row (lda = n + 1: the staging stores meet 4-way
+  // bank conflicts at most, the row reads none)
+  const int lda = n + 1;
+  T* As = c.sm;                                 // n x n, [k lda + j]
+  T* Pn = c.sm + (((long long)n * lda + 3) & ~3LL);   // 32 x n, [i + k * 32] (16-byte aligned)
   const int tid = threadIdx.x;
-  for (int t = tid; t < n * n; t += blockDim.x)
-    cp_async_elem(As + (t % n) * n + t / n, ar + vidx(o.A, t % n, t / n));
+  bool vec = false;
+  if constexpr (sizeof(T) == 4)
+    vec = !o.A.tr && (n & 3) == 0 && (o.A.off & 3) == 0 && (o.A.ld & 3) == 0;
+  if (vec) {
+    // A (column-major, aligned) read with 16-byte loads, stored row-major
+    const int n4 = n >> 2, tot = n4 * n;
+    for (int t0 = tid; t0 < tot; t0 += 4 * blockDim.x) {
+      float4 v[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int t = t0 + q * blockDim.x;
+        if (t < tot)
+          v[q] = *reinterpret_cast<const float4*>(ar + o.A.off + 4LL * (t % n4) + (long long)(t / n4) * o.A.ld);
+      }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int t = t0 + q * blockDim.x;
+        if (t < tot) {
+          const int i = 4 * (t % n4), j = t / n4;
+          As[(i + 0) * lda + j] = v[q].x;
+          As[(i + 1) * lda + j] = v[q].y;
+          As[(i + 2) * lda + j] = v[q].z;
+          As[(i + 3) * lda + j] = v[q].w;
+        }
+      }
+    }
+  } else {
+    for (int t = tid; t < n * n; t += blockDim.x)
+      cp_async_elem(As + (t % n) * lda + t / n, ar + vidx(o.A, t % n, t / n));
+  }
   const int tx = tid & 31, ty = tid >> 5;
   for (int r0 = 0; r0 < m; r0 += 32) {
     const int rp = min(32, m - r0);
     __syncthreads();
-    for (int t = tid; t < rp * n; t += blockDim.x)
-      cp_async_elem(Pn + (t % rp) + (t / rp) * 32, ar + vidx(o.C, r0 + t % rp, t / rp));
+    if (rp == 32) {
+      View Cr = o.C;   // rows r0 .. r0 + 31
+      Cr.off = vidx(o.C, r0, 0);
+      stage_view(Pn, 32, ar, Cr, 32, n);
+    } else {
+      for (int t = tid; t < rp * n; t += blockDim.x)
+        cp_async_elem(Pn + (t % rp) + (t / rp) * 32, ar + vidx(o.C, r0 + t % rp, t / rp));
+    }
     cp_async_wait_all();
     __syncthreads();
     T acc[4][4];
@@ -966,7 +1019,7 @@ __device__ void op_trmm_r(const HOp& o, HCtx<T>& c) {
 #pragma unroll
       for (int p = 0; p < 4; ++p) a[p] = Pn[ty * 4 + p + k * 32];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) b[q] = (tx + 32 * q < n) ? As[k * n + tx + 32 * q] : (T)0;
+      for (int q = 0; q < 4; ++q) b[q] = (tx + 32 * q < n) ? As[k * lda + tx + 32 * q] : (T)0;
 #pragma unroll
       for (int p = 0; p < 4; ++p)
 #pragma unroll
@@ -987,19 +1040,42 @@ __device__ void op_trmm_r(const HOp& o, HCtx<T>& c) {
 // elimination matrix, so X ends as L^-1; every value a step reads is left
 // untouched by that step, hence one barrier per step.  U^-1 = (D^-1 U)^-1 D^-1
 // with D = diag(U), again one barrier per step.
+// named barriers of the leaf LU (ids 1 and 2, all threads of the CTA)
+__device__ __forceinline__ void nbar_sync(int id) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"((int)blockDim.x) : "memory");
+}
+__device__ __forceinline__ void nbar_arrive(int id) {
+  asm volatile("bar.arrive %0, %1;" ::"r"(id), "r"((int)blockDim.x) : "memory");
+}
+
 // FP32 leaves (n <= 128), register resident: thread (tx, ty) holds rows
 // tx + 32 r (r < 4) and columns ty + 8 q (q < 16) of the matrix and of the
-// inverse being built.  Step k sends column k (the multipliers) and row k
-// through two double-buffered shared vectors, so a step costs one barrier and
-// the rank-one update itself touches registers only.  The outer loop over
-// column blocks of 8 is unrolled so that every register index is static.
+// inverse being built.  Forward elimination (S -> U, X -> L^-1): row k of a
+// warp's own columns comes from lane k mod 32 of the same warp (shuffles);
+// only column k (the multipliers) crosses warps.  Its owner computes it one
+// step ahead (look-ahead: it applies step k - 1 to column k first), publishes
+// it in a double-buffered shared vector and arrives at a named barrier (ids
+// alternate), on which the other warps wait; the owner goes on with the rest
+// of step k - 1 meanwhile.  Backward ((D^-1 U)^-1): the scaled upper factor
+// is published once, after which each warp eliminates its own columns
+// without any barrier.  The outer loop over column blocks of 8 is unrolled so
+// that every register index is static.
 __device__ void getrf_inv_reg(const HOp& o, HCtx<float>& c) {
   const int n = o.C.r;
   float* ar = c.ar;
-  float* colb = c.sm;         // [2][128]
-  float* rowb = c.sm + 256;   // [2][128]
-  float* diag = c.sm + 512;   // [128]
+  float* colb = c.sm;            // [2][128] multipliers of a step
+  float* Ut = c.sm + 256;        // [128][129] scaled upper factor (row-major, padded)
+  float* diag = Ut + 128 * 129;  // [128]
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
+  unsigned long long tq = 0;
+  auto tmk = [&](int k) {   // profiling: phase times in tprof[11..14]
+    if (!c.tprof || tid != 0) return;
+    unsigned long long t1;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+    if (k >= 0) atomicAdd(c.tprof + 11 + k, t1 - tq);
+    tq = t1;
+  };
+  tmk(-1);
   float S[4][16], X[4][16];
 #pragma unroll
   for (int r = 0; r < 4; ++r)
@@ -1009,8 +1085,21 @@ __device__ void getrf_inv_reg(const HOp& o, HCtx<float>& c) {
       S[r][q] = (i < n && j < n) ? ar[vidx(o.C, i, j)] : 0.f;
       X[r][q] = (i == j && i < n) ? 1.f : 0.f;
     }
-  int buf = 0;
-  // forward: S -> U (upper part), X -> L^-1
+  // publish the multipliers of step kn from local column cc, pivot in
+  // register row rr of lane kn mod 32
+  auto publish = [&](const float (&col)[4], float pv, int kn) {
+    if (tx == 0 && (pv == 0.f || !isfinite(pv))) atomicExch(c.err, 1);
+    const float inv = 1.f / pv;
+    float* cb_ = colb + 128 * (kn & 1);
+#pragma unroll
+    for (int r = 0; r < 4; ++r) cb_[tx + 32 * r] = col[r] * inv;
+    nbar_arrive(1 + (kn & 1));
+  };
+  tmk(0);
+  if (n > 0 && ty == 0) {   // step 0: column 0 is owned by warp 0 (local column 0)
+    const float col[4] = {S[0][0], S[1][0], S[2][0], S[3][0]};
+    publish(col, __shfl_sync(0xffffffffu, S[0][0], 0), 0);
+  }
 #pragma unroll
   for (int cb = 0; cb < 16; ++cb) {
     const int rb = cb >> 2;   // register row block of rows 8 cb .. 8 cb + 7
@@ -1018,46 +1107,66 @@ __device__ void getrf_inv_reg(const HOp& o, HCtx<float>& c) {
     for (int q = 0; q < 8; ++q) {
       const int k = 8 * cb + q;
       if (k >= n) break;
-      float* col = colb + 128 * buf;
-      float* row = rowb + 128 * buf;
-      if (ty == q) {
+      if (ty != q) nbar_sync(1 + (k & 1));
+      const float* col = colb + 128 * (k & 1);
+      float l[4], rs[16], rx[16];
 #pragma unroll
-        for (int r = rb; r < 4; ++r) col[tx + 32 * r] = S[r][cb];
+      for (int r = 0; r < 4; ++r) {
+        const int i = tx + 32 * r;
+        l[r] = (r >= rb && i > k) ? col[i] : 0.f;
       }
-      if (tx == (k & 31)) {
+      // look-ahead first (it is on the critical path): the owner of column
+      // k + 1 applies step k to it and publishes the multipliers of step k + 1
+      const int kn = k + 1;
+      bool la = false;
+      if (kn < n) {
+        if (q < 7) {   // column 8 cb + q + 1: warp q + 1, local column cb, pivot row block rb
+          if (ty == q + 1) {
+            const float rk = __shfl_sync(0xffffffffu, S[rb][cb], k & 31);
 #pragma unroll
-        for (int c2 = 0; c2 < 16; ++c2) {
-          float v;
-          if (c2 > cb) v = S[rb][c2];
-          else if (c2 < cb) v = X[rb][c2];
-          else v = (ty > q) ? S[rb][c2] : X[rb][c2];
-          row[ty + 8 * c2] = v;
+            for (int r = rb; r < 4; ++r) S[r][cb] -= l[r] * rk;
+            const float cl[4] = {S[0][cb], S[1][cb], S[2][cb], S[3][cb]};
+            publish(cl, __shfl_sync(0xffffffffu, S[rb][cb], kn & 31), kn);
+            la = true;
+          }
+        } else if (cb + 1 < 16) {   // column 8 (cb + 1): warp 0, local column cb + 1
+          if (ty == 0) {
+            const int rn = (cb + 1) >> 2;
+            const float rk = __shfl_sync(0xffffffffu, S[rb][cb + 1], k & 31);
+#pragma unroll
+            for (int r = rb; r < 4; ++r) S[r][cb + 1] -= l[r] * rk;
+            const float cl[4] = {S[0][cb + 1], S[1][cb + 1], S[2][cb + 1], S[3][cb + 1]};
+            float pv;
+            if (rn == 0) pv = __shfl_sync(0xffffffffu, S[0][cb + 1], kn & 31);
+            else if (rn == 1) pv = __shfl_sync(0xffffffffu, S[1][cb + 1], kn & 31);
+            else if (rn == 2) pv = __shfl_sync(0xffffffffu, S[2][cb + 1], kn & 31);
+            else pv = __shfl_sync(0xffffffffu, S[3][cb + 1], kn & 31);
+            publish(cl, pv, kn);
+            la = true;
+          }
         }
       }
-      __syncthreads();
-      const float piv = col[k];
-      if (tid == 0 && (piv == 0.f || !isfinite(piv))) atomicExch(c.err, 1);
-      const float inv = 1.f / piv;
-      float l[4], rv[16];
+      // row k of this warp's columns (lane k mod 32)
 #pragma unroll
-      for (int r = rb; r < 4; ++r) {
-        const int i = tx + 32 * r;
-        l[r] = (i > k) ? col[i] * inv : 0.f;
+      for (int c2 = 0; c2 < 16; ++c2) {
+        rs[c2] = (c2 >= cb) ? __shfl_sync(0xffffffffu, S[rb][c2], k & 31) : 0.f;
+        rx[c2] = (c2 <= cb) ? __shfl_sync(0xffffffffu, X[rb][c2], k & 31) : 0.f;
       }
-#pragma unroll
-      for (int c2 = 0; c2 < 16; ++c2) rv[c2] = row[ty + 8 * c2];
+      const int lac = (q < 7) ? cb : cb + 1;   // the look-ahead column, when la
 #pragma unroll
       for (int r = rb; r < 4; ++r)
 #pragma unroll
         for (int c2 = 0; c2 < 16; ++c2) {
-          if (c2 > cb) S[r][c2] -= l[r] * rv[c2];
-          else if (c2 < cb) X[r][c2] -= l[r] * rv[c2];
-          else if (ty > q) S[r][c2] -= l[r] * rv[c2];
-          else X[r][c2] -= l[r] * rv[c2];
+          if (la && c2 == lac) continue;
+          if (c2 > cb) S[r][c2] -= l[r] * rs[c2];
+          else if (c2 < cb) X[r][c2] -= l[r] * rx[c2];
+          else if (ty > q) S[r][c2] -= l[r] * rs[c2];
+          else X[r][c2] -= l[r] * rx[c2];
         }
-      buf ^= 1;
     }
   }
+  tmk(1);
+  // L^-1 out; diagonal of U to shared memory
 #pragma unroll
   for (int r = 0; r < 4; ++r)
 #pragma unroll
@@ -1067,17 +1176,22 @@ __device__ void getrf_inv_reg(const HOp& o, HCtx<float>& c) {
       if (i == j && i < n) diag[i] = S[r][q];
     }
   __syncthreads();
-  // backward: with D = diag(U), X -> (D^-1 U)^-1, then U^-1 = X D^-1
+  // the scaled upper factor D^-1 U (strict upper part) to shared memory
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
     const int i = tx + 32 * r;
     const float ri = (i < n) ? 1.f / diag[i] : 0.f;
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
-      S[r][q] *= ri;
-      X[r][q] = (i == ty + 8 * q && i < n) ? 1.f : 0.f;
+      const int j = ty + 8 * q;
+      if (i < n && j < n && j > i) Ut[i * 129 + j] = S[r][q] * ri;
+      X[r][q] = (i == j && i < n) ? 1.f : 0.f;
     }
   }
+  __syncthreads();
+  tmk(2);
+  if (c.tprof && tid == 0) atomicAdd(c.tprof + 15, 1ULL);
+  // backward: X[i][j] -= Ut[i][k] X[k][j] for i < k <= j, each warp alone
 #pragma unroll
   for (int cb = 15; cb >= 0; --cb) {
     const int rb = cb >> 2;
@@ -1085,30 +1199,18 @@ __device__ void getrf_inv_reg(const HOp& o, HCtx<float>& c) {
       for (int q = 7; q >= 0; --q) {
         const int k = 8 * cb + q;
         if (k >= n || k == 0) continue;
-        float* col = colb + 128 * buf;
-        float* row = rowb + 128 * buf;
-        if (ty == q) {
-#pragma unroll
-          for (int r = 0; r <= rb; ++r) col[tx + 32 * r] = S[r][cb];
-        }
-        if (tx == (k & 31)) {
-#pragma unroll
-          for (int c2 = cb; c2 < 16; ++c2) row[ty + 8 * c2] = X[rb][c2];
-        }
-        __syncthreads();
         float u[4], rv[16];
 #pragma unroll
-        for (int r = 0; r <= rb; ++r) {
+        for (int r = 0; r < 4; ++r) {
           const int i = tx + 32 * r;
-          u[r] = (i < k) ? col[i] : 0.f;
+          u[r] = (r <= rb && i < k) ? Ut[i * 129 + k] : 0.f;
         }
 #pragma unroll
-        for (int c2 = cb; c2 < 16; ++c2) rv[c2] = row[ty + 8 * c2];
+        for (int c2 = 0; c2 < 16; ++c2) rv[c2] = (c2 >= cb) ? __shfl_sync(0xffffffffu, X[rb][c2], k & 31) : 0.f;
 #pragma unroll
         for (int r = 0; r <= rb; ++r)
 #pragma unroll
           for (int c2 = cb; c2 < 16; ++c2) X[r][c2] -= u[r] * rv[c2];
-        buf ^= 1;
       }
     }
   }
@@ -1123,6 +1225,7 @@ __device__ void getrf_inv_reg(const HOp& o, HCtx<float>& c) {
       if (i < n) ar[vidx(o.B, i, j)] = X[r][q] * cj;
     }
   }
+  tmk(3);
 }
 
 template <class T>
@@ -2297,7 +2400,7 @@ static size_t prog_smem(const HPlan& p, size_t ts) {
   size_t leaf = (size_t)2 * p.leaf_max * p.leaf_max;
   size_t K = (size_t)std::max(p.kconcat_max, 1);
   size_t trunc = 2 * K + 32 + 2 * K * K + 3 * K + 8;
-  size_t trmm = (size_t)p.leaf_max * p.leaf_max + (size_t)std::max(p.leaf_max, 1) * 33;
+  size_t trmm = (size_t)p.leaf_max * (p.leaf_max + 1) + 4 + (size_t)std::max(p.leaf_max, 1) * 33;
   size_t gemm = 2 * 8 * 128 + 128 * 129;   // tiled GEMM: k chunks and the C tile
   return std::max(std::max(leaf, trunc), std::max(trmm, gemm)) * ts + 64;
 }
@@ -2749,6 +2852,9 @@ void hfsem_factor_s::report(const char* what) {
     const unsigned long long* q = &h[ninst * 32];
     if (q[8]) {
       static const char* ph[7] = {"qr U", "qr V", "core", "rrqr", "Z+rows", "apply U", "apply V"};
+      if (q[15])
+        fprintf(stderr, "[hfsem leaf LU] %llu calls, us per call: load %.1f forward %.1f out+scale %.1f backward+out %.1f\n",
+                q[15], q[11] * 1e-3 / q[15], q[12] * 1e-3 / q[15], q[13] * 1e-3 / q[15], q[14] * 1e-3 / q[15]);
       fprintf(stderr, "[hfsem recompression] %llu calls (all instances), mean K %.1f, mean m+n %.0f; us/call:",
               q[8], (double)q[9] / q[8], (double)q[10] / q[8]);
       for (int k = 0; k < 7; ++k) fprintf(stderr, " %s %.1f", ph[k], q[k] * 1e-3 / q[8]);
