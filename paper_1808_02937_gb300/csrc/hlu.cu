@@ -44,6 +44,7 @@ struct LRPairDev {  // an admissible pair: tau (rows of the lower block) right o
   int te0, te1, se0, se1;       // element ranges
   int tlo, thi, slo, shi;       // support nodes
   int td0, tm, sd0, sn;         // unknown ranges
+  long long toff;               // rows of Q (tm x R) then W (sn x R) in the FP64 row buffer
 };
 
 constexpr int kCluster = 8;   // CTAs (one thread-block cluster) per instance
@@ -65,6 +66,7 @@ struct HInstDev {
   int nd;            // unknowns (leading dimension of the rhs area)
   long long ptask0;  // low-rank build: task offsets of the pairs (npairs + 1)
   long long gmax0;   // low-rank build: this instance's first pair in the maxima
+  long long lrt0;    // low-rank build: this instance's FP64 row buffer
   long long st0, job0;  // leaf-solve tables: steps, jobs
   long long pk0;     // this instance's first job in the solve pack
   int jcap;          // jobs per part of the leaf solve
@@ -269,8 +271,7 @@ __global__ void __launch_bounds__(256) k_lowrank(const HInstDev* __restrict__ hi
                                                  const LRPairDev* __restrict__ pairs,
                                                  const SlotDev* __restrict__ slots,
                                                  const int* __restrict__ ptask, const double* D,
-                                                 T* har, unsigned long long* gmax, int pass,
-                                                 int* ranks) {
+                                                 double* lrt, unsigned long long* gmax) {
   using C = T;
   extern __shared__ __align__(16) unsigned char lsm_raw[];
   const HInstDev H = hi[blockIdx.y];
@@ -313,8 +314,8 @@ __global__ void __launch_bounds__(256) k_lowrank(const HInstDev* __restrict__ hi
   };
   const int* pt = ptask + H.ptask0;   // npairs + 1 task offsets
   const int ntask = pt[H.npairs];
-  T* ar = har + H.arena;
   const double* Dv = D + H.d_off;
+  double* rows = lrt + H.lrt0;
   const double ex = 1.0 - I.alpha;
   const C exc = (C)ex;
   // each warp takes a contiguous run of tasks: one search for the first
@@ -410,9 +411,10 @@ __global__ void __launch_bounds__(256) k_lowrank(const HInstDev* __restrict__ hi
     // of e when e < e1
     const double scale_side = ((side == 0) ? I.g0 : 1.0) * fsc;   // gamma0 sits with Q
     const int nb = bub ? P - 1 : 0, nh = hat ? 1 : 0;
-    const SlotDev slo = slots[H.slot0 + pr.lower_slot];
-    const SlotDev sup = slots[H.slot0 + pr.upper_slot];
     unsigned long long* gm = gmax + ((size_t)H.gmax0 + lo) * 64;
+    // FP64 factor rows (before balancing): Q rows of tau then W rows of sigma
+    double* out = rows + pr.toff + (side == 0 ? 0LL : (long long)pr.tm * R);
+    const int nrow = side == 0 ? pr.tm : pr.sn;
     // lane k holds row k (P <= 32 rows per element)
     const int k = lane;
     const bool has = k < nb + nh;
@@ -432,37 +434,64 @@ __global__ void __launch_bounds__(256) k_lowrank(const HInstDev* __restrict__ hi
     }
     for (int nu = 0; nu < R; ++nu) {
       double v = 0.0;
-      if (has) v = rs * (double)((k < nh) ? (sQ0[nu] - sQ[nu]) : sQ[pp * R + nu]);
-      if (pass == 0) {
-        double vmax = fabs(v);
-        for (int o = 16; o > 0; o >>= 1) vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
-        if (lane == 0 && vmax > 0.0)
-          atomicMax(&gm[side * 32 + nu], (unsigned long long)__double_as_longlong(vmax));
-        continue;
+      if (has) {
+        v = rs * (double)((k < nh) ? (sQ0[nu] - sQ[nu]) : sQ[pp * R + nu]);
+        out[row + (long long)nu * nrow] = v;
       }
-      if (!has) continue;
+      double vmax = fabs(v);
+      for (int o = 16; o > 0; o >>= 1) vmax = fmax(vmax, __shfl_xor_sync(0xffffffffu, vmax, o));
+      if (lane == 0 && vmax > 0.0)
+        atomicMax(&gm[side * 32 + nu], (unsigned long long)__double_as_longlong(vmax));
+    }
+    __syncwarp();
+  }
+}
+
+// Balance and store the low-rank factors: per pair and term nu the Q column
+// is scaled by c = sqrt(max|W| / max|Q|) and the W column by 1 / c (the
+// product is unchanged; each factor stays inside the FP32 range on meshes
+// whose element sizes span 10^80), then written to the slots: lower
+// U = theta D Q, V = D W; upper U = D W, V = (1 - theta) D Q.
+template <class T>
+__global__ void k_lowrank_write(const HInstDev* __restrict__ hi, const InstDev* __restrict__ inst,
+                                const LRPairDev* __restrict__ pairs,
+                                const SlotDev* __restrict__ slots, const double* lrt,
+                                const unsigned long long* gmax, T* har, int* ranks) {
+  const HInstDev H = hi[blockIdx.y];
+  const InstDev I = inst[H.sys_inst];
+  const int R = H.R;
+  T* ar = har + H.arena;
+  for (int pi = blockIdx.x; pi < H.npairs; pi += gridDim.x) {
+    const LRPairDev pr = pairs[H.pair0 + pi];
+    const SlotDev slo = slots[H.slot0 + pr.lower_slot];
+    const SlotDev sup = slots[H.slot0 + pr.upper_slot];
+    const unsigned long long* gm = gmax + ((size_t)H.gmax0 + pi) * 64;
+    const double* rows = lrt + H.lrt0 + pr.toff;
+    const int nq = pr.tm * R, nw = pr.sn * R;
+    for (int t = threadIdx.x; t < nq + nw; t += blockDim.x) {
+      const int side = t < nq ? 0 : 1;
+      const int tt = side == 0 ? t : t - nq;
+      const int nrow = side == 0 ? pr.tm : pr.sn;
+      const int row = tt % nrow, nu = tt / nrow;
       const double mq = __longlong_as_double((long long)gm[nu]);
       const double mw = __longlong_as_double((long long)gm[32 + nu]);
       double sc = (mq > 0.0 && mw > 0.0) ? sqrt(mw) / sqrt(mq) : 1.0;   // Q *= sc, W /= sc
       sc = (isfinite(sc) && sc > 0.0) ? sc : 1.0;
+      const double v = rows[t];
       if (side == 0) {
-        v *= sc;
-        // Q row: lower U = theta D Q, upper V = (1-theta) D Q
-        ar[slo.off + row + (long long)nu * slo.m] = (T)(I.theta * v);
-        ar[sup.off + (long long)sup.m * sup.kcap + row + (long long)nu * sup.n] =
-            (T)((1.0 - I.theta) * v);
+        const double q = v * sc;
+        ar[slo.off + row + (long long)nu * slo.m] = (T)(I.theta * q);
+        ar[sup.off + (long long)sup.m * sup.kcap + row + (long long)nu * sup.n] = (T)((1.0 - I.theta) * q);
       } else {
-        v /= sc;
-        // W row: lower V = D W, upper U = D W
-        ar[slo.off + (long long)slo.m * slo.kcap + row + (long long)nu * slo.n] = (T)v;
-        ar[sup.off + row + (long long)nu * sup.m] = (T)v;
+        const double w = v / sc;
+        ar[slo.off + (long long)slo.m * slo.kcap + row + (long long)nu * slo.n] = (T)w;
+        ar[sup.off + row + (long long)nu * sup.m] = (T)w;
       }
     }
-    if (pass == 1 && tl == 0 && lane == 0) {
+    if (threadIdx.x == 0) {
       ranks[H.rk0 + pr.lower_slot] = (I.theta != 0.0) ? R : 0;
       ranks[H.rk0 + pr.upper_slot] = (I.theta != 1.0) ? R : 0;
     }
-    __syncwarp();
   }
 }
 
@@ -2337,6 +2366,7 @@ struct PlanBundle {
   std::vector<DenseDev> dense;
   std::vector<LRPairDev> pairs;
   std::vector<int> ptask;        // low-rank build tasks per pair (prefix sums)
+  long long lrrows = 0;          // entries of the FP64 row buffer of the low-rank build
   std::vector<SlotDev> slots;
   LeafSolve ls;                  // tables of the leaf solves
 };
@@ -2362,6 +2392,7 @@ struct hfsem_factor_s : public hf::Precond {
   hf::DevBuf<hf::LRPairDev> d_pairs;
   hf::DevBuf<int> d_ptask;                  // low-rank build tasks
   hf::DevBuf<unsigned long long> d_gmax;    // low-rank build: per pair and term, the largest entries
+  hf::DevBuf<double> d_lrt;                 // low-rank build: factor rows before balancing (FP64)
   hf::DevBuf<hf::StepInfo> d_steps;   // leaf solve tables
   hf::DevBuf<hf::StepCta> d_step_cta;
   hf::DevBuf<hf::SolJob> d_jobs;
@@ -2522,7 +2553,8 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
           if (mi == slot_of.end()) throw Error(HFSEM_ERR_DEVICE, "block tree is not symmetric");
           const Cluster &ct = p.C[b.t], &cs = p.C[b.s];
           pb->pairs.push_back(LRPairDev{b.slot, mi->second, ct.e0, ct.e1, cs.e0, cs.e1, ct.lo,
-                                        ct.hi, cs.lo, cs.hi, ct.d0, b.m, cs.d0, b.n});
+                                        ct.hi, cs.lo, cs.hi, ct.d0, b.m, cs.d0, b.n, pb->lrrows});
+          pb->lrrows += (long long)(b.m + b.n) * opt.R;
         }
         // one task per element of each side (element e1 only feeds the hat at
         // node e1 and is left out when it is past the last element)
@@ -2570,7 +2602,7 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
     std::map<const PlanBundle*, std::array<long long, 2>> placed_leaf;
     std::map<const PlanBundle*, long long> placed_task;
     std::vector<int> ptask;
-    long long gmax_n = 0, max_tasks = 0;
+    long long gmax_n = 0, max_tasks = 0, lrt_n = 0;
     int jmax = 1, nmax = 1, wcols = 1;
     long long arena = 0, rk = 0, doff = 0, pkoff = 0;
     size_t smem = 0;
@@ -2612,6 +2644,8 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
       H.ptask0 = placed_task[pb];
       H.gmax0 = gmax_n;
       gmax_n += (long long)pb->pairs.size();
+      H.lrt0 = lrt_n;
+      lrt_n += pb->lrrows;
       max_tasks = std::max<long long>(max_tasks, pb->ptask.back());
       H.ops0 = pi->second[0];
 
@@ -2680,6 +2714,7 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
     if (!ptask.empty())
       HF_CHECK(cudaMemcpyAsync(f->d_ptask.p, ptask.data(), ptask.size() * sizeof(int), cudaMemcpyHostToDevice, s->st));
     f->d_gmax.alloc((size_t)std::max<long long>(gmax_n, 1) * 64);
+    f->d_lrt.alloc((size_t)std::max<long long>(lrt_n, 1));
     HF_CHECK(cudaMemsetAsync(f->d_gmax.p, 0, f->d_gmax.n * sizeof(unsigned long long), s->st));
     f->d_steps.alloc(std::max<size_t>(steps.size(), 1));
     if (!steps.empty())
@@ -2718,10 +2753,11 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
     f->d_arena.alloc((size_t)std::max<long long>(arena, 1) * f->tsize);
     HF_CHECK(cudaMemsetAsync(f->d_arena.p, 0, (size_t)std::max<long long>(arena, 1) * f->tsize, s->st));
     // build A~
-    int maxnd = 1, maxdense = 1;
+    int maxnd = 1, maxdense = 1, maxnpairs = 1;
     for (auto& H : f->hidev) {
       maxnd = std::max(maxnd, s->ih[H.sys_inst].Nd);
       maxdense = std::max(maxdense, H.ndense);
+      maxnpairs = std::max(maxnpairs, H.npairs);
     }
     const bool prof = getenv("HFSEM_PROFILE") != nullptr;
     cudaEvent_t ev[5];
@@ -2748,12 +2784,13 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
       if (lr_smem > 48 * 1024)
         HF_CHECK(cudaFuncSetAttribute((const void*)k_lowrank<float>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lr_smem));
-      for (int pass = 0; pass < 2; ++pass) {
-        k_lowrank<float><<<gp, lr_warps * 32, lr_smem, s->st>>>(f->d_hi.p, s->d_inst.p, s->arena.p, s->gl.p,
-                                                            f->d_pairs.p, f->d_slots.p, f->d_ptask.p,
-                                                            f->d_D.p, ar, f->d_gmax.p, pass, f->d_ranks.p);
-        HF_LAUNCH_CHECK();
-      }
+      k_lowrank<float><<<gp, lr_warps * 32, lr_smem, s->st>>>(f->d_hi.p, s->d_inst.p, s->arena.p, s->gl.p,
+                                                          f->d_pairs.p, f->d_slots.p, f->d_ptask.p,
+                                                          f->d_D.p, f->d_lrt.p, f->d_gmax.p);
+      HF_LAUNCH_CHECK();
+      k_lowrank_write<float><<<dim3(std::max(1, std::min(maxnpairs, 1024)), ni), 256, 0, s->st>>>(
+          f->d_hi.p, s->d_inst.p, f->d_pairs.p, f->d_slots.p, f->d_lrt.p, f->d_gmax.p, ar, f->d_ranks.p);
+      HF_LAUNCH_CHECK();
       set_prog_smem<float>(smem);
     } else {
       double* ar = reinterpret_cast<double*>(f->d_arena.p);
@@ -2763,12 +2800,13 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
       if (lr_smem > 48 * 1024)
         HF_CHECK(cudaFuncSetAttribute((const void*)k_lowrank<double>,
                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lr_smem));
-      for (int pass = 0; pass < 2; ++pass) {
-        k_lowrank<double><<<gp, lr_warps * 32, lr_smem, s->st>>>(f->d_hi.p, s->d_inst.p, s->arena.p, s->gl.p,
-                                                            f->d_pairs.p, f->d_slots.p, f->d_ptask.p,
-                                                            f->d_D.p, ar, f->d_gmax.p, pass, f->d_ranks.p);
-        HF_LAUNCH_CHECK();
-      }
+      k_lowrank<double><<<gp, lr_warps * 32, lr_smem, s->st>>>(f->d_hi.p, s->d_inst.p, s->arena.p, s->gl.p,
+                                                          f->d_pairs.p, f->d_slots.p, f->d_ptask.p,
+                                                          f->d_D.p, f->d_lrt.p, f->d_gmax.p);
+      HF_LAUNCH_CHECK();
+      k_lowrank_write<double><<<dim3(std::max(1, std::min(maxnpairs, 1024)), ni), 256, 0, s->st>>>(
+          f->d_hi.p, s->d_inst.p, f->d_pairs.p, f->d_slots.p, f->d_lrt.p, f->d_gmax.p, ar, f->d_ranks.p);
+      HF_LAUNCH_CHECK();
       set_prog_smem<double>(smem);
     }
     if (prof) cudaEventRecord(ev[2], s->st);
