@@ -41,25 +41,56 @@ template <class T>
 struct DevBuf {
   T* p = nullptr;
   size_t n = 0;
+  bool pooled = false;         // allocated stream-ordered (cudaMallocAsync) on st
+  cudaStream_t st = nullptr;
   DevBuf() = default;
   DevBuf(const DevBuf&) = delete;
   DevBuf& operator=(const DevBuf&) = delete;
   ~DevBuf() { release(); }
   void release() {
-    if (p) cudaFree(p);
+    if (p) {
+      if (pooled) cudaFreeAsync(p, st);
+      else cudaFree(p);
+    }
     p = nullptr;
     n = 0;
+    pooled = false;
   }
-  void alloc(size_t count) {
-    release();
-    if (count == 0) return;
-    HF_CHECK(cudaMalloc(&p, count * sizeof(T)));
-    n = count;
-  }
+  // allocates on the calling thread's allocation stream when one is set
+  // (AllocStream below): stream-ordered from the device's memory pool, so a
+  // factorisation repeated on the same stream reuses its memory without a
+  // device synchronisation; otherwise cudaMalloc
+  void alloc(size_t count);
   void ensure(size_t count) {
     if (count > n) alloc(count);
   }
 };
+
+// The stream that DevBuf::alloc allocates on for the calling thread (RAII).
+cudaStream_t& alloc_stream();
+struct AllocStream {
+  cudaStream_t prev;
+  explicit AllocStream(cudaStream_t s) : prev(alloc_stream()) { alloc_stream() = s; }
+  ~AllocStream() { alloc_stream() = prev; }
+};
+// keep freed pool memory cached for reuse (once per device)
+void pool_keep_memory();
+
+template <class T>
+void DevBuf<T>::alloc(size_t count) {
+  release();
+  if (count == 0) return;
+  cudaStream_t s = alloc_stream();
+  if (s != reinterpret_cast<cudaStream_t>(-1)) {
+    pool_keep_memory();
+    HF_CHECK(cudaMallocAsync(reinterpret_cast<void**>(&p), count * sizeof(T), s));
+    pooled = true;
+    st = s;
+  } else {
+    HF_CHECK(cudaMalloc(&p, count * sizeof(T)));
+  }
+  n = count;
+}
 
 // Gauss rules (host): weight (1-x)^a (1+x)^b on [-1, 1].
 void gauss_jacobi_rule(int n, double a, double b, std::vector<double>& x,

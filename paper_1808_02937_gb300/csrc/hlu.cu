@@ -2468,6 +2468,7 @@ static std::string plan_key(const InstHost& I, const PlanOpts& o) {
 }
 
 static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
+  AllocStream as(s->st);   // the factor's buffers come stream-ordered from the pool
   if (opt.R < 1 || opt.R > 32) throw Error(HFSEM_ERR_INVALID_ARG, "R must be in [1, 32]");
   if (!(opt.lambda > 0.0)) throw Error(HFSEM_ERR_INVALID_ARG, "lambda must be > 0");
   if (!(opt.tol_hlu >= 0.0)) throw Error(HFSEM_ERR_INVALID_ARG, "tol_hlu must be >= 0");
@@ -2971,6 +2972,7 @@ void hfsem_factor_s::report_waves(const char* what) {
 
 void hfsem_factor_s::run_prog() {
   if (!d_prof.p && getenv("HFSEM_PROFILE")) {
+    hf::AllocStream plain(reinterpret_cast<cudaStream_t>(-1));
     d_prof.alloc((size_t)sys->n_inst * 32 + 16 + 64);
     cudaMemset(d_prof.p, 0, d_prof.n * sizeof(unsigned long long));
   }
@@ -2980,6 +2982,7 @@ void hfsem_factor_s::run_prog() {
   }
   const char* pe = getenv("HFSEM_PROFILE");
   if (!d_wprof.p && pe && atoi(pe) >= 2) {
+    hf::AllocStream plain(reinterpret_cast<cudaStream_t>(-1));
     int nwmax = 1;
     for (auto& H : hidev) nwmax = std::max(nwmax, H.nfw);
     wstride = nwmax;
@@ -3046,6 +3049,7 @@ void hfsem_factor_s::run_pack() {
 void hfsem_factor_s::run_leaf_solve(int nrhs) {
   const char* pe = getenv("HFSEM_PROFILE");
   if (!d_sprof.p && pe && atoi(pe) >= 2) {
+    hf::AllocStream plain(reinterpret_cast<cudaStream_t>(-1));
     d_sprof.alloc(8);
     cudaMemset(d_sprof.p, 0, 8 * sizeof(unsigned long long));
   }
@@ -3178,6 +3182,7 @@ int hfsem_precond_apply(hfsem_factor* fac, int32_t nrhs, const double* r, double
   try {
     if (!fac || !r || !y || nrhs < 1 || nrhs > 64) throw Error(HFSEM_ERR_INVALID_ARG, "bad arguments");
     hfsem_system* s = fac->sys;
+    AllocStream as(s->st);
     ensure_work(s, nrhs);
     size_t cnt = (size_t)s->total_nd * nrhs;
     DevBuf<double> a, b;
@@ -3193,6 +3198,8 @@ int hfsem_precond_apply(hfsem_factor* fac, int32_t nrhs, const double* r, double
     HF_CHECK(cudaStreamSynchronize(s->st));
     std::vector<int> err(s->n_inst);
     HF_CHECK(cudaMemcpy(err.data(), fac->d_err.p, err.size() * sizeof(int), cudaMemcpyDeviceToHost));
+    for (int e : err)
+      if (e == 2) throw Error(HFSEM_ERR_DEVICE, "an H-solve copy did not complete within its wait limit");
     return HFSEM_OK;
   } catch (const Error& e) {
     set_last_error(e.msg);

@@ -341,6 +341,7 @@ extern "C" int hfsem_solve(hfsem_system* sys, hfsem_factor* fac, const hfsem_rhs
     Precond* M = precond_of(sys, fac);
     int nrhs = rhs[0].nrhs;
     if (nrhs < 1 || nrhs > 64) throw Error(HFSEM_ERR_INVALID_ARG, "nrhs must be in [1, 64]");
+    AllocStream as(sys->st);   // work buffers come stream-ordered from the pool
     ensure_work(sys, nrhs);
     size_t nv = (size_t)sys->total_nd * nrhs;
     KrylovWork& W = sys->kry;

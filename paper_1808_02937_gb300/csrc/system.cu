@@ -80,6 +80,26 @@ void flush_pending() {
 
 bool timing_on() { return g_timing; }
 
+cudaStream_t& alloc_stream() {
+  thread_local cudaStream_t s = reinterpret_cast<cudaStream_t>(-1);   // none: cudaMalloc
+  return s;
+}
+
+void pool_keep_memory() {
+  static std::mutex mu;
+  static bool done[128] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 128) return;
+  std::lock_guard<std::mutex> lk(mu);
+  if (done[dev]) return;
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t thr = UINT64_MAX;   // a process-local attribute of the pool
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+  }
+  done[dev] = true;
+}
+
 Tick::Tick(cudaStream_t s, const char* tag, double work) : st(s) {
   if (!g_timing) return;
   std::lock_guard<std::mutex> lk(g_tmu);
@@ -1095,6 +1115,7 @@ static hfsem_system* assemble(int n, const hfsem_problem* probs, void* stream) {
   auto* s = new hfsem_system();
   try {
     s->st = (cudaStream_t)stream;
+    AllocStream as(s->st);   // the system's buffers come stream-ordered from the pool
     s->n_inst = n;
     s->ih.resize(n);
     s->idv.resize(n);
@@ -1300,6 +1321,7 @@ int hfsem_apply(hfsem_system* sys, int32_t nrhs, const double* x, double* y) {
   return guarded([&] {
     if (!sys || !x || !y || nrhs < 1 || nrhs > 64)
       throw Error(HFSEM_ERR_INVALID_ARG, "bad arguments to hfsem_apply");
+    AllocStream as(sys->st);
     ensure_work(sys, nrhs);
     size_t cnt = (size_t)sys->total_nd * nrhs;
     DevBuf<double> xe, ye;
@@ -1320,6 +1342,7 @@ int hfsem_load_vector(hfsem_system* sys, const hfsem_rhs* rhs, int32_t lifted, d
     int nrhs = rhs[0].nrhs;
     if (nrhs < 1 || nrhs > 64) throw Error(HFSEM_ERR_INVALID_ARG, "nrhs must be in [1, 64]");
     size_t cnt = (size_t)sys->total_nd * nrhs;
+    AllocStream as(sys->st);
     DevBuf<double> ge;
     ge.alloc(cnt);
     load_vector_em(sys, rhs, lifted, ge.p);
