@@ -13,6 +13,8 @@
 //    smaller cluster (Remark after the Lemma).
 //  * k_hprog: one CTA per instance runs the op program the host planner
 //    compiled from the recursive H-LU (or the forward/backward substitution).
+#include <cuda_bf16.h>
+
 #include <algorithm>
 #include <cmath>
 #include <cstdlib>
@@ -518,6 +520,83 @@ __device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// --- mbarriers (completion of asynchronous copies and tensor-core MMAs) ---
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// --- 5th-generation tensor cores (tcgen05): accumulators in tensor memory ---
+// Shared-memory matrix descriptor: start address, leading and stride byte
+// offsets (16-byte units), descriptor version 1, no swizzle.  Operands are
+// K-major in core matrices of 8 rows x 16 bytes (8 x 8 bf16), stored
+// contiguously; SBO steps 8 rows, LBO steps 8 elements of K.
+__device__ __forceinline__ unsigned long long tc_sdesc(const void* smem, unsigned lbo, unsigned sbo) {
+  unsigned long long d = (unsigned long long)((smem_u32(smem) >> 4) & 0x3FFFu);
+  d |= (unsigned long long)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (unsigned long long)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= 1ULL << 46;
+  return d;
+}
+// instruction descriptor: kind::f16, A and B bf16 (K-major), D f32, M x N
+__device__ __forceinline__ unsigned tc_idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(N >> 3) << 17) | ((unsigned)(M >> 4) << 24);
+}
+__device__ __forceinline__ void tc_alloc(unsigned* slot, int ncols) {   // one whole warp
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+               "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tc_dealloc(unsigned taddr, int ncols) {   // one whole warp
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_mma(unsigned dtmem, unsigned long long ad, unsigned long long bd,
+                                       unsigned idesc, int acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(dtmem),
+      "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+      : "memory");
+}
+// the commit names the mbarrier by its shared::cluster address (this CTA's rank)
+__device__ __forceinline__ void tc_commit(unsigned long long* bar) {
+  unsigned rank, a;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(a) : "r"(smem_u32(bar)), "r"(rank));
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(a)
+               : "memory");
+}
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+// 16 consecutive 32-bit columns of this warp's 32 lanes
+__device__ __forceinline__ void tc_ld16(unsigned taddr, float* v) {
+  unsigned r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int t = 0; t < 16; ++t) v[t] = __uint_as_float(r[t]);
+}
+
 __device__ __forceinline__ void cp_async16(void* dst, const void* src) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
 }
@@ -553,6 +632,11 @@ struct HCtx {
   T* sm;
   long long smcap;   // elements of T in the dynamic shared memory
   unsigned long long* tprof;   // optional: recompression phase times (profiling)
+  int tc;                      // dense leaf contractions on the tensor cores (BF16 in, FP32 out)
+  unsigned tmem;               // tensor-memory accumulator (256 columns)
+  unsigned long long* tcbar;   // mbarrier the MMAs commit to
+  unsigned* tcphase;           // its phase
+  unsigned long long* tcdbg;   // diagnostics of a tensor-core wait that ran out
   double tol;
   int* err;
 };
@@ -570,6 +654,96 @@ __device__ T block_sum(T v, T* red) {
   return s;
 }
 
+// BF16 tensor-core tile: D (128 x N) = A (128 x K) B (K x N) with FP32
+// accumulation in tensor memory (tcgen05), A and B read from FP32 views and
+// rounded to bf16 into shared memory as K-major core matrices; then
+// C = beta C + alpha D, with C stored 128 x N (ctr = 0) or N x 128 (ctr = 1).
+// K a multiple of 16, N a multiple of 16 in [16, 256].  One thread issues the
+// MMAs; all threads wait on the mbarrier they commit to (bounded), then read
+// the accumulators back, warp w covering rows 32 (w mod 4) ...
+__device__ bool tc_gemm128(HCtx<float>& c, const View& A, const View& B, const View& Cv, int ctr, int N,
+                           int K, float alpha, float beta) {
+  float* ar = c.ar;
+  // operands on 1024-byte boundaries
+  const unsigned base = smem_u32(c.sm);
+  const unsigned pad = ((base + 1023u) & ~1023u) - base;
+  __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(c.sm) + pad);   // 128 x K
+  __nv_bfloat16* Bs = As + (((size_t)128 * K + 511) & ~(size_t)511);                                      // N x K
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int nc8 = N >> 3;
+  for (int t = tid; t < 128 * K; t += nt) {
+    const int m = t & 127, k = t >> 7;
+    As[((k >> 3) * 16 + (m >> 3)) * 64 + (m & 7) * 8 + (k & 7)] = __float2bfloat16_rn(ar[vidx(A, m, k)]);
+  }
+  for (int t = tid; t < K * N; t += nt) {
+    const int k = t % K, n = t / K;
+    Bs[((k >> 3) * nc8 + (n >> 3)) * 64 + (n & 7) * 8 + (k & 7)] = __float2bfloat16_rn(ar[vidx(B, k, n)]);
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+  if (tid == 0) {
+    tc_fence_after();
+    const unsigned idesc = tc_idesc_bf16(128, N);
+    for (int s = 0; s < K / 16; ++s) {
+      const unsigned long long ad = tc_sdesc(As + s * 2 * 16 * 64, 16 * 64 * 2, 128);
+      const unsigned long long bd = tc_sdesc(Bs + s * 2 * nc8 * 64, nc8 * 64 * 2, 128);
+      tc_mma(c.tmem, ad, bd, idesc, s > 0);
+    }
+    tc_commit(c.tcbar);
+  }
+  // wait for the MMAs, at most ~2 ms of wall time; every thread must agree
+  bool ok = true;
+  {
+    const unsigned ph = *c.tcphase;
+    unsigned long long t0, t1;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+    while (!mbar_try_wait(c.tcbar, ph)) {
+      asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+      if (t1 - t0 > 2000000ULL) {
+        ok = false;
+        break;
+      }
+    }
+  }
+  ok = __syncthreads_and(ok) != 0;
+  tc_fence_after();
+  if (!ok) {
+    // record the barrier word and the descriptors, and stop using the
+    // tensor cores in this CTA (the op is lost; the flag fails the factor)
+    if (tid == 0) {
+      atomicExch(c.err, 4);
+      if (c.tcdbg) {
+        unsigned long long w;
+        asm volatile("ld.shared.b64 %0, [%1];" : "=l"(w) : "r"(smem_u32(c.tcbar)) : "memory");
+        c.tcdbg[0] = w;
+        c.tcdbg[1] = tc_sdesc(As, 16 * 64 * 2, 128);
+        c.tcdbg[2] = tc_sdesc(Bs, nc8 * 64 * 2, 128);
+        c.tcdbg[3] = tc_idesc_bf16(128, N);
+        c.tcdbg[4] = c.tmem;
+        c.tcdbg[5] = ((unsigned long long)N << 32) | (unsigned)K;
+      }
+    }
+    c.tc = 0;
+    __syncthreads();
+    return true;
+  }
+  *c.tcphase ^= 1u;   // every thread tracks the barrier's phase
+  const int warp = tid >> 5, lane = tid & 31, rw = warp & 3, h = warp >> 2;
+  const int row = 32 * rw + lane;
+  for (int col = 16 * h; col < N; col += 32) {
+    float v[16];
+    tc_ld16(c.tmem + ((unsigned)(32 * rw) << 16) + (unsigned)col, v);
+#pragma unroll
+    for (int t = 0; t < 16; ++t) {
+      const long long ci = ctr ? vidx(Cv, col + t, row) : vidx(Cv, row, col + t);
+      ar[ci] = (beta == 0.f ? 0.f : beta * ar[ci]) + alpha * v[t];
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  return true;
+}
+
 template <class T>
 __device__ void op_gemm(const HOp& o, HCtx<T>& c) {
   const int m = dimv(o.C.r, c.rk), n = dimv(o.C.c, c.rk), k = dimv(o.A.c, c.rk);
@@ -583,6 +757,13 @@ __device__ void op_gemm(const HOp& o, HCtx<T>& c) {
       ar[ci] = (beta == (T)0) ? (T)0 : beta * ar[ci];
     }
     return;
+  }
+  if constexpr (sizeof(T) == 4) {
+    // dense leaf products on the tensor cores
+    if (c.tc && m == 128 && n >= 16 && n <= 256 && (n & 15) == 0 && k >= 64 && (k & 15) == 0 &&
+        (long long)(128 + n) * k / 2 + 1024 <= c.smcap) {
+      if (tc_gemm128(c, o.A, o.B, o.C, 0, n, k, alpha, beta)) return;
+    }
   }
   if constexpr (sizeof(T) == 4) {
     // rank-k update of an aligned column-major C (k <= 16): A and B staged,
@@ -905,6 +1086,13 @@ __device__ void op_trmm_l(const HOp& o, HCtx<T>& c) {
   const int n = dimv(o.C.r, c.rk), cc = dimv(o.C.c, c.rk);
   if (n <= 0 || cc <= 0) return;
   T* ar = c.ar;
+  if constexpr (sizeof(T) == 4) {
+    // C <- A C on the tensor cores (C staged before it is overwritten)
+    if (c.tc && n == 128 && cc >= 16 && cc <= 256 && (cc & 15) == 0 &&
+        (long long)(128 + cc) * 128 / 2 + 1024 <= c.smcap) {
+      if (tc_gemm128(c, o.A, o.C, o.C, 0, cc, 128, 1.f, 0.f)) return;
+    }
+  }
   if (cc <= 4 && !o.A.tr) {
     // a few right-hand sides (the H-solves): 2 threads per row split k, four
     // independent loads in flight per thread, A read from L2 (consecutive
@@ -988,6 +1176,15 @@ __device__ void op_trmm_r(const HOp& o, HCtx<T>& c) {
   const int m = dimv(o.C.r, c.rk), n = dimv(o.C.c, c.rk);
   if (m <= 0 || n <= 0) return;
   T* ar = c.ar;
+  if constexpr (sizeof(T) == 4) {
+    // (C A)^T = A^T C^T on the tensor cores: M = n = 128, N = m, stored back transposed
+    if (c.tc && n == 128 && m >= 16 && m <= 256 && (m & 15) == 0 &&
+        (long long)(128 + m) * 128 / 2 + 1024 <= c.smcap) {
+      const View At{o.A.off, o.A.c, o.A.r, o.A.ld, !o.A.tr};
+      const View Ct{o.C.off, o.C.c, o.C.r, o.C.ld, !o.C.tr};
+      if (tc_gemm128(c, At, Ct, o.C, 1, m, 128, 1.f, 0.f)) return;
+    }
+  }
   // A row-major with a padded row (lda = n + 1: the staging stores meet 4-way
   // bank conflicts at most, the row reads none)
   const int lda = n + 1;
@@ -1770,6 +1967,8 @@ struct HProgArgs {
   int wstride;                // waves per instance in wprof
   long long smem_elems;       // dynamic shared memory, in elements of the factor type
   int n_inst_prof;            // instances in prof (the recompression phases follow them)
+  int tc;                     // dense leaf contractions on the tensor cores
+  unsigned long long* tcdbg;  // 8 words of diagnostics for a tensor-core wait that ran out
 };
 
 // algorithmic flops of one op with its run-time shapes
@@ -1839,6 +2038,26 @@ __global__ void __launch_bounds__(kHThreads) k_hprog(HProgArgs a, T* har) {
   c.tprof = a.prof ? a.prof + (size_t)a.n_inst_prof * 32 : nullptr;
   c.tol = a.tol;
   c.err = a.err + cid;
+  // tensor memory (256 columns of FP32 accumulators) and the MMA mbarrier
+  __shared__ unsigned s_tmem;
+  __shared__ __align__(8) unsigned long long s_tcbar;
+  unsigned tcphase = 0;
+  c.tc = a.tc;
+  c.tmem = 0;
+  c.tcbar = &s_tcbar;
+  c.tcphase = &tcphase;
+  c.tcdbg = a.tcdbg;
+  if (a.tc) {
+    if ((threadIdx.x >> 5) == 0) tc_alloc(&s_tmem, 256);
+    if (threadIdx.x == 0) {
+      mbar_init(&s_tcbar, 1);
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    c.tmem = s_tmem;
+  }
   const HOp* ops = a.ops + H.ops0;
   const int* waves = a.waves + H.fw0;
   const int nw = H.nfw;
@@ -1938,28 +2157,59 @@ __global__ void __launch_bounds__(kHThreads) k_hprog(HProgArgs a, T* har) {
     }
   }
   if (threadIdx.x == 0) a.flops[((size_t)cid * kCluster + crank) * 2] += fl;
+  if (a.tc) {   // every tensor-core op has completed and been read back
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if ((threadIdx.x >> 5) == 0) tc_dealloc(c.tmem, 256);
+  }
+}
+
+// Check of the BF16 tensor-core tile on its own: one cluster of kCluster CTAs,
+// each set up as the factorisation sets itself up (tensor memory, MMA
+// barrier, context), computes C_r = A B reps times on one barrier; CTA r
+// writes its own C_r.  err[r] = 4 when a wait ran out.
+__global__ void __launch_bounds__(kHThreads) k_tc_tile_check(float* ar, int N, int K, int reps, int* err,
+                                                              unsigned long long* dbg) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  __shared__ unsigned s_tmem;
+  __shared__ __align__(8) unsigned long long s_tcbar;
+  const unsigned crank = cluster_rank();
+  HCtx<float> c;
+  c.ar = ar;
+  c.rk = nullptr;
+  c.sl = nullptr;
+  c.ws = nullptr;
+  c.sm = reinterpret_cast<float*>(smraw);
+  c.smcap = 0;
+  c.tprof = nullptr;
+  c.tol = 0.0;
+  c.err = err + crank;
+  unsigned tcphase = 0;
+  c.tc = 1;
+  c.tcbar = &s_tcbar;
+  c.tcphase = &tcphase;
+  c.tcdbg = dbg;
+  if ((threadIdx.x >> 5) == 0) tc_alloc(&s_tmem, 256);
+  if (threadIdx.x == 0) {
+    mbar_init(&s_tcbar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  c.tmem = s_tmem;
+  const View A{0, 128, K, 128, 0};
+  const View B{128LL * K, K, N, K, 0};
+  const View C{128LL * K + (long long)K * N + (long long)crank * 128 * N, 128, N, 128, 0};
+  for (int r = 0; r < reps && c.tc; ++r) tc_gemm128(c, A, B, C, 0, N, K, 1.f, 0.f);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if ((threadIdx.x >> 5) == 0) tc_dealloc(c.tmem, 256);
 }
 
 // --- asynchronous bulk copies and distributed shared memory (inline PTX) ---
-__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
-  unsigned ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
 // global -> this CTA's shared memory, completion counted on bar (bytes)
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes,
                                          unsigned long long* bar) {
@@ -2411,6 +2661,7 @@ struct hfsem_factor_s : public hf::Precond {
   hf::DevBuf<unsigned long long> d_prof;   // HFSEM_PROFILE=1: time per op type
   hf::DevBuf<double> d_flops;               // per instance: factor / solve flops
   hf::DevBuf<unsigned long long> d_wprof;   // HFSEM_PROFILE=2: per-wave records
+  hf::DevBuf<unsigned long long> d_tcdbg;   // tensor-core wait diagnostics (8 words)
   int wstride = 0;
   void report(const char* what);
   void report_waves(const char* what);
@@ -2472,7 +2723,8 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
   if (opt.R < 1 || opt.R > 32) throw Error(HFSEM_ERR_INVALID_ARG, "R must be in [1, 32]");
   if (!(opt.lambda > 0.0)) throw Error(HFSEM_ERR_INVALID_ARG, "lambda must be > 0");
   if (!(opt.tol_hlu >= 0.0)) throw Error(HFSEM_ERR_INVALID_ARG, "tol_hlu must be >= 0");
-  if (opt.precision != HFSEM_PREC_FP64 && opt.precision != HFSEM_PREC_MIXED)
+  if (opt.precision != HFSEM_PREC_FP64 && opt.precision != HFSEM_PREC_MIXED &&
+      opt.precision != HFSEM_PREC_MIXED_TC)
     throw Error(HFSEM_ERR_INVALID_ARG, "unknown precision");
   if (opt.leaf_elems < 0 || opt.kmax < 0) throw Error(HFSEM_ERR_INVALID_ARG, "leaf_elems, kmax >= 0");
   auto* f = new hfsem_factor();
@@ -2483,7 +2735,7 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
     // FP32 cannot factor the equilibrated H-matrix of meshes whose element
     // sizes span more than ~1e45 (the preconditioner then loses all digits);
     // such batches are factored in FP64 on the GPU
-    if (f->precision == HFSEM_PREC_MIXED)
+    if (f->precision != HFSEM_PREC_FP64)
       for (const InstHost& I : s->ih) {
         double hmax = *std::max_element(I.h.begin(), I.h.end());
         double hmin = *std::min_element(I.h.begin(), I.h.end());
@@ -2492,7 +2744,7 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
     f->build_only = opt.build_only;
     f->tol = opt.tol_hlu;
     f->R = opt.R;
-    const bool fp32 = f->precision == HFSEM_PREC_MIXED;
+    const bool fp32 = f->precision != HFSEM_PREC_FP64;
     f->tsize = fp32 ? sizeof(float) : sizeof(double);
     size_t sol_budget = 0;   // shared memory the leaf solve may take
     {
@@ -2838,6 +3090,16 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
     HF_CHECK(cudaMemcpy(err.data(), f->d_err.p, ni * sizeof(int), cudaMemcpyDeviceToHost));
     for (int e : err) {
       if (e == 3) throw Error(HFSEM_ERR_DEVICE, "low-rank block above the rank bound of the solves");
+      if (e == 4) {
+        unsigned long long d[8] = {0};
+        if (f->d_tcdbg.p) cudaMemcpy(d, f->d_tcdbg.p, sizeof(d), cudaMemcpyDeviceToHost);
+        char msg[256];
+        snprintf(msg, sizeof(msg),
+                 "a tensor-core product did not complete within its wait limit (mbarrier %llx, "
+                 "a-desc %llx, b-desc %llx, idesc %llx, tmem %llx, N|K %llx)",
+                 d[0], d[1], d[2], d[3], d[4], d[5]);
+        throw Error(HFSEM_ERR_DEVICE, msg);
+      }
       if (e) throw Error(HFSEM_ERR_BREAKDOWN, "zero or non-finite pivot in an H-LU leaf");
     }
   } catch (...) {
@@ -2980,6 +3242,10 @@ void hfsem_factor_s::run_prog() {
     d_flops.alloc((size_t)sys->n_inst * hf::kCluster * 2);
     cudaMemsetAsync(d_flops.p, 0, d_flops.n * sizeof(double), sys->st);
   }
+  if (!d_tcdbg.p && precision == HFSEM_PREC_MIXED_TC) {
+    d_tcdbg.alloc(8);
+    HF_CHECK(cudaMemsetAsync(d_tcdbg.p, 0, 8 * sizeof(unsigned long long), sys->st));
+  }
   const char* pe = getenv("HFSEM_PROFILE");
   if (!d_wprof.p && pe && atoi(pe) >= 2) {
     hf::AllocStream plain(reinterpret_cast<cudaStream_t>(-1));
@@ -2990,7 +3256,8 @@ void hfsem_factor_s::run_prog() {
   }
   if (d_wprof.p) cudaMemsetAsync(d_wprof.p, 0, d_wprof.n * sizeof(unsigned long long), sys->st);
   hf::HProgArgs a{d_hi.p, d_waves.p, d_ops.p, d_slots.p, d_ranks.p, d_err.p, tol, d_prof.p, d_flops.p,
-                  d_wprof.p, wstride, (long long)(smem / tsize) - 8, sys->n_inst};
+                  d_wprof.p, wstride, (long long)(smem / tsize) - 8, sys->n_inst,
+                  precision == HFSEM_PREC_MIXED_TC ? 1 : 0, d_tcdbg.p};
   hf::Tick tk(sys->st, "hlu_factor");
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(sys->n_inst * hf::kCluster));
@@ -3215,3 +3482,68 @@ void hfsem_factor_free(hfsem_factor* f) {
 }
 
 }  // extern "C"
+
+// The tensor-core tile check (hfsem.h).
+extern "C" int hfsem_tc_tile_check(int32_t N, int32_t K, int32_t reps, double* max_rel_err) {
+  using namespace hf;
+  try {
+    if (N < 16 || N > 128 || (N & 15) || K < 64 || K > 128 || (K & 15) || reps < 1 || reps > 8 ||
+        !max_rel_err)
+      throw Error(HFSEM_ERR_INVALID_ARG, "hfsem_tc_tile_check: bad arguments");
+    const size_t nab = (size_t)128 * K + (size_t)K * N;
+    const size_t na = nab + (size_t)kCluster * 128 * N;
+    std::vector<float> h(na, 0.f);
+    for (size_t i = 0; i < nab; ++i) h[i] = (float)(((i * 37) % 101) / 101.0 - 0.5);
+    DevBuf<float> d;
+    DevBuf<int> de;
+    DevBuf<unsigned long long> dd;
+    d.alloc(na);
+    de.alloc(kCluster);
+    dd.alloc(8);
+    HF_CHECK(cudaMemcpy(d.p, h.data(), na * sizeof(float), cudaMemcpyHostToDevice));
+    HF_CHECK(cudaMemset(de.p, 0, kCluster * sizeof(int)));
+    HF_CHECK(cudaMemset(dd.p, 0, 8 * sizeof(unsigned long long)));
+    const int smem = 96 * 1024;   // operands (128 + N) x K bf16 on a 1024-byte boundary
+    HF_CHECK(cudaFuncSetAttribute(k_tc_tile_check, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kCluster);
+    cfg.blockDim = dim3(kHThreads);
+    cfg.dynamicSmemBytes = (size_t)smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = kCluster;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    HF_CHECK(cudaLaunchKernelEx(&cfg, k_tc_tile_check, d.p, (int)N, (int)K, (int)reps, de.p, dd.p));
+    HF_CHECK(cudaDeviceSynchronize());
+    int herr[kCluster] = {0};
+    HF_CHECK(cudaMemcpy(h.data(), d.p, na * sizeof(float), cudaMemcpyDeviceToHost));
+    HF_CHECK(cudaMemcpy(herr, de.p, sizeof(herr), cudaMemcpyDeviceToHost));
+    for (int r = 0; r < kCluster; ++r)
+      if (herr[r]) throw Error(HFSEM_ERR_DEVICE, "hfsem_tc_tile_check: a tensor-core product did not complete within its wait limit");
+    // |C - A B| relative to sum_k |a_mk| |b_kn|, per entry, against FP64
+    double mx = 0.0;
+    for (int r = 0; r < kCluster; ++r)
+      for (int n = 0; n < N; ++n)
+        for (int m = 0; m < 128; ++m) {
+          double ref = 0.0, mag = 0.0;
+          for (int k = 0; k < K; ++k) {
+            const double a = h[(size_t)m + (size_t)k * 128], b = h[(size_t)128 * K + k + (size_t)n * K];
+            ref += a * b;
+            mag += std::fabs(a * b);
+          }
+          const double got = h[nab + (size_t)r * 128 * N + m + (size_t)n * 128];
+          if (mag > 0.0) mx = std::max(mx, std::fabs(ref - got) / mag);
+        }
+    *max_rel_err = mx;
+    return HFSEM_OK;
+  } catch (const Error& e) {
+    set_last_error(e.msg);
+    return e.code;
+  } catch (...) {
+    set_last_error("unknown error");
+    return HFSEM_ERR_DEVICE;
+  }
+}

@@ -25,7 +25,7 @@ HFSEM_ERR_DEVICE = 6
 HFSEM_ERR_UNSUPPORTED = 7
 
 MATVEC_AUTO, MATVEC_DENSE, MATVEC_TOEPLITZ = 0, 1, 2
-PREC_FP64, PREC_MIXED = 0, 1
+PREC_FP64, PREC_MIXED, PREC_MIXED_TC = 0, 1, 2   # PREC_MIXED_TC: dense leaf products of the H-LU on the tensor cores
 RHS_LOAD_VECTOR, RHS_FRAC_POWERS, RHS_LEGENDRE_AB = 0, 1, 2
 
 # every symbol include/hfsem.h declares
@@ -33,7 +33,7 @@ EXPORTED = ["hfsem_assemble", "hfsem_ndof", "hfsem_apply", "hfsem_load_vector",
             "hfsem_hlu_factor", "hfsem_hmatrix_dense", "hfsem_precond_apply",
             "hfsem_solve", "hfsem_factor_free", "hfsem_system_free",
             "hfsem_status_str", "hfsem_timing_enable", "hfsem_timing_reset",
-            "hfsem_timing_read", "hfsem_apply_noalloc"]
+            "hfsem_timing_read", "hfsem_apply_noalloc", "hfsem_tc_tile_check"]
 
 
 class HfsemError(RuntimeError):
@@ -81,6 +81,7 @@ def load_library():
     lib.hfsem_ndof.argtypes = [vp, C.c_int32, C.POINTER(C.c_int32)]
     lib.hfsem_apply.argtypes = [vp, C.c_int32, vp, vp]
     lib.hfsem_apply_noalloc.argtypes = [vp, C.c_int32, vp, vp]
+    lib.hfsem_tc_tile_check.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_double)]
     lib.hfsem_load_vector.argtypes = [vp, C.POINTER(hfsem_rhs), C.c_int32, vp]
     lib.hfsem_hlu_factor.argtypes = [vp, C.POINTER(hfsem_hopts), C.POINTER(vp)]
     lib.hfsem_hmatrix_dense.argtypes = [vp, C.c_int32, vp]
@@ -222,6 +223,14 @@ def hfsem_apply_noalloc(sys: System, x, nrhs: int = 1, out=None):
     _check(load_library().hfsem_apply_noalloc(sys.h, nrhs, _ptr(x), _ptr(y)),
            "hfsem_apply_noalloc")
     return y
+
+
+def hfsem_tc_tile_check(N: int, K: int, reps: int = 1) -> float:
+    """Max entrywise error of the BF16 tensor-core tile C = A B (128 x K times
+    K x N) against FP64, relative to sum_k |a_mk b_kn|."""
+    out = C.c_double(-1.0)
+    _check(load_library().hfsem_tc_tile_check(N, K, reps, C.byref(out)), "hfsem_tc_tile_check")
+    return out.value
 
 
 def _rhs_array(rhs_list):

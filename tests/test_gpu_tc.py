@@ -1,0 +1,58 @@
+"""The BF16 tensor-core mode of the H-LU (dense leaf products with BF16
+operands and FP32 accumulation in tensor memory):
+
+* the tile on its own, every entry within the error bound that BF16 rounding
+  of both operands and FP32 accumulation give, with several products per CTA
+  on one completion barrier;
+* a full-size factorisation and solve (nine uniform instances, N = 1024,
+  P = 8) in that mode: the weaker preconditioner costs iterations, the FP64
+  Krylov loop still reaches the oracle's solution.
+"""
+import numpy as np
+import pytest
+
+from oracle.basis import Mesh
+from oracle.solve import solve_problem
+from paper_1808_02937_gb300 import hfsem as H
+from paper_1808_02937_gb300 import workloads as W
+from tests._common import ensure_built, rel_err
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return ensure_built()
+
+
+@pytest.mark.parametrize("N,K,reps", [(16, 64, 1), (32, 128, 3), (48, 80, 2), (128, 128, 4)])
+def test_tc_tile_within_bf16_bound(lib, N, K, reps):
+    err = H.hfsem_tc_tile_check(N, K, reps)
+    # |fl(a) fl(b) - a b| <= (2u + u^2) |a b| with u = 2^-9 (BF16, nearest),
+    # plus FP32 accumulation over K terms
+    bound = 2.0 ** -8 + 2.0 ** -18 + K * 2.0 ** -24
+    assert 0.0 <= err <= bound, (err, bound)
+
+
+def test_tc_tile_bad_arguments(lib):
+    for N, K in ((8, 64), (24, 64), (32, 48), (32, 136)):
+        with pytest.raises(H.HfsemError) as ei:
+            H.hfsem_tc_tile_check(N, K, 1)
+        assert ei.value.code == H.HFSEM_ERR_INVALID_ARG
+
+
+def test_mixed_tc_config2_reaches_oracle(lib):
+    insts = W.config2()
+    sys_ = H.hfsem_assemble([H.make_problem(p.h, p.P, p.alpha, p.theta, p.rho) for p in insts])
+    fac = H.hfsem_hlu_factor(sys_, H.hopts(R=8, lam=1.0, tol_hlu=1e-3,
+                                           precision=H.PREC_MIXED_TC))
+    X, st, code = H.hfsem_solve(sys_, fac, [H.rhs_legendre([p.rhs[0]]) for p in insts],
+                                tol=1e-14, max_iter=80)
+    assert code == H.HFSEM_OK
+    for s in st:
+        assert s["iters"] <= 40 and s["rel_true_residual"] < 1e-11, st
+    p = insts[4]
+    Xo, _ = solve_problem(Mesh(p.h, 0.0, 1.0), p.P, p.alpha, p.theta, p.rho, 0.0, 0.0,
+                          ("legendre_ab", p.rhs[0]))
+    got = H.split(sys_, X)[4][:, 0]
+    assert rel_err(got, Xo) < 1e-10
