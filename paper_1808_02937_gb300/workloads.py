@@ -149,7 +149,11 @@ class Problem:
     rhs_kind: int = RHS_LEGENDRE_AB
     rhs: list = field(default_factory=list)   # one entry per RHS
     u_exact: object = None                    # polynomial coeffs in (x-a) if known
+                                              # (a list, one per RHS, for several)
     name: str = ""
+    arrival: float = 0.0                      # request streams: arrival time
+    reuse_of: int = -1                        # request streams: earlier request whose
+                                              # mesh and parameters this one repeats
 
     @property
     def N(self) -> int:
@@ -228,3 +232,87 @@ def config4(n_inst: int = 512, nrhs: int = 4, seed: int = 18080004):
                            rhs_kind=RHS_FRAC_POWERS, rhs=rhs,
                            name=f"C4[{i}] {mname} N={N} P={P}"))
     return out
+
+
+def geometric_q_floor(N: int, tiny: float = 1e-280) -> float:
+    """Smallest ratio q for which a two-sided geometric mesh of N elements
+    keeps its smallest element above tiny relative to the largest (FP64
+    underflows near 1e-308)."""
+    return tiny ** (1.0 / max(1, N // 2 - 1))
+
+
+def config5_requests(n: int = 10000, seed: int = 18080005, rate: float = 1.0):
+    """Seeded request stream (a generator, meshes drawn as each request is
+    produced): Poisson arrivals of the given rate; N_d log-uniform on
+    [100, 65535], P~U{2..16}, N = ceil((N_d+1)/P) <= 4096; alpha, theta, rho
+    and the mesh family as config 4 (two-sided geometric q raised to
+    geometric_q_floor(N) where the drawn q would underflow FP64); nrhs~U{1..16}
+    right-hand sides from u = x(1-x)p(x), deg p <= 4 (u_exact holds them);
+    30 % of the requests repeat the mesh and parameters (the factor key) of a
+    uniformly chosen earlier request, with new right-hand sides."""
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    keys = []
+    for i in range(n):
+        t += float(rng.exponential(1.0 / rate))
+        reuse = bool(keys) and rng.uniform() < 0.3
+        if reuse:
+            j = int(rng.integers(0, len(keys)))
+            N, P, alpha, theta, rho, fam, q, r, _ = keys[j]
+            src = keys[j][8]
+        else:
+            Nd = int(round(math.exp(rng.uniform(math.log(100.0), math.log(65535.0)))))
+            P = int(rng.integers(2, 17))
+            N = min(4096, max(1, -(-(Nd + 1) // P)))
+            alpha = float(rng.uniform(1.1, 1.9))
+            theta = float(rng.uniform(0.0, 1.0))
+            rho = float(rng.uniform(0.0, 2.0))
+            fam = int(rng.integers(0, 3))
+            q = float(rng.uniform(0.3, 0.7))
+            r = float(rng.integers(2, 4))
+            if fam == 1:
+                N += N % 2
+                if N > 4096:
+                    N -= 2
+                q = max(q, geometric_q_floor(N))
+            src = i
+            keys.append((N, P, alpha, theta, rho, fam, q, r, i))
+        if fam == 0:
+            h, mname = mesh_uniform(N), "uniform"
+        elif fam == 1:
+            h, mname = mesh_geometric_two_sided(N, q), f"geo2s q={q:.3f}"
+        else:
+            h, mname = mesh_graded(N, r), f"graded r={r:g}"
+        nrhs = int(rng.integers(1, 17))
+        rhs, us = [], []
+        for _ in range(nrhs):
+            pc = rng.standard_normal(int(rng.integers(0, 5)) + 1)
+            u = np.convolve([0.0, 1.0, -1.0], pc)
+            terms, _, _ = manufactured_rhs(u, alpha, theta, rho, 0.0, 1.0)
+            rhs.append(terms)
+            us.append(u)
+        yield Problem(h=h, P=P, alpha=alpha, theta=theta, rho=rho,
+                      rhs_kind=RHS_FRAC_POWERS, rhs=rhs, u_exact=us,
+                      name=f"C5[{i}] {mname} N={N} P={P} nrhs={nrhs}",
+                      arrival=t, reuse_of=(src if reuse else -1))
+
+
+def config5_max_request(family: str = "graded", nrhs: int = 16, seed: int = 18080055):
+    """The largest request of the stream: N = 4096, P = 16 (N_d = 65535),
+    uniform (Toeplitz operator) or graded r = 2 (dense operator), nrhs
+    manufactured right-hand sides from u = x(1-x)p(x), deg p <= 4."""
+    rng = np.random.default_rng(seed)
+    N, P = 4096, 16
+    alpha = float(rng.uniform(1.1, 1.9))
+    theta = float(rng.uniform(0.0, 1.0))
+    rho = float(rng.uniform(0.0, 2.0))
+    h = mesh_uniform(N) if family == "uniform" else mesh_graded(N, 2.0)
+    rhs, us = [], []
+    for _ in range(nrhs):
+        pc = rng.standard_normal(5)
+        u = np.convolve([0.0, 1.0, -1.0], pc)
+        terms, _, _ = manufactured_rhs(u, alpha, theta, rho, 0.0, 1.0)
+        rhs.append(terms)
+        us.append(u)
+    return Problem(h=h, P=P, alpha=alpha, theta=theta, rho=rho, rhs_kind=RHS_FRAC_POWERS,
+                   rhs=rhs, u_exact=us, name=f"C5 max {family} N={N} P={P} nrhs={nrhs}")

@@ -1,0 +1,78 @@
+"""GPU parity on the request stream's shapes (config 5), in the benchmark's
+solver settings (R = 8, lambda = 1, Tol_HLU = 1e-3, mixed precision,
+BiCGSTAB to 1e-14):
+
+* the largest request, N = 4096, P = 16 (N_d = 65535) with 16 right-hand
+  sides, on a uniform mesh (Toeplitz operator) and on a graded mesh (dense
+  operator, 17 GB of element-pair blocks): manufactured polynomial solutions
+  of degree <= 6 < P must come back exactly (a property that holds at any
+  size; the oracle's dense LU does not finish at this size);
+* the first requests of the seeded stream, one solve each (nrhs 1..16,
+  repeated factor keys): exact reproduction where P >= deg u, the oracle's
+  discrete solution where N_d <= 800, the true residual everywhere.
+"""
+import numpy as np
+import pytest
+
+from oracle.basis import Mesh
+from oracle.solve import solve_problem
+from paper_1808_02937_gb300 import hfsem as H
+from paper_1808_02937_gb300 import workloads as W
+from tests._common import ensure_built, rel_err
+from tests.test_oracle_solve import expected_coeffs
+
+pytestmark = pytest.mark.gpu
+
+OPTS = dict(R=8, lam=1.0, tol_hlu=1e-3, precision=H.PREC_MIXED)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    return ensure_built()
+
+
+def _solve(p):
+    sys_ = H.hfsem_assemble([H.make_problem(p.h, p.P, p.alpha, p.theta, p.rho)])
+    fac = H.hfsem_hlu_factor(sys_, H.hopts(**OPTS))
+    X, st, code = H.hfsem_solve(sys_, fac, [H.rhs_frac_powers(p.rhs)], tol=1e-14,
+                                max_iter=100, allow_fail=True)
+    return H.split(sys_, X, nrhs=len(p.rhs))[0], st, code
+
+
+def _check_exact(p, parts):
+    n = 0
+    for r, u in enumerate(p.u_exact):
+        if p.P >= len(u) - 1:
+            Xe = expected_coeffs(Mesh(p.h, 0.0, 1.0), p.P, np.polynomial.Polynomial(u))
+            assert rel_err(parts[:, r], Xe) < 1e-10, (p.name, r)
+            n += 1
+    return n
+
+
+@pytest.mark.parametrize("family", ["uniform", "graded"])
+def test_config5_largest_request(lib, family):
+    p = W.config5_max_request(family)
+    assert p.Nd == 65535 and len(p.rhs) == 16
+    parts, st, code = _solve(p)
+    assert code == H.HFSEM_OK
+    for s in st:
+        assert s["iters"] <= 20 and s["rel_true_residual"] < 1e-11, st
+    assert _check_exact(p, parts) == 16
+
+
+def test_config5_stream_sample(lib):
+    reqs = list(W.config5_requests(12))
+    assert any(p.reuse_of >= 0 for p in reqs)
+    n_exact = n_oracle = 0
+    for p in reqs:
+        parts, st, code = _solve(p)
+        assert code == H.HFSEM_OK, p.name
+        for s in st:
+            assert s["rel_true_residual"] < 1e-11, (p.name, st)
+        n_exact += _check_exact(p, parts)
+        if p.Nd <= 800:
+            Xo, _ = solve_problem(Mesh(p.h, 0.0, 1.0), p.P, p.alpha, p.theta, p.rho, 0.0, 0.0,
+                                  ("frac_powers", p.rhs[0]))
+            assert rel_err(parts[:, 0], Xo) < 1e-10, p.name
+            n_oracle += 1
+    assert n_exact >= 20 and n_oracle >= 3
