@@ -1660,6 +1660,380 @@ __device__ void apply_q_staged(const T* A, int m, int K, const T* tau, T* Y, int
   __syncthreads();
 }
 
+// Column-pivoted Householder QR of the core M (ku x kv, ld K), M Pi = Q_M R_M,
+// stopped at the first pivot below tol |R_M(0,0)| or after rmax steps; then
+// Z = Q_M [I_r; 0] (ku x r, ld K).  On return M holds R_M above its diagonal
+// and the reflectors below, piv the column permutation.  Returns r (the same
+// in every thread).  Called by the whole CTA.
+template <class T, class F>
+__device__ int core_rrqr(T* M, int K, int ku, int kv, int rmax, double tol, T* tauM, T* cn, int* piv,
+                         T* Z, F tmk3) {
+  for (int j = threadIdx.x; j < kv; j += blockDim.x) piv[j] = j;
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int r = 0;
+  __shared__ int s_stop;
+  __shared__ T s_r0;
+  for (int st = 0; st < rmax; ++st) {
+    // exact norms of the remaining parts of the columns (a warp per column)
+    for (int j = st + warp; j < kv; j += nw) {
+      T a = 0;
+      for (int i = st + lane; i < ku; i += 32) a += M[i + j * K] * M[i + j * K];
+      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      if (lane == 0) cn[j] = a;
+    }
+    __syncthreads();
+    // warp 0: pivot (largest remaining norm), stop test, swap, reflector
+    if (warp == 0) {
+      T best = (T)-1;
+      int p = st;
+      for (int j = st + lane; j < kv; j += 32)
+        if (cn[j] > best) {
+          best = cn[j];
+          p = j;
+        }
+      for (int o = 16; o > 0; o >>= 1) {
+        const T ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int op = __shfl_xor_sync(0xffffffffu, p, o);
+        if (ob > best || (ob == best && op < p)) {
+          best = ob;
+          p = op;
+        }
+      }
+      const T nrm = sqrt(fmax(best, (T)0));
+      if (st == 0 && lane == 0) s_r0 = nrm;
+      __syncwarp();
+      const int stop = (nrm == (T)0 || (st > 0 && nrm <= (T)tol * s_r0)) ? 1 : 0;
+      if (lane == 0) s_stop = stop;
+      if (!stop) {
+        if (p != st) {
+          for (int i = lane; i < ku; i += 32) {
+            const T a = M[i + st * K];
+            M[i + st * K] = M[i + p * K];
+            M[i + p * K] = a;
+          }
+          if (lane == 0) {
+            const int a = piv[st];
+            piv[st] = piv[p];
+            piv[p] = a;
+          }
+        }
+        __syncwarp();
+        T a = 0;
+        for (int i = st + 1 + lane; i < ku; i += 32) a += M[i + st * K] * M[i + st * K];
+        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+        const T x0 = M[st + st * K];
+        const T sn = sqrt(x0 * x0 + a);
+        const T alpha = (x0 >= (T)0) ? -sn : sn;
+        const T v0 = x0 - alpha;
+        const bool trivial = (sn == (T)0) || (v0 == (T)0) || a == (T)0;
+        __syncwarp();
+        if (!trivial) {
+          const T iv = (T)1 / v0;
+          for (int i = st + 1 + lane; i < ku; i += 32) M[i + st * K] *= iv;
+        }
+        __syncwarp();
+        if (lane == 0) {
+          tauM[st] = trivial ? (T)0 : (alpha - x0) / alpha;
+          if (!trivial) M[st + st * K] = alpha;
+        }
+      }
+    }
+    __syncthreads();
+    if (s_stop) break;
+    const T tj = tauM[st];
+    if (tj != (T)0)
+      for (int l = st + 1 + warp; l < kv; l += nw) {
+        T w = 0;
+        for (int i = st + 1 + lane; i < ku; i += 32) w += M[i + st * K] * M[i + l * K];
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        w = (w + M[st + l * K]) * tj;
+        __syncwarp();
+        if (lane == 0) M[st + l * K] -= w;
+        for (int i = st + 1 + lane; i < ku; i += 32) M[i + l * K] -= w * M[i + st * K];
+      }
+    __syncthreads();
+    r = st + 1;
+  }
+  // (all threads agree on r: every exit is uniform)
+  tmk3();
+  // Z = Q_M [I_r; 0] (ku x r): apply the r reflectors of M in reverse
+  for (int t = threadIdx.x; t < ku * r; t += blockDim.x) Z[(t % ku) + (t / ku) * K] = (t % ku == t / ku) ? (T)1 : (T)0;
+  __syncthreads();
+  for (int j = r - 1; j >= 0; --j) {
+    T tj = tauM[j];
+    if (tj != (T)0)
+      for (int col = warp; col < r; col += nw) {
+        T w = 0;
+        for (int i = j + 1 + lane; i < ku; i += 32) w += M[i + j * K] * Z[i + col * K];
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
+        w = __shfl_sync(0xffffffffu, w, 0);
+        w = (w + Z[j + col * K]) * tj;
+        if (lane == 0) Z[j + col * K] -= w;
+        for (int i = j + 1 + lane; i < ku; i += 32) Z[i + col * K] -= w * M[i + j * K];
+      }
+    __syncthreads();
+  }
+  return r;
+}
+
+// x y added to the double-float sum (hi, lo): the product is split exactly
+// (x y = p + e by fma), the sum by TwoSum; explicit rounding intrinsics keep
+// the compiler from contracting the error terms away.
+__device__ __forceinline__ void df_add_prod(float& hi, float& lo, float x, float y) {
+  const float p = __fmul_rn(x, y);
+  const float e = __fmaf_rn(x, y, -p);
+  const float s = __fadd_rn(hi, p);
+  const float bb = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(p, bb));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(err, e));
+}
+__device__ __forceinline__ void df_add(float& hi, float& lo, float h2, float l2) {
+  const float s = __fadd_rn(hi, h2);
+  const float bb = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(h2, bb));
+  hi = s;
+  lo = __fadd_rn(lo, __fadd_rn(err, l2));
+}
+
+// Pivoted Cholesky of the symmetric K x K matrix G (row-major, K <= 32, FP64)
+// by one warp: Pi^T G Pi = R^T R + E, stopped when the largest remaining
+// diagonal falls to thr times the first pivot.  R (rank x K, pivoted column
+// order) overwrites the upper triangle of G's first rank rows; piv[q] is the
+// original column of pivoted column q.  Returns the rank (in every lane).
+__device__ int pchol_warp(double* G, int K, int* piv, double thr) {
+  const int lane = threadIdx.x & 31;
+  if (lane < K) piv[lane] = lane;
+  __syncwarp();
+  double d0 = 0.0;
+  int r = 0;
+  for (int k = 0; k < K; ++k) {
+    double best = -1.0;
+    int p = k;
+    if (lane >= k && lane < K) {
+      best = G[lane * K + lane];
+      if (!(best >= 0.0)) best = -1.0;   // NaN or negative: never a pivot
+      p = lane;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const int op = __shfl_xor_sync(0xffffffffu, p, o);
+      if (ob > best || (ob == best && op < p)) {
+        best = ob;
+        p = op;
+      }
+    }
+    if (k == 0) d0 = best;
+    if (!(best > 0.0) || !(best > thr * d0)) break;
+    if (p != k) {   // symmetric swap of k and p (columns across every row: R's too)
+      if (lane < K) {
+        const double a = G[k * K + lane];
+        G[k * K + lane] = G[p * K + lane];
+        G[p * K + lane] = a;
+      }
+      __syncwarp();
+      if (lane < K) {
+        const double a = G[lane * K + k];
+        G[lane * K + k] = G[lane * K + p];
+        G[lane * K + p] = a;
+      }
+      if (lane == 0) {
+        const int a = piv[k];
+        piv[k] = piv[p];
+        piv[p] = a;
+      }
+      __syncwarp();
+    }
+    const double rkk = sqrt(G[k * K + k]);
+    __syncwarp();
+    if (lane > k && lane < K) G[k * K + lane] /= rkk;
+    if (lane == 0) G[k * K + k] = rkk;
+    __syncwarp();
+    if (lane > k && lane < K) {
+      const double rkj = G[k * K + lane];
+      for (int i = k + 1; i < K; ++i) G[i * K + lane] -= G[k * K + i] * rkj;
+    }
+    __syncwarp();
+    r = k + 1;
+  }
+  return r;
+}
+
+// c_q (q < n) of R11^-1 z by one warp, R11 upper triangular (ld K, FP64, the
+// first n rows and columns of R), z and the result ld-1 vectors (FP32)
+__device__ void backsub_warp(const double* R, int K, int n, const float* z, float* out) {
+  const int lane = threadIdx.x & 31;
+  double cq = 0.0;
+  for (int i = n - 1; i >= 0; --i) {
+    double part = (lane > i && lane < n) ? R[i * K + lane] * cq : 0.0;
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if (lane == i) cq = ((double)z[i] - part) / R[i * K + i];
+  }
+  __syncwarp();   // every z[i] is read before out (which may be z) is written
+  if (lane < n) out[lane] = (float)cq;
+}
+
+// Recompression of FP32 factors from their Gram matrices (K <= 32): G_U = U^T U
+// and G_V = V^T V summed exactly in double-float from the FP32 entries, pivoted
+// Cholesky in FP64, U Pi_U = Q_U R_U with Q_U = (U Pi_U)[:, :r_u] R_U11^-1
+// (directions whose remaining diagonal falls below 2^-40 of the first are
+// dropped: singular values under ~1e-6 of the largest, the FP32 rounding
+// level of the factors); then the core RRQR of the Householder path on
+// M = (R_U Pi_U^T)(R_V Pi_V^T)^T and
+//   U_new = (U Pi_U)[:, :r_u] (R_U11^-1 Z),  V_new = (V Pi_V)[:, :r_v] (R_V11^-1 Pi_M R_M[:r, :]^T).
+// The same truncated product as the Householder path, with a handful of CTA
+// barriers instead of several per column.
+__device__ void trunc_gram(HCtx<float>& c, int slot, const float* Ut, const float* Vt, int K) {
+  const SlotDev s = c.sl[slot];
+  const int m = s.m, n = s.n;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int lane = tid & 31, warp = tid >> 5, nw = nt >> 5;
+  double* GU = reinterpret_cast<double*>(c.sm);        // K x K
+  double* GV = GU + K * K;                             // K x K
+  float* RUo = reinterpret_cast<float*>(GV + K * K);   // r_u x K (original columns)
+  float* RVo = RUo + K * K;
+  float* M = RVo + K * K;                              // core, ld K
+  float* Z = M + K * K;
+  float* WU = Z + K * K;                               // r_u x r, ld K
+  float* WV = WU + K * K;                              // r_v x r (Y_V first), ld K
+  float* tauM = WV + K * K;
+  float* cn = tauM + K;
+  int* pivU = reinterpret_cast<int*>(cn + K);
+  int* pivV = pivU + K;
+  int* piv = pivV + K;
+  const long long small = ((long long)(4 * K * K + 6 * K * K + 5 * K) + 3) & ~3LL;
+  float* stage = c.sm + small;
+  const long long cap = c.smcap - small;
+  __shared__ int s_ru, s_rv;
+  unsigned long long tq = 0;
+  auto tmk = [&](int k) {
+    if (!c.tprof || tid != 0) return;
+    unsigned long long t1;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
+    if (k >= 0) atomicAdd(c.tprof + k, t1 - tq);
+    tq = t1;
+  };
+  tmk(-1);
+  // the tall factors, staged when they fit
+  const float* SU = Ut;
+  const float* SV = Vt;
+  if ((long long)(m + n) * K <= cap) {
+    float* su = stage;
+    float* sv = stage + (long long)m * K;
+    for (long long t = tid; t < (long long)m * K; t += nt) su[t] = Ut[t];
+    for (long long t = tid; t < (long long)n * K; t += nt) sv[t] = Vt[t];
+    SU = su;
+    SV = sv;
+    __syncthreads();
+  }
+  // Gram matrices: a warp per entry (i <= j) of G_U, then of G_V
+  const int E = K * (K + 1) / 2;
+  for (int task = warp; task < 2 * E; task += nw) {
+    const bool isv = task >= E;
+    int e = isv ? task - E : task;
+    int i = 0;
+    while (e >= K - i) {
+      e -= K - i;
+      ++i;
+    }
+    const int j = i + e;
+    const float* A = isv ? SV : SU;
+    const int rows = isv ? n : m;
+    const float* ai = A + (long long)i * rows;
+    const float* aj = A + (long long)j * rows;
+    float hi = 0.f, lo = 0.f;
+    for (int t = lane; t < rows; t += 32) df_add_prod(hi, lo, ai[t], aj[t]);
+    for (int o = 16; o > 0; o >>= 1) {
+      const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
+      const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
+      df_add(hi, lo, h2, l2);
+    }
+    if (lane == 0) {
+      double* G = isv ? GV : GU;
+      const double g = (double)hi + (double)lo;
+      G[i * K + j] = g;
+      G[j * K + i] = g;
+    }
+  }
+  __syncthreads();
+  tmk(0);
+  // pivoted Cholesky of both, one warp each
+  const double thr = 0x1p-40;
+  if (warp == 0) {
+    const int r = pchol_warp(GU, K, pivU, thr);
+    if (lane == 0) s_ru = min(r, m);
+  } else if (warp == 1) {
+    const int r = pchol_warp(GV, K, pivV, thr);
+    if (lane == 0) s_rv = min(r, n);
+  }
+  __syncthreads();
+  tmk(1);
+  const int ru = s_ru, rv = s_rv;
+  float* Ud = c.ar + s.off;
+  float* Vd = c.ar + s.off + (long long)m * s.kcap;
+  if (ru == 0 || rv == 0) {
+    if (tid == 0) c.rk[slot] = 0;
+    __syncthreads();
+    return;
+  }
+  // R in original column order, then the core M = RUo RVo^T (ru x rv, ld K)
+  for (int t = tid; t < ru * K; t += nt) {
+    const int i = t / K, q = t % K;
+    RUo[i * K + pivU[q]] = (q >= i) ? (float)GU[i * K + q] : 0.f;
+  }
+  for (int t = tid; t < rv * K; t += nt) {
+    const int i = t / K, q = t % K;
+    RVo[i * K + pivV[q]] = (q >= i) ? (float)GV[i * K + q] : 0.f;
+  }
+  __syncthreads();
+  for (int t = tid; t < ru * rv; t += nt) {
+    const int i = t % ru, j = t / ru;
+    float acc = 0.f;
+    for (int l = 0; l < K; ++l) acc += RUo[i * K + l] * RVo[j * K + l];
+    M[i + j * K] = acc;
+  }
+  tmk(2);
+  const int rmax = min(min(ru, rv), s.kmax);
+  const int r = core_rrqr(M, K, ru, rv, rmax, c.tol, tauM, cn, piv, Z, [&]() { tmk(3); });
+  // Y_V = Pi_M R_M[:r, :]^T (rv x r), then the two triangular solves
+  for (int t = tid; t < rv * r; t += nt) WV[(t % rv) + (t / rv) * K] = 0.f;
+  __syncthreads();
+  for (int t = tid; t < rv * r; t += nt) {
+    const int j = t % rv, i = t / rv;   // R_M[i][j], j >= i
+    if (j >= i) WV[piv[j] + i * K] = M[i + j * K];
+  }
+  __syncthreads();
+  for (int task = warp; task < 2 * r; task += nw) {
+    if (task < r) backsub_warp(GU, K, ru, Z + task * K, WU + task * K);
+    else backsub_warp(GV, K, rv, WV + (task - r) * K, WV + (task - r) * K);
+  }
+  __syncthreads();
+  tmk(4);
+  // U_new = (U Pi_U)[:, :ru] W_U, V_new = (V Pi_V)[:, :rv] W_V
+  for (long long t = tid; t < (long long)m * r; t += nt) {
+    const int i = (int)(t % m), j = (int)(t / m);
+    float acc = 0.f;
+    for (int q = 0; q < ru; ++q) acc += SU[i + (long long)pivU[q] * m] * WU[q + j * K];
+    Ud[i + (long long)j * m] = acc;
+  }
+  tmk(5);
+  for (long long t = tid; t < (long long)n * r; t += nt) {
+    const int i = (int)(t % n), j = (int)(t / n);
+    float acc = 0.f;
+    for (int q = 0; q < rv; ++q) acc += SV[i + (long long)pivV[q] * n] * WV[q + j * K];
+    Vd[i + (long long)j * n] = acc;
+  }
+  tmk(6);
+  if (c.tprof && tid == 0) {
+    atomicAdd(c.tprof + 8, 1ULL);
+    atomicAdd(c.tprof + 9, (unsigned long long)K);
+    atomicAdd(c.tprof + 10, (unsigned long long)(m + n));
+  }
+  if (tid == 0) c.rk[slot] = r;
+  __syncthreads();
+}
+
 // Recompress U V^T given as Ut (m x K) and Vt (n x K) in the workspace into
 // LR slot `slot`.  U = Q_U R_U, V = Q_V R_V (Householder), then a column-
 // pivoted QR of the small core M = R_U R_V^T, M Pi = Q_M R_M, stopped at the
@@ -1667,6 +2041,12 @@ __device__ void apply_q_staged(const T* A, int m, int K, const T* tau, T* Y, int
 //   U V^T ~ (Q_U Q_M[:, :r]) (Q_V Pi R_M[:r, :]^T)^T.
 template <class T>
 __device__ void trunc_core(HCtx<T>& c, int slot, T* Ut, T* Vt, int K) {
+  if constexpr (sizeof(T) == 4) {
+    if (K <= 32) {
+      trunc_gram(c, slot, Ut, Vt, K);
+      return;
+    }
+  }
   const SlotDev s = c.sl[slot];
   const int m = s.m, n = s.n;
   T* tauU = c.sm;
@@ -1681,8 +2061,6 @@ __device__ void trunc_core(HCtx<T>& c, int slot, T* Ut, T* Vt, int K) {
   const long long small = ((2LL * K + 32 + 2LL * K * K + 3LL * K + K + 8) + 3) & ~3LL;
   T* stage = c.sm + small;
   const long long cap = c.smcap - small;
-  __shared__ int s_stop;
-  __shared__ T s_r0;
   // Householder QR of the tall factors, in shared memory when they fit (the
   // reflector loops are latency bound), written back for the final products
   unsigned long long tq = 0;
@@ -1740,114 +2118,11 @@ __device__ void trunc_core(HCtx<T>& c, int slot, T* Ut, T* Vt, int K) {
     for (int l = max(i, j); l < K; ++l) acc += RU[i + l * ldu] * RV[j + l * ldv];
     M[i + j * K] = acc;
   }
-  for (int j = threadIdx.x; j < kv; j += blockDim.x) piv[j] = j;
-  __syncthreads();
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
   const int rmax = min(min(ku, kv), s.kmax);
-  int r = 0;
   tmk(2);
-  for (int st = 0; st < rmax; ++st) {
-    // exact norms of the remaining parts of the columns (a warp per column)
-    for (int j = st + warp; j < kv; j += nw) {
-      T a = 0;
-      for (int i = st + lane; i < ku; i += 32) a += M[i + j * K] * M[i + j * K];
-      for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-      if (lane == 0) cn[j] = a;
-    }
-    __syncthreads();
-    // warp 0: pivot (largest remaining norm), stop test, swap, reflector
-    if (warp == 0) {
-      T best = (T)-1;
-      int p = st;
-      for (int j = st + lane; j < kv; j += 32)
-        if (cn[j] > best) {
-          best = cn[j];
-          p = j;
-        }
-      for (int o = 16; o > 0; o >>= 1) {
-        const T ob = __shfl_xor_sync(0xffffffffu, best, o);
-        const int op = __shfl_xor_sync(0xffffffffu, p, o);
-        if (ob > best || (ob == best && op < p)) {
-          best = ob;
-          p = op;
-        }
-      }
-      const T nrm = sqrt(fmax(best, (T)0));
-      if (st == 0 && lane == 0) s_r0 = nrm;
-      __syncwarp();
-      const int stop = (nrm == (T)0 || (st > 0 && nrm <= (T)c.tol * s_r0)) ? 1 : 0;
-      if (lane == 0) s_stop = stop;
-      if (!stop) {
-        if (p != st) {
-          for (int i = lane; i < ku; i += 32) {
-            const T a = M[i + st * K];
-            M[i + st * K] = M[i + p * K];
-            M[i + p * K] = a;
-          }
-          if (lane == 0) {
-            const int a = piv[st];
-            piv[st] = piv[p];
-            piv[p] = a;
-          }
-        }
-        __syncwarp();
-        T a = 0;
-        for (int i = st + 1 + lane; i < ku; i += 32) a += M[i + st * K] * M[i + st * K];
-        for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-        const T x0 = M[st + st * K];
-        const T sn = sqrt(x0 * x0 + a);
-        const T alpha = (x0 >= (T)0) ? -sn : sn;
-        const T v0 = x0 - alpha;
-        const bool trivial = (sn == (T)0) || (v0 == (T)0) || a == (T)0;
-        __syncwarp();
-        if (!trivial) {
-          const T iv = (T)1 / v0;
-          for (int i = st + 1 + lane; i < ku; i += 32) M[i + st * K] *= iv;
-        }
-        __syncwarp();
-        if (lane == 0) {
-          tauM[st] = trivial ? (T)0 : (alpha - x0) / alpha;
-          if (!trivial) M[st + st * K] = alpha;
-        }
-      }
-    }
-    __syncthreads();
-    if (s_stop) break;
-    const T tj = tauM[st];
-    if (tj != (T)0)
-      for (int l = st + 1 + warp; l < kv; l += nw) {
-        T w = 0;
-        for (int i = st + 1 + lane; i < ku; i += 32) w += M[i + st * K] * M[i + l * K];
-        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
-        w = (w + M[st + l * K]) * tj;
-        __syncwarp();
-        if (lane == 0) M[st + l * K] -= w;
-        for (int i = st + 1 + lane; i < ku; i += 32) M[i + l * K] -= w * M[i + st * K];
-      }
-    __syncthreads();
-    r = st + 1;
-  }
-  // (all threads agree on r: every exit is uniform)
+  const int r = core_rrqr(M, K, ku, kv, rmax, c.tol, tauM, cn, piv, Z, [&]() { tmk(3); });
   T* Ud = c.ar + s.off;
   T* Vd = c.ar + s.off + (long long)m * s.kcap;
-  tmk(3);
-  // Z = Q_M [I_r; 0] (ku x r): apply the r reflectors of M in reverse
-  for (int t = threadIdx.x; t < ku * r; t += blockDim.x) Z[(t % ku) + (t / ku) * K] = (t % ku == t / ku) ? (T)1 : (T)0;
-  __syncthreads();
-  for (int j = r - 1; j >= 0; --j) {
-    T tj = tauM[j];
-    if (tj != (T)0)
-      for (int col = warp; col < r; col += nw) {
-        T w = 0;
-        for (int i = j + 1 + lane; i < ku; i += 32) w += M[i + j * K] * Z[i + col * K];
-        for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(0xffffffffu, w, o);
-        w = __shfl_sync(0xffffffffu, w, 0);
-        w = (w + Z[j + col * K]) * tj;
-        if (lane == 0) Z[j + col * K] -= w;
-        for (int i = j + 1 + lane; i < ku; i += 32) Z[i + col * K] -= w * M[i + j * K];
-      }
-    __syncthreads();
-  }
   // U_new = Q_U [Z; 0], V_new = Q_V [Pi R_M[:r,:]^T; 0] (row piv[j] of the
   // core factor is R_M[:, j]); built in shared memory when both fit
   T* YU = both ? SV + (long long)n * K : Ud;
