@@ -1797,35 +1797,55 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float h2, float l2)
   lo = __fadd_rn(lo, __fadd_rn(err, l2));
 }
 
+// 1/sqrt(d) for d > 0 in FP64: Newton-Raphson on y = 1/sqrt(m), m the mantissa
+// of d scaled to [0.5, 2) with an even exponent, from the FP32 estimate
+// rsqrtf(m) (two steps y <- y (3 - m y^2) / 2 take its ~2^-22 relative error
+// below FP64 rounding), then the exponent is put back.
+__device__ __forceinline__ double rsqrt_newton(double d) {
+  int e;
+  double mt = frexp(d, &e);   // d = mt 2^e, mt in [0.5, 1)
+  if (e & 1) {
+    mt *= 2.0;
+    e -= 1;
+  }
+  double y = (double)rsqrtf((float)mt);
+  y = y * (1.5 - 0.5 * mt * y * y);
+  y = y * (1.5 - 0.5 * mt * y * y);
+  return ldexp(y, -e / 2);
+}
+
 // Pivoted Cholesky of the symmetric K x K matrix G (row-major, K <= 32, FP64)
 // by one warp: Pi^T G Pi = R^T R + E, stopped when the largest remaining
 // diagonal falls to thr times the first pivot.  R (rank x K, pivoted column
 // order) overwrites the upper triangle of G's first rank rows; piv[q] is the
-// original column of pivoted column q.  Returns the rank (in every lane).
-__device__ int pchol_warp(double* G, int K, int* piv, double thr) {
+// original column of pivoted column q; invd[q] = 1 / R[q][q] (FP32).
+// Returns the rank (in every lane).  The pivot is chosen on FP32 copies of
+// the remaining diagonal (FP64 instructions are the scarce resource here).
+__device__ int pchol_warp(double* G, int K, int* piv, float* invd, double thr) {
   const int lane = threadIdx.x & 31;
   if (lane < K) piv[lane] = lane;
   __syncwarp();
   double d0 = 0.0;
   int r = 0;
   for (int k = 0; k < K; ++k) {
-    double best = -1.0;
+    float best = -1.f;
     int p = k;
     if (lane >= k && lane < K) {
-      best = G[lane * K + lane];
-      if (!(best >= 0.0)) best = -1.0;   // NaN or negative: never a pivot
+      best = (float)G[lane * K + lane];
+      if (!(best >= 0.f)) best = -1.f;   // NaN or negative: never a pivot
       p = lane;
     }
     for (int o = 16; o > 0; o >>= 1) {
-      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const float ob = __shfl_xor_sync(0xffffffffu, best, o);
       const int op = __shfl_xor_sync(0xffffffffu, p, o);
       if (ob > best || (ob == best && op < p)) {
         best = ob;
         p = op;
       }
     }
-    if (k == 0) d0 = best;
-    if (!(best > 0.0) || !(best > thr * d0)) break;
+    const double dp = G[p * K + p];
+    if (k == 0) d0 = dp;
+    if (!(dp > 0.0) || !(dp > thr * d0)) break;
     if (p != k) {   // symmetric swap of k and p (columns across every row: R's too)
       if (lane < K) {
         const double a = G[k * K + lane];
@@ -1845,10 +1865,13 @@ __device__ int pchol_warp(double* G, int K, int* piv, double thr) {
       }
       __syncwarp();
     }
-    const double rkk = sqrt(G[k * K + k]);
+    const double inv = rsqrt_newton(dp);   // dp = G[k][k] after the swap
     __syncwarp();
-    if (lane > k && lane < K) G[k * K + lane] /= rkk;
-    if (lane == 0) G[k * K + k] = rkk;
+    if (lane > k && lane < K) G[k * K + lane] *= inv;
+    if (lane == 0) {
+      G[k * K + k] = dp * inv;
+      invd[k] = (float)inv;
+    }
     __syncwarp();
     if (lane > k && lane < K) {
       const double rkj = G[k * K + lane];
@@ -1860,18 +1883,39 @@ __device__ int pchol_warp(double* G, int K, int* piv, double thr) {
   return r;
 }
 
-// c_q (q < n) of R11^-1 z by one warp, R11 upper triangular (ld K, FP64, the
-// first n rows and columns of R), z and the result ld-1 vectors (FP32)
-__device__ void backsub_warp(const double* R, int K, int n, const float* z, float* out) {
+// c = R11^-1 z by one warp in FP32 (backward stable): R11 the leading n x n
+// upper triangle of R (row-major, ld K), invd its inverse diagonal; z and out
+// are vectors (out may be z)
+__device__ void backsub_warp(const float* R, const float* invd, int K, int n, const float* z,
+                             float* out) {
   const int lane = threadIdx.x & 31;
-  double cq = 0.0;
+  float cq = 0.f;
   for (int i = n - 1; i >= 0; --i) {
-    double part = (lane > i && lane < n) ? R[i * K + lane] * cq : 0.0;
+    float part = (lane > i && lane < n) ? R[i * K + lane] * cq : 0.f;
     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    if (lane == i) cq = ((double)z[i] - part) / R[i * K + i];
+    if (lane == i) cq = (z[i] - part) * invd[i];
   }
   __syncwarp();   // every z[i] is read before out (which may be z) is written
-  if (lane < n) out[lane] = (float)cq;
+  if (lane < n) out[lane] = cq;
+}
+
+// Shared-memory floats in front of the staged factors in trunc_gram
+// (Gram matrices in FP64, the small FP32 work arrays, pivots)
+__host__ __device__ __forceinline__ long long gram_small(int K) {
+  return ((long long)(12 * K * K + 7 * K) + 3) & ~3LL;
+}
+
+// n consecutive floats global -> shared as asynchronous copies (16-byte ones
+// when both sides are aligned), every copy in flight at once; the caller
+// waits (cp_async_wait_all) and synchronises
+__device__ __forceinline__ void cp_async_range(float* dst, const float* src, long long n) {
+  long long t0 = 0;
+  if (((smem_u32(dst) & 15u) == 0) && ((reinterpret_cast<unsigned long long>(src) & 15ULL) == 0)) {
+    const long long n4 = n >> 2;
+    for (long long t = threadIdx.x; t < n4; t += blockDim.x) cp_async16(dst + 4 * t, src + 4 * t);
+    t0 = n4 << 2;
+  }
+  for (long long t = t0 + threadIdx.x; t < n; t += blockDim.x) cp_async_elem(dst + t, src + t);
 }
 
 // Recompression of FP32 factors from their Gram matrices (K <= 32): G_U = U^T U
@@ -1884,7 +1928,11 @@ __device__ void backsub_warp(const double* R, int K, int n, const float* z, floa
 //   U_new = (U Pi_U)[:, :r_u] (R_U11^-1 Z),  V_new = (V Pi_V)[:, :r_v] (R_V11^-1 Pi_M R_M[:r, :]^T).
 // The same truncated product as the Householder path, with a handful of CTA
 // barriers instead of several per column.
-__device__ void trunc_gram(HCtx<float>& c, int slot, const float* Ut, const float* Vt, int K) {
+// staged: the factors are already in shared memory at c.sm + gram_small(K)
+// (U, m x K, then V, n x K); else they are read from Ut, Vt (staged here when
+// they fit).
+__device__ void trunc_gram(HCtx<float>& c, int slot, const float* Ut, const float* Vt, int K,
+                           bool staged) {
   const SlotDev s = c.sl[slot];
   const int m = s.m, n = s.n;
   const int tid = threadIdx.x, nt = blockDim.x;
@@ -1897,12 +1945,16 @@ __device__ void trunc_gram(HCtx<float>& c, int slot, const float* Ut, const floa
   float* Z = M + K * K;
   float* WU = Z + K * K;                               // r_u x r, ld K
   float* WV = WU + K * K;                              // r_v x r (Y_V first), ld K
-  float* tauM = WV + K * K;
+  float* RUp = WV + K * K;                             // R_U11, R_V11 in FP32 (pivoted order)
+  float* RVp = RUp + K * K;
+  float* tauM = RVp + K * K;
   float* cn = tauM + K;
-  int* pivU = reinterpret_cast<int*>(cn + K);
+  float* invdU = cn + K;
+  float* invdV = invdU + K;
+  int* pivU = reinterpret_cast<int*>(invdV + K);
   int* pivV = pivU + K;
   int* piv = pivV + K;
-  const long long small = ((long long)(4 * K * K + 6 * K * K + 5 * K) + 3) & ~3LL;
+  const long long small = gram_small(K);
   float* stage = c.sm + small;
   const long long cap = c.smcap - small;
   __shared__ int s_ru, s_rv;
@@ -1918,42 +1970,64 @@ __device__ void trunc_gram(HCtx<float>& c, int slot, const float* Ut, const floa
   // the tall factors, staged when they fit
   const float* SU = Ut;
   const float* SV = Vt;
-  if ((long long)(m + n) * K <= cap) {
+  if (staged) {
+    SU = stage;
+    SV = stage + (long long)m * K;
+  } else if ((long long)(m + n) * K <= cap) {
     float* su = stage;
     float* sv = stage + (long long)m * K;
-    for (long long t = tid; t < (long long)m * K; t += nt) su[t] = Ut[t];
-    for (long long t = tid; t < (long long)n * K; t += nt) sv[t] = Vt[t];
+    cp_async_range(su, Ut, (long long)m * K);
+    cp_async_range(sv, Vt, (long long)n * K);
+    cp_async_wait_all();
     SU = su;
     SV = sv;
     __syncthreads();
   }
-  // Gram matrices: a warp per entry (i <= j) of G_U, then of G_V
-  const int E = K * (K + 1) / 2;
-  for (int task = warp; task < 2 * E; task += nw) {
-    const bool isv = task >= E;
-    int e = isv ? task - E : task;
-    int i = 0;
-    while (e >= K - i) {
-      e -= K - i;
-      ++i;
+  // Gram matrices: a warp per 2 x 2 block (block row <= block column) of G_U,
+  // then of G_V; four independent double-float sums per lane
+  const int nb = (K + 1) / 2;
+  const int EB = nb * (nb + 1) / 2;
+  for (int task = warp; task < 2 * EB; task += nw) {
+    const bool isv = task >= EB;
+    int e = isv ? task - EB : task;
+    int bi = 0;
+    while (e >= nb - bi) {
+      e -= nb - bi;
+      ++bi;
     }
-    const int j = i + e;
+    const int bj = bi + e;
+    const int i0 = 2 * bi, i1 = min(2 * bi + 1, K - 1), j0 = 2 * bj, j1 = min(2 * bj + 1, K - 1);
     const float* A = isv ? SV : SU;
     const int rows = isv ? n : m;
-    const float* ai = A + (long long)i * rows;
-    const float* aj = A + (long long)j * rows;
-    float hi = 0.f, lo = 0.f;
-    for (int t = lane; t < rows; t += 32) df_add_prod(hi, lo, ai[t], aj[t]);
+    const float* a0 = A + (long long)i0 * rows;
+    const float* a1 = A + (long long)i1 * rows;
+    const float* b0 = A + (long long)j0 * rows;
+    const float* b1 = A + (long long)j1 * rows;
+    float h[4] = {0.f, 0.f, 0.f, 0.f}, l[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int t = lane; t < rows; t += 32) {
+      const float x0 = a0[t], x1 = a1[t], y0 = b0[t], y1 = b1[t];
+      df_add_prod(h[0], l[0], x0, y0);
+      df_add_prod(h[1], l[1], x0, y1);
+      df_add_prod(h[2], l[2], x1, y0);
+      df_add_prod(h[3], l[3], x1, y1);
+    }
     for (int o = 16; o > 0; o >>= 1) {
-      const float h2 = __shfl_xor_sync(0xffffffffu, hi, o);
-      const float l2 = __shfl_xor_sync(0xffffffffu, lo, o);
-      df_add(hi, lo, h2, l2);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float h2 = __shfl_xor_sync(0xffffffffu, h[q], o);
+        const float l2 = __shfl_xor_sync(0xffffffffu, l[q], o);
+        df_add(h[q], l[q], h2, l2);
+      }
     }
     if (lane == 0) {
       double* G = isv ? GV : GU;
-      const double g = (double)hi + (double)lo;
-      G[i * K + j] = g;
-      G[j * K + i] = g;
+      const int ri[4] = {i0, i0, i1, i1}, cj[4] = {j0, j1, j0, j1};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const double g = (double)h[q] + (double)l[q];
+        G[ri[q] * K + cj[q]] = g;
+        G[cj[q] * K + ri[q]] = g;
+      }
     }
   }
   __syncthreads();
@@ -1961,10 +2035,10 @@ __device__ void trunc_gram(HCtx<float>& c, int slot, const float* Ut, const floa
   // pivoted Cholesky of both, one warp each
   const double thr = 0x1p-40;
   if (warp == 0) {
-    const int r = pchol_warp(GU, K, pivU, thr);
+    const int r = pchol_warp(GU, K, pivU, invdU, thr);
     if (lane == 0) s_ru = min(r, m);
   } else if (warp == 1) {
-    const int r = pchol_warp(GV, K, pivV, thr);
+    const int r = pchol_warp(GV, K, pivV, invdV, thr);
     if (lane == 0) s_rv = min(r, n);
   }
   __syncthreads();
@@ -1980,11 +2054,15 @@ __device__ void trunc_gram(HCtx<float>& c, int slot, const float* Ut, const floa
   // R in original column order, then the core M = RUo RVo^T (ru x rv, ld K)
   for (int t = tid; t < ru * K; t += nt) {
     const int i = t / K, q = t % K;
-    RUo[i * K + pivU[q]] = (q >= i) ? (float)GU[i * K + q] : 0.f;
+    const float v = (q >= i) ? (float)GU[i * K + q] : 0.f;
+    RUo[i * K + pivU[q]] = v;
+    RUp[i * K + q] = v;
   }
   for (int t = tid; t < rv * K; t += nt) {
     const int i = t / K, q = t % K;
-    RVo[i * K + pivV[q]] = (q >= i) ? (float)GV[i * K + q] : 0.f;
+    const float v = (q >= i) ? (float)GV[i * K + q] : 0.f;
+    RVo[i * K + pivV[q]] = v;
+    RVp[i * K + q] = v;
   }
   __syncthreads();
   for (int t = tid; t < ru * rv; t += nt) {
@@ -2005,8 +2083,8 @@ __device__ void trunc_gram(HCtx<float>& c, int slot, const float* Ut, const floa
   }
   __syncthreads();
   for (int task = warp; task < 2 * r; task += nw) {
-    if (task < r) backsub_warp(GU, K, ru, Z + task * K, WU + task * K);
-    else backsub_warp(GV, K, rv, WV + (task - r) * K, WV + (task - r) * K);
+    if (task < r) backsub_warp(RUp, invdU, K, ru, Z + task * K, WU + task * K);
+    else backsub_warp(RVp, invdV, K, rv, WV + (task - r) * K, WV + (task - r) * K);
   }
   __syncthreads();
   tmk(4);
@@ -2043,7 +2121,7 @@ template <class T>
 __device__ void trunc_core(HCtx<T>& c, int slot, T* Ut, T* Vt, int K) {
   if constexpr (sizeof(T) == 4) {
     if (K <= 32) {
-      trunc_gram(c, slot, Ut, Vt, K);
+      trunc_gram(c, slot, Ut, Vt, K, false);
       return;
     }
   }
@@ -2196,6 +2274,36 @@ __device__ bool op_append(const HOp& o, HCtx<T>& c) {
   T* Vt = c.ws + (long long)s.m * K;
   const T* Us = ar + s.off;
   const T* Vs = ar + s.off + (long long)s.m * s.kcap;
+  if constexpr (sizeof(T) == 4) {
+    // the concatenated factors go straight into the Gram recompression's
+    // shared memory (asynchronous copies), not through the workspace
+    const long long small = gram_small(K);
+    if (K <= 32 && (long long)(s.m + s.n) * K <= c.smcap - small) {
+      float* su = c.sm + small;
+      float* sv = su + (long long)s.m * K;
+      const long long mr = (long long)s.m * r0, nr = (long long)s.n * r0;
+      cp_async_range(su, Us, mr);
+      for (int t = threadIdx.x; t < s.m * k; t += blockDim.x)
+        cp_async_elem(su + mr + t, ar + vidx(o.A, t % s.m, t / s.m));
+      cp_async_range(sv, Vs, nr);
+      if (ident) {
+        for (int t = threadIdx.x; t < s.n * k; t += blockDim.x) {
+          const int i = t % s.n, j = t / s.n;
+          sv[nr + t] = (i == ioff + j) ? 1.f : 0.f;
+        }
+      } else {
+        for (int t = threadIdx.x; t < s.n * k; t += blockDim.x)
+          cp_async_elem(sv + nr + t, ar + vidx(o.B, t % s.n, t / s.n));
+      }
+      cp_async_wait_all();
+      __syncthreads();
+      if (alpha != (T)1)
+        for (int t = threadIdx.x; t < s.m * k; t += blockDim.x) su[mr + t] *= alpha;
+      __syncthreads();
+      trunc_gram(c, slot, nullptr, nullptr, K, true);
+      return true;
+    }
+  }
   for (int t = threadIdx.x; t < s.m * K; t += blockDim.x) {
     int i = t % s.m, j = t / s.m;
     Ut[t] = (j < r0) ? Us[i + (long long)j * s.m] : alpha * ar[vidx(o.A, i, j - r0)];
@@ -2221,6 +2329,18 @@ __device__ void op_trunc(const HOp& o, HCtx<T>& c) {
   T* Vt = c.ws + (long long)s.m * K;
   const T* Us = c.ar + s.off;
   const T* Vs = c.ar + s.off + (long long)s.m * s.kcap;
+  if constexpr (sizeof(T) == 4) {
+    const long long small = gram_small(K);
+    if (K <= 32 && (long long)(s.m + s.n) * K <= c.smcap - small) {
+      float* su = c.sm + small;
+      cp_async_range(su, Us, (long long)s.m * K);
+      cp_async_range(su + (long long)s.m * K, Vs, (long long)s.n * K);
+      cp_async_wait_all();
+      __syncthreads();
+      trunc_gram(c, slot, nullptr, nullptr, K, true);
+      return;
+    }
+  }
   for (int t = threadIdx.x; t < s.m * K; t += blockDim.x) Ut[t] = Us[t];
   for (int t = threadIdx.x; t < s.n * K; t += blockDim.x) Vt[t] = Vs[t];
   __syncthreads();
