@@ -1797,11 +1797,18 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float h2, float l2)
   lo = __fadd_rn(lo, __fadd_rn(err, l2));
 }
 
-// 1/sqrt(d) for d > 0 in FP64: Newton-Raphson on y = 1/sqrt(m), m the mantissa
-// of d scaled to [0.5, 2) with an even exponent, from the FP32 estimate
-// rsqrtf(m) (two steps y <- y (3 - m y^2) / 2 take its ~2^-22 relative error
-// below FP64 rounding), then the exponent is put back.
+// 1/sqrt(d) for d > 0 in FP64 by Newton-Raphson, y <- y (3 - d y^2) / 2, from
+// the FP32 estimate rsqrtf (~2^-22 relative error): one step when d is well
+// inside FP32 range; otherwise on the mantissa m of d scaled to [0.5, 2) with
+// an even exponent, two steps (below FP64 rounding), then the exponent is
+// put back.
 __device__ __forceinline__ double rsqrt_newton(double d) {
+  if (d > 1e-30 && d < 1e30) {
+    // in FP32 range: one step from the FP32 estimate leaves ~3e-13 relative
+    // error, far below what the FP32 factors built from it can hold
+    double y = (double)rsqrtf((float)d);
+    return y * (1.5 - 0.5 * d * y * y);
+  }
   int e;
   double mt = frexp(d, &e);   // d = mt 2^e, mt in [0.5, 1)
   if (e & 1) {
