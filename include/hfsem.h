@@ -92,8 +92,12 @@ typedef struct {
   int32_t R;          /* Taylor rank of eq. (eqn:Lexpan), 1 <= R <= 32       */
   double  lambda;     /* admissibility parameter of eq. (admis), > 0 (1.0)  */
   double  tol_hlu;    /* Tol_HLU: singular values below tol_hlu * sigma_1
-                         are dropped when blocks are recompressed; 0 keeps
-                         every nonzero one (up to kmax). 1e-3 in Sec. 5     */
+                         are dropped when blocks are recompressed (pivots of
+                         a rank-revealing QR of the core); 0 keeps every
+                         nonzero one (up to kmax).  In the FP32 modes the
+                         factors' own directions below ~1e-6 of their
+                         largest singular value (their rounding level) are
+                         dropped as well. 1e-3 in Sec. 5                     */
   int32_t precision;  /* HFSEM_PREC_*                                        */
   int32_t leaf_elems; /* elements per leaf cluster; 0 = automatic           */
   int32_t kmax;       /* rank cap after recompression; 0 = automatic        */
