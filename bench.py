@@ -23,6 +23,7 @@ import math
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -112,7 +113,9 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.proc = None
         self.gpu = gpu_index
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{gpu_index}.csv")
+        # raw samples: HFSEM_CLOCKS_CSV if set, else the system temp directory
+        self.path = os.environ.get("HFSEM_CLOCKS_CSV") or os.path.join(
+            tempfile.gettempdir(), f"hfsem_clocks_{gpu_index}.csv")
 
     def start(self):
         try:
