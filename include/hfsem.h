@@ -46,7 +46,7 @@ extern "C" {
 #define HFSEM_ERR_NOT_CONVERGED  3  /* Krylov hit max_iter; X = last iterate */
 #define HFSEM_ERR_BREAKDOWN      4  /* BiCGSTAB breakdown (rho or omega = 0) */
 #define HFSEM_ERR_DEVICE         6  /* CUDA error                           */
-#define HFSEM_ERR_UNSUPPORTED    7  /* valid request this build cannot do   */
+#define HFSEM_ERR_UNSUPPORTED    7  /* valid request the library cannot do  */
 
 /* ---- enumerations ------------------------------------------------------ */
 #define HFSEM_MATVEC_AUTO      0  /* Toeplitz when the mesh is uniform or

@@ -12,7 +12,7 @@
 //   * the waves partition the program;
 //   * the leaf-solve tables stay inside the arena and the shared-memory budget.
 // Input: N P leaf_elems R lambda mode, then N element lengths; mode 1 checks
-// the whole program as if it were one wave (the checker's own test: the H-LU
+// the whole program as if it were one wave (the verifier's own test: the H-LU
 // has dependencies, so that must fail).  Prints "OK ..." or the first
 // violation ("FAIL ...") and exits non-zero.
 #include <algorithm>

@@ -19,7 +19,7 @@ CSRC = os.path.join(ROOT, "paper_1808_02937_gb300", "csrc")
 
 
 @pytest.fixture(scope="module")
-def checker(tmp_path_factory):
+def verifier(tmp_path_factory):
     cxx = shutil.which("g++") or shutil.which("c++")
     if not cxx:
         pytest.skip("no host C++ compiler")
@@ -33,9 +33,9 @@ def checker(tmp_path_factory):
     return out
 
 
-def _run(checker, h, P, leaf, R, lam=1.0, mode=0):
+def _run(verifier, h, P, leaf, R, lam=1.0, mode=0):
     inp = f"{len(h)} {P} {leaf} {R} {lam} {mode}\n" + " ".join(repr(float(v)) for v in h) + "\n"
-    return subprocess.run([checker], input=inp, capture_output=True, text=True, timeout=300)
+    return subprocess.run([verifier], input=inp, capture_output=True, text=True, timeout=300)
 
 
 CASES = [
@@ -49,16 +49,16 @@ CASES = [
 
 
 @pytest.mark.parametrize("case", CASES, ids=lambda c: c[0])
-def test_plan_is_race_free_and_in_bounds(checker, case):
+def test_plan_is_race_free_and_in_bounds(verifier, case):
     name, h, P, leaf, R = case
-    r = _run(checker, h, P, leaf, R)
+    r = _run(verifier, h, P, leaf, R)
     assert r.returncode == 0 and r.stdout.startswith("OK"), (r.stdout, r.stderr)
 
 
-def test_checker_sees_conflicts(checker):
+def test_verifier_sees_conflicts(verifier):
     # the whole H-LU program as one wave must conflict: the factorisation is a
-    # chain of dependent ops, so a checker that passes this is not looking
+    # chain of dependent ops, so a verifier that passes this is not looking
     h = W.mesh_uniform(48)
-    r = _run(checker, h, 4, 4, 4, mode=1)
+    r = _run(verifier, h, 4, 4, 4, mode=1)
     assert r.returncode != 0 and r.stdout.startswith("FAIL"), r.stdout
     assert "wave" in r.stdout
