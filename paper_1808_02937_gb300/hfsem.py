@@ -158,6 +158,9 @@ class System:
 
 
 class Factor:
+    """Handle to an H-LU factorisation of every instance of a System
+    (hfsem_factor*); freed with it or by free()."""
+
     def __init__(self, handle, system):
         self.h = handle
         self.system = system
@@ -174,6 +177,10 @@ class Factor:
 
 def make_problem(h, P, alpha, theta, rho, a=0.0, b=None, c1=0.0, c2=0.0,
                  matvec=MATVEC_AUTO):
+    """One instance: element lengths h (N of them, summing to b - a; b defaults
+    to a + sum h), degree P, 1 < alpha < 2, 0 <= theta <= 1, rho >= 0,
+    boundary values c1 = u(a), c2 = u(b), operator MATVEC_AUTO / _DENSE /
+    _TOEPLITZ."""
     h = np.ascontiguousarray(h, dtype=np.float64)
     if b is None:
         b = a + float(h.sum())
@@ -183,6 +190,8 @@ def make_problem(h, P, alpha, theta, rho, a=0.0, b=None, c1=0.0, c2=0.0,
 
 
 def hfsem_assemble(problems, stream=None) -> System:
+    """Assemble a batch of make_problem() instances on `stream` (a CUDA stream
+    handle; default torch's current stream)."""
     lib = load_library()
     arr = (hfsem_problem * len(problems))()
     keep = []
@@ -199,6 +208,7 @@ def hfsem_assemble(problems, stream=None) -> System:
 
 
 def hfsem_ndof(sys: System, inst: int) -> int:
+    """N_d = N P - 1 of instance inst."""
     nd = C.c_int32()
     _check(load_library().hfsem_ndof(sys.h, inst, C.byref(nd)), "hfsem_ndof")
     return nd.value
@@ -212,6 +222,9 @@ def _like(x, n):
 
 
 def hfsem_apply(sys: System, x, nrhs: int = 1):
+    """y = A x for every instance (zero boundary values); x holds nrhs columns
+    of N_d per instance, instances concatenated; y is allocated like x (numpy
+    array or tensor on x's device)."""
     y = _like(x, sys.total_ndof * nrhs)
     _check(load_library().hfsem_apply(sys.h, nrhs, _ptr(x), _ptr(y)), "hfsem_apply")
     return y
@@ -256,6 +269,8 @@ def rhs_frac_powers(terms_per_rhs):
 
 
 def rhs_legendre(coeffs_per_rhs):
+    """f = sum_k g_k L_k(xi_[a,b](x)) per rhs, coefficients g_0..g_K ->
+    (kind, nrhs, n_terms, data); shorter lists are padded with zeros."""
     K1 = max(len(c) for c in coeffs_per_rhs)
     data = np.zeros((len(coeffs_per_rhs), K1))
     for r, c in enumerate(coeffs_per_rhs):
@@ -264,11 +279,14 @@ def rhs_legendre(coeffs_per_rhs):
 
 
 def rhs_load_vector(G, nrhs=1):
+    """A ready load vector: N_d x nrhs column-major in the unknowns' order."""
     G = np.ascontiguousarray(G, dtype=np.float64)
     return (RHS_LOAD_VECTOR, nrhs, 0, G)
 
 
 def hfsem_load_vector(sys: System, rhs_list, lifted: int = 0, out=None):
+    """G = (f, phi_i) for every instance (rhs_list: one rhs_* tuple per
+    instance); lifted = 1 subtracts the boundary lifting's contribution."""
     arr, keep = _rhs_array(rhs_list)
     nrhs = rhs_list[0][1]
     G = np.zeros(sys.total_ndof * nrhs) if out is None else out
@@ -278,10 +296,14 @@ def hfsem_load_vector(sys: System, rhs_list, lifted: int = 0, out=None):
 
 def hopts(R=8, lam=1.0, tol_hlu=1e-3, precision=PREC_MIXED, leaf_elems=0, kmax=0,
           build_only=0):
+    """H-matrix / H-LU options: Taylor rank R, admissibility lambda, Tol_HLU,
+    PREC_FP64 / PREC_MIXED / PREC_MIXED_TC, elements per leaf and rank cap
+    (0 = automatic), build_only = 1 to build the H-matrix without factoring."""
     return hfsem_hopts(R, lam, tol_hlu, precision, leaf_elems, kmax, build_only)
 
 
 def hfsem_hlu_factor(sys: System, opts: hfsem_hopts) -> Factor:
+    """H-matrix approximation and H-LU factorisation of every instance."""
     out = C.c_void_p()
     _check(load_library().hfsem_hlu_factor(sys.h, C.byref(opts), C.byref(out)),
            "hfsem_hlu_factor")
@@ -289,6 +311,8 @@ def hfsem_hlu_factor(sys: System, opts: hfsem_hopts) -> Factor:
 
 
 def hfsem_hmatrix_dense(fac: Factor, inst: int):
+    """The H-matrix of instance inst as a dense N_d x N_d array (factors built
+    with build_only = 1)."""
     nd = fac.system.ndofs[inst]
     out = np.zeros(nd * nd)
     _check(load_library().hfsem_hmatrix_dense(fac.h, inst, _ptr(out)), "hfsem_hmatrix_dense")
@@ -296,6 +320,7 @@ def hfsem_hmatrix_dense(fac: Factor, inst: int):
 
 
 def hfsem_precond_apply(fac: Factor, r, nrhs: int = 1):
+    """y = U^-1 L^-1 r (the two H-triangular solves) for every instance."""
     y = _like(r, fac.system.total_ndof * nrhs)
     _check(load_library().hfsem_precond_apply(fac.h, nrhs, _ptr(r), _ptr(y)),
            "hfsem_precond_apply")
@@ -304,6 +329,11 @@ def hfsem_precond_apply(fac: Factor, r, nrhs: int = 1):
 
 def hfsem_solve(sys: System, fac, rhs_list, tol=1e-14, max_iter=200, X=None,
                 allow_fail=False):
+    """BiCGSTAB on every instance and right-hand side, right-preconditioned by
+    fac (None: unpreconditioned).  X (numpy array or CUDA tensor, N_d x nrhs
+    per instance, concatenated) is the initial guess and receives the
+    solution.  Returns (X, per-column stats dicts, status); raises HfsemError
+    on failure unless allow_fail."""
     arr, keep = _rhs_array(rhs_list)
     nrhs = rhs_list[0][1]
     if X is None:
@@ -321,6 +351,8 @@ def hfsem_solve(sys: System, fac, rhs_list, tol=1e-14, max_iter=200, X=None,
 def split(sys: System, v, nrhs: int = 1):
     """Split a concatenated vector into per-instance (N_d, nrhs) column-major views."""
     out, off = [], 0
+    if hasattr(v, "detach"):   # a torch tensor, possibly on the GPU
+        v = v.detach().cpu().numpy()
     v = np.asarray(v)
     for nd in sys.ndofs:
         out.append(v[off: off + nd * nrhs].reshape(nrhs, nd).T)
@@ -329,6 +361,7 @@ def split(sys: System, v, nrhs: int = 1):
 
 
 def hfsem_timing_enable(on: bool = True):
+    """Per-kernel CUDA-event timing inside the library (for the benchmark)."""
     _check(load_library().hfsem_timing_enable(1 if on else 0), "hfsem_timing_enable")
 
 
