@@ -106,3 +106,20 @@ def test_preconditioned_solve_batch_mixed_meshes(lib):
     X, st, code = H.hfsem_solve(sys, fac, rhs, tol=1e-15, max_iter=100, allow_fail=True)
     for k, Xk in enumerate(H.split(sys, X)):
         assert rel_err(Xk[:, 0], refs[k]) < 1e-10, (k, st[k])
+
+
+def test_factor_is_tied_to_its_system(lib):
+    # a factor is valid only for the system it was built from, and one built
+    # for inspection only cannot precondition
+    h = W.mesh_uniform(12)
+    s1 = H.hfsem_assemble([H.make_problem(h, 3, 1.5, 0.5, 1.0)])
+    s2 = H.hfsem_assemble([H.make_problem(h, 3, 1.5, 0.5, 1.0)])
+    f1 = H.hfsem_hlu_factor(s1, H.hopts(R=4))
+    rhs = [H.rhs_legendre([np.array([1.0, 0.5])])]
+    X, st, code = H.hfsem_solve(s2, f1, rhs, tol=1e-12, max_iter=20, allow_fail=True)
+    assert code == H.HFSEM_ERR_INVALID_ARG
+    fb = H.hfsem_hlu_factor(s1, H.hopts(R=4, build_only=1))
+    X, st, code = H.hfsem_solve(s1, fb, rhs, tol=1e-12, max_iter=20, allow_fail=True)
+    assert code == H.HFSEM_ERR_INVALID_ARG
+    X, st, code = H.hfsem_solve(s1, f1, rhs, tol=1e-12, max_iter=20)
+    assert code == H.HFSEM_OK
