@@ -218,6 +218,10 @@ int hfsem_timing_read(const char *tag, double *total_ms, int64_t *launches, doub
 /* Static string for a status code. */
 const char *hfsem_status_str(int status);
 
+/* Message of the last call on the calling thread that failed ("" if none):
+ * owned by the library, valid until that thread's next failing call. */
+const char *hfsem_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

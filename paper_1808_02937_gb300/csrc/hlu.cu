@@ -3806,6 +3806,9 @@ int hfsem_hlu_factor(hfsem_system* sys, const hfsem_hopts* opts, hfsem_factor** 
   } catch (const Error& e) {
     set_last_error(e.msg);
     return e.code;
+  } catch (const std::bad_alloc&) {
+    set_last_error("host allocation failed");
+    return HFSEM_ERR_OOM;
   } catch (...) {
     set_last_error("unknown error");
     return HFSEM_ERR_DEVICE;
@@ -3844,6 +3847,12 @@ int hfsem_hmatrix_dense(const hfsem_factor* fac, int32_t inst, double* out) {
   } catch (const Error& e) {
     set_last_error(e.msg);
     return e.code;
+  } catch (const std::bad_alloc&) {
+    set_last_error("host allocation failed");
+    return HFSEM_ERR_OOM;
+  } catch (...) {
+    set_last_error("unknown error");
+    return HFSEM_ERR_DEVICE;
   }
 }
 
@@ -3873,6 +3882,12 @@ int hfsem_precond_apply(hfsem_factor* fac, int32_t nrhs, const double* r, double
   } catch (const Error& e) {
     set_last_error(e.msg);
     return e.code;
+  } catch (const std::bad_alloc&) {
+    set_last_error("host allocation failed");
+    return HFSEM_ERR_OOM;
+  } catch (...) {
+    set_last_error("unknown error");
+    return HFSEM_ERR_DEVICE;
   }
 }
 
@@ -3944,6 +3959,9 @@ extern "C" int hfsem_tc_tile_check(int32_t N, int32_t K, int32_t reps, double* m
   } catch (const Error& e) {
     set_last_error(e.msg);
     return e.code;
+  } catch (const std::bad_alloc&) {
+    set_last_error("host allocation failed");
+    return HFSEM_ERR_OOM;
   } catch (...) {
     set_last_error("unknown error");
     return HFSEM_ERR_DEVICE;

@@ -369,6 +369,9 @@ extern "C" int hfsem_solve(hfsem_system* sys, hfsem_factor* fac, const hfsem_rhs
   } catch (const Error& e) {
     set_last_error(e.msg);
     return e.code;
+  } catch (const std::bad_alloc&) {
+    set_last_error("host allocation failed");
+    return HFSEM_ERR_OOM;
   } catch (...) {
     set_last_error("unknown error");
     return HFSEM_ERR_DEVICE;

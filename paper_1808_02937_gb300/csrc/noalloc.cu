@@ -144,6 +144,9 @@ extern "C" int hfsem_apply_noalloc(hfsem_system* s, int32_t nrhs, const double* 
   } catch (const Error& e) {
     set_last_error(e.msg);
     return e.code;
+  } catch (const std::bad_alloc&) {
+    set_last_error("host allocation failed");
+    return HFSEM_ERR_OOM;
   } catch (...) {
     set_last_error("unknown error");
     return HFSEM_ERR_DEVICE;

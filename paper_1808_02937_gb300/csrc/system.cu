@@ -1374,34 +1374,37 @@ const char* hfsem_status_str(int status) {
 const char* hfsem_last_error(void) { return hf::g_last_error.c_str(); }
 
 int hfsem_timing_enable(int32_t on) {
-  std::lock_guard<std::mutex> lk(g_tmu);
-  g_timing = on != 0;
-  return HFSEM_OK;
+  return guarded([&] {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    g_timing = on != 0;
+  });
 }
 
 int hfsem_timing_reset(void) {
-  std::lock_guard<std::mutex> lk(g_tmu);
-  flush_pending();
-  g_tim.clear();
-  return HFSEM_OK;
+  return guarded([&] {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    flush_pending();
+    g_tim.clear();
+  });
 }
 
 int hfsem_timing_read(const char* tag, double* total_ms, int64_t* launches, double* work) {
-  if (!tag) return HFSEM_ERR_INVALID_ARG;
-  std::lock_guard<std::mutex> lk(g_tmu);
-  flush_pending();
-  if (std::string(tag) == "launches") {   // kernels launched so far
-    if (total_ms) *total_ms = 0.0;
-    if (launches) *launches = g_launches;
-    if (work) *work = 0.0;
-    return HFSEM_OK;
-  }
-  auto it = g_tim.find(tag);
-  TimerRec r = (it == g_tim.end()) ? TimerRec() : it->second;
-  if (total_ms) *total_ms = r.ms;
-  if (launches) *launches = r.launches;
-  if (work) *work = r.work;
-  return HFSEM_OK;
+  return guarded([&] {
+    if (!tag) throw Error(HFSEM_ERR_INVALID_ARG, "hfsem_timing_read: tag is NULL");
+    std::lock_guard<std::mutex> lk(g_tmu);
+    flush_pending();
+    if (std::string(tag) == "launches") {   // kernels launched so far
+      if (total_ms) *total_ms = 0.0;
+      if (launches) *launches = g_launches;
+      if (work) *work = 0.0;
+      return;
+    }
+    auto it = g_tim.find(tag);
+    TimerRec r = (it == g_tim.end()) ? TimerRec() : it->second;
+    if (total_ms) *total_ms = r.ms;
+    if (launches) *launches = r.launches;
+    if (work) *work = r.work;
+  });
 }
 
 }  // extern "C"

@@ -33,7 +33,8 @@ EXPORTED = ["hfsem_assemble", "hfsem_ndof", "hfsem_apply", "hfsem_load_vector",
             "hfsem_hlu_factor", "hfsem_hmatrix_dense", "hfsem_precond_apply",
             "hfsem_solve", "hfsem_factor_free", "hfsem_system_free",
             "hfsem_status_str", "hfsem_timing_enable", "hfsem_timing_reset",
-            "hfsem_timing_read", "hfsem_apply_noalloc", "hfsem_tc_tile_check"]
+            "hfsem_timing_read", "hfsem_apply_noalloc", "hfsem_tc_tile_check",
+            "hfsem_last_error"]
 
 
 class HfsemError(RuntimeError):

@@ -109,3 +109,22 @@ def test_status_strings_cover_every_code(lib):
         s = lib.hfsem_status_str(code)
         assert isinstance(s, bytes) and len(s) > 0
     assert len(lib.hfsem_status_str(12345)) > 0
+
+
+def test_last_error_names_the_problem(lib):
+    prob, keep = _problem(alpha=2.5)
+    arr = (H.hfsem_problem * 1)(prob)
+    out = C.c_void_p(None)
+    assert lib.hfsem_assemble(1, arr, None, C.byref(out)) == H.HFSEM_ERR_INVALID_ARG
+    assert b"alpha" in lib.hfsem_last_error()
+    with pytest.raises(H.HfsemError) as ei:
+        H.hfsem_assemble([H.make_problem(np.full(4, 0.25), 3, 1.5, 1.5, 0.0)])
+    assert ei.value.code == H.HFSEM_ERR_INVALID_ARG and "theta" in str(ei.value)
+
+
+def test_timing_read_rejects_null_tag(lib):
+    ms = C.c_double(-1.0)
+    assert lib.hfsem_timing_read(None, C.byref(ms), None, None) == H.HFSEM_ERR_INVALID_ARG
+    assert ms.value == -1.0
+    assert lib.hfsem_timing_read(b"no-such-kernel", C.byref(ms), None, None) == H.HFSEM_OK
+    assert ms.value == 0.0
