@@ -85,8 +85,11 @@ void gauss_jacobi_rule(int n, double al, double be, std::vector<double>& x,
   }
   for (int k = 1; k < n; ++k) {
     double s = 2.0 * k + al + be;
-    b[k] = 4.0 * k * (k + al) * (k + be) * (k + al + be) /
-           (s * s * (s + 1.0) * (s - 1.0));
+    // at k = 1 the factors k + al + be and s - 1 are equal and cancel (and
+    // vanish together when al + be = -1, e.g. the Chebyshev weight)
+    b[k] = (k == 1) ? 4.0 * (1.0 + al) * (1.0 + be) / (s * s * (s + 1.0))
+                    : 4.0 * k * (k + al) * (k + be) * (k + al + be) /
+                          (s * s * (s + 1.0) * (s - 1.0));
   }
   double mu0 = std::exp((al + be + 1.0) * std::log(2.0) + std::lgamma(al + 1.0) +
                         std::lgamma(be + 1.0) - std::lgamma(al + be + 2.0));
