@@ -72,12 +72,15 @@ def load_frac_powers(mesh: Mesh, P: int, terms) -> np.ndarray:
 
 
 def load_legendre_ab(mesh: Mesh, P: int, coeffs) -> np.ndarray:
+    """f = sum_k g_k L_k(xi_[a,b](x)) against the local basis (Sec. 2.2 load
+    vector): f phi has degree K + P on every element, so the n-point
+    Gauss-Legendre rule with 2n - 1 >= K + P, n = (K + P) // 2 + 1, is exact."""
     coeffs = np.asarray(coeffs, dtype=np.float64)
     K = len(coeffs) - 1
     N = mesh.N
     idx = global_index(N, P)
     G = np.zeros(n_dof(N, P) + 2)
-    x, w = gauss_legendre((K + P) // 2 + 2)
+    x, w = gauss_legendre((K + P) // 2 + 1)
     V = local_values(P, x)
     L = mesh.b - mesh.a
     for e in range(N):
