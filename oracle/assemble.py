@@ -64,9 +64,9 @@ def pair_touch(he: float, hf: float, P: int, alpha: float,
     """Test element e immediately right of trial element f (shared node).
 
     The angular rule is doubled until two successive results agree to tol
-    (relative) or their difference stops shrinking below 1e-12 (the roundoff
-    level of the sum, reached for high P); the radial Gauss-Jacobi rule is
-    exact for the basis."""
+    (relative) or their difference stops shrinking below 1e-13 (the roundoff
+    level of the sum, 1-2e-14 of the largest entry at P = 16); the radial
+    Gauss-Jacobi rule is exact for the basis."""
     xr, wr = gauss_jacobi(P + 1, 0.0, 2.0 - alpha)
     rho = 0.5 * (1.0 + xr)
     cr = 2.0 ** (alpha - 3.0) * wr                    # int_0^1 rho^(2-alpha) F
@@ -98,7 +98,7 @@ def pair_touch(he: float, hf: float, P: int, alpha: float,
         if d <= tol:
             return cur
         # the difference has stopped shrinking at the roundoff level of the sum
-        if d < 1e-12 and d >= 0.5 * last:
+        if d < 1e-13 and d >= 0.5 * last:
             return cur
         if nw >= 1024:
             raise RuntimeError("touching-pair quadrature did not converge")

@@ -187,3 +187,112 @@ def test_mass_closed_form():
     # shared hat at node 1: h0/3 + h1/3
     assert abs(M[idx[0, 1], idx[0, 1]] - (0.4 + 0.9) / 3) < 1e-15
     assert abs(M[idx[0, 1], idx[1, 1]] - 0.9 / 6) < 1e-15
+
+
+# ---------------------------------------------------------------------------
+# Touching pair at high degree, against a closed form in hypergeometric
+# functions evaluated with 90 significant digits (mpmath), every entry.
+#
+# With u = t - x_e in [0, h_e] and v = x_e - s in [0, h_f], the derivative of
+# trial function b is a polynomial q_b(v) = sum_j q_bj v^j, and
+#   int_0^{h_f} (u + v)^(1-alpha) v^j dv
+#     = sum_i C(j, i) (-u)^(j-i) [(u + h_f)^e_i - u^e_i] / e_i,  e_i = 2 - alpha + i
+# (v = (u + v) - u, binomial expansion).  Against the test derivative
+# g_a(u) = sum_k g_ak u^k the outer integral needs only
+#   int_0^{h_e} u^m (u + h_f)^beta du
+#     = h_f^beta h_e^(m+1) / (m+1) 2F1(-beta, m+1; m+2; -h_e/h_f)
+# and int_0^{h_e} u^(m + e_i) du.  The alternating binomial sums cancel
+# heavily, hence the 90 digits.
+# ---------------------------------------------------------------------------
+
+def _legendre_power_coeffs(n):
+    """Exact power-basis coefficients of L_n (explicit sum formula)."""
+    from fractions import Fraction
+    c = [Fraction(0)] * (n + 1)
+    for k in range(n // 2 + 1):
+        c[n - 2 * k] += Fraction((-1) ** k * math.comb(n, k) * math.comb(2 * n - 2 * k, n), 2 ** n)
+    return c
+
+
+def _local_deriv_power_coeffs(P, a):
+    """d/dxi of local function a (0: left hat, 1: right hat, 1+p: psi_p)."""
+    from fractions import Fraction
+    if a == 0:
+        return [Fraction(-1, 2)]
+    if a == 1:
+        return [Fraction(1, 2)]
+    p = a - 1
+    c = [Fraction(0)] * (p + 2)
+    for i, v in enumerate(_legendre_power_coeffs(p - 1)):
+        c[i] += v
+    for i, v in enumerate(_legendre_power_coeffs(p + 1)):
+        c[i] -= v
+    return [i * c[i] for i in range(1, len(c))]
+
+
+def _touch_closed_form(he, hf, P, alpha):
+    mp = pytest.importorskip("mpmath")
+    mp.mp.dps = 90
+    he, hf, al = mp.mpf(he), mp.mpf(hf), mp.mpf(alpha)
+
+    def in_powers_of(c, s0, s1, scale):
+        # scale * sum_k c_k (s0 + s1 y)^k as coefficients of y^j
+        out = [mp.mpf(0)] * len(c)
+        for k, ck in enumerate(c):
+            ck = mp.mpf(ck.numerator) / ck.denominator
+            for j in range(k + 1):
+                out[j] += ck * mp.binomial(k, j) * s0 ** (k - j) * s1 ** j
+        return [scale * x for x in out]
+
+    G = [in_powers_of(_local_deriv_power_coeffs(P, a), mp.mpf(-1), 2 / he, 2 / he)
+         for a in range(P + 1)]                       # xi = -1 + 2u/h_e
+    Q = [in_powers_of(_local_deriv_power_coeffs(P, b), mp.mpf(1), -2 / hf, 2 / hf)
+         for b in range(P + 1)]                       # eta = 1 - 2v/h_f
+    cache = {}
+
+    def J(m, beta):
+        if (m, beta) not in cache:
+            cache[(m, beta)] = (hf ** beta * he ** (m + 1) / (m + 1)
+                                * mp.hyp2f1(-beta, m + 1, m + 2, -he / hf))
+        return cache[(m, beta)]
+
+    T = [[mp.mpf(0)] * (P + 1) for _ in range(P + 1)]   # T[k][j]
+    for k in range(P + 1):
+        for j in range(P + 1):
+            acc = mp.mpf(0)
+            for i in range(j + 1):
+                e = 2 - al + i
+                m = k + j - i
+                acc += (mp.binomial(j, i) * (-1) ** (j - i) / e
+                        * (J(m, e) - he ** (m + e + 1) / (m + e + 1)))
+            T[k][j] = acc
+    g0 = 1 / mp.gamma(2 - al)
+    K = np.zeros((P + 1, P + 1))
+    for a in range(P + 1):
+        for b in range(P + 1):
+            acc = mp.mpf(0)
+            for k, gk in enumerate(G[a]):
+                for j, qj in enumerate(Q[b]):
+                    acc += gk * qj * T[k][j]
+            K[a, b] = float(g0 * acc)
+    return K
+
+
+@pytest.mark.parametrize("he,hf,alpha", [(0.7, 0.3, 1.3), (0.25, 0.5, 1.05),
+                                         (1.0, 1e-3, 1.7), (1e-3, 1.0, 1.95)])
+def test_touching_pair_P16_closed_form(he, hf, alpha):
+    P = 16
+    ref = _touch_closed_form(he, hf, P, alpha)
+    got = pair_touch(he, hf, P, alpha)
+    assert np.abs(got - ref).max() <= 1e-13 * np.abs(ref).max()
+
+
+def test_touching_pair_closed_form_agrees_with_quadpack():
+    """The closed form itself against QUADPACK at low degree (P = 3)."""
+    mesh = Mesh(np.array([0.3, 0.7]))
+    ref = _touch_closed_form(mesh.h[1], mesh.h[0], 3, 1.35)
+    for a, b in [(0, 0), (1, 2), (3, 3), (2, 0)]:
+        with warnings.catch_warnings():
+            warnings.simplefilter("ignore")
+            q = _brute_pair(mesh, 3, 1.35, 1, 0, a, b)
+        assert abs(q - ref[a, b]) <= 2e-10 * np.abs(ref).max()
