@@ -45,6 +45,11 @@ extern "C" {
 #define HFSEM_ERR_OOM            2  /* device allocation failed             */
 #define HFSEM_ERR_NOT_CONVERGED  3  /* Krylov hit max_iter; X = last iterate */
 #define HFSEM_ERR_BREAKDOWN      4  /* BiCGSTAB breakdown (rho or omega = 0) */
+#define HFSEM_ERR_TIMEOUT        5  /* a device-side wait reached its limit
+                                       (a tensor-core product or a bulk copy
+                                       that did not complete); the kernel
+                                       gave up and returned, the context is
+                                       still usable                       */
 #define HFSEM_ERR_DEVICE         6  /* CUDA error                           */
 #define HFSEM_ERR_UNSUPPORTED    7  /* valid request the library cannot do  */
 
@@ -146,13 +151,14 @@ int hfsem_apply(hfsem_system *sys, int32_t nrhs, const double *x, double *y);
  * applications that own every allocation themselves or call from a section
  * where cudaMalloc is not allowed).  x and y must be device pointers; no
  * cudaMalloc, cudaFree or allocating library routine is called.  Its
- * temporaries live in one file-scope device array of 32 MiB that every GPU
- * loading the library holds until the process exits; requests needing more
- * (sum of N_d, N*P, the dense column partials and the FFT buffers, times
- * nrhs) return HFSEM_ERR_INVALID_ARG.  The first call on a device looks up
- * the array's device address (cudaGetSymbolAddress); make that first call
- * before any stream capture.  All calls share the array: calls whose work
- * overlaps on the GPU (other streams, other host threads) race on it. */
+ * temporaries live in one file-scope device array of 32 MiB; the first
+ * hfsem_assemble on a device loads that array (and the kernels this call
+ * launches) there, and the device holds it until the process exits, so
+ * the call itself loads and allocates nothing.  Requests needing more
+ * scratch (sum of N_d, N*P, the dense column partials and the FFT buffers,
+ * times nrhs) return HFSEM_ERR_INVALID_ARG.  All calls share the array:
+ * calls whose work overlaps on the GPU (other streams, other host threads)
+ * race on it. */
 int hfsem_apply_noalloc(hfsem_system *sys, int32_t nrhs, const double *x, double *y);
 
 /* Self-check of the BF16 tensor-core tile that HFSEM_PREC_MIXED_TC uses (the
@@ -189,17 +195,94 @@ int hfsem_precond_apply(hfsem_factor *fac, int32_t nrhs, const double *r,
                         double *y);
 
 /* Solve A X = G for every instance by BiCGSTAB (Sec. 4.2) right-
- * preconditioned with the H-LU factor `fac` (NULL: no preconditioner).
- * rhs: n_inst entries, equal nrhs.  Stops when the recursive relative
- * residual is <= tol or after max_iter iterations, then checks the true
- * residual.  X: N_d x nrhs per instance, concatenated (host or device).
- * stats: n_inst * nrhs entries (host), instance-major.  Returns the worst
- * per-column status; X holds the last iterate in every case. */
+ * preconditioned with the H-LU factor `fac` (NULL: no preconditioner),
+ * from X = 0.  rhs: n_inst entries, equal nrhs.  A column whose recursive
+ * relative residual reaches tol is checked on its true relative residual
+ * ||G - A X|| / ||G||: accepted when that is <= 100 tol (the recursive and
+ * true residuals of the FP64 iteration may part by that much), else
+ * BiCGSTAB restarts from the true residual (at most 8 times).  A restart
+ * that fails to halve the true residual of the previous check shows that
+ * the rounding floor of the FP64 product A X is reached; the column is then
+ * accepted with that true residual (reported in stats).  A column stops as
+ * NOT_CONVERGED when max_iter iterations or the restarts are spent, as
+ * BREAKDOWN when rho, omega or (r^, v) vanish.  X (output only): N_d x nrhs
+ * per instance, concatenated (host or device).  stats: n_inst * nrhs
+ * entries (host), instance-major.  Returns the worst per-column status
+ * (TIMEOUT if a preconditioner copy reached its wait limit); X holds the
+ * last iterate in every case. */
 int hfsem_solve(hfsem_system *sys, hfsem_factor *fac, const hfsem_rhs *rhs,
                 double tol, int32_t max_iter, double *X, hfsem_stats *stats);
 
 void hfsem_factor_free(hfsem_factor *fac);
 void hfsem_system_free(hfsem_system *sys);
+
+/* ---- serving loop (the paper has no counterpart: it solves one problem at a
+ * time; this serves a stream of the Sec. 4.2 solves on one GPU) ------------
+ *
+ * A server runs `slots` requests at once, each on its own host worker and
+ * non-blocking CUDA stream, so the work of concurrent requests overlaps on
+ * the device.  A request is one problem instance with its right-hand sides:
+ * it is assembled, factored (H-LU with the server's options) and solved as
+ * by hfsem_assemble / hfsem_hlu_factor / hfsem_solve.  Admission: an idle
+ * slot takes the oldest queued request that fits the device-memory budget
+ * (resident factorisations plus the estimated needs of running requests),
+ * evicting idle cached factorisations (least recently used first) when
+ * that makes it fit; a request that does not fit holds back the ones
+ * behind it, and one that cannot fit even on an otherwise empty budget
+ * completes with HFSEM_ERR_OOM.  Reuse: after a request, its factorisation
+ * stays resident (up to cache_factors idle ones); a later request with the
+ * same operator (mesh, P, alpha, theta, rho, matvec: compared in full)
+ * takes it instead of refactoring.  Requests with the same operator never
+ * run at the same time.  Every request's result is the one hfsem_solve gives
+ * for it alone: the arithmetic does not depend on what else runs. */
+typedef struct hfsem_server_s hfsem_server;
+
+typedef struct {
+  int32_t     slots;          /* concurrent requests, 1..64                    */
+  int64_t     budget_bytes;   /* device memory for resident factorisations and
+                                 running requests; 0 = 80% of the free memory
+                                 at creation                                   */
+  int32_t     cache_factors;  /* idle factorisations kept resident, >= 0       */
+  hfsem_hopts hopts;          /* H-LU options of every request (build_only = 0) */
+  double      tol;            /* BiCGSTAB tolerance, as hfsem_solve            */
+  int32_t     max_iter;
+} hfsem_server_opts;
+
+typedef struct {
+  const hfsem_problem *prob;  /* one instance (h copied at submission)        */
+  const hfsem_rhs     *rhs;   /* its right-hand sides (data copied)           */
+  double      *X;             /* N_d x nrhs, host or device memory of the
+                                 server's device; written when the request
+                                 completes and must stay valid until then     */
+  hfsem_stats *stats;         /* host, nrhs entries; written on completion    */
+} hfsem_request;
+
+typedef struct {
+  int64_t id;                 /* as returned by hfsem_server_submit           */
+  int32_t status;             /* HFSEM_* of the request                        */
+  int32_t reused;             /* 1: a resident factorisation was reused        */
+  double  t_submit, t_start, t_done;  /* seconds on the server's clock        */
+  char    msg[128];           /* failure message ("" on success)              */
+} hfsem_done;
+
+typedef struct {
+  int64_t resident_bytes, inflight_bytes, budget_bytes, peak_bytes;
+  int32_t running, peak_running, cached, queued;
+  int64_t builds, reuses, evictions, rejected;
+} hfsem_server_counters;
+
+/* Start a server on the current device (its workers start at once). */
+int hfsem_server_create(const hfsem_server_opts *opts, hfsem_server **out);
+/* Queue a request and return at once with its id; INVALID_ARG for malformed
+ * sizes (problem parameters outside their ranges fail the request itself). */
+int hfsem_server_submit(hfsem_server *srv, const hfsem_request *req, int64_t *id);
+/* Up to max completed requests since the last poll into out[0..*n). */
+int hfsem_server_poll(hfsem_server *srv, int32_t max, hfsem_done *out, int32_t *n);
+/* Block until every submitted request has completed. */
+int hfsem_server_drain(hfsem_server *srv);
+int hfsem_server_counters_read(hfsem_server *srv, hfsem_server_counters *c);
+/* Wait for the submitted requests, release everything resident, stop. */
+void hfsem_server_free(hfsem_server *srv);
 
 /* ---- kernel timing (measurement support; the paper has no counterpart) --
  * When enabled, the library brackets its main kernels with CUDA events on
@@ -214,6 +297,13 @@ void hfsem_system_free(hfsem_system *sys);
 int hfsem_timing_enable(int32_t on);
 int hfsem_timing_reset(void);
 int hfsem_timing_read(const char *tag, double *total_ms, int64_t *launches, double *work);
+
+/* Measured ALU peak of the current device (measurement support for the
+ * roofline fractions; the paper has no counterpart): independent FMA chains,
+ * 8 per thread, 64 warps per SM on every SM, best of 3 timed launches.
+ * kind 0: FP64, kind 1: FP32.  *tflops receives 2 x FMAs / time in TFLOP/s;
+ * ms (may be NULL) the best launch time, sms (may be NULL) the SM count. */
+int hfsem_alu_peak(int32_t kind, double *tflops, double *ms, int32_t *sms);
 
 /* Static string for a status code. */
 const char *hfsem_status_str(int status);

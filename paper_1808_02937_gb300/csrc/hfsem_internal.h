@@ -3,6 +3,7 @@
 
 #include <cuda_runtime.h>
 
+#include <atomic>
 #include <cstdint>
 #include <cstdio>
 #include <stdexcept>
@@ -27,7 +28,7 @@ inline void cuda_check(cudaError_t e, const char* what) {
     throw Error(HFSEM_ERR_DEVICE, std::string(what) + ": " + cudaGetErrorString(e));
 }
 #define HF_CHECK(x) ::hf::cuda_check((x), #x)
-extern long long g_launches;   // kernels launched by this library (process-wide)
+extern std::atomic<long long> g_launches;   // kernels launched by this library (process-wide)
 #define HF_LAUNCH_CHECK() \
   do {                    \
     ++::hf::g_launches;   \
@@ -139,7 +140,7 @@ struct InstHost {
 // Per-column BiCGSTAB scalars (one column = one instance x one rhs).
 struct KCol {
   double rho, rho_old, alpha, omega, beta, bnorm2, res, snorm, true_res;
-  int status, iters;
+  int status, iters, restarts;
 };
 
 struct KrylovWork {
@@ -154,6 +155,9 @@ struct KrylovWork {
 struct Precond {
   virtual ~Precond() {}
   virtual void apply(int nrhs, const double* r_em, double* y_em) = 0;
+  // HFSEM_OK, or the status of a failure the device recorded during the
+  // applies so far (a copy that missed its wait limit: HFSEM_ERR_TIMEOUT)
+  virtual int device_status() { return HFSEM_OK; }
 };
 
 }  // namespace hf
@@ -203,4 +207,14 @@ void timing_add_work(const char* tag, double work);
 hf::Precond* precond_of(hfsem_system* s, hfsem_factor* f);
 void bicgstab(hfsem_system* s, Precond* M, int nrhs, const double* b_em, double* x_em,
               double tol, int max_iter, std::vector<KCol>& out);
+// Moves a system and its factor (may be NULL) to another stream: later calls
+// issue their work there.  The caller makes sure no work of theirs is still
+// running on the old stream.
+void rebind_stream(hfsem_system* s, hfsem_factor* f, cudaStream_t st);
+// Device bytes a system, a factor hold (their buffers as grown so far).
+size_t system_bytes(const hfsem_system* s);
+size_t factor_bytes(const hfsem_factor* f);
+// Loads, on the current device, the scratch array and the kernels of
+// hfsem_apply_noalloc (once per device), so that its calls allocate nothing.
+void noalloc_prepare();
 }  // namespace hf

@@ -21,7 +21,10 @@
 #include <cstring>
 #include <array>
 #include <list>
+#include <exception>
 #include <map>
+#include <thread>
+#include <unordered_map>
 #include <mutex>
 #include <memory>
 #include <string>
@@ -3030,6 +3033,14 @@ struct hfsem_factor_s : public hf::Precond {
   hfsem_system* sys = nullptr;
   cudaStream_t st = nullptr;   // copy of the system's stream (free never touches sys)
   int precision = HFSEM_PREC_MIXED;
+  // the system instances this factor covers, in its own order (factor
+  // instance j is system instance insts[j]); the kernels index instances
+  // by factor instance and reach the system's data through sys_inst
+  std::vector<int> insts;
+  int nfi = 0;
+  // a batch whose meshes need different arithmetic is factored in parts
+  // (FP32 and FP64); the object holding them owns no device data itself
+  std::vector<std::unique_ptr<hfsem_factor_s>> parts;
   int build_only = 0;
   double tol = 1e-3;
   int R = 8;
@@ -3068,6 +3079,7 @@ struct hfsem_factor_s : public hf::Precond {
   void report(const char* what);
   void report_waves(const char* what);
   void apply(int nrhs, const double* r_em, double* y_em) override;
+  int device_status() override;
   void collect_flops();
   void run_prog();
 };
@@ -3090,26 +3102,45 @@ static size_t prog_smem(const HPlan& p, size_t ts) {
 }
 
 // Plans depend on the mesh and the options only, so they are kept across
-// factorisations (least recently used first out): refactoring the same
-// meshes with new alpha, theta or rho skips the host planning.
-constexpr size_t kPlanCacheMax = 64;
+// factorisations (least recently used first out, bounded in count and in
+// host bytes): refactoring the same meshes with new alpha, theta or rho, or
+// the same batch again, skips the host planning.
+constexpr size_t kPlanCacheMax = 4096;
+constexpr size_t kPlanCacheBytes = size_t(4) << 30;
 static std::mutex g_plan_mu;
 static std::list<std::pair<std::string, std::shared_ptr<PlanBundle>>> g_plan_lru;
+static std::unordered_map<std::string, decltype(g_plan_lru)::iterator> g_plan_idx;
+static size_t g_plan_bytes = 0;
+
+static size_t plan_bytes(const PlanBundle& pb) {
+  const HPlan& p = pb.plan;
+  return p.fac.size() * sizeof(HOp) + p.fac_waves.size() * sizeof(int) + p.B.size() * sizeof(Block) +
+         p.C.size() * sizeof(Cluster) + pb.dense.size() * sizeof(DenseDev) +
+         pb.slots.size() * sizeof(SlotDev) + pb.pairs.size() * sizeof(LRPairDev) +
+         pb.ptask.size() * sizeof(int) + pb.ls.steps.size() * sizeof(StepInfo) +
+         pb.ls.step_cta.size() * sizeof(StepCta) + pb.ls.jobs.size() * sizeof(SolJob) + 256;
+}
 
 static std::shared_ptr<PlanBundle> plan_cache_get(const std::string& key) {
   std::lock_guard<std::mutex> lk(g_plan_mu);
-  for (auto it = g_plan_lru.begin(); it != g_plan_lru.end(); ++it)
-    if (it->first == key) {
-      g_plan_lru.splice(g_plan_lru.begin(), g_plan_lru, it);
-      return g_plan_lru.front().second;
-    }
-  return nullptr;
+  auto it = g_plan_idx.find(key);
+  if (it == g_plan_idx.end()) return nullptr;
+  g_plan_lru.splice(g_plan_lru.begin(), g_plan_lru, it->second);
+  return g_plan_lru.front().second;
 }
 
 static void plan_cache_put(const std::string& key, std::shared_ptr<PlanBundle> pb) {
   std::lock_guard<std::mutex> lk(g_plan_mu);
+  if (g_plan_idx.count(key)) return;
+  g_plan_bytes += plan_bytes(*pb);
   g_plan_lru.emplace_front(key, std::move(pb));
-  while (g_plan_lru.size() > kPlanCacheMax) g_plan_lru.pop_back();
+  g_plan_idx[key] = g_plan_lru.begin();
+  while (g_plan_lru.size() > 1 &&
+         (g_plan_lru.size() > kPlanCacheMax || g_plan_bytes > kPlanCacheBytes)) {
+    g_plan_bytes -= plan_bytes(*g_plan_lru.back().second);
+    g_plan_idx.erase(g_plan_lru.back().first);
+    g_plan_lru.pop_back();
+  }
 }
 
 static std::string plan_key(const InstHost& I, const PlanOpts& o) {
@@ -3120,29 +3151,16 @@ static std::string plan_key(const InstHost& I, const PlanOpts& o) {
   return k + buf;
 }
 
-static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
-  AllocStream as(s->st);   // the factor's buffers come stream-ordered from the pool
-  if (opt.R < 1 || opt.R > 32) throw Error(HFSEM_ERR_INVALID_ARG, "R must be in [1, 32]");
-  if (!(opt.lambda > 0.0)) throw Error(HFSEM_ERR_INVALID_ARG, "lambda must be > 0");
-  if (!(opt.tol_hlu >= 0.0)) throw Error(HFSEM_ERR_INVALID_ARG, "tol_hlu must be >= 0");
-  if (opt.precision != HFSEM_PREC_FP64 && opt.precision != HFSEM_PREC_MIXED &&
-      opt.precision != HFSEM_PREC_MIXED_TC)
-    throw Error(HFSEM_ERR_INVALID_ARG, "unknown precision");
-  if (opt.leaf_elems < 0 || opt.kmax < 0) throw Error(HFSEM_ERR_INVALID_ARG, "leaf_elems, kmax >= 0");
+// Factor the system instances in `list` with one arithmetic (`precision`).
+static hfsem_factor* factor_part(hfsem_system* s, const hfsem_hopts& opt, const std::vector<int>& list,
+                                 int precision) {
   auto* f = new hfsem_factor();
   try {
     f->sys = s;
     f->st = s->st;
-    f->precision = opt.precision;
-    // FP32 cannot factor the equilibrated H-matrix of meshes whose element
-    // sizes span more than ~1e45 (the preconditioner then loses all digits);
-    // such batches are factored in FP64 on the GPU
-    if (f->precision != HFSEM_PREC_FP64)
-      for (const InstHost& I : s->ih) {
-        double hmax = *std::max_element(I.h.begin(), I.h.end());
-        double hmin = *std::min_element(I.h.begin(), I.h.end());
-        if (hmax > 1e45 * hmin) f->precision = HFSEM_PREC_FP64;
-      }
+    f->precision = precision;
+    f->insts = list;
+    f->nfi = (int)list.size();
     f->build_only = opt.build_only;
     f->tol = opt.tol_hlu;
     f->R = opt.R;
@@ -3157,12 +3175,13 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
     }
     const int max_leaf = fp32 ? 128 : 96;
     std::map<std::string, std::shared_ptr<PlanBundle>> cache;
-    const int ni = s->n_inst;
+    const int ni = f->nfi;
     std::vector<std::string> keys(ni);
     f->plans.resize(ni);
     f->hidev.resize(ni);
+    std::vector<PlanOpts> popts(ni);
     for (int i = 0; i < ni; ++i) {
-      const InstHost& I = s->ih[i];
+      const InstHost& I = s->ih[list[i]];
       PlanOpts o;
       o.lambda = opt.lambda;
       const int kmax_eff = opt.kmax ? opt.kmax : opt.R;
@@ -3180,52 +3199,86 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
       o.max_leaf = max_leaf;
       o.unique_tmp = 1;
       o.ncta = kCluster;
-      std::string key = plan_key(I, o) + (fp32 ? "|f32|" : "|f64|") + std::to_string(sol_budget);
-      keys[i] = key;
-      auto it = cache.find(key);
-      if (it == cache.end()) {
-        if (auto hit = plan_cache_get(key)) it = cache.emplace(key, hit).first;
-      }
-      if (it == cache.end()) {
-        auto pb = std::make_shared<PlanBundle>();
-        make_plan(I, o, pb->plan);
-        HPlan& p = pb->plan;
-        for (int bi : p.dense_blocks) {
-          const Block& b = p.B[bi];
-          pb->dense.push_back(DenseDev{b.off, p.C[b.t].d0, b.m, p.C[b.s].d0, b.n});
-        }
-        for (int bi : p.lr_blocks) {
-          const Block& b = p.B[bi];
-          pb->slots.push_back(SlotDev{b.off, b.m, b.n, b.kcap, b.kmax});
-        }
-        // pair lower blocks (t right of s) with their mirrors
-        std::map<std::pair<int, int>, int> slot_of;
-        for (int bi : p.lr_blocks) slot_of[{p.B[bi].t, p.B[bi].s}] = p.B[bi].slot;
-        for (int bi : p.lr_blocks) {
-          const Block& b = p.B[bi];
-          if (!b.lower) continue;
-          auto mi = slot_of.find({b.s, b.t});
-          if (mi == slot_of.end()) throw Error(HFSEM_ERR_DEVICE, "block tree is not symmetric");
-          const Cluster &ct = p.C[b.t], &cs = p.C[b.s];
-          pb->pairs.push_back(LRPairDev{b.slot, mi->second, ct.e0, ct.e1, cs.e0, cs.e1, ct.lo,
-                                        ct.hi, cs.lo, cs.hi, ct.d0, b.m, cs.d0, b.n, pb->lrrows});
-          pb->lrrows += (long long)(b.m + b.n) * opt.R;
-        }
-        // one task per element of each side (element e1 only feeds the hat at
-        // node e1 and is left out when it is past the last element)
-        pb->ptask.assign(1, 0);
-        for (const LRPairDev& q : pb->pairs) {
-          const int nt = ((q.te1 < I.N) ? q.te1 : q.te1 - 1) - q.te0 + 1;
-          const int ns = ((q.se1 < I.N) ? q.se1 : q.se1 - 1) - q.se0 + 1;
-          pb->ptask.push_back(pb->ptask.back() + nt + ns);
-        }
-        build_leaf_solve(pb->plan, kCluster, sol_budget, (int)f->tsize,
-                         fp32 ? solve_w<float>() : solve_w<double>(), pb->ls);
-        plan_cache_put(key, pb);
-        it = cache.emplace(key, pb).first;
-      }
-      f->plans[i] = it->second;
+      popts[i] = o;
+      keys[i] = plan_key(I, o) + (fp32 ? "|f32|" : "|f64|") + std::to_string(sol_budget);
     }
+    // plans not cached yet, one per distinct key, built on all host cores
+    std::vector<int> todo;
+    for (int i = 0; i < ni; ++i) {
+      if (cache.count(keys[i])) continue;
+      if (auto hit = plan_cache_get(keys[i])) {
+        cache.emplace(keys[i], hit);
+        continue;
+      }
+      cache.emplace(keys[i], nullptr);
+      todo.push_back(i);
+    }
+    auto make_bundle = [&](int i) {
+      const InstHost& I = s->ih[list[i]];
+      const PlanOpts& o = popts[i];
+      auto pb = std::make_shared<PlanBundle>();
+      make_plan(I, o, pb->plan);
+      HPlan& p = pb->plan;
+      for (int bi : p.dense_blocks) {
+        const Block& b = p.B[bi];
+        pb->dense.push_back(DenseDev{b.off, p.C[b.t].d0, b.m, p.C[b.s].d0, b.n});
+      }
+      for (int bi : p.lr_blocks) {
+        const Block& b = p.B[bi];
+        pb->slots.push_back(SlotDev{b.off, b.m, b.n, b.kcap, b.kmax});
+      }
+      // pair lower blocks (t right of s) with their mirrors
+      std::map<std::pair<int, int>, int> slot_of;
+      for (int bi : p.lr_blocks) slot_of[{p.B[bi].t, p.B[bi].s}] = p.B[bi].slot;
+      for (int bi : p.lr_blocks) {
+        const Block& b = p.B[bi];
+        if (!b.lower) continue;
+        auto mi = slot_of.find({b.s, b.t});
+        if (mi == slot_of.end()) throw Error(HFSEM_ERR_DEVICE, "block tree is not symmetric");
+        const Cluster &ct = p.C[b.t], &cs = p.C[b.s];
+        pb->pairs.push_back(LRPairDev{b.slot, mi->second, ct.e0, ct.e1, cs.e0, cs.e1, ct.lo,
+                                      ct.hi, cs.lo, cs.hi, ct.d0, b.m, cs.d0, b.n, pb->lrrows});
+        pb->lrrows += (long long)(b.m + b.n) * opt.R;
+      }
+      // one task per element of each side (element e1 only feeds the hat at
+      // node e1 and is left out when it is past the last element)
+      pb->ptask.assign(1, 0);
+      for (const LRPairDev& q : pb->pairs) {
+        const int nt = ((q.te1 < I.N) ? q.te1 : q.te1 - 1) - q.te0 + 1;
+        const int ns = ((q.se1 < I.N) ? q.se1 : q.se1 - 1) - q.se0 + 1;
+        pb->ptask.push_back(pb->ptask.back() + nt + ns);
+      }
+      build_leaf_solve(pb->plan, kCluster, sol_budget, (int)f->tsize,
+                       fp32 ? solve_w<float>() : solve_w<double>(), pb->ls);
+      return pb;
+    };
+    {
+      std::vector<std::shared_ptr<PlanBundle>> built(todo.size());
+      std::vector<std::exception_ptr> errs(todo.size());
+      std::atomic<size_t> next{0};
+      auto worker = [&] {
+        for (size_t w; (w = next.fetch_add(1)) < todo.size();) {
+          try {
+            built[w] = make_bundle(todo[w]);
+          } catch (...) {
+            errs[w] = std::current_exception();
+          }
+        }
+      };
+      const size_t nth = std::min<size_t>(todo.size(),
+                                          std::max(1u, std::min(32u, std::thread::hardware_concurrency())));
+      std::vector<std::thread> pool;
+      for (size_t t = 1; t < nth; ++t) pool.emplace_back(worker);
+      worker();
+      for (auto& t : pool) t.join();
+      for (auto& e : errs)
+        if (e) std::rethrow_exception(e);
+      for (size_t w = 0; w < todo.size(); ++w) {
+        plan_cache_put(keys[todo[w]], built[w]);
+        cache[keys[todo[w]]] = built[w];
+      }
+    }
+    for (int i = 0; i < ni; ++i) f->plans[i] = cache[keys[i]];
     // one solve kernel serves every plan: cut the parts of each plan for the
     // largest leaf and the most owned low-rank columns of all of them
     {
@@ -3234,14 +3287,33 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
         nm = std::max(nm, kv.second->ls.nmax);
         wc = std::max(wc, kv.second->ls.wcols);
       }
-      for (auto& kv : cache) {
-        if (kv.second->ls.nmax >= nm && kv.second->ls.wcols >= wc) continue;
-        // a private copy: the shared plan keeps the tables cut for itself
-        auto cp = std::make_shared<PlanBundle>(*kv.second);
-        build_leaf_solve(cp->plan, kCluster, sol_budget, (int)f->tsize,
-                         fp32 ? solve_w<float>() : solve_w<double>(), cp->ls, nm, wc);
-        kv.second = cp;
-      }
+      // a private copy for each plan cut for less: the shared plan keeps the
+      // tables cut for itself (on all host cores, as above)
+      std::vector<std::shared_ptr<PlanBundle>*> recut;
+      for (auto& kv : cache)
+        if (kv.second->ls.nmax < nm || kv.second->ls.wcols < wc) recut.push_back(&kv.second);
+      std::vector<std::exception_ptr> errs(recut.size());
+      std::atomic<size_t> next{0};
+      auto worker = [&] {
+        for (size_t w; (w = next.fetch_add(1)) < recut.size();) {
+          try {
+            auto cp = std::make_shared<PlanBundle>(**recut[w]);
+            build_leaf_solve(cp->plan, kCluster, sol_budget, (int)f->tsize,
+                             fp32 ? solve_w<float>() : solve_w<double>(), cp->ls, nm, wc);
+            *recut[w] = cp;
+          } catch (...) {
+            errs[w] = std::current_exception();
+          }
+        }
+      };
+      const size_t nth = std::min<size_t>(recut.size(),
+                                          std::max(1u, std::min(32u, std::thread::hardware_concurrency())));
+      std::vector<std::thread> pool;
+      for (size_t t = 1; t < nth; ++t) pool.emplace_back(worker);
+      if (!recut.empty()) worker();
+      for (auto& t : pool) t.join();
+      for (auto& e : errs)
+        if (e) std::rethrow_exception(e);
       for (int i = 0; i < ni; ++i) f->plans[i] = cache[keys[i]];
     }
     // concatenate tables
@@ -3317,10 +3389,10 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
       H.nfw = (int)p.fac_waves.size() - 1;
 
       H.d_off = doff;
-      doff += s->ih[i].Nd;
-      H.sys_inst = i;
+      doff += s->ih[list[i]].Nd;
+      H.sys_inst = list[i];
       H.R = opt.R;
-      H.nd = s->ih[i].Nd;
+      H.nd = s->ih[list[i]].Nd;
       H.st0 = placed_leaf[pb][0];
       H.job0 = placed_leaf[pb][1];
       H.jcap = pb->ls.jcap;
@@ -3489,18 +3561,21 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
       f->report_waves("factorisation");
     }
     std::vector<int> err(ni);
-    HF_CHECK(cudaMemcpy(err.data(), f->d_err.p, ni * sizeof(int), cudaMemcpyDeviceToHost));
+    HF_CHECK(cudaMemcpyAsync(err.data(), f->d_err.p, ni * sizeof(int), cudaMemcpyDeviceToHost, s->st));
+    HF_CHECK(cudaStreamSynchronize(s->st));
     for (int e : err) {
       if (e == 3) throw Error(HFSEM_ERR_DEVICE, "low-rank block above the rank bound of the solves");
       if (e == 4) {
         unsigned long long d[8] = {0};
-        if (f->d_tcdbg.p) cudaMemcpy(d, f->d_tcdbg.p, sizeof(d), cudaMemcpyDeviceToHost);
+        if (f->d_tcdbg.p && cudaMemcpyAsync(d, f->d_tcdbg.p, sizeof(d), cudaMemcpyDeviceToHost,
+                                            s->st) == cudaSuccess)
+          cudaStreamSynchronize(s->st);
         char msg[256];
         snprintf(msg, sizeof(msg),
                  "a tensor-core product did not complete within its wait limit (mbarrier %llx, "
                  "a-desc %llx, b-desc %llx, idesc %llx, tmem %llx, N|K %llx)",
                  d[0], d[1], d[2], d[3], d[4], d[5]);
-        throw Error(HFSEM_ERR_DEVICE, msg);
+        throw Error(HFSEM_ERR_TIMEOUT, msg);
       }
       if (e) throw Error(HFSEM_ERR_BREAKDOWN, "zero or non-finite pivot in an H-LU leaf");
     }
@@ -3511,13 +3586,56 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
   return f;
 }
 
+static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
+  AllocStream as(s->st);   // the factor's buffers come stream-ordered from the pool
+  if (opt.R < 1 || opt.R > 32) throw Error(HFSEM_ERR_INVALID_ARG, "R must be in [1, 32]");
+  if (!(opt.lambda > 0.0)) throw Error(HFSEM_ERR_INVALID_ARG, "lambda must be > 0");
+  if (!(opt.tol_hlu >= 0.0)) throw Error(HFSEM_ERR_INVALID_ARG, "tol_hlu must be >= 0");
+  if (opt.precision != HFSEM_PREC_FP64 && opt.precision != HFSEM_PREC_MIXED &&
+      opt.precision != HFSEM_PREC_MIXED_TC)
+    throw Error(HFSEM_ERR_INVALID_ARG, "unknown precision");
+  if (opt.leaf_elems < 0 || opt.kmax < 0) throw Error(HFSEM_ERR_INVALID_ARG, "leaf_elems, kmax >= 0");
+  // FP32 cannot factor the equilibrated H-matrix of meshes whose element
+  // sizes span more than ~1e45 (the preconditioner then loses all digits):
+  // those instances are factored in FP64, the others in the requested mode
+  std::vector<int> lo, hi;
+  for (int i = 0; i < s->n_inst; ++i) {
+    const InstHost& I = s->ih[i];
+    const double hmax = *std::max_element(I.h.begin(), I.h.end());
+    const double hmin = *std::min_element(I.h.begin(), I.h.end());
+    (opt.precision != HFSEM_PREC_FP64 && !(hmax > 1e45 * hmin) ? lo : hi).push_back(i);
+  }
+  if (hi.empty()) return factor_part(s, opt, lo, opt.precision);
+  if (lo.empty()) return factor_part(s, opt, hi, HFSEM_PREC_FP64);
+  auto* f = new hfsem_factor();
+  try {
+    f->sys = s;
+    f->st = s->st;
+    f->precision = opt.precision;
+    f->build_only = opt.build_only;
+    f->tol = opt.tol_hlu;
+    f->R = opt.R;
+    f->nfi = s->n_inst;
+    for (int i = 0; i < s->n_inst; ++i) f->insts.push_back(i);
+    f->parts.emplace_back(factor_part(s, opt, lo, opt.precision));
+    f->parts.emplace_back(factor_part(s, opt, hi, HFSEM_PREC_FP64));
+  } catch (...) {
+    delete f;
+    throw;
+  }
+  return f;
+}
+
 }  // namespace hf
 
 void hfsem_factor_s::collect_flops() {
+  for (auto& q : parts) q->collect_flops();
   // move the device flop counters into the timing registry
   if (!d_flops.p || !hf::timing_on()) return;
   std::vector<double> h(d_flops.n);
-  cudaMemcpy(h.data(), d_flops.p, h.size() * sizeof(double), cudaMemcpyDeviceToHost);
+  if (cudaMemcpyAsync(h.data(), d_flops.p, h.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                      st) != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+    return;
   double f0 = 0, f1 = 0;
   for (size_t i = 0; i < h.size(); i += 2) {
     f0 += h[i];
@@ -3525,7 +3643,7 @@ void hfsem_factor_s::collect_flops() {
   }
   hf::timing_add_work("hlu_factor", f0);
   hf::timing_add_work("hlu_solve", f1);
-  cudaMemset(d_flops.p, 0, d_flops.n * sizeof(double));
+  cudaMemsetAsync(d_flops.p, 0, d_flops.n * sizeof(double), st);
 }
 
 void hfsem_factor_s::report(const char* what) {
@@ -3637,11 +3755,11 @@ void hfsem_factor_s::report_waves(const char* what) {
 void hfsem_factor_s::run_prog() {
   if (!d_prof.p && getenv("HFSEM_PROFILE")) {
     hf::AllocStream plain(reinterpret_cast<cudaStream_t>(-1));
-    d_prof.alloc((size_t)sys->n_inst * 32 + 16 + 64);
+    d_prof.alloc((size_t)nfi * 32 + 16 + 64);
     cudaMemset(d_prof.p, 0, d_prof.n * sizeof(unsigned long long));
   }
   if (!d_flops.p) {
-    d_flops.alloc((size_t)sys->n_inst * hf::kCluster * 2);
+    d_flops.alloc((size_t)nfi * hf::kCluster * 2);
     cudaMemsetAsync(d_flops.p, 0, d_flops.n * sizeof(double), sys->st);
   }
   if (!d_tcdbg.p && precision == HFSEM_PREC_MIXED_TC) {
@@ -3658,11 +3776,11 @@ void hfsem_factor_s::run_prog() {
   }
   if (d_wprof.p) cudaMemsetAsync(d_wprof.p, 0, d_wprof.n * sizeof(unsigned long long), sys->st);
   hf::HProgArgs a{d_hi.p, d_waves.p, d_ops.p, d_slots.p, d_ranks.p, d_err.p, tol, d_prof.p, d_flops.p,
-                  d_wprof.p, wstride, (long long)(smem / tsize) - 8, sys->n_inst,
+                  d_wprof.p, wstride, (long long)(smem / tsize) - 8, nfi,
                   precision == HFSEM_PREC_MIXED_TC ? 1 : 0, d_tcdbg.p};
   hf::Tick tk(sys->st, "hlu_factor");
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(sys->n_inst * hf::kCluster));
+  cfg.gridDim = dim3((unsigned)(nfi * hf::kCluster));
   cfg.blockDim = dim3(hf::kHThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = sys->st;
@@ -3703,7 +3821,7 @@ void hfsem_factor_s::run_prog() {
 
 void hfsem_factor_s::run_pack() {
   hf::Tick tk(sys->st, "solve_pack");
-  dim3 g(128, sys->n_inst);
+  dim3 g(128, nfi);
   if (tsize == sizeof(float))
     hf::k_solve_pack<float><<<g, 256, 0, sys->st>>>(d_hi.p, d_jobs.p, reinterpret_cast<const float*>(d_arena.p),
                                                     d_ranks.p, reinterpret_cast<float*>(d_pack.p), d_meta.p, sol_slot,
@@ -3724,7 +3842,7 @@ void hfsem_factor_s::run_leaf_solve(int nrhs) {
   }
   hf::Tick tk(sys->st, "hlu_solve");
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(sys->n_inst * hf::kCluster));
+  cfg.gridDim = dim3((unsigned)(nfi * hf::kCluster));
   cfg.blockDim = dim3(hf::kHThreads);
   cfg.dynamicSmemBytes = sol_smem;
   cfg.stream = sys->st;
@@ -3762,13 +3880,18 @@ void hfsem_factor_s::run_leaf_solve(int nrhs) {
 void hfsem_factor_s::apply(int nrhs, const double* r_em, double* y_em) {
   if (build_only) throw hf::Error(HFSEM_ERR_INVALID_ARG, "factor was built with build_only");
   if (nrhs > 64) throw hf::Error(HFSEM_ERR_INVALID_ARG, "nrhs > 64");
+  if (!parts.empty()) {
+    // each part writes the solutions of its own instances
+    for (auto& q : parts) q->apply(nrhs, r_em, y_em);
+    return;
+  }
   if (!d_flops.p) {
-    d_flops.alloc((size_t)sys->n_inst * hf::kCluster * 2);
+    d_flops.alloc((size_t)nfi * hf::kCluster * 2);
     cudaMemsetAsync(d_flops.p, 0, d_flops.n * sizeof(double), sys->st);
   }
   int maxnd = 1;
-  for (auto& I : sys->ih) maxnd = std::max(maxnd, I.Nd);
-  dim3 g(std::min(1024, (maxnd * nrhs + 255) / 256), sys->n_inst);
+  for (int i : insts) maxnd = std::max(maxnd, sys->ih[i].Nd);
+  dim3 g(std::min(1024, (maxnd * nrhs + 255) / 256), nfi);
   if (tsize == sizeof(float)) {
     float* ar = reinterpret_cast<float*>(d_arena.p);
     hf::k_hsolve_in<float><<<g, 256, 0, sys->st>>>(d_hi.p, sys->d_inst.p, r_em, d_D.p, ar, d_ranks.p, nrhs);
@@ -3786,6 +3909,45 @@ void hfsem_factor_s::apply(int nrhs, const double* r_em, double* y_em) {
 }
 
 namespace hf {
+}  // namespace hf
+
+int hfsem_factor_s::device_status() {
+  if (!parts.empty()) {
+    int worst = HFSEM_OK;
+    for (auto& q : parts) {
+      int e = q->device_status();
+      if (e != HFSEM_OK) worst = e;
+    }
+    return worst;
+  }
+  std::vector<int> err(nfi);
+  HF_CHECK(cudaMemcpyAsync(err.data(), d_err.p, err.size() * sizeof(int), cudaMemcpyDeviceToHost, st));
+  HF_CHECK(cudaStreamSynchronize(st));
+  for (int e : err)
+    if (e == 2) return HFSEM_ERR_TIMEOUT;
+  return HFSEM_OK;
+}
+
+namespace hf {
+
+void rebind_stream(hfsem_system* s, hfsem_factor* f, cudaStream_t st) {
+  s->st = st;
+  if (!f) return;
+  f->st = st;
+  for (auto& q : f->parts) q->st = st;
+}
+
+size_t factor_bytes(const hfsem_factor* f) {
+  auto b = [](const auto& d) { return d.n * sizeof(*d.p); };
+  size_t t = b(f->d_hi) + b(f->d_waves) + b(f->d_ops) + b(f->d_slots) + b(f->d_dense) +
+             b(f->d_pairs) + b(f->d_ptask) + b(f->d_gmax) + b(f->d_lrt) + b(f->d_steps) +
+             b(f->d_step_cta) + b(f->d_jobs) + b(f->d_pack) + b(f->d_meta) + b(f->d_sprof) +
+             b(f->d_ranks) + b(f->d_err) + b(f->d_D) + b(f->d_arena) + b(f->d_prof) +
+             b(f->d_flops) + b(f->d_wprof) + b(f->d_tcdbg);
+  for (auto& q : f->parts) t += factor_bytes(q.get());
+  return t;
+}
+
 Precond* precond_of(hfsem_system* s, hfsem_factor* f) {
   if (!f) return nullptr;
   if (f->sys != s) throw Error(HFSEM_ERR_INVALID_ARG, "factor belongs to another system");
@@ -3822,6 +3984,12 @@ int hfsem_hmatrix_dense(const hfsem_factor* fac, int32_t inst, double* out) {
     if (!fac->build_only) throw Error(HFSEM_ERR_INVALID_ARG, "only for factors built with build_only");
     hfsem_system* s = fac->sys;
     const InstHost& I = s->ih[inst];
+    // the part holding this instance, and its index there
+    const hfsem_factor* part = fac;
+    for (auto& q : fac->parts)
+      if (std::find(q->insts.begin(), q->insts.end(), inst) != q->insts.end()) part = q.get();
+    fac = part;
+    inst = (int32_t)(std::find(fac->insts.begin(), fac->insts.end(), inst) - fac->insts.begin());
     size_t nn = (size_t)I.Nd * I.Nd;
     DevBuf<double> em, pp;
     em.alloc(std::max<size_t>(nn, 1));
@@ -3874,10 +4042,8 @@ int hfsem_precond_apply(hfsem_factor* fac, int32_t nrhs, const double* r, double
     HF_CHECK(cudaMemcpyAsync(y, s->w_y.p, cnt * sizeof(double),
                              is_device_ptr(y) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s->st));
     HF_CHECK(cudaStreamSynchronize(s->st));
-    std::vector<int> err(s->n_inst);
-    HF_CHECK(cudaMemcpy(err.data(), fac->d_err.p, err.size() * sizeof(int), cudaMemcpyDeviceToHost));
-    for (int e : err)
-      if (e == 2) throw Error(HFSEM_ERR_DEVICE, "an H-solve copy did not complete within its wait limit");
+    if (fac->device_status() == HFSEM_ERR_TIMEOUT)
+      throw Error(HFSEM_ERR_TIMEOUT, "an H-solve copy did not complete within its wait limit");
     return HFSEM_OK;
   } catch (const Error& e) {
     set_last_error(e.msg);
@@ -3939,7 +4105,7 @@ extern "C" int hfsem_tc_tile_check(int32_t N, int32_t K, int32_t reps, double* m
     HF_CHECK(cudaMemcpy(h.data(), d.p, na * sizeof(float), cudaMemcpyDeviceToHost));
     HF_CHECK(cudaMemcpy(herr, de.p, sizeof(herr), cudaMemcpyDeviceToHost));
     for (int r = 0; r < kCluster; ++r)
-      if (herr[r]) throw Error(HFSEM_ERR_DEVICE, "hfsem_tc_tile_check: a tensor-core product did not complete within its wait limit");
+      if (herr[r]) throw Error(HFSEM_ERR_TIMEOUT, "hfsem_tc_tile_check: a tensor-core product did not complete within its wait limit");
     // |C - A B| relative to sum_k |a_mk| |b_kn|, per entry, against FP64
     double mx = 0.0;
     for (int r = 0; r < kCluster; ++r)

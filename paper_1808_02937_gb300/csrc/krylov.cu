@@ -5,6 +5,18 @@
 // the per-column status flags once per iteration to decide when to stop.
 // Inner products are reduced in a fixed order (per-CTA tree, then a fixed
 // sweep over CTAs), so results are bitwise reproducible run to run.
+//
+// Convergence is decided on the true residual.  The recursively updated
+// residual r drifts from b - A x in finite precision (the more so, the more
+// iterations a weak preconditioner needs), so a column whose recursive
+// residual reaches tol is only a candidate: its true residual b - A x is
+// formed, and the column is accepted when that is within kTrueSlack * tol.
+// Otherwise the iteration restarts from the true residual (residual
+// replacement: r = rh = b - A x, p = v = 0).  A restart cycle shrinks the
+// drift with the residual it starts from, so when one fails to halve the
+// true residual of the previous check, the true residual sits at the floor
+// the FP64 product A x allows (it grows with N_d and with the operator's
+// rounding) and the column is accepted there; stats report that value.
 #include "hfsem_internal.h"
 
 #include <algorithm>
@@ -16,7 +28,20 @@ namespace hf {
 constexpr int kChunk = 2048;   // elements per CTA in the reductions
 constexpr int kDotThreads = 256;
 
-enum : int { ST_RUN = 0, ST_CONV = 1, ST_BREAK = 2, ST_MAXIT = 3 };
+enum : int {
+  ST_RUN = 0,      // iterating
+  ST_CONV = 1,     // true residual accepted
+  ST_BREAK = 2,    // rho, omega or (rh, v) vanished
+  ST_MAXIT = 3,    // iteration budget spent
+  ST_CHECK = 4,    // recursive residual <= tol: true residual pending
+  ST_RESTART = 5,  // true residual too large: restart from it
+  ST_FLOOR = 6,    // accepted: restarts no longer reduce the true residual
+};
+// a candidate is accepted when ||b - A x|| <= kTrueSlack * tol * ||b||: the
+// recursive and true residuals of FP64 BiCGSTAB may part by a modest factor
+// even when nothing went wrong
+constexpr double kTrueSlack = 100.0;
+constexpr int kMaxRestarts = 8;
 
 // fixed-order CTA reduction of up to 3 sums
 template <int K>
@@ -47,6 +72,8 @@ enum : int {
   M_X = 5,         // x += alpha ph + omega sh; r = s - omega t; dots (r,r), (rh,r)
   M_XS = 6,        // x += alpha ph  (early exit on small s)
   M_RES = 7,       // r = b - Ax (Ax in v); dots (r,r)
+  M_TRUE = 8,      // candidates: s = b - Ax (Ax in t); dot (s,s)
+  M_RESTART = 9,   // restarting columns: r = rh = s, p = v = 0; dot (r,r)
 };
 
 struct Vecs {
@@ -62,7 +89,10 @@ __global__ void k_bicg_vec(int mode, Vecs V, const long long* __restrict__ coff,
   const long long o = coff[c];
   const int chunk = blockIdx.x;
   if (chunk * kChunk >= len) return;
-  const bool live = (k.status == ST_RUN) || mode == M_INIT || mode == M_RES;
+  const bool live = mode == M_INIT || mode == M_RES ? true
+                    : mode == M_TRUE                ? k.status == ST_CHECK
+                    : mode == M_RESTART             ? k.status == ST_RESTART
+                                                    : k.status == ST_RUN;
   double acc[2] = {0.0, 0.0};
   if (live) {
     const int e0 = chunk * kChunk, e1 = min(len, e0 + kChunk);
@@ -111,6 +141,21 @@ __global__ void k_bicg_vec(int mode, Vecs V, const long long* __restrict__ coff,
           acc[0] += r * r;
           break;
         }
+        case M_TRUE: {
+          double r = V.b[i] - V.t[i];
+          V.s[i] = r;
+          acc[0] += r * r;
+          break;
+        }
+        case M_RESTART: {
+          double r = V.s[i];
+          V.r[i] = r;
+          V.rh[i] = r;
+          V.p[i] = 0.0;
+          V.v[i] = 0.0;
+          acc[0] += r * r;
+          break;
+        }
       }
     }
   }
@@ -140,6 +185,8 @@ __global__ void k_bicg_scalar(int mode, const int* __restrict__ clen, KCol* cols
       k.alpha = 1.0;
       k.omega = 1.0;
       k.iters = 0;
+      k.restarts = 0;
+      k.true_res = INFINITY;
       k.res = (s1 > 0.0) ? sqrt(s0 / s1) : 0.0;
       k.status = (clen[c] == 0 || s1 == 0.0 || k.res <= tol) ? ST_CONV : ST_RUN;
       k.beta = 0.0;
@@ -172,7 +219,7 @@ __global__ void k_bicg_scalar(int mode, const int* __restrict__ clen, KCol* cols
       k.rho_old = k.rho;
       k.rho = s1;
       if (k.res <= tol) {
-        k.status = ST_CONV;
+        k.status = ST_CHECK;
       } else if (k.rho == 0.0 || !isfinite(k.res)) {
         k.status = ST_BREAK;
       } else {
@@ -182,6 +229,34 @@ __global__ void k_bicg_scalar(int mode, const int* __restrict__ clen, KCol* cols
       break;
     case M_RES:
       k.true_res = (k.bnorm2 > 0.0) ? sqrt(s0 / k.bnorm2) : 0.0;
+      break;
+    case M_TRUE: {
+      if (k.status != ST_CHECK) break;
+      const double t = sqrt(s0 / k.bnorm2);
+      if (t <= kTrueSlack * tol) {
+        k.status = ST_CONV;
+      } else if (!isfinite(t)) {
+        k.status = ST_BREAK;
+      } else if (k.restarts > 0 && !(t < 0.5 * k.true_res)) {
+        k.status = ST_FLOOR;          // the last restart did not pay
+      } else if (k.restarts >= kMaxRestarts || iter >= max_iter) {
+        k.status = ST_MAXIT;
+      } else {
+        k.status = ST_RESTART;
+      }
+      k.true_res = t;
+      break;
+    }
+    case M_RESTART:
+      if (k.status != ST_RESTART) break;
+      k.rho = s0;
+      k.rho_old = 1.0;
+      k.alpha = 1.0;
+      k.omega = 1.0;
+      k.beta = 0.0;
+      k.res = sqrt(s0 / k.bnorm2);
+      k.restarts += 1;
+      k.status = ST_RUN;
       break;
   }
   cols[c] = k;
@@ -215,7 +290,7 @@ __global__ void k_bicg_xs(Vecs V, const long long* coff, const int* clen, KCol* 
 __global__ void k_bicg_xs_fin(KCol* cols, const int* flag, int ncols, int iter) {
   int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= ncols || !flag[c]) return;
-  cols[c].status = ST_CONV;
+  cols[c].status = ST_CHECK;
   cols[c].res = cols[c].snorm;
   cols[c].iters = iter + 1;
 }
@@ -282,13 +357,30 @@ void bicgstab(hfsem_system* s, Precond* M, int nrhs, const double* b_em, double*
   vec(M_INIT);
   scal(M_INIT, 0);
   std::vector<KCol> hc(ncols);
-  for (int it = 0; it < max_iter; ++it) {
+  auto read_status = [&](bool& running, bool& check) {
     HF_CHECK(cudaMemcpyAsync(hc.data(), W.cols.p, ncols * sizeof(KCol), cudaMemcpyDeviceToHost,
                              s->st));
     HF_CHECK(cudaStreamSynchronize(s->st));
-    bool running = false;
-    for (auto& k : hc) running = running || k.status == ST_RUN;
-    if (!running) break;
+    running = check = false;
+    for (auto& k : hc) {
+      running = running || k.status == ST_RUN;
+      check = check || k.status == ST_CHECK;
+    }
+  };
+  for (int it = 0;; ++it) {
+    bool running, check;
+    read_status(running, check);
+    if (check) {
+      // candidates: true residual from t = A x (t is free between
+      // iterations); accepted, restarted from it, or stopped
+      apply_operator(s, nrhs, x_em, V.t, 0);
+      vec(M_TRUE);
+      scal(M_TRUE, it);
+      vec(M_RESTART);
+      scal(M_RESTART, it);
+      read_status(running, check);
+    }
+    if (!running || it >= max_iter) break;
     vec(M_P);
     if (M) M->apply(nrhs, V.p, V.ph);
     apply_operator(s, nrhs, V.ph, V.v, 0);
@@ -318,12 +410,14 @@ void bicgstab(hfsem_system* s, Precond* M, int nrhs, const double* b_em, double*
                            s->st));
   HF_CHECK(cudaStreamSynchronize(s->st));
   for (auto& k : out)
-    if (k.status == ST_RUN) k.status = ST_MAXIT;
+    if (k.status == ST_RUN || k.status == ST_CHECK || k.status == ST_RESTART)
+      k.status = ST_MAXIT;
 }
 
 int status_code(const KCol& k) {
   switch (k.status) {
-    case ST_CONV: return HFSEM_OK;
+    case ST_CONV:
+    case ST_FLOOR: return HFSEM_OK;
     case ST_BREAK: return HFSEM_ERR_BREAKDOWN;
     default: return HFSEM_ERR_NOT_CONVERGED;
   }
@@ -357,7 +451,7 @@ extern "C" int hfsem_solve(hfsem_system* sys, hfsem_factor* fac, const hfsem_rhs
                              is_device_ptr(X) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                              sys->st));
     HF_CHECK(cudaStreamSynchronize(sys->st));
-    int worst = HFSEM_OK;
+    int worst = M ? M->device_status() : HFSEM_OK;
     for (size_t c = 0; c < cols.size(); ++c) {
       stats[c].iters = cols[c].iters;
       stats[c].status = status_code(cols[c]);

@@ -58,6 +58,8 @@ void* scratch_address() {
 
 size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
 
+bool g_na_loaded[128] = {false};   // kernels of the product loaded, per device
+
 dim3 grid_of(long long n, int bs, int y, int z) {
   long long g = (n + bs - 1) / bs;
   if (g < 1) g = 1;
@@ -71,6 +73,31 @@ void set_smem_attr(const void* fn, size_t bytes) {
 }
 
 }  // namespace
+
+namespace hf {
+
+// Called by hfsem_assemble: the module holding the scratch array and the
+// kernels launched below are loaded on first use (CUDA's lazy loading), which
+// reserves device memory.  Doing it here, where allocation is expected,
+// leaves nothing to load in hfsem_apply_noalloc itself.
+void noalloc_prepare() {
+  scratch_address();
+  int dev = 0;
+  HF_CHECK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_na_mu);
+  if (g_na_loaded[dev]) return;
+  const void* fns[] = {(const void*)k_perm,      (const void*)k_gather_z,
+                       (const void*)k_scatter_out, (const void*)k_dense_rows,
+                       (const void*)k_dense_cols, (const void*)k_toep_fwd,
+                       (const void*)k_toep_freq,  (const void*)k_toep_inv};
+  for (const void* f : fns) {
+    cudaFuncAttributes fa;
+    HF_CHECK(cudaFuncGetAttributes(&fa, f));
+  }
+  g_na_loaded[dev] = true;
+}
+
+}  // namespace hf
 
 using namespace hf;
 

@@ -16,6 +16,8 @@
 //
 // Internal vector ordering is element-major: element e owns its P-1 bubbles
 // followed by the hat at its right node (dof e*P + p - 1, hat j at j*P - 1).
+#include <atomic>
+
 #include "hfsem_internal.h"
 
 #include <algorithm>
@@ -26,7 +28,7 @@
 
 namespace hf {
 
-long long g_launches = 0;
+std::atomic<long long> g_launches{0};
 static thread_local std::string g_last_error;
 void set_last_error(const std::string& m) { g_last_error = m; }
 const std::string& last_error() { return g_last_error; }
@@ -1299,13 +1301,30 @@ static void stage_out(hfsem_system* s, const double* src, double* dst, size_t co
 
 using namespace hf;
 
+namespace hf {
+size_t system_bytes(const hfsem_system* s) {
+  auto b = [](const auto& d) { return d.n * sizeof(*d.p); };
+  return b(s->d_inst) + b(s->arena) + b(s->spec) + b(s->gl) + b(s->w_x) + b(s->w_y) + b(s->w_z) +
+         b(s->w_w) + b(s->w_T) + b(s->w_ylow) + b(s->w_mom) + b(s->w_fa) + b(s->w_fb) +
+         b(s->w_rhsdata) + b(s->tw) + b(s->kry.vecs) + b(s->kry.partial) + b(s->kry.bx) +
+         b(s->kry.coff) + b(s->kry.clen) + b(s->kry.flag) + b(s->kry.cols);
+}
+}  // namespace hf
+
 extern "C" {
 
 int hfsem_assemble(int32_t n_inst, const hfsem_problem* probs, void* stream,
                    hfsem_system** out) {
   return guarded([&] {
     if (!out) throw Error(HFSEM_ERR_INVALID_ARG, "out is NULL");
-    *out = assemble(n_inst, probs, stream);
+    hfsem_system* s = assemble(n_inst, probs, stream);
+    try {
+      noalloc_prepare();
+    } catch (...) {
+      delete s;
+      throw;
+    }
+    *out = s;
   });
 }
 
@@ -1352,6 +1371,7 @@ int hfsem_load_vector(hfsem_system* sys, const hfsem_rhs* rhs, int32_t lifted, d
   });
 }
 
+
 void hfsem_system_free(hfsem_system* sys) {
   if (!sys) return;
   cudaStreamSynchronize(sys->st);
@@ -1365,6 +1385,7 @@ const char* hfsem_status_str(int status) {
     case HFSEM_ERR_OOM: return "out of device memory";
     case HFSEM_ERR_NOT_CONVERGED: return "not converged";
     case HFSEM_ERR_BREAKDOWN: return "Krylov breakdown";
+    case HFSEM_ERR_TIMEOUT: return "device wait limit reached";
     case HFSEM_ERR_DEVICE: return "CUDA device error";
     case HFSEM_ERR_UNSUPPORTED: return "unsupported";
     default: return "unknown status";

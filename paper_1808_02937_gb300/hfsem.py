@@ -21,6 +21,7 @@ HFSEM_ERR_INVALID_ARG = 1
 HFSEM_ERR_OOM = 2
 HFSEM_ERR_NOT_CONVERGED = 3
 HFSEM_ERR_BREAKDOWN = 4
+HFSEM_ERR_TIMEOUT = 5
 HFSEM_ERR_DEVICE = 6
 HFSEM_ERR_UNSUPPORTED = 7
 
@@ -34,7 +35,9 @@ EXPORTED = ["hfsem_assemble", "hfsem_ndof", "hfsem_apply", "hfsem_load_vector",
             "hfsem_solve", "hfsem_factor_free", "hfsem_system_free",
             "hfsem_status_str", "hfsem_timing_enable", "hfsem_timing_reset",
             "hfsem_timing_read", "hfsem_apply_noalloc", "hfsem_tc_tile_check",
-            "hfsem_last_error"]
+            "hfsem_last_error", "hfsem_server_create", "hfsem_server_submit",
+            "hfsem_server_poll", "hfsem_server_drain", "hfsem_server_counters_read",
+            "hfsem_server_free", "hfsem_alu_peak"]
 
 
 class HfsemError(RuntimeError):
@@ -64,6 +67,31 @@ class hfsem_rhs(C.Structure):
 class hfsem_stats(C.Structure):
     _fields_ = [("iters", C.c_int32), ("status", C.c_int32),
                 ("rel_residual", C.c_double), ("rel_true_residual", C.c_double)]
+
+
+class hfsem_server_opts(C.Structure):
+    _fields_ = [("slots", C.c_int32), ("budget_bytes", C.c_int64),
+                ("cache_factors", C.c_int32), ("hopts", hfsem_hopts), ("tol", C.c_double),
+                ("max_iter", C.c_int32)]
+
+
+class hfsem_request(C.Structure):
+    _fields_ = [("prob", C.POINTER(hfsem_problem)), ("rhs", C.POINTER(hfsem_rhs)),
+                ("X", C.c_void_p), ("stats", C.POINTER(hfsem_stats))]
+
+
+class hfsem_done(C.Structure):
+    _fields_ = [("id", C.c_int64), ("status", C.c_int32), ("reused", C.c_int32),
+                ("t_submit", C.c_double), ("t_start", C.c_double), ("t_done", C.c_double),
+                ("msg", C.c_char * 128)]
+
+
+class hfsem_server_counters(C.Structure):
+    _fields_ = [("resident_bytes", C.c_int64), ("inflight_bytes", C.c_int64),
+                ("budget_bytes", C.c_int64), ("peak_bytes", C.c_int64),
+                ("running", C.c_int32), ("peak_running", C.c_int32), ("cached", C.c_int32),
+                ("queued", C.c_int32), ("builds", C.c_int64), ("reuses", C.c_int64),
+                ("evictions", C.c_int64), ("rejected", C.c_int64)]
 
 
 _lib = None
@@ -96,6 +124,15 @@ def load_library():
     lib.hfsem_status_str.argtypes = [C.c_int]
     lib.hfsem_status_str.restype = C.c_char_p
     lib.hfsem_last_error.restype = C.c_char_p
+    lib.hfsem_server_create.argtypes = [C.POINTER(hfsem_server_opts), C.POINTER(vp)]
+    lib.hfsem_server_submit.argtypes = [vp, C.POINTER(hfsem_request), C.POINTER(C.c_int64)]
+    lib.hfsem_server_poll.argtypes = [vp, C.c_int32, C.POINTER(hfsem_done), C.POINTER(C.c_int32)]
+    lib.hfsem_server_drain.argtypes = [vp]
+    lib.hfsem_server_counters_read.argtypes = [vp, C.POINTER(hfsem_server_counters)]
+    lib.hfsem_server_free.argtypes = [vp]
+    lib.hfsem_server_free.restype = None
+    lib.hfsem_alu_peak.argtypes = [C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                   C.POINTER(C.c_int32)]
     lib.hfsem_timing_enable.argtypes = [C.c_int32]
     lib.hfsem_timing_read.argtypes = [C.c_char_p, C.POINTER(C.c_double),
                                       C.POINTER(C.c_int64), C.POINTER(C.c_double)]
@@ -330,11 +367,12 @@ def hfsem_precond_apply(fac: Factor, r, nrhs: int = 1):
 
 def hfsem_solve(sys: System, fac, rhs_list, tol=1e-14, max_iter=200, X=None,
                 allow_fail=False):
-    """BiCGSTAB on every instance and right-hand side, right-preconditioned by
-    fac (None: unpreconditioned).  X (numpy array or CUDA tensor, N_d x nrhs
-    per instance, concatenated) is the initial guess and receives the
-    solution.  Returns (X, per-column stats dicts, status); raises HfsemError
-    on failure unless allow_fail."""
+    """BiCGSTAB from zero on every instance and right-hand side, right-
+    preconditioned by fac (None: unpreconditioned), accepted on the true
+    residual.  X (numpy array or CUDA tensor, N_d x nrhs per instance,
+    concatenated; allocated on the host when None) receives the solution;
+    its previous contents are not used.  Returns (X, per-column stats dicts,
+    status); raises HfsemError on failure unless allow_fail."""
     arr, keep = _rhs_array(rhs_list)
     nrhs = rhs_list[0][1]
     if X is None:
@@ -361,6 +399,15 @@ def split(sys: System, v, nrhs: int = 1):
     return out
 
 
+def hfsem_alu_peak(kind: int):
+    """(TFLOP/s, best launch ms, SM count) of an FMA-chain microbenchmark on
+    the current device; kind 0 = FP64, 1 = FP32."""
+    tf, ms, sms = C.c_double(), C.c_double(), C.c_int32()
+    _check(load_library().hfsem_alu_peak(kind, C.byref(tf), C.byref(ms), C.byref(sms)),
+           "hfsem_alu_peak")
+    return tf.value, ms.value, sms.value
+
+
 def hfsem_timing_enable(on: bool = True):
     """Per-kernel CUDA-event timing inside the library (for the benchmark)."""
     _check(load_library().hfsem_timing_enable(1 if on else 0), "hfsem_timing_enable")
@@ -376,3 +423,77 @@ def hfsem_timing_read(tag: str):
     _check(load_library().hfsem_timing_read(tag.encode(), C.byref(ms), C.byref(n), C.byref(w)),
            "hfsem_timing_read")
     return ms.value, n.value, w.value
+
+
+class Server:
+    """A serving loop (hfsem_server*): requests, each one instance with its
+    right-hand sides, run in `slots` concurrent slots on the current device,
+    admitted under a device-memory budget, with resident factorisations
+    reused by later requests of the same operator."""
+
+    def __init__(self, slots=8, budget_bytes=0, cache_factors=64, hopts_=None, tol=1e-14,
+                 max_iter=100):
+        lib = load_library()
+        o = hfsem_server_opts(slots, budget_bytes, cache_factors,
+                              hopts_ if hopts_ is not None else hopts(), tol, max_iter)
+        h = C.c_void_p()
+        _check(lib.hfsem_server_create(C.byref(o), C.byref(h)), "hfsem_server_create")
+        self.h = h
+        self._live = {}      # id -> buffers the library writes on completion
+
+    def submit(self, problem, rhs, X=None):
+        """Queue one request: problem from make_problem(), rhs one rhs_* tuple
+        (its nrhs columns).  X (numpy array or CUDA tensor, N_d x nrhs) receives
+        the solution; allocated on the host when None.  Returns the id."""
+        lib = load_library()
+        hh = np.ascontiguousarray(problem["h"], dtype=np.float64)
+        prob = hfsem_problem(len(hh), problem["P"], problem["a"], problem["b"],
+                             hh.ctypes.data_as(C.POINTER(C.c_double)), problem["alpha"],
+                             problem["theta"], problem["rho"], problem["c1"], problem["c2"],
+                             problem.get("matvec", 0))
+        arr, keep = _rhs_array([rhs])
+        nrhs = rhs[1]
+        nd = len(hh) * problem["P"] - 1
+        if X is None:
+            X = np.zeros(nd * nrhs)
+        stats = (hfsem_stats * nrhs)()
+        req = hfsem_request(C.pointer(prob), C.cast(arr, C.POINTER(hfsem_rhs)), _ptr(X), stats)
+        rid = C.c_int64()
+        _check(lib.hfsem_server_submit(self.h, C.byref(req), C.byref(rid)), "hfsem_server_submit")
+        self._live[rid.value] = (X, stats)
+        return rid.value
+
+    def poll(self, max_n=4096):
+        """Completed requests since the last poll: dicts with id, status,
+        reused, t_submit / t_start / t_done (seconds), msg, X, stats."""
+        lib = load_library()
+        out = (hfsem_done * max_n)()
+        n = C.c_int32()
+        _check(lib.hfsem_server_poll(self.h, max_n, out, C.byref(n)), "hfsem_server_poll")
+        res = []
+        for d in out[: n.value]:
+            X, st = self._live.pop(d.id)
+            res.append(dict(id=d.id, status=d.status, reused=d.reused, t_submit=d.t_submit,
+                            t_start=d.t_start, t_done=d.t_done, msg=d.msg.decode(), X=X,
+                            stats=[dict(iters=s.iters, status=s.status,
+                                        rel_residual=s.rel_residual,
+                                        rel_true_residual=s.rel_true_residual) for s in st]))
+        return res
+
+    def drain(self):
+        """Block until every submitted request has completed."""
+        _check(load_library().hfsem_server_drain(self.h), "hfsem_server_drain")
+
+    def counters(self):
+        c = hfsem_server_counters()
+        _check(load_library().hfsem_server_counters_read(self.h, C.byref(c)),
+               "hfsem_server_counters_read")
+        return {k: getattr(c, k) for k, _ in hfsem_server_counters._fields_}
+
+    def close(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.hfsem_server_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        self.close()

@@ -16,6 +16,7 @@ from oracle.solve import solve_problem
 from paper_1808_02937_gb300 import hfsem as H
 from paper_1808_02937_gb300 import workloads as W
 from tests._common import ensure_built, rel_err
+from tests._oracle_pool import config2_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -43,16 +44,16 @@ def test_tc_tile_bad_arguments(lib):
 
 def test_mixed_tc_config2_reaches_oracle(lib):
     insts = W.config2()
+    ref = config2_oracle()
     sys_ = H.hfsem_assemble([H.make_problem(p.h, p.P, p.alpha, p.theta, p.rho) for p in insts])
     fac = H.hfsem_hlu_factor(sys_, H.hopts(R=8, lam=1.0, tol_hlu=1e-3,
                                            precision=H.PREC_MIXED_TC))
     X, st, code = H.hfsem_solve(sys_, fac, [H.rhs_legendre([p.rhs[0]]) for p in insts],
                                 tol=1e-14, max_iter=80)
-    assert code == H.HFSEM_OK
+    assert code == H.HFSEM_OK, st
     for s in st:
+        # accepted on the true residual (<= 100 tol, or at the FP64 floor)
         assert s["iters"] <= 40 and s["rel_true_residual"] < 1e-11, st
-    p = insts[4]
-    Xo, _ = solve_problem(Mesh(p.h, 0.0, 1.0), p.P, p.alpha, p.theta, p.rho, 0.0, 0.0,
-                          ("legendre_ab", p.rhs[0]))
-    got = H.split(sys_, X)[4][:, 0]
-    assert rel_err(got, Xo) < 1e-10
+    parts = H.split(sys_, X)
+    for k in range(len(insts)):
+        assert rel_err(parts[k][:, 0], ref[k]) < 1e-10, k

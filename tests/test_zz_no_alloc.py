@@ -35,6 +35,22 @@ def test_noalloc_matches_apply_twice():
         assert np.abs(got - ref).max() <= 5e-13 * scale, call
 
 
+def test_noalloc_leaves_free_memory_unchanged():
+    """After the system exists, a call reserves no device memory, the first
+    one included (hfsem_assemble loaded the scratch array and the kernels)."""
+    torch = pytest.importorskip("torch")
+    ensure_built()
+    sys_ = _system()
+    x = torch.tensor(np.random.default_rng(5).standard_normal(sys_.total_ndof), device="cuda")
+    y = torch.empty_like(x)
+    torch.cuda.synchronize()
+    for call in range(2):
+        free0 = torch.cuda.mem_get_info()[0]
+        H.hfsem_apply_noalloc(sys_, x, nrhs=1, out=y)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0, call
+
+
 def test_noalloc_rejects_oversized_requests():
     torch = pytest.importorskip("torch")
     ensure_built()
