@@ -128,3 +128,31 @@ def test_timing_read_rejects_null_tag(lib):
     assert ms.value == -1.0
     assert lib.hfsem_timing_read(b"no-such-kernel", C.byref(ms), None, None) == H.HFSEM_OK
     assert ms.value == 0.0
+
+
+@pytest.mark.parametrize("bad", [dict(slots=0), dict(slots=65), dict(budget_bytes=-1),
+                                 dict(cache_factors=-1), dict(tol=0.0), dict(max_iter=0),
+                                 dict(R=0), dict(R=33), dict(build_only=1)])
+def test_server_create_rejects_bad_options(lib, bad):
+    ho = H.hopts(R=bad.get("R", 8), build_only=bad.get("build_only", 0))
+    o = H.hfsem_server_opts(bad.get("slots", 4), bad.get("budget_bytes", 0),
+                            bad.get("cache_factors", 8), ho, bad.get("tol", 1e-12),
+                            bad.get("max_iter", 50))
+    out = C.c_void_p()
+    assert lib.hfsem_server_create(C.byref(o), C.byref(out)) == H.HFSEM_ERR_INVALID_ARG
+    assert out.value is None
+
+
+def test_server_null_handles(lib):
+    out = C.c_void_p()
+    assert lib.hfsem_server_create(None, C.byref(out)) == H.HFSEM_ERR_INVALID_ARG
+    rid = C.c_int64(-7)
+    assert lib.hfsem_server_submit(None, None, C.byref(rid)) == H.HFSEM_ERR_INVALID_ARG
+    assert rid.value == -7
+    n = C.c_int32(-1)
+    d = (H.hfsem_done * 4)()
+    assert lib.hfsem_server_poll(None, 4, d, C.byref(n)) == H.HFSEM_ERR_INVALID_ARG
+    assert lib.hfsem_server_drain(None) == H.HFSEM_ERR_INVALID_ARG
+    c = H.hfsem_server_counters()
+    assert lib.hfsem_server_counters_read(None, C.byref(c)) == H.HFSEM_ERR_INVALID_ARG
+    lib.hfsem_server_free(None)
