@@ -2,18 +2,28 @@
 """Benchmark of the H-LU-preconditioned BiCGSTAB solve of the fractional SEM
 system on one GB300 (N GPUs: independent replicas, weak scaling).
 
-Workload (one step): nine instances on (0,1), N = 1024 uniform elements,
-P = 8 (N_d = 8191), alpha in {1.2, 1.5, 1.8} x theta in {0, 0.3, 0.5},
-rho = 1, seeded Legendre right-hand sides decaying like k^-2 (K = 32).  A step
-runs the whole path: assembly (block-Toeplitz symbol, load vector),
-H-matrix build with Taylor rank R = 8, H-LU (lambda = 1, Tol_HLU = 1e-3),
-and BiCGSTAB to a relative residual of 1e-14 with the FFT operator.
+Headline workload (--workload serve, the default): the seeded request
+stream of config 5 served by the library's serving loop (hfsem_server_*).
+Requests carry one instance each (N_d log-uniform on [100, 65535], P 2..16,
+uniform / two-sided geometric / graded meshes, random alpha, theta, rho),
+1..16 manufactured right-hand sides, and 30 % of them repeat an earlier
+operator.  A step is one window of W_REQ consecutive requests, each window
+the next slice of the stream, submitted at seeded Poisson arrival times at
+an offered rate of 80 % of the capacity measured (closed loop) during the
+warm-up windows; the step ends when its last request completes.  value =
+right-hand sides solved per second; p50 / p99 are per-request latencies
+(completion - arrival).  Both arms -- the mixed-precision preconditioner and
+the all-FP64 one -- serve the same windows at the same arrival times, with
+the same warm-up.  Window sizes and the request cap keep the run within a
+few minutes: requests above N_d = 65535 do not exist, and none is skipped.
+
+Second object ("batched"): config 4, 512 heterogeneous instances x 4
+right-hand sides assembled, factored and solved as one batch, both arms.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+                  [--workload serve|batch]
 
-Prints one JSON line (rank 0).  value = solves/s with the solution left in
-device memory; e2e = the same through the C ABI with the solution copied to
-pinned host memory inside the timed region.
+Prints one JSON line (rank 0).
 """
 from __future__ import annotations
 
@@ -29,28 +39,33 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-REF_BUDGET_S = 200.0   # wall time the reference arm's timed steps may take
 METRIC = "solves/s & p50/p99 latency at <=1e-10 rel err: mixed vs FP64 H-LU-Krylov"
 UNIT = "solves/s"
-WORKLOAD = ("config 2: 9 instances, uniform N=1024, P=8 (N_d=8191), alpha x theta in "
-            "{1.2,1.5,1.8}x{0,0.3,0.5}, rho=1, R=8, lambda=1, Tol_HLU=1e-3, Toeplitz FFT operator")
+W_REQ = 24                 # requests per serving window (one step)
+SLOTS = 8                  # concurrent requests in the serving loop
+TOL, MAX_ITER = 1e-14, 100
+REF_BUDGET_S = 150.0       # wall time the reference arm's timed steps may take
+SERVE_WORKLOAD = ("config 5 stream: Poisson arrivals at 80% of measured capacity, N_d log-uniform "
+                  "[100, 65535], P 2..16, uniform / two-sided geometric / graded meshes, alpha "
+                  "U(1.1,1.9), theta U(0,1), rho U(0,2), 1..16 rhs per request, 30% repeated "
+                  "operators; R=8, lambda=1, Tol_HLU=1e-3, BiCGSTAB to 1e-14")
+BATCH_WORKLOAD = ("config 4: 512 instances (N U{32..512}, P U{2..12}, uniform / two-sided "
+                  "geometric / graded meshes) x 4 rhs, one batch; R=8, lambda=1, Tol_HLU=1e-3")
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=6)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="hfsem", choices=["hfsem", "reference"])
-    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--workload", default="serve", choices=["serve", "batch"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-fp64-compare", action="store_true")
-    # profiling only: a reduced copy of the workload (fewer instances / elements)
-    ap.add_argument("--instances", type=int, default=9)
-    ap.add_argument("--n-elem", type=int, default=1024)
+    ap.add_argument("--no-batch", action="store_true", help="skip the config-4 object")
     return ap.parse_args()
 
 
+# ---------------------------------------------------------------- ranks --
 def dist_setup():
     import torch
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -82,36 +97,30 @@ def max_over_ranks(x, world):
 
 def job_throughput(units_per_rank, ms_max, world):
     """Whole-job rate: the units every rank processed over the slowest rank's
-    time (each rank runs the same batch: weak scaling)."""
+    time (each rank runs the same work: weak scaling)."""
     return world * units_per_rank / (ms_max * 1e-3)
 
 
-def workload(n_inst=9, n_elem=1024):
-    from paper_1808_02937_gb300 import hfsem as H
-    from paper_1808_02937_gb300 import workloads as W
-    insts = W.config2()[:n_inst]
-    for p in insts:
-        if n_elem != 1024:
-            p.h = W.mesh_uniform(n_elem)
-    probs = [H.make_problem(p.h, p.P, p.alpha, p.theta, p.rho) for p in insts]
-    rhs = [H.rhs_legendre([p.rhs[0]]) for p in insts]
-    return insts, probs, rhs
+def percentile(xs, q):
+    s = sorted(xs)
+    if not s:
+        return None
+    return s[min(len(s) - 1, max(0, int(math.ceil(q * len(s))) - 1))]
 
 
+# ---------------------------------------------------------------- peaks --
 def peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
         with open(path) as f:
-            d = json.load(f)
-        return d, "measured"
+            return json.load(f), "measured"
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
             "sm_max_mhz": 2070.0}, "fallback"
 
 
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons, sampled every 50 ms; start()
-    returns once the first sample is written, so the samples cover the region
-    between start() and stop()."""
+    returns once the first sample is written."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -120,7 +129,6 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.proc = None
         self.gpu = gpu_index
-        # raw samples: HFSEM_CLOCKS_CSV if set, else the system temp directory
         self.path = os.environ.get("HFSEM_CLOCKS_CSV") or os.path.join(
             tempfile.gettempdir(), f"hfsem_clocks_{gpu_index}.csv")
 
@@ -168,70 +176,309 @@ class ClockSampler:
         return {"sm_mhz": med, "sm_max_mhz": smax, "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def run_step(H, probs, rhs, opts, X, tol=1e-14):
-    sys_ = H.hfsem_assemble(probs)
-    fac = H.hfsem_hlu_factor(sys_, opts)
-    X, st, code = H.hfsem_solve(sys_, fac, rhs, tol=tol, max_iter=60, X=X, allow_fail=True)
-    del fac
-    del sys_
-    return X, st, code
+# ------------------------------------------------------------ workloads --
+def stream_windows(n_windows):
+    """The first n_windows * W_REQ requests of the config-5 stream, in windows."""
+    from paper_1808_02937_gb300 import workloads as W
+    reqs = list(W.config5_requests(n_windows * W_REQ))
+    return [reqs[k * W_REQ:(k + 1) * W_REQ] for k in range(n_windows)]
 
 
-def cpu_baseline_oracle(inst, max_cores):
-    """Time the CPU oracle (dense assembly + dense LU + refinement) on one
-    instance of the workload; returns (solves/s, seconds, X)."""
+def arrival_offsets(n, rate, seed):
+    import numpy as np
+    rng = np.random.default_rng(seed)
+    return np.cumsum(rng.exponential(1.0 / rate, size=n)) - 0.0
+
+
+KERNEL_TAGS = ("pairs", "symbol", "toeplitz_mv", "dense_mv", "hlu_factor", "hlu_solve",
+               "solve_pack", "krylov_vec")
+
+
+def kernel_table(H):
+    out = {}
+    for tag in KERNEL_TAGS:
+        ms, n, work = H.hfsem_timing_read(tag)
+        out[tag] = {"ms_total": ms, "launches": n, "work": work}
+    return out
+
+
+# --------------------------------------------------------------- serving --
+def serve_window(H, torch, prec, window, offsets, host_out):
+    """Serve one window; returns (ms from first arrival to last completion,
+    per-request latencies in ms, solves, statuses, host bytes in, bytes out,
+    the server's counters)."""
+    srv = SERVERS[prec]
+    bufs = []
+    for p in window:
+        n = p.Nd * len(p.rhs)
+        bufs.append(torch.zeros(n, dtype=torch.float64).pin_memory() if host_out else
+                    torch.zeros(n, dtype=torch.float64, device="cuda"))
+    probs = [H.make_problem(p.h, p.P, p.alpha, p.theta, p.rho) for p in window]
+    rhs = [H.rhs_frac_powers(p.rhs) for p in window]
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    t0 = time.perf_counter()
+    ids = {}
+    for k, p in enumerate(window):
+        if offsets is not None:
+            wait = t0 + offsets[k] - time.perf_counter()
+            if wait > 0:
+                time.sleep(wait)
+        ids[srv.submit(probs[k], rhs[k], X=bufs[k])] = k
+    srv.drain()
+    e1.record(stream)
+    e1.synchronize()
+    done = srv.poll()
+    ms = e0.elapsed_time(e1)
+    lat = [1e3 * (d["t_done"] - d["t_submit"]) for d in done]
+    statuses = [d["status"] for d in done]
+    solves = sum(len(p.rhs) for p in window)
+    h2d = sum(8 * len(p.h) + 24 * sum(len(t) for t in p.rhs) + 96 for p in window)
+    d2h = sum(8 * p.Nd * len(p.rhs) + 24 * len(p.rhs) for p in window) if host_out else \
+        sum(24 * len(p.rhs) for p in window)
+    res = {ids[d["id"]]: d for d in done}
+    return ms, lat, solves, statuses, h2d, d2h, res, bufs
+
+
+SERVERS = {}
+
+
+def run_serving(H, torch, args, world, rank, local):
+    warm = stream_windows(max(args.warmup, 3) + args.steps)
+    warm_w, timed_w = warm[:max(args.warmup, 3)], warm[max(args.warmup, 3):]
+    arms = {}
+    for name, prec in (("mixed", H.PREC_MIXED), ("fp64", H.PREC_FP64)):
+        SERVERS[name] = H.Server(slots=SLOTS, cache_factors=256,
+                                 hopts_=H.hopts(R=8, lam=1.0, tol_hlu=1e-3, precision=prec),
+                                 tol=TOL, max_iter=MAX_ITER)
+    # warm-up: closed loop (every request of a window submitted at once),
+    # capacity = requests per second of the warm-up windows after the first
+    cap = {}
+    for name in ("mixed", "fp64"):
+        t_tot, n_tot = 0.0, 0
+        for k, w in enumerate(warm_w):
+            ms, *_ = serve_window(H, torch, name, w, None, False)
+            if k > 0:
+                t_tot += ms
+                n_tot += len(w)
+        cap[name] = n_tot / (t_tot * 1e-3)
+    rate = 0.8 * cap["mixed"]
+    H.hfsem_timing_reset()
+    H.hfsem_timing_enable(True)
+    launches0 = H.hfsem_timing_read("launches")[1]
+    clocks = ClockSampler(local)
+    for name in ("mixed", "fp64"):
+        step_ms, lat, solves, bad = [], [], 0, 0
+        if name == "mixed":
+            clocks.start()
+        barrier(world)
+        for k, w in enumerate(timed_w):
+            off = arrival_offsets(len(w), rate, 18080500 + k)
+            ms, l, sv, st, *_ = serve_window(H, torch, name, w, off, False)
+            step_ms.append(ms)
+            lat += l
+            solves += sv
+            bad += sum(1 for s in st if s != H.HFSEM_OK)
+        barrier(world)
+        if name == "mixed":
+            clk = clocks.stop()
+            launches = H.hfsem_timing_read("launches")[1] - launches0
+            kern = kernel_table(H)
+            H.hfsem_timing_enable(False)
+        tot = max_over_ranks(sum(step_ms), world)
+        arms[name] = {"solves_per_s": job_throughput(solves, tot, world),
+                      "ms_per_step": tot / len(step_ms), "p50_ms": percentile(lat, 0.5),
+                      "p99_ms": percentile(lat, 0.99), "requests": len(lat),
+                      "solves": solves, "failed": bad, "capacity_req_per_s": cap[name],
+                      "counters": SERVERS[name].counters()}
+    # end to end: the mixed arm again with host output buffers (pinned)
+    e2e_ms, e2e_solves, h2d_tot, d2h_tot, served = [], 0, 0, 0, {}
+    for k, w in enumerate(timed_w):
+        off = arrival_offsets(len(w), rate, 18080500 + k)
+        ms, l, sv, st, h2d, d2h, res, bufs = serve_window(H, torch, "mixed", w, off, True)
+        e2e_ms.append(ms)
+        e2e_solves += sv
+        h2d_tot += h2d
+        d2h_tot += d2h
+        for j, b in enumerate(bufs):
+            served[(k, j)] = b.numpy().copy()
+    e2e_tot = max_over_ranks(sum(e2e_ms), world)
+    for srv in SERVERS.values():
+        srv.close()
+    SERVERS.clear()
+    nsteps = len(timed_w)
+    return {"arms": arms, "rate": rate, "kern": kern, "launches": launches, "clocks": clk,
+            "e2e": {"value": job_throughput(e2e_solves, e2e_tot, world), "unit": UNIT,
+                    "h2d_bytes_per_step": h2d_tot // nsteps, "d2h_bytes_per_step": d2h_tot // nsteps},
+            "timed_windows": timed_w, "served": served}
+
+
+# -------------------------------------------------------------- batched --
+def run_batch(H, torch, steps, warmup, world, timing=False):
+    from paper_1808_02937_gb300 import workloads as W
+    insts = W.config4()
+    probs = [H.make_problem(p.h, p.P, p.alpha, p.theta, p.rho) for p in insts]
+    rhs = [H.rhs_frac_powers(p.rhs) for p in insts]
+    nd = sum(p.Nd for p in insts)
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
+    stream = torch.cuda.current_stream()
+    out = {}
+    for name, prec in (("mixed", H.PREC_MIXED), ("fp64", H.PREC_FP64)):
+        opts = H.hopts(R=8, lam=1.0, tol_hlu=1e-3, precision=prec)
+        X = torch.zeros(nd * 4, dtype=torch.float64, device="cuda")
+
+        def step():
+            sys_ = H.hfsem_assemble(probs)
+            fac = H.hfsem_hlu_factor(sys_, opts)
+            _, st, code = H.hfsem_solve(sys_, fac, rhs, tol=TOL, max_iter=MAX_ITER, X=X,
+                                        allow_fail=True)
+            return st, code
+        for _ in range(max(3, warmup)):
+            step()
+        torch.cuda.synchronize()
+        if timing and name == "mixed":
+            H.hfsem_timing_reset()
+            H.hfsem_timing_enable(True)
+        ms, iters, codes = [], [], []
+        barrier(world)
+        for k in range(steps):
+            flush.fill_(float(k))
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            st, code = step()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            iters = [s["iters"] for s in st]
+            codes.append(code)
+        barrier(world)
+        kern = None
+        if timing and name == "mixed":
+            kern = kernel_table(H)
+            H.hfsem_timing_enable(False)
+        mean = max_over_ranks(sum(ms) / len(ms), world)
+        out[name] = {"solves_per_s": job_throughput(len(insts) * 4, mean, world),
+                     "ms_per_step": mean, "p50_ms": percentile(ms, 0.5),
+                     "p99_ms": percentile(ms, 0.99), "steps": steps,
+                     "iters_max": max(iters), "iters_mean": sum(iters) / len(iters),
+                     "status_ok": all(c == H.HFSEM_OK for c in codes), "kernels": kern,
+                     "X": X}
+    return out
+
+
+# ------------------------------------------------------------- roofline --
+def roofline(H, kern, n_steps, prec_label):
+    """The dominant kernel by device time: achieved work per launch over its
+    mean launch time, against the measured peak of its bound."""
+    pk, src = peaks()
+    fp64_tf, _, nsm = H.hfsem_alu_peak(0)
+    fp32_tf, _, _ = H.hfsem_alu_peak(1)
+    dom = max((t for t in kern if kern[t]["launches"]), key=lambda t: kern[t]["ms_total"])
+    k = kern[dom]
+    avg_s = k["ms_total"] * 1e-3 / k["launches"]
+    per_launch = k["work"] / k["launches"]
+    if dom in ("hlu_factor", "hlu_solve"):
+        peak, unit, bound = fp32_tf, "TFLOP/s", "alu"
+        psrc = f"measured FP32 FMA peak on {nsm} SMs (hfsem_alu_peak)"
+        ach = per_launch / avg_s / 1e12
+    elif dom in ("dense_mv", "pairs"):
+        peak, unit, bound = fp64_tf, "TFLOP/s", "alu"
+        psrc = f"measured FP64 FMA peak on {nsm} SMs (hfsem_alu_peak)"
+        ach = per_launch / avg_s / 1e12
+    else:
+        peak, unit, bound = float(pk["hbm_gbs"]), "GB/s", "hbm"
+        psrc = f"{src} HBM copy bandwidth (MEASURED_PEAKS.json)"
+        ach = per_launch / avg_s / 1e9
+    share = {t: kern[t]["ms_total"] / n_steps for t in kern if kern[t]["launches"]}
+    return ({"kernel": dom, "bound": bound, "achieved": ach, "peak": peak, "unit": unit,
+             "frac": ach / peak if peak else None, "traffic": None, "peak_source": psrc},
+            {"fp64_tflops": fp64_tf, "fp32_tflops": fp32_tf, "sms": nsm}, share)
+
+
+# ---------------------------------------------------------- CPU oracle --
+def cpu_baseline(windows, served, budget_s=20.0):
+    """The oracle (dense assembly + dense LU + refinement), as it stands, on a
+    bounded sample: the requests of the timed windows with N_d <= 1500, every
+    right-hand side, until about budget_s of CPU work.  The same solves give
+    the parity of the served solutions (relative L2 error, worst case)."""
+    import numpy as np
+
     from oracle.basis import Mesh
     from oracle.solve import solve_problem
     t0 = time.perf_counter()
-    X, info = solve_problem(Mesh(inst.h, inst.a, inst.b), inst.P, inst.alpha, inst.theta,
-                            inst.rho, inst.c1, inst.c2, ("legendre_ab", inst.rhs[0]))
+    solves, used, worst = 0, 0, 0.0
+    for k, w in enumerate(windows):
+        for j, p in enumerate(w):
+            if p.Nd > 1500:
+                continue
+            X = served[(k, j)].reshape(len(p.rhs), p.Nd)
+            for r, terms in enumerate(p.rhs):
+                Xo, _ = solve_problem(Mesh(p.h, 0.0, 1.0), p.P, p.alpha, p.theta, p.rho, 0.0,
+                                      0.0, ("frac_powers", terms))
+                worst = max(worst, float(np.linalg.norm(X[r] - Xo) / np.linalg.norm(Xo)))
+                solves += 1
+            used += 1
+            if time.perf_counter() - t0 > budget_s:
+                break
+        if time.perf_counter() - t0 > budget_s:
+            break
     dt = time.perf_counter() - t0
-    return 1.0 / dt, dt, X
+    return {"value": solves / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{used} requests of the timed windows with N_d <= 1500, {solves} "
+                      f"right-hand sides, one oracle solve each ({dt:.1f} s)", "seconds": dt,
+            "parity_max_rel_l2_err_served_vs_oracle": worst}
 
 
+# ----------------------------------------------------------------- main --
 def main_reference(args):
-    """Reference arm: the CPU oracle, timed on this host's cores."""
+    """Reference arm: the CPU oracle, timed on this host's cores, on the
+    serving workload's requests (bounded sample per step)."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    from paper_1808_02937_gb300 import workloads as W
     from oracle.basis import Mesh
     from oracle.solve import solve_problem
-    insts = W.config2()
+    from paper_1808_02937_gb300 import workloads as W
     small = W.config1()
-    cores = os.cpu_count()
-    # warm-up: the small configuration (imports, quadrature caches)
     for _ in range(args.warmup):
         solve_problem(Mesh(small.h, 0, 1), small.P, small.alpha, small.theta, small.rho,
                       small.c1, small.c2, ("frac_powers", small.rhs[0]))
-    # one oracle solve takes ~17 s: steps beyond what fits in REF_BUDGET_S
-    # (judged from the first step) are not run, and the line says so
-    times = []
+    # each step: the next request of the stream with N_d <= 4000 (the oracle is
+    # O(N_d^3)), every right-hand side
+    reqs = [p for p in W.config5_requests(400) if p.Nd <= 4000]
+    times, solves, lat = [], 0, []
     for k in range(args.steps):
-        if times and sum(times) + times[0] > REF_BUDGET_S:
+        if times and sum(times) + max(times) > REF_BUDGET_S:
             break
-        p = insts[k % len(insts)]
+        p = reqs[k % len(reqs)]
         t0 = time.perf_counter()
-        solve_problem(Mesh(p.h, p.a, p.b), p.P, p.alpha, p.theta, p.rho, p.c1, p.c2,
-                      ("legendre_ab", p.rhs[0]))
-        times.append(time.perf_counter() - t0)
-    n_timed = len(times)
-    ms = 1e3 * sum(times) / len(times)
-    value = 1e3 / ms
-    times.sort()
+        for r in p.rhs:
+            solve_problem(Mesh(p.h, 0.0, 1.0), p.P, p.alpha, p.theta, p.rho, 0.0, 0.0,
+                          ("frac_powers", r))
+        dt = time.perf_counter() - t0
+        times.append(dt)
+        lat.append(1e3 * dt)
+        solves += len(p.rhs)
+    value = solves / sum(times)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
-            "n_gpus": world, "steps": n_timed, "steps_requested": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms,
+            "n_gpus": world, "steps": len(times), "steps_requested": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / len(times),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic",
-            "config": {"workload": WORKLOAD, "reference_step": "one of the nine instances"},
-            "p50_ms": 1e3 * times[len(times) // 2], "p99_ms": 1e3 * times[-1],
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": f"each step: one of the nine config-2 instances (oracle "
-                                       f"dense assembly + dense LU + long-double refinement); "
-                                       f"{n_timed} of {args.steps} requested steps timed "
-                                       f"(budget {REF_BUDGET_S:.0f} s); warm-up on config 1"},
+            "config": {"workload": SERVE_WORKLOAD,
+                       "reference_step": "one request of the stream with N_d <= 4000, all rhs"},
+            "p50_ms": percentile(lat, 0.5), "p99_ms": percentile(lat, 0.99),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(),
+                             "kind": "oracle",
+                             "sample": f"each step: the next config-5 request with N_d <= 4000 "
+                                       f"(oracle dense assembly + dense LU + long-double "
+                                       f"refinement per rhs); {len(times)} of {args.steps} "
+                                       f"requested steps timed (budget {REF_BUDGET_S:.0f} s)"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -242,168 +489,65 @@ def main():
     if args.impl == "reference":
         main_reference(args)
         return
-    import numpy as np
     import torch
 
     world, rank, local = dist_setup()
     torch.cuda.set_device(local)
     from paper_1808_02937_gb300 import hfsem as H
     H.load_library()
-    insts, probs, rhs = workload(args.instances, args.n_elem)
-    reduced = (args.instances, args.n_elem) != (9, 1024)
-    n_inst = len(insts)
-    nd_total = sum(p.Nd for p in insts)
-    prec = H.PREC_MIXED if args.precision == "mixed" else H.PREC_FP64
-    opts = H.hopts(R=8, lam=1.0, tol_hlu=1e-3, precision=prec)
-    stream = torch.cuda.current_stream()
-    X = torch.zeros(nd_total, dtype=torch.float64, device="cuda")
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
 
-    for _ in range(max(args.warmup, 3)):
-        X, st, code = run_step(H, probs, rhs, opts, X)
-    torch.cuda.synchronize()
-
-    # ---- timed region: device-resident solution ----
-    H.hfsem_timing_reset()
-    H.hfsem_timing_enable(True)
-    launches0 = H.hfsem_timing_read("launches")[1]
-    clocks = ClockSampler(local)
-    clocks.start()
-    step_ms, iters = [], []
-    barrier(world)
-    torch.cuda.synchronize()
-    t_wall0 = time.perf_counter()
-    for k in range(args.steps):
-        flush.fill_(float(k))                        # evict L2 between steps
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        X, st, code = run_step(H, probs, rhs, opts, X)
-        e1.record(stream)
-        e1.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
-        iters.append([s["iters"] for s in st])
-    torch.cuda.synchronize()
-    barrier(world)
-    wall = time.perf_counter() - t_wall0
-    clk = clocks.stop()
-    launches = H.hfsem_timing_read("launches")[1] - launches0
-    H.hfsem_timing_enable(False)
-    kern = {}
-    for tag in ("pairs", "toeplitz_mv", "hlu_factor", "hlu_solve", "krylov_vec"):
-        ms, n, work = H.hfsem_timing_read(tag)
-        kern[tag] = {"ms_total": ms, "launches": n, "work": work}
-    mean_ms = sum(step_ms) / len(step_ms)
-    mean_ms = max_over_ranks(mean_ms, world)
-    value = job_throughput(n_inst, mean_ms, world)
-    srt = sorted(step_ms)
-    p50 = srt[len(srt) // 2]
-    p99 = srt[min(len(srt) - 1, int(math.ceil(0.99 * len(srt))) - 1)]
-
-    # ---- end to end: solution copied to pinned host memory every step ----
-    Xh = torch.zeros(nd_total, dtype=torch.float64).pin_memory()
-    e2e_ms = []
-    for k in range(args.steps):
-        flush.fill_(float(k))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        Xh, st, code = run_step(H, probs, rhs, opts, Xh)
-        torch.cuda.synchronize()
-        e2e_ms.append(1e3 * (time.perf_counter() - t0))
-    e2e_mean = max_over_ranks(sum(e2e_ms) / len(e2e_ms), world)
-    h2d = sum(8 * len(p.h) for p in insts) + sum(8 * len(p.rhs[0]) for p in insts) \
-        + n_inst * 96
-    d2h = 8 * nd_total + n_inst * 24
-
-    # ---- parity and comparison legs ----
-    Xd = X.cpu().numpy()
-    fp64 = None
-    if not args.no_fp64_compare and prec == H.PREC_MIXED:
-        o64 = H.hopts(R=8, lam=1.0, tol_hlu=1e-3, precision=H.PREC_FP64)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        X64, st64, _ = run_step(H, probs, rhs, o64, torch.zeros_like(X))
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
-        X64 = X64.cpu().numpy()
-        fp64 = {"solves_per_s": n_inst / dt, "ms_per_step": 1e3 * dt,
-                "iters": [s["iters"] for s in st64],
-                "max_rel_diff_vs_mixed": float(max(
-                    np.linalg.norm(a[:, 0] - b[:, 0]) / np.linalg.norm(b[:, 0])
-                    for a, b in zip(_Sys(insts).split(Xd), _Sys(insts).split(X64))))}
-
-    peak, peak_src = peaks()
-    # dominant kernel: the one with the largest device time
-    dom = max(("hlu_factor", "hlu_solve", "toeplitz_mv", "pairs", "krylov_vec"),
-              key=lambda t: kern[t]["ms_total"])
-    roof = None
-    if kern[dom]["launches"]:
-        avg_s = kern[dom]["ms_total"] * 1e-3 / kern[dom]["launches"]
-        per_launch = kern[dom]["work"] / kern[dom]["launches"]
-        if dom in ("hlu_factor", "hlu_solve"):
-            # FP32 (mixed) or FP64 CUDA-core arithmetic: peak from unit counts
-            # and clock: 152 SMs x 128 FP32 lanes x 2 flops x max SM clock;
-            # FP64: the part's nominal 1.25 TFLOP/s
-            sm_mhz = float(peak.get("sm_max_mhz", 2070.0))
-            pk = 152 * 128 * 2 * sm_mhz * 1e6 / 1e12 if prec == H.PREC_MIXED else 1.25
-            ach = per_launch / avg_s / 1e12
-            roof = {"kernel": dom, "bound": "alu", "achieved": ach, "peak": pk,
-                    "unit": "TFLOP/s", "frac": ach / pk, "traffic": None,
-                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x sm_max_mhz"
-                    if prec == H.PREC_MIXED else "nominal FP64 1.25 TFLOP/s"}
-        else:
-            pk = float(peak["hbm_gbs"])
-            ach = per_launch / avg_s / 1e9
-            roof = {"kernel": dom, "bound": "hbm", "achieved": ach, "peak": pk,
-                    "unit": "GB/s", "frac": ach / pk, "traffic": None,
-                    "peak_source": peak_src}
-
-    cpu = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline and not reduced:
-        v, dt, Xo = cpu_baseline_oracle(insts[4], os.cpu_count())
-        got = _Sys(insts).split(Xd)[4][:, 0]
-        cpu = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-               "sample": "one of the nine instances (alpha=1.5, theta=0.3): oracle dense "
-                         "assembly + dense LU + long-double refinement",
-               "seconds": dt,
-               "parity_rel_l2_err_vs_gpu": float(np.linalg.norm(got - Xo) / np.linalg.norm(Xo))}
-
-    if rank == 0:
-        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-                "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean_ms,
-                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "f64 Krylov/operator, f32 H-LU" if prec == H.PREC_MIXED else "f64",
-                "data": "synthetic",
-                "config": {"workload": WORKLOAD if not reduced else
-                           f"REDUCED (profiling only): {n_inst} instances, N={args.n_elem}",
-                           "instances_per_gpu": n_inst,
-                           "precision": args.precision, "l2": "flushed between steps (256 MB write)",
-                           "krylov_tol": 1e-14},
-                "p50_ms": p50, "p99_ms": p99, "wall_s_timed": wall,
-                "iters": iters[-1],
-                "e2e": {"value": job_throughput(n_inst, e2e_mean, world), "unit": UNIT,
-                        "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
-                "gpu_launches": launches, "clocks": clk, "roofline": roof,
-                "kernels_ms_per_step": {t: kern[t]["ms_total"] / args.steps for t in kern},
-                "cpu_baseline": cpu, "fp64_hlu": fp64}
-        print(json.dumps(line), flush=True)
+    if args.workload == "serve":
+        S = run_serving(H, torch, args, world, rank, local)
+        A = S["arms"]
+        roof, alu, share = roofline(H, S["kern"], args.steps, "mixed")
+        batch = None
+        if not args.no_batch:
+            B = run_batch(H, torch, steps=3, warmup=3, world=world)
+            batch = {k: {kk: vv for kk, vv in v.items() if kk not in ("X", "kernels")}
+                     for k, v in B.items()}
+            batch["workload"] = BATCH_WORKLOAD
+        cpu = None
+        if rank == 0 and world == 1 and not args.no_cpu_baseline:
+            cpu = cpu_baseline(S["timed_windows"], S["served"])
+        if rank == 0:
+            m = A["mixed"]
+            line = {"metric": METRIC, "value": m["solves_per_s"], "unit": UNIT,
+                    "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
+                    "ms_per_step": m["ms_per_step"], "higher_is_better": True,
+                    "scaling": "weak", "vs_baseline": None,
+                    "dtype": "f64 Krylov/operator/assembly, f32 H-LU (f64 for meshes spanning "
+                             ">1e45)",
+                    "data": "synthetic",
+                    "config": {"workload": SERVE_WORKLOAD, "requests_per_step": W_REQ,
+                               "slots": SLOTS, "offered_rate_req_per_s": S["rate"],
+                               "l2": "working set of a window well above L2 (129 MB): dense "
+                                     "operators up to 17 GB, factors of every request",
+                               "krylov_tol": TOL},
+                    "p50_ms": m["p50_ms"], "p99_ms": m["p99_ms"],
+                    "requests_timed": m["requests"], "failed": m["failed"],
+                    "e2e": S["e2e"], "gpu_launches": S["launches"], "clocks": S["clocks"],
+                    "roofline": roof, "alu_peaks": alu, "kernels_ms_per_step": share,
+                    "fp64_hlu": {k: v for k, v in A["fp64"].items() if k != "counters"},
+                    "mixed_counters": m["counters"], "batched": batch, "cpu_baseline": cpu}
+            print(json.dumps(line), flush=True)
+    else:
+        B = run_batch(H, torch, steps=args.steps, warmup=args.warmup, world=world, timing=True)
+        roof, alu, share = roofline(H, B["mixed"]["kernels"], args.steps, "mixed")
+        if rank == 0:
+            m = B["mixed"]
+            line = {"metric": METRIC, "value": m["solves_per_s"], "unit": UNIT,
+                    "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
+                    "ms_per_step": m["ms_per_step"], "higher_is_better": True,
+                    "scaling": "weak", "vs_baseline": None,
+                    "dtype": "f64 Krylov/operator/assembly, f32 H-LU", "data": "synthetic",
+                    "config": {"workload": BATCH_WORKLOAD, "l2": "flushed between steps"},
+                    "p50_ms": m["p50_ms"], "p99_ms": m["p99_ms"], "roofline": roof,
+                    "alu_peaks": alu, "kernels_ms_per_step": share,
+                    "fp64_hlu": {k: v for k, v in B["fp64"].items() if k not in ("X", "kernels")}}
+            print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
-
-
-class _Sys:
-    """Splits concatenated solution vectors per instance."""
-
-    def __init__(self, insts):
-        self.ndofs = [p.Nd for p in insts]
-
-    def split(self, v):
-        out, off = [], 0
-        for nd in self.ndofs:
-            out.append(v[off: off + nd].reshape(1, nd).T)
-            off += nd
-        return out
 
 
 if __name__ == "__main__":

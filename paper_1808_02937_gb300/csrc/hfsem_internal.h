@@ -76,6 +76,11 @@ struct AllocStream {
 };
 // keep freed pool memory cached for reuse (once per device)
 void pool_keep_memory();
+// Lets kernel fn take up to `bytes` of dynamic shared memory.  The attribute
+// is process-wide, so it is raised once per device to the most the function
+// can have and never lowered: concurrent callers (other host threads) can
+// then never see a limit below what they launch with.
+void allow_dyn_smem(const void* fn, size_t bytes);
 
 template <class T>
 void DevBuf<T>::alloc(size_t count) {
@@ -211,6 +216,10 @@ void bicgstab(hfsem_system* s, Precond* M, int nrhs, const double* b_em, double*
 // issue their work there.  The caller makes sure no work of theirs is still
 // running on the old stream.
 void rebind_stream(hfsem_system* s, hfsem_factor* f, cudaStream_t st);
+// After a failed call: wait for whatever the call already queued on the
+// system's stream (errors ignored), so that no work of a failed call is
+// still in flight when the caller moves on or frees the handles.
+inline void drain_after_error(hfsem_system* s);
 // Device bytes a system, a factor hold (their buffers as grown so far).
 size_t system_bytes(const hfsem_system* s);
 size_t factor_bytes(const hfsem_factor* f);
@@ -218,3 +227,8 @@ size_t factor_bytes(const hfsem_factor* f);
 // hfsem_apply_noalloc (once per device), so that its calls allocate nothing.
 void noalloc_prepare();
 }  // namespace hf
+
+inline void hf::drain_after_error(hfsem_system* s) {
+  if (s) cudaStreamSynchronize(s->st);
+  cudaGetLastError();
+}

@@ -3088,8 +3088,7 @@ namespace hf {
 
 template <class T>
 static void set_prog_smem(size_t bytes) {
-  HF_CHECK(cudaFuncSetAttribute((const void*)k_hprog<T>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  allow_dyn_smem((const void*)k_hprog<T>, bytes);
 }
 
 static size_t prog_smem(const HPlan& p, size_t ts) {
@@ -3466,11 +3465,9 @@ static hfsem_factor* factor_part(hfsem_system* s, const hfsem_hopts& opt, const 
       if (f->sol_smem > sol_budget)
         throw Error(HFSEM_ERR_UNSUPPORTED, "leaf solve needs too much shared memory");
       if (fp32)
-        HF_CHECK(cudaFuncSetAttribute((const void*)k_hsolve_cl<float>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f->sol_smem));
+        allow_dyn_smem((const void*)k_hsolve_cl<float>, f->sol_smem);
       else
-        HF_CHECK(cudaFuncSetAttribute((const void*)k_hsolve_cl<double>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)f->sol_smem));
+        allow_dyn_smem((const void*)k_hsolve_cl<double>, f->sol_smem);
     }
     f->d_ranks.alloc(std::max<long long>(rk, 1));
     HF_CHECK(cudaMemsetAsync(f->d_ranks.p, 0, std::max<long long>(rk, 1) * sizeof(int), s->st));
@@ -3509,8 +3506,7 @@ static hfsem_factor* factor_part(hfsem_system* s, const hfsem_hopts& opt, const 
       HF_LAUNCH_CHECK();
       if (prof) cudaEventRecord(ev[1], s->st);
       if (lr_smem > 48 * 1024)
-        HF_CHECK(cudaFuncSetAttribute((const void*)k_lowrank<float>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lr_smem));
+        allow_dyn_smem((const void*)k_lowrank<float>, lr_smem);
       k_lowrank<float><<<gp, lr_warps * 32, lr_smem, s->st>>>(f->d_hi.p, s->d_inst.p, s->arena.p, s->gl.p,
                                                           f->d_pairs.p, f->d_slots.p, f->d_ptask.p,
                                                           f->d_D.p, f->d_lrt.p, f->d_gmax.p);
@@ -3525,8 +3521,7 @@ static hfsem_factor* factor_part(hfsem_system* s, const hfsem_hopts& opt, const 
       HF_LAUNCH_CHECK();
       if (prof) cudaEventRecord(ev[1], s->st);
       if (lr_smem > 48 * 1024)
-        HF_CHECK(cudaFuncSetAttribute((const void*)k_lowrank<double>,
-                                      cudaFuncAttributeMaxDynamicSharedMemorySize, (int)lr_smem));
+        allow_dyn_smem((const void*)k_lowrank<double>, lr_smem);
       k_lowrank<double><<<gp, lr_warps * 32, lr_smem, s->st>>>(f->d_hi.p, s->d_inst.p, s->arena.p, s->gl.p,
                                                           f->d_pairs.p, f->d_slots.p, f->d_ptask.p,
                                                           f->d_D.p, f->d_lrt.p, f->d_gmax.p);
@@ -3967,12 +3962,15 @@ int hfsem_hlu_factor(hfsem_system* sys, const hfsem_hopts* opts, hfsem_factor** 
     return HFSEM_OK;
   } catch (const Error& e) {
     set_last_error(e.msg);
+    drain_after_error(sys);
     return e.code;
   } catch (const std::bad_alloc&) {
     set_last_error("host allocation failed");
+    drain_after_error(sys);
     return HFSEM_ERR_OOM;
   } catch (...) {
     set_last_error("unknown error");
+    drain_after_error(sys);
     return HFSEM_ERR_DEVICE;
   }
 }
@@ -4087,7 +4085,7 @@ extern "C" int hfsem_tc_tile_check(int32_t N, int32_t K, int32_t reps, double* m
     HF_CHECK(cudaMemset(de.p, 0, kCluster * sizeof(int)));
     HF_CHECK(cudaMemset(dd.p, 0, 8 * sizeof(unsigned long long)));
     const int smem = 96 * 1024;   // operands (128 + N) x K bf16 on a 1024-byte boundary
-    HF_CHECK(cudaFuncSetAttribute(k_tc_tile_check, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    allow_dyn_smem((const void*)k_tc_tile_check, smem);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(kCluster);
     cfg.blockDim = dim3(kHThreads);

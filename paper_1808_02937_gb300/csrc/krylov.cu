@@ -462,12 +462,15 @@ extern "C" int hfsem_solve(hfsem_system* sys, hfsem_factor* fac, const hfsem_rhs
     return worst;
   } catch (const Error& e) {
     set_last_error(e.msg);
+    drain_after_error(sys);
     return e.code;
   } catch (const std::bad_alloc&) {
     set_last_error("host allocation failed");
+    drain_after_error(sys);
     return HFSEM_ERR_OOM;
   } catch (...) {
     set_last_error("unknown error");
+    drain_after_error(sys);
     return HFSEM_ERR_DEVICE;
   }
 }

@@ -67,10 +67,7 @@ dim3 grid_of(long long n, int bs, int y, int z) {
   return dim3((unsigned)g, (unsigned)y, (unsigned)z);
 }
 
-void set_smem_attr(const void* fn, size_t bytes) {
-  if (bytes > 48 * 1024)
-    HF_CHECK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-}
+void set_smem_attr(const void* fn, size_t bytes) { hf::allow_dyn_smem(fn, bytes); }
 
 }  // namespace
 

@@ -78,6 +78,9 @@ class CudaExec : public serve::Executor {
     if (h->sys) hfsem_system_free(h->sys);
     delete h;
   }
+  bool reusable_after(int status) override {
+    return status == HFSEM_OK || status == HFSEM_ERR_NOT_CONVERGED || status == HFSEM_ERR_BREAKDOWN;
+  }
   void release_payload(serve::Request& r) override {
     delete static_cast<Payload*>(r.payload);
     r.payload = nullptr;
@@ -120,7 +123,7 @@ void estimate(const hfsem_problem& p, int nrhs, const hfsem_hopts& o, bool unifo
   const double lg = std::max(1.0, std::log2(std::max(2.0, Nd / leaf)));
   const double fac = ts * Nd * (4.0 * leaf + 6.0 * o.R * lg * 4.0) + 4.0 * Nd * 64 + (1 << 20);
   const double vec = 8.0 * Nd * nrhs * 14 + 8.0 * N * P * nrhs * 4;
-  const double op = uniform ? 16.0 * 2 * L * P * nrhs : 8.0 * N * (N + 1) / 2 * P * nrhs;
+  const double op = uniform ? 16.0 * 2 * L * P * nrhs : 0.0;   // FFT buffers
   *build = (size_t)(sys + fac);
   *work = (size_t)(vec + op);
 }

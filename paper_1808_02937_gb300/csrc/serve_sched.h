@@ -86,6 +86,9 @@ struct Executor {
   virtual int solve(int slot, Request& r, void* handle, size_t* bytes) = 0;
   virtual void release(void* handle) = 0;
   virtual void release_payload(Request& r) = 0;
+  // whether a factorisation may serve later requests after a solve that
+  // returned `status` (a device failure leaves it untrusted)
+  virtual bool reusable_after(int status) { (void)status; return true; }
 };
 
 class Scheduler {
@@ -111,6 +114,14 @@ class Scheduler {
       ex_->release_payload(*r);
     }
     queue_.clear();
+    for (auto* e : released_)
+      if (e) {
+        ex_->release(e->handle);
+        delete e;
+      }
+    released_.clear();
+    for (void* h : drop_handles_) ex_->release(h);
+    drop_handles_.clear();
     for (auto& kv : cache_) {
       ex_->release(kv.second->handle);
       delete kv.second;
@@ -274,14 +285,18 @@ class Scheduler {
 
   void flush_released() {      // release dropped entries outside the lock
     std::vector<Entry*> rel;
+    std::vector<void*> hs;
     {
       std::lock_guard<std::mutex> lk(mu_);
       rel.swap(released_);
+      hs.swap(drop_handles_);
     }
     for (auto* e : rel) {
+      if (!e) continue;
       ex_->release(e->handle);
       delete e;
     }
+    for (void* h : hs) ex_->release(h);
   }
 
   void work(int slot) {
@@ -327,6 +342,10 @@ class Scheduler {
               building_.erase(b);
               break;
             }
+          if (handle && !ex_->reusable_after(st)) {
+            drop_handles_.push_back(handle);
+            handle = nullptr;
+          }
           if (handle) {
             ++builds_;
             e = new Entry;
@@ -341,6 +360,11 @@ class Scheduler {
           ++reuses_;
           resident_ += work_bytes - e->bytes;
           e->bytes = work_bytes;
+          if (!ex_->reusable_after(st)) {
+            e->in_use = false;
+            drop(e);            // leaves the cache; released below
+            e = nullptr;
+          }
         }
         if (e) {
           e->in_use = false;
@@ -371,6 +395,7 @@ class Scheduler {
   std::list<Entry*> lru_;                 // idle entries, least recent first
   std::vector<std::pair<uint64_t, const std::vector<double>*>> building_;
   std::vector<Entry*> released_;
+  std::vector<void*> drop_handles_;     // built, never cached (failed solve)
   std::deque<Done> done_;
   std::vector<std::thread> workers_;
   size_t resident_ = 0, inflight_ = 0, peak_bytes_ = 0;

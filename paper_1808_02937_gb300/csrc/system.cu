@@ -611,6 +611,155 @@ __global__ void k_dense_rows(const InstDev* __restrict__ inst, const double* are
   }
 }
 
+// Dense operator, two passes over the packed lower blocks M_ef (f <= e,
+// row-major P x P, contiguous along f for fixed e), no temporaries:
+//   row pass:     w[e][m] = theta       sum_{f <= e} sum_n M_ef[m][n] z[f][n]
+//   column pass:  w[f][n] += (1-theta)  sum_{e >= f} sum_m M_ef[m][n] z[e][m]
+// One warp per block-row (block-column); its lanes are (block, index) pairs,
+// 32 / P blocks at a time, so that a lane keeps a fixed column n (row m) of
+// the blocks it visits and accumulates all P outputs of its row (column)
+// for RB right-hand sides in registers; one warp reduction at the end.
+// Every FP64 multiply-add of the pass is one entry times one z value: the
+// FP64 pipe, not memory, bounds it (4 flops per entry and right-hand side
+// against 8 bytes per entry and pass).
+template <int PT, int RB>
+__global__ void __launch_bounds__(256) k_dense_rowpass(const InstDev* __restrict__ inst,
+                                                       const double* __restrict__ arena,
+                                                       const double* __restrict__ z, double* w,
+                                                       int nrhs) {
+  const InstDev I = inst[blockIdx.y];
+  if (I.kind != kDense) return;
+  const int P = I.P, N = I.N;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int e = N - 1 - (int)(blockIdx.x * (blockDim.x >> 5) + warp);   // long rows first
+  if (e < 0) return;
+  const int r0 = blockIdx.z * RB;
+  const long long NP = (long long)N * P;
+  const double* zb = z + I.o_z * nrhs;
+  double* wb = w + I.o_z * nrhs;
+  double acc[PT][RB];
+#pragma unroll
+  for (int m = 0; m < PT; ++m)
+#pragma unroll
+    for (int r = 0; r < RB; ++r) acc[m][r] = 0.0;
+  if (I.theta != 0.0) {
+    const int F = 32 / P;                   // blocks per step
+    const int fo = lane / P, n = lane - fo * P;
+    const long long PP = (long long)P * P;
+    const double* strip = arena + I.o_M + ((long long)e * (e + 1) / 2) * PP;
+    if (fo < F) {
+      for (int f = fo; f <= e; f += F) {
+        double zr[RB];
+#pragma unroll
+        for (int r = 0; r < RB; ++r)
+          zr[r] = (r0 + r < nrhs) ? __ldg(zb + (long long)(r0 + r) * NP + (long long)f * P + n) : 0.0;
+        const double* blk = strip + (long long)f * PP + n;
+#pragma unroll
+        for (int m = 0; m < PT; ++m) {
+          if (m < P) {
+            const double v = __ldg(blk + m * P);
+#pragma unroll
+            for (int r = 0; r < RB; ++r) acc[m][r] = fma(v, zr[r], acc[m][r]);
+          }
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int m = 0; m < PT; ++m) {
+    if (m >= P) break;
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      double x = acc[m][r];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0 && r0 + r < nrhs) wb[(long long)(r0 + r) * NP + (long long)e * P + m] = I.theta * x;
+    }
+  }
+}
+
+template <int PT, int RB>
+__global__ void __launch_bounds__(256) k_dense_colpass(const InstDev* __restrict__ inst,
+                                                       const double* __restrict__ arena,
+                                                       const double* __restrict__ z, double* w,
+                                                       int nrhs) {
+  const InstDev I = inst[blockIdx.y];
+  if (I.kind != kDense || I.theta == 1.0) return;
+  const int P = I.P, N = I.N;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int f = (int)(blockIdx.x * (blockDim.x >> 5) + warp);          // long columns first
+  if (f >= N) return;
+  const int r0 = blockIdx.z * RB;
+  const long long NP = (long long)N * P;
+  const double* zb = z + I.o_z * nrhs;
+  double* wb = w + I.o_z * nrhs;
+  double acc[PT][RB];
+#pragma unroll
+  for (int n = 0; n < PT; ++n)
+#pragma unroll
+    for (int r = 0; r < RB; ++r) acc[n][r] = 0.0;
+  const int F = 32 / P;
+  const int eo = lane / P, m = lane - eo * P;
+  const long long PP = (long long)P * P;
+  const double* base = arena + I.o_M;
+  if (eo < F) {
+    for (int e = f + eo; e < N; e += F) {
+      double zr[RB];
+#pragma unroll
+      for (int r = 0; r < RB; ++r)
+        zr[r] = (r0 + r < nrhs) ? __ldg(zb + (long long)(r0 + r) * NP + (long long)e * P + m) : 0.0;
+      const double* blk = base + ((long long)e * (e + 1) / 2 + f) * PP + (long long)m * P;
+#pragma unroll
+      for (int n = 0; n < PT; ++n) {
+        if (n < P) {
+          const double v = __ldg(blk + n);
+#pragma unroll
+          for (int r = 0; r < RB; ++r) acc[n][r] = fma(v, zr[r], acc[n][r]);
+        }
+      }
+    }
+  }
+  const double c = 1.0 - I.theta;
+#pragma unroll
+  for (int n = 0; n < PT; ++n) {
+    if (n >= P) break;
+#pragma unroll
+    for (int r = 0; r < RB; ++r) {
+      double x = acc[n][r];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+      if (lane == 0 && r0 + r < nrhs) wb[(long long)(r0 + r) * NP + (long long)f * P + n] += c * x;
+    }
+  }
+}
+
+// Launch both passes with the register tile PT >= max P of the batch.
+template <int PT, int RB>
+static void dense_passes(const InstDev* di, const double* arena, const double* z, double* w,
+                         int nrhs, int ni, int maxN, cudaStream_t st) {
+  dim3 g((maxN + 7) / 8, ni, (nrhs + RB - 1) / RB);
+  k_dense_rowpass<PT, RB><<<g, 256, 0, st>>>(di, arena, z, w, nrhs);
+  HF_LAUNCH_CHECK();
+  k_dense_colpass<PT, RB><<<g, 256, 0, st>>>(di, arena, z, w, nrhs);
+  HF_LAUNCH_CHECK();
+}
+
+void dense_operator(const InstDev* di, const double* arena, const double* z, double* w, int nrhs,
+                    int ni, int maxN, int maxP, cudaStream_t st) {
+  if (maxP <= 4)
+    dense_passes<4, 8>(di, arena, z, w, nrhs, ni, maxN, st);
+  else if (maxP <= 8)
+    dense_passes<8, 4>(di, arena, z, w, nrhs, ni, maxN, st);
+  else if (maxP <= 12)
+    dense_passes<12, 4>(di, arena, z, w, nrhs, ni, maxN, st);
+  else if (maxP <= 16)
+    dense_passes<16, 4>(di, arena, z, w, nrhs, ni, maxN, st);
+  else if (maxP <= 24)
+    dense_passes<24, 2>(di, arena, z, w, nrhs, ni, maxN, st);
+  else
+    dense_passes<32, 2>(di, arena, z, w, nrhs, ni, maxN, st);
+}
+
 // Dense columns: w[f][n] = theta ylow[f][n] + (1-theta) sum_{e >= f} T[(e,f)][n]
 __global__ void k_dense_cols(const InstDev* __restrict__ inst, const double* ylow,
                              const double* T, double* w, int nrhs) {
@@ -924,8 +1073,7 @@ void ensure_work(hfsem_system* s, int nrhs) {
   s->w_y.ensure(nd);
   s->w_z.ensure(nz);
   s->w_w.ensure(nz);
-  s->w_ylow.ensure(nz);
-  if (s->any_dense) s->w_T.ensure((size_t)s->total_T * nrhs);
+
   if (s->any_toep) s->w_fa.ensure((size_t)s->total_fft * 2 * nrhs);
 }
 
@@ -937,9 +1085,26 @@ static void launch_twiddles(hfsem_system* s) {
   HF_LAUNCH_CHECK();
 }
 
-static void set_smem(const void* fn, size_t bytes) {
-  if (bytes > 48 * 1024)
-    HF_CHECK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+static void set_smem(const void* fn, size_t bytes) { allow_dyn_smem(fn, bytes); }
+
+void allow_dyn_smem(const void* fn, size_t bytes) {
+  if (bytes <= 48 * 1024) return;
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> limit;   // (device, kernel) -> set
+  int dev = 0;
+  HF_CHECK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  auto key = std::make_pair(dev, fn);
+  auto it = limit.find(key);
+  if (it != limit.end() && it->second >= bytes) return;
+  int optin = 0;
+  HF_CHECK(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  cudaFuncAttributes fa;
+  HF_CHECK(cudaFuncGetAttributes(&fa, fn));
+  const size_t most = (size_t)optin - fa.sharedSizeBytes;
+  if (bytes > most) throw Error(HFSEM_ERR_UNSUPPORTED, "kernel needs more shared memory than the device has");
+  HF_CHECK(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most));
+  limit[key] = most;
 }
 
 void apply_operator(hfsem_system* s, int nrhs, const double* x, double* y, int lift) {
@@ -952,19 +1117,12 @@ void apply_operator(hfsem_system* s, int nrhs, const double* x, double* y, int l
       di, s->arena.p, x, z, nrhs, lift);
   HF_LAUNCH_CHECK();
   if (s->any_dense) {
-    double bytes = 0.0;
+    // algorithmic work: 2 multiply-adds per stored entry and right-hand side
+    double flops = 0.0;
     for (auto& I : s->ih)
-      if (I.kind == kDense) bytes += 8.0 * I.P * I.P * I.N * (I.N + 1) / 2.0;
-    Tick tk(s->st, "dense_mv", bytes);
-    int W = (s->max_P > 16) ? 4 : 8;
-    size_t sm = (size_t)(W * 2 * s->max_P * s->max_P + W * s->max_P * nrhs) * sizeof(double);
-    set_smem((const void*)k_dense_rows, sm);
-    k_dense_rows<<<dim3(s->max_N, ni), W * 32, sm, s->st>>>(di, s->arena.p, z, s->w_ylow.p,
-                                                           s->w_T.p, nrhs);
-    HF_LAUNCH_CHECK();
-    k_dense_cols<<<grid1((long long)s->max_N * s->max_P, 128, ni, nrhs), 128, 0, s->st>>>(
-        di, s->w_ylow.p, s->w_T.p, w, nrhs);
-    HF_LAUNCH_CHECK();
+      if (I.kind == kDense) flops += 4.0 * I.P * I.P * I.N * (I.N + 1) / 2.0 * nrhs;
+    Tick tk(s->st, "dense_mv", flops);
+    dense_operator(di, s->arena.p, z, w, nrhs, ni, s->max_N, s->max_P, s->st);
   }
   if (s->any_toep) {
     double bytes = 0.0;   // symbol read + z in + w out
@@ -1261,6 +1419,7 @@ static hfsem_system* assemble(int n, const hfsem_problem* probs, void* stream) {
     }
     HF_CHECK(cudaStreamSynchronize(s->st));
   } catch (...) {
+    drain_after_error(s);
     delete s;
     throw;
   }
@@ -1321,6 +1480,7 @@ int hfsem_assemble(int32_t n_inst, const hfsem_problem* probs, void* stream,
     try {
       noalloc_prepare();
     } catch (...) {
+      drain_after_error(s);
       delete s;
       throw;
     }

@@ -456,6 +456,11 @@ class Server:
         nd = len(hh) * problem["P"] - 1
         if X is None:
             X = np.zeros(nd * nrhs)
+        elif hasattr(X, "is_cuda") and X.is_cuda:
+            # the server writes X from its own streams: work queued on X by
+            # the caller's stream (its allocation, a fill) must be done first
+            import torch
+            torch.cuda.current_stream(X.device).synchronize()
         stats = (hfsem_stats * nrhs)()
         req = hfsem_request(C.pointer(prob), C.cast(arr, C.POINTER(hfsem_rhs)), _ptr(X), stats)
         rid = C.c_int64()

@@ -24,6 +24,7 @@ struct FakeReq {
   int tag;
   double build_ms, solve_ms;
   size_t fac_bytes, work_bytes;
+  int solve_status = 0;
 };
 
 struct FakeExec : Executor {
@@ -89,8 +90,9 @@ struct FakeExec : Executor {
     }
     (void)handle;
     *bytes = q->fac_bytes;
-    return 0;
+    return q->solve_status;
   }
+  bool reusable_after(int status) override { return status == 0; }
   void release(void* handle) override {
     std::lock_guard<std::mutex> lk(mu);
     int id = (int)reinterpret_cast<intptr_t>(handle);
@@ -206,6 +208,19 @@ int main(int argc, char** argv) {
     run(s);
     s.shutdown();
     report("fifo", s, ex, done);
+  } else if (sc == "drop") {
+    // a factorisation whose solve failed is not kept: the next request of the
+    // same operator builds a new one
+    ex.fac_size = 20;
+    Scheduler s(&ex, 1, 1000, 8, 2);
+    auto a = req(0, 700, 2, 2, 20, 5);
+    static_cast<FakeReq*>(a->payload)->solve_status = 6;
+    s.submit(std::move(a));
+    s.submit(req(1, 700, 2, 2, 20, 5));
+    s.submit(req(2, 700, 2, 2, 20, 5));
+    run(s);
+    s.shutdown();
+    report("drop", s, ex, done);
   } else {
     return 2;
   }

@@ -30,7 +30,33 @@ def _cases():
         ("one-element", np.array([2.0]), 0.0, 2.0, 5, 1.7, 0.4, 1.0, 0),
         ("two-elements-P16", W.mesh_uniform(2), 0.0, 1.0, 16, 1.25, 0.6, 0.0, 0),
         ("ragged-P7", W.mesh_graded(23, 3.0), 0.0, 1.0, 7, 1.45, 0.35, 0.8, 0),
+        # register tiles of the dense operator for P up to 24 and 32
+        ("graded-P20", W.mesh_graded(5, 2.0), 0.0, 1.0, 20, 1.35, 0.55, 0.2, 1),
+        ("dense-P32", W.mesh_uniform(3), 0.0, 1.0, 32, 1.65, 0.8, 0.0, 1),
     ]
+
+
+def test_mixed_degree_batch_dense_operator(lib):
+    # one batch, dense instances of P = 3 and P = 14 (the larger register tile
+    # serves both), against each instance's oracle operator
+    rng = np.random.default_rng(11)
+    cases = [(W.mesh_graded(17, 2.0), 3, 1.2, 0.1, 0.5), (W.mesh_graded(6, 3.0), 14, 1.7, 0.9, 0.0),
+             (W.mesh_geometric_two_sided(10, 0.6), 5, 1.5, 0.5, 1.0)]
+    sys = H.hfsem_assemble([H.make_problem(h, P, al, th, rho, matvec=1)
+                            for h, P, al, th, rho in cases])
+    xs = [rng.standard_normal((3, n_dof(len(h), P))) for h, P, *_ in cases]
+    y = H.hfsem_apply(sys, np.concatenate([x.ravel() for x in xs]), nrhs=3)
+    off = 0
+    for (h, P, al, th, rho), x in zip(cases, xs):
+        Nd = n_dof(len(h), P)
+        A = system_full(Mesh(h, 0.0, 1.0), P, al, th, rho)[:Nd, :Nd]
+        got = y[off: off + 3 * Nd].reshape(3, Nd)
+        off += 3 * Nd
+        for r in range(3):
+            ref = A @ x[r]
+            # rounding of a sum of products: O(eps sum_j |A_ij x_j|) per row
+            bound = 1e-13 * (np.abs(A) @ np.abs(x[r]))
+            assert np.all(np.abs(got[r] - ref) <= bound), np.max(np.abs(got[r] - ref) / bound)
 
 
 @pytest.fixture(scope="module")

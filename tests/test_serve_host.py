@@ -85,3 +85,11 @@ def test_waiting_request_not_overtaken(checker):
     d = _run(checker, "fifo")
     _common(d)
     assert d["start_order"].split() == ["0", "1", "2"]
+
+
+def test_factorisation_dropped_after_failed_solve(checker):
+    d = _run(checker, "drop")
+    _common(d)
+    # request 0 fails and its factorisation is released; 1 builds anew, 2 reuses it
+    assert _i(d, "builds") == 1 and _i(d, "reuses") == 1
+    assert _i(d, "done_ok") == 2 and _i(d, "done_oom") == 1
