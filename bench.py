@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--workload", default="serve", choices=["serve", "batch"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the config-4 object")
+    # profiling only: the first n instances of the config-4 batch (--workload batch)
+    ap.add_argument("--batch-instances", type=int, default=512)
     return ap.parse_args()
 
 
@@ -317,9 +319,9 @@ def run_serving(H, torch, args, world, rank, local):
 
 
 # -------------------------------------------------------------- batched --
-def run_batch(H, torch, steps, warmup, world, timing=False):
+def run_batch(H, torch, steps, warmup, world, timing=False, n_inst=512):
     from paper_1808_02937_gb300 import workloads as W
-    insts = W.config4()
+    insts = W.config4()[:n_inst]
     probs = [H.make_problem(p.h, p.P, p.alpha, p.theta, p.rho) for p in insts]
     rhs = [H.rhs_frac_powers(p.rhs) for p in insts]
     nd = sum(p.Nd for p in insts)
@@ -531,7 +533,8 @@ def main():
                     "mixed_counters": m["counters"], "batched": batch, "cpu_baseline": cpu}
             print(json.dumps(line), flush=True)
     else:
-        B = run_batch(H, torch, steps=args.steps, warmup=args.warmup, world=world, timing=True)
+        B = run_batch(H, torch, steps=args.steps, warmup=args.warmup, world=world, timing=True,
+                      n_inst=args.batch_instances)
         roof, alu, share = roofline(H, B["mixed"]["kernels"], args.steps, "mixed")
         if rank == 0:
             m = B["mixed"]
@@ -540,7 +543,9 @@ def main():
                     "ms_per_step": m["ms_per_step"], "higher_is_better": True,
                     "scaling": "weak", "vs_baseline": None,
                     "dtype": "f64 Krylov/operator/assembly, f32 H-LU", "data": "synthetic",
-                    "config": {"workload": BATCH_WORKLOAD, "l2": "flushed between steps"},
+                    "config": {"workload": BATCH_WORKLOAD if args.batch_instances == 512 else
+                               f"REDUCED (profiling only): first {args.batch_instances} "
+                               f"instances of config 4", "l2": "flushed between steps"},
                     "p50_ms": m["p50_ms"], "p99_ms": m["p99_ms"], "roofline": roof,
                     "alu_peaks": alu, "kernels_ms_per_step": share,
                     "fp64_hlu": {k: v for k, v in B["fp64"].items() if k not in ("X", "kernels")}}
