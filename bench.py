@@ -48,9 +48,11 @@ REF_BUDGET_S = 150.0       # wall time the reference arm's timed steps may take
 SERVE_WORKLOAD = ("config 5 stream: Poisson arrivals at 80% of measured capacity, N_d log-uniform "
                   "[100, 65535], P 2..16, uniform / two-sided geometric / graded meshes, alpha "
                   "U(1.1,1.9), theta U(0,1), rho U(0,2), 1..16 rhs per request, 30% repeated "
-                  "operators; R=8, lambda=1, Tol_HLU=1e-3, BiCGSTAB to 1e-14")
+                  "operators; R=8, lambda=1 (min-diameter admissibility), Tol_HLU=1e-3, "
+                  "BiCGSTAB to 1e-14")
 BATCH_WORKLOAD = ("config 4: 512 instances (N U{32..512}, P U{2..12}, uniform / two-sided "
-                  "geometric / graded meshes) x 4 rhs, one batch; R=8, lambda=1, Tol_HLU=1e-3")
+                  "geometric / graded meshes) x 4 rhs, one batch; R=8, lambda=1 (min-diameter "
+                  "admissibility), Tol_HLU=1e-3")
 
 
 def parse():
@@ -254,7 +256,8 @@ def run_serving(H, torch, args, world, rank, local):
     arms = {}
     for name, prec in (("mixed", H.PREC_MIXED), ("fp64", H.PREC_FP64)):
         SERVERS[name] = H.Server(slots=SLOTS, cache_factors=256,
-                                 hopts_=H.hopts(R=8, lam=1.0, tol_hlu=1e-3, precision=prec),
+                                 hopts_=H.hopts(R=8, lam=1.0, tol_hlu=1e-3, precision=prec,
+                                                admissibility=H.ADM_MIN),
                                  tol=TOL, max_iter=MAX_ITER)
     # warm-up: closed loop (every request of a window submitted at once),
     # capacity = requests per second of the warm-up windows after the first
@@ -329,7 +332,7 @@ def run_batch(H, torch, steps, warmup, world, timing=False, n_inst=512):
     stream = torch.cuda.current_stream()
     out = {}
     for name, prec in (("mixed", H.PREC_MIXED), ("fp64", H.PREC_FP64)):
-        opts = H.hopts(R=8, lam=1.0, tol_hlu=1e-3, precision=prec)
+        opts = H.hopts(R=8, lam=1.0, tol_hlu=1e-3, precision=prec, admissibility=H.ADM_MIN)
         X = torch.zeros(nd * 4, dtype=torch.float64, device="cuda")
 
         def step():

@@ -107,7 +107,21 @@ typedef struct {
   int32_t leaf_elems; /* elements per leaf cluster; 0 = automatic           */
   int32_t kmax;       /* rank cap after recompression; 0 = automatic        */
   int32_t build_only; /* 1: build the H-matrix, do not factor (inspection)  */
+  int32_t admissibility; /* HFSEM_ADM_MAX (eq. (admis), the default) or
+                         HFSEM_ADM_MIN                                      */
 } hfsem_hopts;
+
+/* Admissibility of a cluster pair (tau, sigma) (Sec. 3.1, eq. (admis)):
+ * MAX: max(diam tau, diam sigma) <= lambda dist(tau, sigma), as printed.
+ * MIN: min(diam tau, diam sigma) <= lambda dist(tau, sigma).  The Taylor
+ * expansion is always taken about the centre of the smaller cluster (Remark
+ * after the Lemma), and the Lemma's bound (lambda / (2 + lambda))^R depends
+ * only on that cluster's diameter over the distance, so MIN keeps the bound
+ * while admitting far more blocks on geometrically graded meshes (index
+ * clusters next to the refined ends are then much smaller than their
+ * neighbours); on uniform meshes the two coincide. */
+#define HFSEM_ADM_MAX 0
+#define HFSEM_ADM_MIN 1
 
 /* ---- right-hand sides -------------------------------------------------- */
 typedef struct {

@@ -8,7 +8,11 @@ N_d unknowns in X's ordering.
     elements' right nodes (never the boundary node b).
   * The support of a cluster is the union of its functions' supports
     (Sec. 3.2): [x_e0, x_{min(e1+1, N)}].
-  * Admissibility, eq. (admis): max(diam tau, diam sigma) <= lambda * dist.
+  * Admissibility, eq. (admis): max(diam tau, diam sigma) <= lambda * dist
+    (rule "max"); rule "min" admits min(diam tau, diam sigma) <= lambda *
+    dist, the expansion then being taken about the smaller cluster (Remark
+    after the Lemma), whose diameter over the distance is all the Lemma's
+    bound (lambda/(2+lambda))^R needs.
   * Admissible block with the test cluster tau right of the trial cluster
     sigma: S_l(tau, sigma) ~ Q W^T, Q_{i,nu} = gamma0 int h_nu phi_i',
     W_{j,nu} = int g_nu phi_j' (Sec. 3.2), from the Taylor expansion
@@ -69,17 +73,18 @@ def dist(mesh: Mesh, c1: Cluster, c2: Cluster) -> float:
     return 0.0
 
 
-def admissible(mesh: Mesh, t: Cluster, s: Cluster, lam: float) -> bool:
+def admissible(mesh: Mesh, t: Cluster, s: Cluster, lam: float, rule: str = "max") -> bool:
     d = dist(mesh, t, s)
-    return d > 0.0 and max(diam(mesh, t), diam(mesh, s)) <= lam * d
+    pick = max if rule == "max" else min
+    return d > 0.0 and pick(diam(mesh, t), diam(mesh, s)) <= lam * d
 
 
-def block_leaves(mesh: Mesh, root: Cluster, lam: float):
+def block_leaves(mesh: Mesh, root: Cluster, lam: float, rule: str = "max"):
     """Leaves of the block tree: list of (tau, sigma, is_admissible)."""
     out = []
 
     def rec(t, s):
-        if admissible(mesh, t, s, lam):
+        if admissible(mesh, t, s, lam, rule):
             out.append((t, s, True))
         elif not t.kids or not s.kids:
             out.append((t, s, False))
@@ -178,7 +183,7 @@ def lowrank_factors(mesh: Mesh, P: int, alpha: float, tau: Cluster,
 
 def hmatrix_dense(mesh: Mesh, P: int, alpha: float, theta: float,
                   A_full: np.ndarray, R: int, lam: float = 1.0, leaf: int = 2,
-                  expand: str = "auto"):
+                  expand: str = "auto", rule: str = "max"):
     """Dense A~ over the N_d unknowns, built from the exact A (A_full from
     assemble.system_full) by replacing every admissible block.  Returns
     (A_tilde, blocks) with blocks = list of (tau, sigma, admissible)."""
@@ -186,7 +191,7 @@ def hmatrix_dense(mesh: Mesh, P: int, alpha: float, theta: float,
     Nd = n_dof(N, P)
     At = np.array(A_full[:Nd, :Nd], copy=True)
     root = cluster_tree(N, leaf)
-    blocks = block_leaves(mesh, root, lam)
+    blocks = block_leaves(mesh, root, lam, rule)
     for t, s, adm in blocks:
         if not adm:
             continue

@@ -3145,8 +3145,8 @@ static void plan_cache_put(const std::string& key, std::shared_ptr<PlanBundle> p
 static std::string plan_key(const InstHost& I, const PlanOpts& o) {
   std::string k(reinterpret_cast<const char*>(I.h.data()), I.h.size() * sizeof(double));
   char buf[128];
-  snprintf(buf, sizeof(buf), "|%d|%d|%.17g|%d|%d|%d|%d", I.N, I.P, o.lambda, o.leaf_elems, o.R,
-           o.kmax, o.max_concat);
+  snprintf(buf, sizeof(buf), "|%d|%d|%.17g|%d|%d|%d|%d|%d", I.N, I.P, o.lambda, o.leaf_elems, o.R,
+           o.kmax, o.max_concat, o.adm_min);
   return k + buf;
 }
 
@@ -3183,6 +3183,7 @@ static hfsem_factor* factor_part(hfsem_system* s, const hfsem_hopts& opt, const 
       const InstHost& I = s->ih[list[i]];
       PlanOpts o;
       o.lambda = opt.lambda;
+      o.adm_min = opt.admissibility == HFSEM_ADM_MIN ? 1 : 0;
       const int kmax_eff = opt.kmax ? opt.kmax : opt.R;
       const int max_concat = fp32 ? 160 : 112;   // shared memory of the recompression
       // a dense product appended to a low-rank block adds one leaf's worth of rank
@@ -3590,6 +3591,8 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
       opt.precision != HFSEM_PREC_MIXED_TC)
     throw Error(HFSEM_ERR_INVALID_ARG, "unknown precision");
   if (opt.leaf_elems < 0 || opt.kmax < 0) throw Error(HFSEM_ERR_INVALID_ARG, "leaf_elems, kmax >= 0");
+  if (opt.admissibility != HFSEM_ADM_MAX && opt.admissibility != HFSEM_ADM_MIN)
+    throw Error(HFSEM_ERR_INVALID_ARG, "admissibility: HFSEM_ADM_MAX or HFSEM_ADM_MIN");
   // FP32 cannot factor the equilibrated H-matrix of meshes whose element
   // sizes span more than ~1e45 (the preconditioner then loses all digits):
   // those instances are factored in FP64, the others in the requested mode

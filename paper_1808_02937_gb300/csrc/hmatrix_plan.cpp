@@ -92,7 +92,8 @@ struct Builder {
   }
   bool admissible(int t, int s) const {
     double d = dist(t, s);
-    return d > 0.0 && std::max(diam(t), diam(s)) <= o.lambda * d;
+    const double dm = o.adm_min ? std::min(diam(t), diam(s)) : std::max(diam(t), diam(s));
+    return d > 0.0 && dm <= o.lambda * d;
   }
 
   int block(int t, int s) {

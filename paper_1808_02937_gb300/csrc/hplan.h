@@ -95,7 +95,7 @@ struct HPlan {
 constexpr int kKcapMult = 2;
 
 struct PlanOpts {
-  double lambda;
+  double lambda;       // admissibility parameter of eq. (admis)
   int leaf_elems;
   int R;
   int kmax;
@@ -104,6 +104,9 @@ struct PlanOpts {
   int max_leaf;      // limit on diagonal leaf size
   int unique_tmp = 0;  // 1: never reuse temporary storage (independent ops stay independent)
   int ncta = 1;        // CTAs per instance (one truncation workspace each)
+  int adm_min = 0;     // 0: max(diam tau, diam sigma) <= lambda dist (eq. (admis));
+                       // 1: min(...) <= lambda dist, the expansion being taken
+                       // about the smaller cluster (Remark after the Lemma)
 };
 
 // Build clusters, blocks, storage and the two programs.

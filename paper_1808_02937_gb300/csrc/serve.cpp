@@ -174,7 +174,8 @@ int hfsem_server_create(const hfsem_server_opts* o, hfsem_server** out) {
       throw Error(HFSEM_ERR_INVALID_ARG, "budget_bytes, cache_factors >= 0");
     if (!(o->tol > 0.0) || o->max_iter < 1) throw Error(HFSEM_ERR_INVALID_ARG, "tol > 0, max_iter >= 1");
     if (o->hopts.R < 1 || o->hopts.R > 32 || !(o->hopts.lambda > 0.0) || !(o->hopts.tol_hlu >= 0.0) ||
-        o->hopts.build_only)
+        o->hopts.build_only ||
+        (o->hopts.admissibility != HFSEM_ADM_MAX && o->hopts.admissibility != HFSEM_ADM_MIN))
       throw Error(HFSEM_ERR_INVALID_ARG, "bad H-LU options");
     int dev = 0;
     HF_CHECK(cudaGetDevice(&dev));

@@ -28,6 +28,7 @@ HFSEM_ERR_UNSUPPORTED = 7
 MATVEC_AUTO, MATVEC_DENSE, MATVEC_TOEPLITZ = 0, 1, 2
 PREC_FP64, PREC_MIXED, PREC_MIXED_TC = 0, 1, 2   # PREC_MIXED_TC: dense leaf products of the H-LU on the tensor cores
 RHS_LOAD_VECTOR, RHS_FRAC_POWERS, RHS_LEGENDRE_AB = 0, 1, 2
+ADM_MAX, ADM_MIN = 0, 1   # admissibility: eq. (admis) as printed, or min(diam) <= lambda dist
 
 # every symbol include/hfsem.h declares
 EXPORTED = ["hfsem_assemble", "hfsem_ndof", "hfsem_apply", "hfsem_load_vector",
@@ -56,7 +57,7 @@ class hfsem_problem(C.Structure):
 class hfsem_hopts(C.Structure):
     _fields_ = [("R", C.c_int32), ("lambda_", C.c_double), ("tol_hlu", C.c_double),
                 ("precision", C.c_int32), ("leaf_elems", C.c_int32),
-                ("kmax", C.c_int32), ("build_only", C.c_int32)]
+                ("kmax", C.c_int32), ("build_only", C.c_int32), ("admissibility", C.c_int32)]
 
 
 class hfsem_rhs(C.Structure):
@@ -333,11 +334,12 @@ def hfsem_load_vector(sys: System, rhs_list, lifted: int = 0, out=None):
 
 
 def hopts(R=8, lam=1.0, tol_hlu=1e-3, precision=PREC_MIXED, leaf_elems=0, kmax=0,
-          build_only=0):
+          build_only=0, admissibility=ADM_MAX):
     """H-matrix / H-LU options: Taylor rank R, admissibility lambda, Tol_HLU,
     PREC_FP64 / PREC_MIXED / PREC_MIXED_TC, elements per leaf and rank cap
-    (0 = automatic), build_only = 1 to build the H-matrix without factoring."""
-    return hfsem_hopts(R, lam, tol_hlu, precision, leaf_elems, kmax, build_only)
+    (0 = automatic), build_only = 1 to build the H-matrix without factoring,
+    ADM_MAX (eq. (admis)) or ADM_MIN."""
+    return hfsem_hopts(R, lam, tol_hlu, precision, leaf_elems, kmax, build_only, admissibility)
 
 
 def hfsem_hlu_factor(sys: System, opts: hfsem_hopts) -> Factor:

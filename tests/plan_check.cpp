@@ -2,7 +2,7 @@
 // model (which works on rectangles): for one mesh read from stdin,
 //   * the leaf blocks of the block tree cover the N_d x N_d matrix exactly
 //     once, and every low-rank block is admissible in the sense of Sec. 3.1,
-//     max(diam tau, diam sigma) <= lambda dist(tau, sigma), with the supports
+//     max (or min) (diam tau, diam sigma) <= lambda dist(tau, sigma), with the supports
 //     of the clusters' basis functions derived here from their unknowns;
 //   * within each wave of the H-LU program (ops that the CTAs of a cluster
 //     run concurrently) no op writes an arena element, or the rank of a
@@ -11,7 +11,8 @@
 //     capacity;
 //   * the waves partition the program;
 //   * the leaf-solve tables stay inside the arena and the shared-memory budget.
-// Input: N P leaf_elems R lambda mode, then N element lengths; mode 1 checks
+// Input: N P leaf_elems R lambda mode rule, then N element lengths (rule 0:
+// max(diam) <= lambda dist, rule 1: min(diam) <= lambda dist); mode 1 checks
 // the whole program as if it were one wave (the verifier's own test: the H-LU
 // has dependencies, so that must fail).  Prints "OK ..." or the first
 // violation ("FAIL ...") and exits non-zero.
@@ -115,9 +116,10 @@ Foot footprint(const HPlan& p, const HOp& o) {
 }  // namespace
 
 int main() {
-  int N, P, leaf, R, mode;
+  int N, P, leaf, R, mode, rule;
   double lambda;
-  if (std::scanf("%d %d %d %d %lf %d", &N, &P, &leaf, &R, &lambda, &mode) != 6) return fail("input");
+  if (std::scanf("%d %d %d %d %lf %d %d", &N, &P, &leaf, &R, &lambda, &mode, &rule) != 7)
+    return fail("input");
   InstHost I{};
   I.N = N;
   I.P = P;
@@ -132,21 +134,28 @@ int main() {
   PlanOpts o{lambda, leaf, R, R, 64, 160, 128};
   o.unique_tmp = 1;
   o.ncta = 8;
+  o.adm_min = rule;
   HPlan p;
   make_plan(I, o, p);
 
   // ---- block tree: exact cover and admissibility ----
   const int Nd = I.Nd;
-  std::vector<double> x(N + 1, 0.0);
-  for (int k = 0; k < N; ++k) x[k + 1] = x[k] + I.h[k];
-  auto support = [&](const Cluster& c, double& lo, double& hi) {
-    lo = 1e300;
-    hi = -1e300;
+  // node positions as distances to a (prefix sums) and to b (suffix sums):
+  // a difference of nodes is taken from whichever is smaller, so meshes
+  // refined far below the rounding of 1 keep their element sizes
+  std::vector<double> da(N + 1, 0.0), db(N + 1, 0.0);
+  for (int k = 0; k < N; ++k) da[k + 1] = da[k] + I.h[k];
+  for (int k = N - 1; k >= 0; --k) db[k] = db[k + 1] + I.h[k];
+  auto diff = [&](int i, int j) {   // x_i - x_j, i >= j
+    return (da[i] <= db[j]) ? da[i] - da[j] : db[j] - db[i];
+  };
+  auto support = [&](const Cluster& c, int& lo, int& hi) {   // node indices
+    lo = N + 1;
+    hi = -1;
     for (int u = c.d0; u < c.d1; ++u) {
       const int e = u / P, q = u % P;
-      const double a = x[e], b = (q < P - 1) ? x[e + 1] : x[std::min(e + 2, N)];
-      lo = std::min(lo, a);
-      hi = std::max(hi, b);
+      lo = std::min(lo, e);
+      hi = std::max(hi, (q < P - 1) ? e + 1 : std::min(e + 2, N));
     }
   };
   std::vector<unsigned char> cover((size_t)Nd * Nd, 0);
@@ -160,11 +169,12 @@ int main() {
         if (cover[(size_t)i * Nd + j]++) fail("entry covered twice", i, j);
     if (b.type == B_LR) {
       ++n_lr;
-      double tl, th, sl, sh;
+      int tl, th, sl, sh;
       support(t, tl, th);
       support(s, sl, sh);
-      const double dist = std::max(sl - th, tl - sh);
-      const double diam = std::max(th - tl, sh - sl);
+      const double dist = (sl > th) ? diff(sl, th) : (tl > sh) ? diff(tl, sh) : 0.0;
+      const double dt = diff(th, tl), ds = diff(sh, sl);
+      const double diam = rule ? std::min(dt, ds) : std::max(dt, ds);
       if (!(dist > 0.0) || diam > lambda * dist * (1.0 + 1e-9)) fail("inadmissible low-rank block", b.t, b.s);
     }
   }

@@ -19,6 +19,7 @@ from oracle.solve import solve_problem
 from paper_1808_02937_gb300 import hfsem as H
 from paper_1808_02937_gb300 import workloads as W
 from tests._common import ensure_built, rel_err
+from tests._oracle_pool import oracle_solve_many
 from tests.test_oracle_solve import expected_coeffs
 
 pytestmark = pytest.mark.gpu
@@ -76,3 +77,24 @@ def test_config5_stream_sample(lib):
             assert rel_err(parts[:, 0], Xo) < 1e-10, p.name
             n_oracle += 1
     assert n_exact >= 20 and n_oracle >= 3
+
+
+@pytest.mark.parametrize("idx", [14, 26, 45])
+def test_config5_extreme_geometric_requests_min_admissibility(lib, idx):
+    # two-sided geometric requests whose elements span 1e-89 .. 1e-230 of the
+    # largest: with min(diam) <= lambda dist their H-LU stays small (they are
+    # factored in FP64); the solutions reproduce the manufactured polynomials
+    # where the space holds them, and request 45 (N_d = 4299) the oracle
+    p = list(W.config5_requests(idx + 1))[idx]
+    assert p.name.split()[1] == "geo2s"
+    sys_ = H.hfsem_assemble([H.make_problem(p.h, p.P, p.alpha, p.theta, p.rho)])
+    fac = H.hfsem_hlu_factor(sys_, H.hopts(**OPTS, admissibility=H.ADM_MIN))
+    X, st, code = H.hfsem_solve(sys_, fac, [H.rhs_frac_powers(p.rhs)], tol=1e-14,
+                                max_iter=100, allow_fail=True)
+    assert code == H.HFSEM_OK, (p.name, st)
+    parts = H.split(sys_, X, nrhs=len(p.rhs))[0]
+    assert _check_exact(p, parts) >= 1
+    if p.Nd <= 5000:
+        ref = oracle_solve_many([(p.h, 0.0, 1.0, p.P, p.alpha, p.theta, p.rho, 0.0, 0.0,
+                                  ("frac_powers", p.rhs[0]))])[0]
+        assert rel_err(parts[:, 0], ref) < 1e-10, p.name

@@ -27,29 +27,35 @@ def lib():
     return ensure_built()
 
 
+@pytest.mark.parametrize("rule", ["max", "min"])
 @pytest.mark.parametrize("prec", [H.PREC_FP64, H.PREC_MIXED])
 @pytest.mark.parametrize("case", CASES, ids=lambda c: c[0])
-def test_hmatrix_entries_match_oracle(lib, case, prec):
+def test_hmatrix_entries_match_oracle(lib, case, prec, rule):
     name, h, a, b, P, alpha, theta, rho, leaf, R = case
     sys = H.hfsem_assemble([H.make_problem(h, P, alpha, theta, rho, a=a, b=b, matvec=1)])
+    adm = H.ADM_MAX if rule == "max" else H.ADM_MIN
     fac = H.hfsem_hlu_factor(sys, H.hopts(R=R, lam=1.0, tol_hlu=0.0, precision=prec,
-                                          leaf_elems=leaf, build_only=1))
+                                          leaf_elems=leaf, build_only=1, admissibility=adm))
     At_gpu = H.hfsem_hmatrix_dense(fac, 0)
     m = Mesh(h, a, b)
-    At, _ = hmatrix_dense(m, P, alpha, theta, system_full(m, P, alpha, theta, rho), R, 1.0, leaf)
+    At, _ = hmatrix_dense(m, P, alpha, theta, system_full(m, P, alpha, theta, rho), R, 1.0, leaf,
+                          rule=rule)
     tol = 1e-12 if prec == H.PREC_FP64 else 2e-6
     assert np.abs(At_gpu - At).max() <= tol * np.abs(At).max()
 
 
+@pytest.mark.parametrize("rule", ["max", "min"])
 @pytest.mark.parametrize("case", CASES, ids=lambda c: c[0])
-def test_hlu_exact_at_zero_tolerance(lib, case):
+def test_hlu_exact_at_zero_tolerance(lib, case, rule):
     # Tol_HLU = 0 and no rank cap: H-LU is an exact LU of A~
     name, h, a, b, P, alpha, theta, rho, leaf, R = case
     sys = H.hfsem_assemble([H.make_problem(h, P, alpha, theta, rho, a=a, b=b, matvec=1)])
+    adm = H.ADM_MAX if rule == "max" else H.ADM_MIN
     fac = H.hfsem_hlu_factor(sys, H.hopts(R=R, lam=1.0, tol_hlu=0.0, precision=H.PREC_FP64,
-                                          leaf_elems=leaf, kmax=48))
+                                          leaf_elems=leaf, kmax=48, admissibility=adm))
     m = Mesh(h, a, b)
-    At, _ = hmatrix_dense(m, P, alpha, theta, system_full(m, P, alpha, theta, rho), R, 1.0, leaf)
+    At, _ = hmatrix_dense(m, P, alpha, theta, system_full(m, P, alpha, theta, rho), R, 1.0, leaf,
+                          rule=rule)
     rng = np.random.default_rng(11)
     Nd = n_dof(len(h), P)
     r = rng.standard_normal((3, Nd))

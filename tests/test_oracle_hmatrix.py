@@ -124,3 +124,55 @@ def test_large_rank_recovers_exact_matrix(graded):
                               28, 1.0, leaf=2, expand=expand)
         A2 = system_full(mesh, P, alpha, 0.6, 0.3)[:Nd, :Nd]
         assert np.abs(At - A2).max() < 1e-13 * np.abs(A2).max()
+
+
+# ---- the "min" admissibility on a geometrically graded mesh ----------------
+@pytest.fixture(scope="module")
+def geometric():
+    N, P, alpha = 36, 3, 1.45
+    mesh = Mesh(W.mesh_geometric_two_sided(N, 0.45), 0.0, 1.0)
+    A = system_full(mesh, P, alpha, 0.7, 0.4)
+    return mesh, P, alpha, A
+
+
+def test_min_rule_admits_more_and_partitions(geometric):
+    mesh, P, alpha, A = geometric
+    N = mesh.N
+    Nd = n_dof(N, P)
+    root = cluster_tree(N, 2)
+    bmax = block_leaves(mesh, root, 1.0, "max")
+    bmin = block_leaves(mesh, root, 1.0, "min")
+    cover = np.zeros((Nd, Nd), dtype=int)
+    for t, s, adm in bmin:
+        cover[np.ix_(cluster_dofs(N, P, t), cluster_dofs(N, P, s))] += 1
+    assert np.all(cover == 1)
+
+    def dense_entries(bl):
+        return sum(len(cluster_dofs(N, P, t)) * len(cluster_dofs(N, P, s))
+                   for t, s, adm in bl if not adm)
+    assert dense_entries(bmin) < 0.5 * dense_entries(bmax)
+
+
+@pytest.mark.parametrize("expand", ["auto", "s_always"])
+def test_min_rule_converges_only_about_the_smaller_cluster(geometric, expand):
+    # with min(diam) <= lambda dist only the smaller cluster's expansion is
+    # covered by the Lemma: about it the error decays like (1/3)^R; expanding
+    # about the trial cluster regardless (a plausible mistake) does not
+    mesh, P, alpha, A = geometric
+    Nd = n_dof(mesh.N, P)
+    ex = "auto" if expand == "auto" else "s"
+    errs = []
+    for R in (4, 8, 12):
+        At, blocks = hmatrix_dense(mesh, P, alpha, 0.7, A, R, 1.0, leaf=2, expand=ex, rule="min")
+        errs.append(np.abs(A[:Nd, :Nd] - At).max())
+    if expand == "auto":
+        assert errs[1] < 0.05 * errs[0] and errs[2] < 0.05 * errs[1], errs
+    else:
+        assert not (errs[1] < 0.05 * errs[0] and errs[2] < 0.05 * errs[1]), errs
+
+
+def test_min_rule_large_rank_recovers_exact_matrix(geometric):
+    mesh, P, alpha, A = geometric
+    Nd = n_dof(mesh.N, P)
+    At, _ = hmatrix_dense(mesh, P, alpha, 0.7, A, 30, 1.0, leaf=2, rule="min")
+    assert np.abs(At - A[:Nd, :Nd]).max() < 1e-13 * np.abs(A[:Nd, :Nd]).max()

@@ -33,8 +33,9 @@ def verifier(tmp_path_factory):
     return out
 
 
-def _run(verifier, h, P, leaf, R, lam=1.0, mode=0):
-    inp = f"{len(h)} {P} {leaf} {R} {lam} {mode}\n" + " ".join(repr(float(v)) for v in h) + "\n"
+def _run(verifier, h, P, leaf, R, lam=1.0, mode=0, rule=0):
+    inp = (f"{len(h)} {P} {leaf} {R} {lam} {mode} {rule}\n" +
+           " ".join(repr(float(v)) for v in h) + "\n")
     return subprocess.run([verifier], input=inp, capture_output=True, text=True, timeout=300)
 
 
@@ -49,9 +50,17 @@ CASES = [
 
 
 @pytest.mark.parametrize("case", CASES, ids=lambda c: c[0])
-def test_plan_is_race_free_and_in_bounds(verifier, case):
+@pytest.mark.parametrize("rule", [0, 1], ids=["adm-max", "adm-min"])
+def test_plan_is_race_free_and_in_bounds(verifier, case, rule):
     name, h, P, leaf, R = case
-    r = _run(verifier, h, P, leaf, R)
+    r = _run(verifier, h, P, leaf, R, rule=rule)
+    assert r.returncode == 0 and r.stdout.startswith("OK"), (r.stdout, r.stderr)
+
+
+def test_min_admissibility_on_geometric_mesh(verifier):
+    # an extreme two-sided geometric mesh (elements from 1 down to ~1e-60)
+    h = W.mesh_geometric_two_sided(200, 0.25)
+    r = _run(verifier, h, 3, 8, 6, rule=1)
     assert r.returncode == 0 and r.stdout.startswith("OK"), (r.stdout, r.stderr)
 
 
