@@ -99,13 +99,16 @@ struct Term {
 __device__ __forceinline__ int terms_of(const InstDev& I, const double* h, int i, Term* t) {
   const int P = I.P;
   int e = i / P, p = i % P + 1;
+  // coefficients of the length-scaled map z = h Pi x (the system's pair
+  // blocks are stored divided by h_e h_f)
+  (void)h;
   if (p < P) {
-    t[0] = Term{e, p, -(2.0 * p + 1.0) * (2.0 / h[e])};
+    t[0] = Term{e, p, -2.0 * (2.0 * p + 1.0)};
     return 1;
   }
   int j = e + 1;   // hat at node j: right hat of element j-1, left hat of element j
-  t[0] = Term{j - 1, 0, 1.0 / h[j - 1]};
-  t[1] = Term{j, 0, -1.0 / h[j]};
+  t[0] = Term{j - 1, 0, 1.0};
+  t[1] = Term{j, 0, -1.0};
   return 2;
 }
 

@@ -341,8 +341,15 @@ void bicgstab(hfsem_system* s, Precond* M, int nrhs, const double* b_em, double*
   }
   dim3 gv(maxchunk, ncols), bv(kDotThreads);
   int sb = (ncols + 127) / 128;
+  // algorithmic bytes of one fused vector pass over every column: 8 bytes
+  // per vector element read or written (running columns only in practice;
+  // counted for all, so the rate is a lower bound)
+  auto vec_bytes = [&](int mode) {
+    static const int touched[10] = {6, 4, 2, 3, 2, 8, 3, 2, 3, 5};
+    return 8.0 * (double)nv * touched[mode];
+  };
   auto vec = [&](int mode) {
-    Tick tk(s->st, "krylov_vec");
+    Tick tk(s->st, "krylov_vec", vec_bytes(mode));
     k_bicg_vec<<<gv, bv, 0, s->st>>>(mode, V, W.coff.p, W.clen.p, W.cols.p, W.partial.p,
                                      maxchunk);
     HF_LAUNCH_CHECK();

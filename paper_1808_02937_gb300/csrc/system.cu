@@ -193,7 +193,9 @@ __device__ inline PairScratch carve(double* base, int P) {
 }
 
 // acc[m][n] += sum_ij wu_i wv_j L_m(xi(u_i)) (g+u_i+v_j)^(1-alpha) L_n(eta(v_j))
-// over the box [u0,u1] x [v0,v1]; xi = -1 + 2u/he, eta = 1 - 2v/hf.
+// over the box [u0,u1] x [v0,v1]; xi = -1 + 2u/he, eta = 1 - 2v/hf; the
+// weights are divided by he and hf (the block is stored scaled, see
+// pair_block).
 __device__ void box_quad(PairScratch& s, int P, double alpha, double he,
                          double hf, double g, double u0, double u1, double v0,
                          double v1, int nq, const double* gl, int lane) {
@@ -205,8 +207,8 @@ __device__ void box_quad(PairScratch& s, int P, double alpha, double he,
     double v = v0 + 0.5 * lv * (1.0 + X[i]);
     s.su[i] = u;
     s.sv[i] = v;
-    legendre_strided(P, -1.0 + 2.0 * u / he, s.A + i, NQ, 0.5 * lu * Wt[i]);
-    legendre_strided(P, 1.0 - 2.0 * v / hf, s.B + i, NQ, 0.5 * lv * Wt[i]);
+    legendre_strided(P, -1.0 + 2.0 * u / he, s.A + i, NQ, 0.5 * (lu / he) * Wt[i]);
+    legendre_strided(P, 1.0 - 2.0 * v / hf, s.B + i, NQ, 0.5 * (lv / hf) * Wt[i]);
   }
   __syncwarp();
   const double ex = 1.0 - alpha;
@@ -240,7 +242,8 @@ __device__ void duffy_tri(PairScratch& s, int P, double alpha, double he,
   const double* X = gl + gl_off(nw);
   const double* Wt = X + nw;
   const double ex = 1.0 - alpha;
-  const double cfac = pow(c, 3.0 - alpha) * exp2(alpha - 3.0);
+  // c^(3-alpha) 2^(alpha-3) / (he hf), in factors that stay in range
+  const double cfac = pow(c, 1.0 - alpha) * (c / he) * (c / hf) * exp2(alpha - 3.0);
   // per outer node k: T[q][k] = sum_j K_kj * basis_q(inner point (k, j))
   for (int k = lane; k < ngj; k += 32) {
     double rho = 0.5 * (1.0 + gjx[k]);
@@ -281,7 +284,12 @@ __device__ void duffy_tri(PairScratch& s, int P, double alpha, double he,
 }
 
 // Element-pair block (unscaled by gamma0) for test element e right of (or
-// equal to) trial element f.  kind: 0 self, 1 touching, 2 separated (gap g).
+// equal to) trial element f, divided by he hf: the block of the
+// derivative-coefficient operator scales like he hf (distance)^(1-alpha),
+// (h/2)^(3-alpha) for the self pair, which leaves the FP64 range for
+// elements below ~1e-160; divided it scales like (distance)^(1-alpha) and
+// pairs with the scale-free coefficient map of k_gather_z.
+// kind: 0 self, 1 touching, 2 separated (gap g).
 __device__ void pair_block(PairScratch& s, int P, double alpha, double he,
                            double hf, double g, int kind, const double* D,
                            const double* gjx, const double* gjw, int ngj,
@@ -289,7 +297,7 @@ __device__ void pair_block(PairScratch& s, int P, double alpha, double he,
   for (int e = lane; e < P * P; e += 32) s.acc[e] = 0.0;
   __syncwarp();
   if (kind == 0) {
-    double sc = pow(0.5 * he, 3.0 - alpha);
+    double sc = 0.25 * pow(0.5 * he, 1.0 - alpha);   // (he/2)^(3-alpha) / he^2
     for (int e = lane; e < P * P; e += 32) s.acc[e] = sc * D[e];
     __syncwarp();
     return;
@@ -476,27 +484,28 @@ __global__ void k_symbol(const InstDev* __restrict__ inst, const double* arena,
 // operator application
 // ---------------------------------------------------------------------------
 
-// z = Pi x  (lift: boundary hats carry c1, c2 instead of 0)
+// z = Pi x, Pi scaled by the element length (z_e = h_e times the Legendre
+// coefficients of u' on element e): z_e[0] = u(x_{e+1}) - u(x_e),
+// z_e[m] = -2(2m+1) (coefficient of psi_m); the pair blocks carry the
+// matching 1/(h_e h_f).  (lift: boundary hats carry c1, c2 instead of 0)
 __global__ void k_gather_z(const InstDev* __restrict__ inst, const double* arena,
                            const double* __restrict__ x, double* z, int nrhs,
                            int lift) {
   const InstDev I = inst[blockIdx.y];
   const int r = blockIdx.z;
   const int P = I.P, N = I.N;
-  const double* h = arena + I.o_h;
   const double* xv = x + I.o_vec * nrhs + (size_t)r * I.Nd;
   double* zv = z + I.o_z * nrhs + (size_t)r * N * P;
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < N * P;
        t += gridDim.x * blockDim.x) {
     int e = t / P, m = t % P;
-    double he = h[e];
     double val;
     if (m == 0) {
       double uL = (e == 0) ? (lift ? I.c1 : 0.0) : xv[e * P - 1];
       double uR = (e == N - 1) ? (lift ? I.c2 : 0.0) : xv[(e + 1) * P - 1];
-      val = (uR - uL) / he;
+      val = uR - uL;
     } else {
-      val = -(2.0 * m + 1.0) * (2.0 / he) * xv[e * P + m - 1];
+      val = -2.0 * (2.0 * m + 1.0) * xv[e * P + m - 1];
     }
     zv[t] = val;
   }
@@ -519,7 +528,7 @@ __global__ void k_scatter_out(const InstDev* __restrict__ inst, const double* ar
     double out;
     if (p < P) {
       double he = h[e];
-      out = -(2.0 * p + 1.0) * (2.0 / he) * wv[e * P + p];
+      out = -2.0 * (2.0 * p + 1.0) * wv[e * P + p];
       if (I.rho != 0.0) {
         // local mass on [L, R, psi_1..]: scaled by h/2
         double uL = (e == 0) ? (lift ? I.c1 : 0.0) : xv[e * P - 1];
@@ -536,7 +545,7 @@ __global__ void k_scatter_out(const InstDev* __restrict__ inst, const double* ar
       // hat at node j = e+1: right hat of element e, left hat of element e+1
       int j = e + 1;
       double hl = h[j - 1], hr = h[j];
-      out = wv[(j - 1) * P] / hl - wv[j * P] / hr;
+      out = wv[(j - 1) * P] - wv[j * P];
       if (I.rho != 0.0) {
         double uj = xv[i];
         double ul = (j - 1 == 0) ? (lift ? I.c1 : 0.0) : xv[(j - 1) * P - 1];
@@ -1381,9 +1390,11 @@ static hfsem_system* assemble(int n, const hfsem_problem* probs, void* stream) {
       gauss_jacobi_rule(D.n_gj, 0.0, 2.0 - I.alpha, x, w);
       std::copy(x.begin(), x.end(), host.begin() + D.o_gj);
       std::copy(w.begin(), w.end(), host.begin() + D.o_gj + D.n_gj);
+      // Toeplitz row / column scalings of the stored (divided) blocks:
+      // M_ef / (h_e h_f) = (1/2) (g0/2 h_f^(1-alpha)) m_{e-f}
       for (int k = 0; k < I.N; ++k) {
-        host[D.o_rs + k] = 0.5 * I.h[k];
-        host[D.o_cs + k] = I.g0 * 0.5 * I.h[k] * std::pow(I.h[k], 1.0 - I.alpha);
+        host[D.o_rs + k] = 0.5;
+        host[D.o_cs + k] = I.g0 * 0.5 * std::pow(I.h[k], 1.0 - I.alpha);
       }
     }
     HF_CHECK(cudaMemcpyAsync(s->arena.p, host.data(), host.size() * sizeof(double),
