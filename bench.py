@@ -383,7 +383,7 @@ BOUND_OF = {   # kernel tag -> (bound, unit of its counted work)
     "toeplitz_mv": ("hbm", "byte"),        # symbol + vectors per apply
     "hlu_factor": ("alu_fp32", "flop"),    # flops of the executed shapes
     "hlu_solve": ("alu_fp32", "flop"),
-    "solve_pack": ("hbm", None),
+    "solve_pack": ("hbm", "byte"),        # packed factor columns read and written
     "krylov_vec": ("hbm", "byte"),         # vector elements read and written
 }
 

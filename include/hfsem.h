@@ -59,6 +59,17 @@ extern "C" {
 #define HFSEM_MATVEC_DENSE     1  /* O(N_d^2) dense operator (Sec. 4.2)      */
 #define HFSEM_MATVEC_TOEPLITZ  2  /* block-Toeplitz FFT operator (Sec. 4.3);
                                      needs h_{i+1}/h_i constant               */
+#define HFSEM_MATVEC_HMATRIX   3  /* FP64 H-matrix operator (Sec. 3 at high
+                                     rank): exact near-field pairs, Taylor
+                                     rank 24, min-diameter admissibility with
+                                     lambda = 1 (bound (1/3)^24, below FP64
+                                     rounding); O(N_d log N) storage and
+                                     product instead of O(N_d^2).  An H-LU
+                                     factor of such a system must use
+                                     HFSEM_ADM_MIN with lambda >= 1 and
+                                     automatic leaves (its near field must
+                                     lie in the operator's); otherwise
+                                     hfsem_hlu_factor returns UNSUPPORTED    */
 
 #define HFSEM_PREC_FP64   0       /* H-matrix, H-LU and H-solves in FP64     */
 #define HFSEM_PREC_MIXED  1       /* H-matrix, H-LU and H-solves in FP32;
@@ -170,7 +181,8 @@ int hfsem_apply(hfsem_system *sys, int32_t nrhs, const double *x, double *y);
  * launches) there, and the device holds it until the process exits, so
  * the call itself loads and allocates nothing.  Requests needing more
  * scratch (sum of N_d, N*P, the dense column partials and the FFT buffers,
- * times nrhs) return HFSEM_ERR_INVALID_ARG.  All calls share the array:
+ * times nrhs) return HFSEM_ERR_INVALID_ARG, as do systems holding an
+ * HFSEM_MATVEC_HMATRIX instance.  All calls share the array:
  * calls whose work overlaps on the GPU (other streams, other host threads)
  * race on it. */
 int hfsem_apply_noalloc(hfsem_system *sys, int32_t nrhs, const double *x, double *y);

@@ -110,6 +110,14 @@ constexpr int kMaxP = 32;
 // Kinds of operator storage.
 constexpr int kDense = 0;
 constexpr int kToeplitz = 1;
+constexpr int kHmat = 2;     // FP64 H-matrix operator over a near-field band of pairs
+
+// Options of the H-matrix operator (kHmat): Taylor rank, admissibility
+// parameter (min-diameter rule) and leaf size in unknowns.  At rank 24 the
+// Lemma's bound (1/3)^24 is below the FP64 rounding of the entries.
+constexpr int kHopRank = 24;
+constexpr double kHopLambda = 1.0;
+constexpr int kHopLeafDofs = 128;
 
 // Per-instance descriptor as seen by the kernels (plain data).
 struct InstDev {
@@ -129,6 +137,9 @@ struct InstDev {
   long long o_T;               // dense: sum of N(N+1)/2 * P over earlier
   long long o_fft;             // Toeplitz: sum of L*P over earlier instances
   long long o_N;               // sum of N over earlier instances
+  long long o_flo, o_off;      // kHmat: first stored f of row e; pair offsets (N+1)
+  long long o_c0, o_rN;        // kHmat: column f = 0 (mode 0) and row e = N-1 (mode 0)
+  long long band;              // kHmat: stored pairs
 };
 
 struct InstHost {
@@ -137,6 +148,7 @@ struct InstHost {
   std::vector<double> h, dl, dr;   // lengths; node distances to a and to b
   bool uniform = false;
   double q = 1.0;
+  std::vector<int> flo;            // kHmat: first stored trial element of row e
   double node_diff(int i, int j) const {  // x_i - x_j, i >= j
     return (dl[i] <= dr[j]) ? dl[i] - dl[j] : dr[j] - dr[i];
   }
@@ -178,11 +190,13 @@ struct hfsem_system_s {
   hf::DevBuf<double> gl;          // Gauss-Legendre table: rule n at gl_off(n)
   long long total_nd = 0, total_nz = 0, total_T = 0, total_fft = 0, total_N = 0;
   int max_P = 0, max_N = 0, max_L = 0;
-  bool any_dense = false, any_toep = false;
+  bool any_dense = false, any_toep = false, any_hmat = false;
+  hfsem_factor* hop = nullptr;    // the H-matrix operator of the kHmat instances
   // scratch, grown on demand
   hf::DevBuf<double> w_x, w_y, w_z, w_w, w_T, w_ylow, w_mom;
   hf::DevBuf<double2> w_fa, w_fb;
   hf::DevBuf<double> w_rhsdata;
+  hf::DevBuf<double> w_hop;       // H-matrix operator: low-rank projections
   hf::DevBuf<double2> tw;         // FFT twiddles exp(-2 pi i j / tw_L)
   int tw_L = 0;
   hf::KrylovWork kry;
@@ -223,6 +237,13 @@ inline void drain_after_error(hfsem_system* s);
 // Device bytes a system, a factor hold (their buffers as grown so far).
 size_t system_bytes(const hfsem_system* s);
 size_t factor_bytes(const hfsem_factor* f);
+// The H-matrix operator of the kHmat instances of s (built at assembly from
+// the band of pair blocks) and its product y += A x on element-major vectors.
+void build_operator(hfsem_system* s);
+void hop_apply(hfsem_system* s, int nrhs, const double* x_em, double* y_em);
+// Near-field band of the kHmat operator: for every element e the first
+// trial element f of the pairs (e, f <= e) its dense blocks need.
+void hop_band(const InstHost& I, std::vector<int>& flo);
 // Loads, on the current device, the scratch array and the kernels of
 // hfsem_apply_noalloc (once per device), so that its calls allocate nothing.
 void noalloc_prepare();

@@ -118,6 +118,10 @@ __device__ __forceinline__ double mb_entry(const InstDev& I, const double* arena
   const int P = I.P;
   if (I.kind == kDense)
     return arena[I.o_M + ((long long)e * (e + 1) / 2 + f) * P * P + m * P + n];
+  if (I.kind == kHmat) {   // the band: pairs (e, flo[e] .. e), checked on the host
+    const long long q = (long long)arena[I.o_off + e] + (f - (int)arena[I.o_flo + e]);
+    return arena[I.o_M + q * P * P + m * P + n];
+  }
   return arena[I.o_rs + e] * arena[I.o_cs + f] * arena[I.o_M + (long long)(e - f) * P * P + m * P + n];
 }
 
@@ -3032,6 +3036,28 @@ struct PlanBundle {
 
 }  // namespace hf
 
+namespace hf {
+// Product tables of the H-matrix operator (kHmat instances), see hop_apply.
+struct HopRow {        // one leaf row cluster of one instance
+  int inst;            // factor instance
+  int d0, nr;          // its unknowns [d0, d0 + nr) (instance-local)
+  int it0, it1;        // its items
+};
+struct HopItem {       // one block whose rows contain the leaf
+  long long off;       // element offset of the block in the factor arena
+  int kind;            // 0 dense (m x n, column-major), 1 low-rank (U: m x kcap)
+  int ld;              // rows of the block
+  int roff;            // the leaf's first row inside the block
+  int c0;              // dense: first column (instance-local); low-rank: slot record
+  int nc;              // dense: columns
+};
+struct HopSlot {       // one low-rank block: w = V^T x~ over its columns
+  long long offV;      // element offset of V (n x kcap, column-major)
+  long long w0;        // offset of its w in the projection buffer
+  int inst, c0, n, kcap, rk;   // factor instance, first column, columns, capacity, rank index
+};
+}  // namespace hf
+
 struct hfsem_factor_s : public hf::Precond {
   hfsem_system* sys = nullptr;
   cudaStream_t st = nullptr;   // copy of the system's stream (free never touches sys)
@@ -3078,6 +3104,13 @@ struct hfsem_factor_s : public hf::Precond {
   hf::DevBuf<double> d_flops;               // per instance: factor / solve flops
   hf::DevBuf<unsigned long long> d_wprof;   // HFSEM_PROFILE=2: per-wave records
   hf::DevBuf<unsigned long long> d_tcdbg;   // tensor-core wait diagnostics (8 words)
+  // operator use (build_only factors of kHmat instances): product tables
+  hf::DevBuf<hf::HopRow> d_hrow;
+  hf::DevBuf<hf::HopItem> d_hitem;
+  hf::DevBuf<hf::HopSlot> d_hslot;
+  int hop_nrows = 0, hop_nslots = 0, hop_kmax = 1;
+  long long hop_wsize = 0;        // projection entries per right-hand side
+  double hop_flops = 0.0;         // per right-hand side
   int wstride = 0;
   void report(const char* what);
   void report_waves(const char* what);
@@ -3148,9 +3181,28 @@ static void plan_cache_put(const std::string& key, std::shared_ptr<PlanBundle> p
 static std::string plan_key(const InstHost& I, const PlanOpts& o) {
   std::string k(reinterpret_cast<const char*>(I.h.data()), I.h.size() * sizeof(double));
   char buf[128];
-  snprintf(buf, sizeof(buf), "|%d|%d|%.17g|%d|%d|%d|%d|%d", I.N, I.P, o.lambda, o.leaf_elems, o.R,
-           o.kmax, o.max_concat, o.adm_min);
+  snprintf(buf, sizeof(buf), "|%d|%d|%.17g|%d|%d|%d|%d|%d|%d", I.N, I.P, o.lambda, o.leaf_elems, o.R,
+           o.kmax, o.max_concat, o.adm_min, o.structure_only);
   return k + buf;
+}
+
+// For every element e, the first trial element f of the pairs (e, f <= e)
+// that the dense blocks of plan p read (entries of A in rows and columns of
+// a cluster involve the elements of its bubbles and of its hats' supports).
+static void band_need(const HPlan& p, int N, std::vector<int>& flo) {
+  flo.resize(N);
+  for (int e = 0; e < N; ++e) flo[e] = e;
+  auto lo_of = [&](const Cluster& c) { return c.e0; };
+  auto hi_of = [&](const Cluster& c) { return std::min(c.e1, N - 1); };
+  for (int bi : p.dense_blocks) {
+    const Cluster &t = p.C[p.B[bi].t], &c = p.C[p.B[bi].s];
+    for (int pass = 0; pass < 2; ++pass) {
+      const Cluster& a = pass ? c : t;   // test side
+      const Cluster& b = pass ? t : c;   // trial side
+      const int blo = lo_of(b);
+      for (int e = std::max(lo_of(a), blo); e <= hi_of(a); ++e) flo[e] = std::min(flo[e], blo);
+    }
+  }
 }
 
 // Factor the system instances in `list` with one arithmetic (`precision`).
@@ -3193,7 +3245,14 @@ static hfsem_factor* factor_part(hfsem_system* s, const hfsem_hopts& opt, const 
       // (in slices of 32 columns) to a block holding up to kKcapMult kmax
       const int leaf_cap = std::min(max_leaf, max_concat - kKcapMult * kmax_eff);
       int leaf = opt.leaf_elems ? opt.leaf_elems : std::max(1, leaf_cap / I.P);
-      leaf = std::min(leaf, std::max(1, leaf_cap / I.P));
+      if (opt.build_only) {
+        // an H-matrix built, never factored: no shared-memory limit on its
+        // leaves (128 unknowns by default)
+        leaf = opt.leaf_elems ? opt.leaf_elems : std::max(1, 128 / I.P);
+        o.structure_only = 1;
+      } else {
+        leaf = std::min(leaf, std::max(1, leaf_cap / I.P));
+      }
       o.leaf_elems = leaf;
       o.R = opt.R;
       o.kmax = kmax_eff;
@@ -3251,8 +3310,9 @@ static hfsem_factor* factor_part(hfsem_system* s, const hfsem_hopts& opt, const 
         const int ns = ((q.se1 < I.N) ? q.se1 : q.se1 - 1) - q.se0 + 1;
         pb->ptask.push_back(pb->ptask.back() + nt + ns);
       }
-      build_leaf_solve(pb->plan, kCluster, sol_budget, (int)f->tsize,
-                       fp32 ? solve_w<float>() : solve_w<double>(), pb->ls);
+      if (!o.structure_only)
+        build_leaf_solve(pb->plan, kCluster, sol_budget, (int)f->tsize,
+                         fp32 ? solve_w<float>() : solve_w<double>(), pb->ls);
       return pb;
     };
     {
@@ -3282,6 +3342,20 @@ static hfsem_factor* factor_part(hfsem_system* s, const hfsem_hopts& opt, const 
       }
     }
     for (int i = 0; i < ni; ++i) f->plans[i] = cache[keys[i]];
+    // an instance assembled with the H-matrix operator stores only the pairs
+    // of the operator's near field: this factor's must lie inside it
+    for (int i = 0; i < ni; ++i) {
+      const InstHost& I = s->ih[list[i]];
+      if (I.kind != kHmat) continue;
+      std::vector<int> need;
+      band_need(f->plans[i]->plan, I.N, need);
+      for (int e = 0; e < I.N; ++e)
+        if (need[e] < I.flo[e])
+          throw Error(HFSEM_ERR_UNSUPPORTED,
+                      "the H-LU near field reaches pairs the H-matrix operator does not store: "
+                      "factor with HFSEM_ADM_MIN, lambda >= 1 and automatic leaves, or assemble "
+                      "with HFSEM_MATVEC_DENSE");
+    }
     // one solve kernel serves every plan: cut the parts of each plan for the
     // largest leaf and the most owned low-rank columns of all of them
     {
@@ -3294,7 +3368,8 @@ static hfsem_factor* factor_part(hfsem_system* s, const hfsem_hopts& opt, const 
       // tables cut for itself (on all host cores, as above)
       std::vector<std::shared_ptr<PlanBundle>*> recut;
       for (auto& kv : cache)
-        if (kv.second->ls.nmax < nm || kv.second->ls.wcols < wc) recut.push_back(&kv.second);
+        if (!opt.build_only && (kv.second->ls.nmax < nm || kv.second->ls.wcols < wc))
+          recut.push_back(&kv.second);
       std::vector<std::exception_ptr> errs(recut.size());
       std::atomic<size_t> next{0};
       auto worker = [&] {
@@ -3419,7 +3494,8 @@ static hfsem_factor* factor_part(hfsem_system* s, const hfsem_hopts& opt, const 
       else
         HF_CHECK(cudaFuncGetAttributes(&fa, k_hprog<double>));
       const size_t avail = (size_t)optin - fa.sharedSizeBytes - 1024;
-      if (smem > avail) throw Error(HFSEM_ERR_UNSUPPORTED, "H-LU kernel needs too much shared memory");
+      if (smem > avail && !opt.build_only)
+        throw Error(HFSEM_ERR_UNSUPPORTED, "H-LU kernel needs too much shared memory");
       smem = avail & ~(size_t)15;
     }
     f->smem = smem;
@@ -3465,7 +3541,7 @@ static hfsem_factor* factor_part(hfsem_system* s, const hfsem_hopts& opt, const 
     f->sol_smem = solve_smem(jmax, nmax, wcols, (int)f->tsize, sw);
     f->d_pack.alloc((size_t)std::max<long long>(pkoff, 1) * f->sol_slot * f->tsize);
     f->d_meta.alloc((size_t)std::max<long long>(pkoff, 1));
-    {
+    if (!opt.build_only) {
       if (f->sol_smem > sol_budget)
         throw Error(HFSEM_ERR_UNSUPPORTED, "leaf solve needs too much shared memory");
       if (fp32)
@@ -3625,6 +3701,243 @@ static hfsem_factor* factor(hfsem_system* s, const hfsem_hopts& opt) {
     throw;
   }
   return f;
+}
+
+// ---------------------------------------------------------------------------
+// H-matrix operator (kHmat instances): A~ in FP64 at rank kHopRank with the
+// min-diameter rule (Sec. 3 at a rank where the Lemma's bound is below the
+// rounding of FP64), built by the same kernels as the preconditioner's
+// H-matrix, applied as y += D^-1 (D A~ D) D^-1 x.
+// ---------------------------------------------------------------------------
+static PlanOpts hop_plan_opts(int P) {
+  PlanOpts o{};
+  o.lambda = kHopLambda;
+  o.leaf_elems = std::max(1, kHopLeafDofs / P);
+  o.R = kHopRank;
+  o.kmax = kHopRank;
+  o.nrhs_max = 64;
+  o.max_concat = 112;
+  o.max_leaf = kHopLeafDofs;
+  o.unique_tmp = 1;
+  o.ncta = kCluster;
+  o.structure_only = 1;
+  o.adm_min = 1;
+  return o;
+}
+
+void hop_band(const InstHost& I, std::vector<int>& flo) {
+  HPlan p;
+  make_plan(I, hop_plan_opts(I.P), p);
+  band_need(p, I.N, flo);
+}
+
+void build_operator(hfsem_system* s) {
+  std::vector<int> list;
+  for (int i = 0; i < s->n_inst; ++i)
+    if (s->ih[i].kind == kHmat) list.push_back(i);
+  if (list.empty()) return;
+  hfsem_hopts o{};
+  o.R = kHopRank;
+  o.lambda = kHopLambda;
+  o.tol_hlu = 0.0;
+  o.precision = HFSEM_PREC_FP64;
+  o.leaf_elems = 0;
+  o.kmax = 0;
+  o.build_only = 1;
+  o.admissibility = HFSEM_ADM_MIN;
+  hfsem_factor* f = factor_part(s, o, list, HFSEM_PREC_FP64);
+  s->hop = f;
+  // product tables: per leaf row cluster, the blocks whose rows hold it
+  std::vector<HopRow> rows;
+  std::vector<HopItem> items;
+  std::vector<HopSlot> slots;
+  long long w0 = 0;
+  double flops = 0.0;
+  int kmax = 1;
+  for (int j = 0; j < f->nfi; ++j) {
+    const HPlan& p = f->plans[j]->plan;
+    const HInstDev& H = f->hidev[j];
+    const int nc = (int)p.C.size();
+    std::vector<std::vector<int>> at(nc);   // blocks by row cluster
+    for (int bi : p.dense_blocks) at[p.B[bi].t].push_back(bi);
+    std::vector<int> slot_rec(p.n_slots, -1);
+    for (int bi : p.lr_blocks) {
+      const Block& b = p.B[bi];
+      at[b.t].push_back(bi);
+      slot_rec[b.slot] = (int)slots.size();
+      const int k = std::min(kHopRank, std::min(b.m, b.n));
+      slots.push_back(HopSlot{H.arena + b.off + (long long)b.m * b.kcap, w0, j, p.C[b.s].d0, b.n,
+                              b.kcap, (int)(H.rk0 + b.slot)});
+      w0 += b.kcap;
+      kmax = std::max(kmax, b.kcap);
+      flops += 2.0 * (b.m + b.n) * k;
+    }
+    for (int bi : p.dense_blocks) flops += 2.0 * p.B[bi].m * p.B[bi].n;
+    // leaves, with the chain of their ancestors
+    std::vector<int> parent(nc, -1);
+    for (int c = 0; c < nc; ++c)
+      for (int k = 0; k < 2; ++k)
+        if (p.C[c].kid[k] >= 0) parent[p.C[c].kid[k]] = c;
+    for (int c = 0; c < nc; ++c) {
+      if (p.C[c].kid[0] >= 0 || p.C[c].d1 <= p.C[c].d0) continue;
+      HopRow r{j, p.C[c].d0, p.C[c].d1 - p.C[c].d0, (int)items.size(), 0};
+      for (int a = c; a >= 0; a = parent[a])
+        for (int bi : at[a]) {
+          const Block& b = p.B[bi];
+          const int roff = p.C[c].d0 - p.C[b.t].d0;
+          if (b.type == B_DENSE)
+            items.push_back(HopItem{H.arena + b.off, 0, b.m, roff, p.C[b.s].d0, b.n});
+          else
+            items.push_back(HopItem{H.arena + b.off, 1, b.m, roff, slot_rec[b.slot], b.kcap});
+        }
+      r.it1 = (int)items.size();
+      rows.push_back(r);
+    }
+  }
+  f->hop_nrows = (int)rows.size();
+  f->hop_nslots = (int)slots.size();
+  f->hop_wsize = w0;
+  f->hop_kmax = kmax;
+  f->hop_flops = flops;
+  f->d_hrow.alloc(std::max<size_t>(rows.size(), 1));
+  f->d_hitem.alloc(std::max<size_t>(items.size(), 1));
+  f->d_hslot.alloc(std::max<size_t>(slots.size(), 1));
+  if (!rows.empty())
+    HF_CHECK(cudaMemcpyAsync(f->d_hrow.p, rows.data(), rows.size() * sizeof(HopRow),
+                             cudaMemcpyHostToDevice, s->st));
+  if (!items.empty())
+    HF_CHECK(cudaMemcpyAsync(f->d_hitem.p, items.data(), items.size() * sizeof(HopItem),
+                             cudaMemcpyHostToDevice, s->st));
+  if (!slots.empty())
+    HF_CHECK(cudaMemcpyAsync(f->d_hslot.p, slots.data(), slots.size() * sizeof(HopSlot),
+                             cudaMemcpyHostToDevice, s->st));
+  HF_CHECK(cudaStreamSynchronize(s->st));   // host tables go out of scope
+}
+
+constexpr int kHopRB = 4;   // right-hand sides per pass
+
+// x~ = D^-1 x on the kHmat instances (instance-local unknowns, rhs-major).
+__global__ void k_hop_scale(const HInstDev* __restrict__ hi, const InstDev* __restrict__ inst,
+                            const double* __restrict__ D, const double* __restrict__ x, double* xt,
+                            int nrhs) {
+  const HInstDev H = hi[blockIdx.y];
+  const InstDev I = inst[H.sys_inst];
+  const int r = blockIdx.z;
+  const double* xv = x + I.o_vec * nrhs + (long long)r * I.Nd;
+  double* tv = xt + I.o_vec * nrhs + (long long)r * I.Nd;
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < I.Nd; i += gridDim.x * blockDim.x)
+    tv[i] = xv[i] / D[H.d_off + i];
+}
+
+// w_b[k] = sum_j V_b[j][k] x~[c0 + j] for k below the block's rank (0 above),
+// one warp per (block, column k).
+__global__ void k_hop_proj(const HInstDev* __restrict__ hi, const InstDev* __restrict__ inst,
+                           const HopSlot* __restrict__ slots, const int* __restrict__ ranks,
+                           const double* __restrict__ ar, const double* __restrict__ xt, double* w,
+                           long long wsize, int nrhs) {
+  const HopSlot S = slots[blockIdx.x];
+  const HInstDev H = hi[S.inst];
+  const InstDev I = inst[H.sys_inst];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int rank = ranks[S.rk];
+  for (int k = warp; k < S.kcap; k += nw) {
+    for (int r0 = 0; r0 < nrhs; r0 += kHopRB) {
+      double acc[kHopRB];
+#pragma unroll
+      for (int q = 0; q < kHopRB; ++q) acc[q] = 0.0;
+      if (k < rank) {
+        const double* v = ar + S.offV + (long long)k * S.n;
+        for (int j = lane; j < S.n; j += 32) {
+          const double vj = v[j];
+#pragma unroll
+          for (int q = 0; q < kHopRB; ++q)
+            if (r0 + q < nrhs) acc[q] = fma(vj, xt[I.o_vec * nrhs + (long long)(r0 + q) * I.Nd + S.c0 + j], acc[q]);
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kHopRB; ++q) {
+        double t = acc[q];
+        for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+        if (lane == 0 && r0 + q < nrhs) w[(long long)(r0 + q) * wsize + S.w0 + k] = t;
+      }
+    }
+  }
+}
+
+// y_i += D_i^-1 sum over the leaf's blocks (dense: row of D A~ D times x~;
+// low-rank: row of U times w), a thread per row of the leaf.
+__global__ void __launch_bounds__(128) k_hop_rows(const HInstDev* __restrict__ hi,
+                                                  const InstDev* __restrict__ inst,
+                                                  const HopRow* __restrict__ rows,
+                                                  const HopItem* __restrict__ items,
+                                                  const HopSlot* __restrict__ slots,
+                                                  const int* __restrict__ ranks,
+                                                  const double* __restrict__ D,
+                                                  const double* __restrict__ ar,
+                                                  const double* __restrict__ xt,
+                                                  const double* __restrict__ w, long long wsize,
+                                                  double* y, int nrhs) {
+  const HopRow Rw = rows[blockIdx.x];
+  const HInstDev H = hi[Rw.inst];
+  const InstDev I = inst[H.sys_inst];
+  const int r0 = blockIdx.y * kHopRB;
+  const double* xb = xt + I.o_vec * nrhs;
+  for (int i = threadIdx.x; i < Rw.nr; i += blockDim.x) {
+    double acc[kHopRB];
+#pragma unroll
+    for (int q = 0; q < kHopRB; ++q) acc[q] = 0.0;
+    for (int t = Rw.it0; t < Rw.it1; ++t) {
+      const HopItem It = items[t];
+      if (It.kind == 0) {
+        const double* a = ar + It.off + It.roff + i;
+        for (int j = 0; j < It.nc; ++j) {
+          const double aj = a[(long long)j * It.ld];
+#pragma unroll
+          for (int q = 0; q < kHopRB; ++q)
+            if (r0 + q < nrhs) acc[q] = fma(aj, xb[(long long)(r0 + q) * I.Nd + It.c0 + j], acc[q]);
+        }
+      } else {
+        const HopSlot S = slots[It.c0];
+        const int rank = ranks[S.rk];
+        const double* u = ar + It.off + It.roff + i;
+        for (int k = 0; k < rank; ++k) {
+          const double uk = u[(long long)k * It.ld];
+#pragma unroll
+          for (int q = 0; q < kHopRB; ++q)
+            if (r0 + q < nrhs) acc[q] = fma(uk, w[(long long)(r0 + q) * wsize + S.w0 + k], acc[q]);
+        }
+      }
+    }
+    const double di = D[H.d_off + Rw.d0 + i];
+#pragma unroll
+    for (int q = 0; q < kHopRB; ++q)
+      if (r0 + q < nrhs) y[I.o_vec * nrhs + (long long)(r0 + q) * I.Nd + Rw.d0 + i] += acc[q] / di;
+  }
+}
+
+void hop_apply(hfsem_system* s, int nrhs, const double* x, double* y) {
+  hfsem_factor* f = s->hop;
+  if (!f || f->nfi == 0) return;
+  Tick tk(s->st, "hmat_mv", f->hop_flops * nrhs);
+  const long long nx = s->total_nd * nrhs;
+  s->w_hop.ensure((size_t)(nx + f->hop_wsize * nrhs + 1));
+  double* xt = s->w_hop.p;
+  double* w = s->w_hop.p + nx;
+  const double* ar = reinterpret_cast<const double*>(f->d_arena.p);
+  int maxnd = 1;
+  for (int i : f->insts) maxnd = std::max(maxnd, s->ih[i].Nd);
+  k_hop_scale<<<dim3(std::min(1024, (maxnd + 255) / 256), f->nfi, nrhs), 256, 0, s->st>>>(
+      f->d_hi.p, s->d_inst.p, f->d_D.p, x, xt, nrhs);
+  HF_LAUNCH_CHECK();
+  if (f->hop_nslots > 0) {
+    k_hop_proj<<<f->hop_nslots, 256, 0, s->st>>>(f->d_hi.p, s->d_inst.p, f->d_hslot.p, f->d_ranks.p,
+                                                 ar, xt, w, f->hop_wsize, nrhs);
+    HF_LAUNCH_CHECK();
+  }
+  k_hop_rows<<<dim3(f->hop_nrows, (nrhs + kHopRB - 1) / kHopRB), 128, 0, s->st>>>(
+      f->d_hi.p, s->d_inst.p, f->d_hrow.p, f->d_hitem.p, f->d_hslot.p, f->d_ranks.p, f->d_D.p, ar,
+      xt, w, f->hop_wsize, y, nrhs);
+  HF_LAUNCH_CHECK();
 }
 
 }  // namespace hf
@@ -3821,8 +4134,13 @@ void hfsem_factor_s::run_prog() {
 }
 
 void hfsem_factor_s::run_pack() {
-  hf::Tick tk(sys->st, "solve_pack");
-  dim3 g(128, nfi);
+  // algorithmic bytes: every packed column read from the arena and written
+  hf::Tick tk(sys->st, "solve_pack", 2.0 * (double)d_pack.n);
+  // a warp per job column, about four jobs per warp: enough warps in flight
+  // to keep the copy memory-bound for one large instance as for many small
+  int maxjob = 1;
+  for (const auto& H : hidev) maxjob = std::max(maxjob, H.njob);
+  dim3 g((unsigned)std::min(8192, std::max(1, (maxjob + 31) / 32)), nfi);
   if (tsize == sizeof(float))
     hf::k_solve_pack<float><<<g, 256, 0, sys->st>>>(d_hi.p, d_jobs.p, reinterpret_cast<const float*>(d_arena.p),
                                                     d_ranks.p, reinterpret_cast<float*>(d_pack.p), d_meta.p, sol_slot,
@@ -3933,6 +4251,7 @@ namespace hf {
 
 void rebind_stream(hfsem_system* s, hfsem_factor* f, cudaStream_t st) {
   s->st = st;
+  if (s->hop) s->hop->st = st;
   if (!f) return;
   f->st = st;
   for (auto& q : f->parts) q->st = st;
@@ -3944,7 +4263,8 @@ size_t factor_bytes(const hfsem_factor* f) {
              b(f->d_pairs) + b(f->d_ptask) + b(f->d_gmax) + b(f->d_lrt) + b(f->d_steps) +
              b(f->d_step_cta) + b(f->d_jobs) + b(f->d_pack) + b(f->d_meta) + b(f->d_sprof) +
              b(f->d_ranks) + b(f->d_err) + b(f->d_D) + b(f->d_arena) + b(f->d_prof) +
-             b(f->d_flops) + b(f->d_wprof) + b(f->d_tcdbg);
+             b(f->d_flops) + b(f->d_wprof) + b(f->d_tcdbg) + b(f->d_hrow) + b(f->d_hitem) +
+             b(f->d_hslot);
   for (auto& q : f->parts) t += factor_bytes(q.get());
   return t;
 }

@@ -135,7 +135,7 @@ struct Builder {
         b.off = top;
         top = align4(top + (long long)b.m * b.n);
         p.dense_blocks.push_back((int)i);
-        if (b.t == b.s) {
+        if (b.t == b.s && !o.structure_only) {   // room for the inverted factors
           if (b.m > o.max_leaf)
             throw Error(HFSEM_ERR_UNSUPPORTED, "diagonal leaf larger than the kernel supports");
           p.leaf_max = std::max(p.leaf_max, b.m);
@@ -522,6 +522,12 @@ void make_plan(const InstHost& I, const PlanOpts& o, HPlan& p) {
   int root = b.cluster(0, I.N);
   b.block(root, root);
   b.storage();
+  if (o.structure_only) {   // an H-matrix to be built, never factored
+    p.arena = align4(b.top);
+    p.fac_waves.assign(1, 0);
+    p.ncta = std::max(o.ncta, 1);
+    return;
+  }
   b.dirty.assign(p.B.size(), 0);
   b.rank_est.assign(p.n_slots, o.R);
   // right-hand-side area, then temporaries, then the truncation workspace

@@ -104,6 +104,7 @@ struct PlanOpts {
   int max_leaf;      // limit on diagonal leaf size
   int unique_tmp = 0;  // 1: never reuse temporary storage (independent ops stay independent)
   int ncta = 1;        // CTAs per instance (one truncation workspace each)
+  int structure_only = 0;  // 1: clusters, blocks and storage only (no H-LU program)
   int adm_min = 0;     // 0: max(diam tau, diam sigma) <= lambda dist (eq. (admis));
                        // 1: min(...) <= lambda dist, the expansion being taken
                        // about the smaller cluster (Remark after the Lemma)

@@ -104,6 +104,9 @@ extern "C" int hfsem_apply_noalloc(hfsem_system* s, int32_t nrhs, const double* 
       throw Error(HFSEM_ERR_INVALID_ARG, "hfsem_apply_noalloc: bad arguments");
     if (!is_device_ptr(x) || !is_device_ptr(y))
       throw Error(HFSEM_ERR_INVALID_ARG, "hfsem_apply_noalloc: x and y must be device pointers");
+    if (s->any_hmat)
+      throw Error(HFSEM_ERR_INVALID_ARG,
+                  "hfsem_apply_noalloc: dense and Toeplitz operators only (not HFSEM_MATVEC_HMATRIX)");
     // carve the scratch: x and y in element-major order, z, w, ylow, the
     // dense column partials and the FFT buffers
     const size_t nd = (size_t)s->total_nd * nrhs, nz = (size_t)s->total_nz * nrhs;

@@ -396,15 +396,38 @@ __global__ void k_pairs(const InstDev* __restrict__ inst, double* arena,
   const double* D = arena + I.o_D;
   const double* gjx = arena + I.o_gj;
   const double* gjw = gjx + I.n_gj;
-  long long np = (I.kind == kDense) ? (long long)I.N * (I.N + 1) / 2 : I.N;
+  const long long np = (I.kind == kDense)  ? (long long)I.N * (I.N + 1) / 2
+                       : (I.kind == kHmat) ? I.band + 2LL * I.N
+                                           : I.N;
+  const double* off = arena + I.o_off;   // kHmat: pairs before row e
   for (long long p = (long long)blockIdx.x * wpc + warp; p < np;
        p += (long long)gridDim.x * wpc) {
     int e, f;
+    int out_kind = 0;   // 0: block at p; 1: column f = 0 (c0); 2: row e = N-1 (rN)
     if (I.kind == kDense) {
       e = (int)((sqrt(8.0 * (double)p + 1.0) - 1.0) * 0.5);
       while ((long long)e * (e + 1) / 2 > p) --e;
       while ((long long)(e + 1) * (e + 2) / 2 <= p) ++e;
       f = (int)(p - (long long)e * (e + 1) / 2);
+    } else if (I.kind == kHmat) {
+      if (p < I.band) {
+        int lo = 0, hi = I.N - 1;   // the row e with off[e] <= p < off[e+1]
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if ((long long)off[mid] <= p) lo = mid;
+          else hi = mid - 1;
+        }
+        e = lo;
+        f = (int)arena[I.o_flo + e] + (int)(p - (long long)off[e]);
+      } else if (p < I.band + I.N) {
+        e = (int)(p - I.band);
+        f = 0;
+        out_kind = 1;
+      } else {
+        e = I.N - 1;
+        f = (int)(p - I.band - I.N);
+        out_kind = 2;
+      }
     } else {
       e = (int)p;
       f = 0;
@@ -417,8 +440,14 @@ __global__ void k_pairs(const InstDev* __restrict__ inst, double* arena,
     pair_block(s, P, I.alpha, h[e], h[f], g, kind, D, gjx, gjw, I.n_gj, gl, lane);
     double sc = I.g0;
     if (I.kind == kToeplitz) sc /= arena[I.o_rs + e] * arena[I.o_cs + f];
-    double* out = arena + I.o_M + p * P * P;
-    for (int k = lane; k < P * P; k += 32) out[k] = sc * s.acc[k];
+    if (out_kind == 0) {
+      double* out = arena + I.o_M + p * P * P;
+      for (int k = lane; k < P * P; k += 32) out[k] = sc * s.acc[k];
+    } else if (out_kind == 1) {   // mode n = 0 of block (e, 0): c0[e][m]
+      for (int m = lane; m < P; m += 32) arena[I.o_c0 + (long long)e * P + m] = sc * s.acc[m * P];
+    } else {                      // mode m = 0 of block (N-1, f): rN[f][n]
+      for (int n = lane; n < P; n += 32) arena[I.o_rN + (long long)f * P + n] = sc * s.acc[n];
+    }
     __syncwarp();
   }
 }
@@ -499,13 +528,16 @@ __global__ void k_gather_z(const InstDev* __restrict__ inst, const double* arena
   for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < N * P;
        t += gridDim.x * blockDim.x) {
     int e = t / P, m = t % P;
+    // kHmat instances: the boundary values only (the H-matrix operator adds
+    // the interior unknowns' product itself)
+    const bool bnd_only = I.kind == kHmat;
     double val;
     if (m == 0) {
-      double uL = (e == 0) ? (lift ? I.c1 : 0.0) : xv[e * P - 1];
-      double uR = (e == N - 1) ? (lift ? I.c2 : 0.0) : xv[(e + 1) * P - 1];
+      double uL = (e == 0) ? (lift ? I.c1 : 0.0) : (bnd_only ? 0.0 : xv[e * P - 1]);
+      double uR = (e == N - 1) ? (lift ? I.c2 : 0.0) : (bnd_only ? 0.0 : xv[(e + 1) * P - 1]);
       val = uR - uL;
     } else {
-      val = -2.0 * (2.0 * m + 1.0) * xv[e * P + m - 1];
+      val = bnd_only ? 0.0 : -2.0 * (2.0 * m + 1.0) * xv[e * P + m - 1];
     }
     zv[t] = val;
   }
@@ -520,6 +552,9 @@ __global__ void k_scatter_out(const InstDev* __restrict__ inst, const double* ar
   const int P = I.P, N = I.N;
   const double* h = arena + I.o_h;
   const double* xv = x + I.o_vec * nrhs + (size_t)r * I.Nd;
+  // kHmat instances: the mass of the boundary hats only (the H-matrix
+  // operator holds rho M on the interior unknowns)
+  const bool bnd_only = I.kind == kHmat;
   const double* wv = w + I.o_z * nrhs + (size_t)r * N * P;
   double* yv = y + I.o_vec * nrhs + (size_t)r * I.Nd;
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < I.Nd;
@@ -531,14 +566,14 @@ __global__ void k_scatter_out(const InstDev* __restrict__ inst, const double* ar
       out = -2.0 * (2.0 * p + 1.0) * wv[e * P + p];
       if (I.rho != 0.0) {
         // local mass on [L, R, psi_1..]: scaled by h/2
-        double uL = (e == 0) ? (lift ? I.c1 : 0.0) : xv[e * P - 1];
-        double uR = (e == N - 1) ? (lift ? I.c2 : 0.0) : xv[(e + 1) * P - 1];
+        double uL = (e == 0) ? (lift ? I.c1 : 0.0) : (bnd_only ? 0.0 : xv[e * P - 1]);
+        double uR = (e == N - 1) ? (lift ? I.c2 : 0.0) : (bnd_only ? 0.0 : xv[(e + 1) * P - 1]);
         double acc = 0.0;
         if (p == 1) acc += uL + uR;
         if (p == 2) acc += (-uL + uR) / 3.0;
-        acc += (2.0 / (2 * p - 1) + 2.0 / (2 * p + 3)) * xv[e * P + p - 1];
-        if (p + 2 < P) acc += -2.0 / (2 * p + 3) * xv[e * P + p + 1];
-        if (p - 2 >= 1) acc += -2.0 / (2 * p - 1) * xv[e * P + p - 3];
+        acc += (2.0 / (2 * p - 1) + 2.0 / (2 * p + 3)) * (bnd_only ? 0.0 : xv[e * P + p - 1]);
+        if (p + 2 < P) acc += -2.0 / (2 * p + 3) * (bnd_only ? 0.0 : xv[e * P + p + 1]);
+        if (p - 2 >= 1) acc += -2.0 / (2 * p - 1) * (bnd_only ? 0.0 : xv[e * P + p - 3]);
         out += I.rho * 0.5 * he * acc;
       }
     } else {
@@ -547,17 +582,17 @@ __global__ void k_scatter_out(const InstDev* __restrict__ inst, const double* ar
       double hl = h[j - 1], hr = h[j];
       out = wv[(j - 1) * P] - wv[j * P];
       if (I.rho != 0.0) {
-        double uj = xv[i];
-        double ul = (j - 1 == 0) ? (lift ? I.c1 : 0.0) : xv[(j - 1) * P - 1];
-        double ur = (j + 1 == N) ? (lift ? I.c2 : 0.0) : xv[(j + 1) * P - 1];
+        double uj = (bnd_only ? 0.0 : xv[i]);
+        double ul = (j - 1 == 0) ? (lift ? I.c1 : 0.0) : (bnd_only ? 0.0 : xv[(j - 1) * P - 1]);
+        double ur = (j + 1 == N) ? (lift ? I.c2 : 0.0) : (bnd_only ? 0.0 : xv[(j + 1) * P - 1]);
         // element j-1 (local R): RR = 2/3, RL = 1/3, R psi_1 = 1, R psi_2 = 1/3
         double accl = (2.0 / 3.0) * uj + (1.0 / 3.0) * ul;
-        if (P > 1) accl += xv[(j - 1) * P + 0];
-        if (P > 2) accl += xv[(j - 1) * P + 1] / 3.0;
+        if (P > 1) accl += (bnd_only ? 0.0 : xv[(j - 1) * P + 0]);
+        if (P > 2) accl += (bnd_only ? 0.0 : xv[(j - 1) * P + 1]) / 3.0;
         // element j (local L): LL = 2/3, LR = 1/3, L psi_1 = 1, L psi_2 = -1/3
         double accr = (2.0 / 3.0) * uj + (1.0 / 3.0) * ur;
-        if (P > 1) accr += xv[j * P + 0];
-        if (P > 2) accr -= xv[j * P + 1] / 3.0;
+        if (P > 1) accr += (bnd_only ? 0.0 : xv[j * P + 0]);
+        if (P > 2) accr -= (bnd_only ? 0.0 : xv[j * P + 1]) / 3.0;
         out += I.rho * (0.5 * hl * accl + 0.5 * hr * accr);
       }
     }
@@ -617,6 +652,38 @@ __global__ void k_dense_rows(const InstDev* __restrict__ inst, const double* are
     double s = 0.0;
     for (int w = 0; w < W; ++w) s += yacc[(w * nrhs + r) * P + m];
     ylow[I.o_z * nrhs + r * NP + (size_t)e * P + m] = s;
+  }
+}
+
+// Boundary columns of a kHmat instance (lifting): z holds only the boundary
+// values (z_0[0] = -c1, z_{N-1}[0] = c2; c2 - c1 for N = 1), and
+//   w = theta M z + (1 - theta) M^T z
+// needs of the stored pairs only the column f = 0 and the row e = N-1 (plus
+// the diagonal pairs (0,0) and (N-1,N-1) of the band).
+__global__ void k_lift_hmat(const InstDev* __restrict__ inst, const double* __restrict__ arena,
+                            const double* __restrict__ z, double* w, int nrhs) {
+  const InstDev I = inst[blockIdx.y];
+  if (I.kind != kHmat) return;
+  const int P = I.P, N = I.N, r = blockIdx.z;
+  const double* zv = z + I.o_z * nrhs + (size_t)r * N * P;
+  double* wv = w + I.o_z * nrhs + (size_t)r * N * P;
+  const double a0 = zv[0];
+  const double aN = (N > 1) ? zv[(size_t)(N - 1) * P] : 0.0;
+  const double* c0 = arena + I.o_c0;
+  const double* rN = arena + I.o_rN;
+  const double* M = arena + I.o_M;
+  const long long PP = (long long)P * P;
+  const long long d0 = (long long)arena[I.o_off];                       // pair (0, 0)
+  const long long dN = (long long)arena[I.o_off + N] - 1;               // pair (N-1, N-1)
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < N * P; t += gridDim.x * blockDim.x) {
+    const int e = t / P, m = t % P;
+    double lo = a0 * c0[t];                                   // (M z)_e[m], column 0
+    double up = (e == 0) ? a0 * M[d0 * PP + m] : 0.0;         // (M^T z)_e[m], row 0
+    if (N > 1) {
+      if (e == N - 1) lo += aN * M[dN * PP + (long long)m * P];
+      up += aN * rN[t];                                       // row N-1
+    }
+    wv[t] = I.theta * lo + (1.0 - I.theta) * up;
   }
 }
 
@@ -1151,9 +1218,15 @@ void apply_operator(hfsem_system* s, int nrhs, const double* x, double* y, int l
                                                              s->tw.p, s->tw_L, nrhs);
     HF_LAUNCH_CHECK();
   }
+  if (s->any_hmat) {
+    k_lift_hmat<<<grid1((long long)s->max_N * s->max_P, 256, ni, nrhs), 256, 0, s->st>>>(
+        di, s->arena.p, z, w, nrhs);
+    HF_LAUNCH_CHECK();
+  }
   k_scatter_out<<<grid1((long long)s->max_N * s->max_P, 256, ni, nrhs), 256, 0, s->st>>>(
       di, s->arena.p, w, x, y, nrhs, lift);
   HF_LAUNCH_CHECK();
+  if (s->any_hmat) hop_apply(s, nrhs, x, y);   // y += A x on the kHmat instances
 }
 
 void perm_to_elem(hfsem_system* s, int nrhs, const double* xp, double* xe) {
@@ -1257,6 +1330,8 @@ void load_vector_em(hfsem_system* s, const hfsem_rhs* rhs, int lifted, double* G
 }
 
 static void validate(const hfsem_problem& p) {
+  if (p.matvec < HFSEM_MATVEC_AUTO || p.matvec > HFSEM_MATVEC_HMATRIX)
+    throw Error(HFSEM_ERR_INVALID_ARG, "unknown matvec kind");
   if (p.n_elem < 1) throw Error(HFSEM_ERR_INVALID_ARG, "n_elem must be >= 1");
   if (p.P < 1 || p.P > kMaxP) throw Error(HFSEM_ERR_INVALID_ARG, "P must be in [1, 32]");
   if (!(p.alpha > 1.0 && p.alpha < 2.0)) throw Error(HFSEM_ERR_INVALID_ARG, "alpha must be in (1, 2)");
@@ -1323,7 +1398,7 @@ static hfsem_system* assemble(int n, const hfsem_problem* probs, void* stream) {
         throw Error(HFSEM_ERR_INVALID_ARG, "Toeplitz operator needs h_{i+1}/h_i constant");
       bool toep = (p.matvec == HFSEM_MATVEC_TOEPLITZ) ||
                   (p.matvec == HFSEM_MATVEC_AUTO && geo && hmax <= 16.0 * hmin && I.N >= 2);
-      I.kind = toep ? kToeplitz : kDense;
+      I.kind = toep ? kToeplitz : (p.matvec == HFSEM_MATVEC_HMATRIX ? kHmat : kDense);
       D.N = I.N;
       D.P = I.P;
       D.Nd = I.Nd;
@@ -1350,9 +1425,28 @@ static hfsem_system* assemble(int n, const hfsem_problem* probs, void* stream) {
       arena += I.N;
       D.o_cs = arena;
       arena += I.N;
-      D.o_M = arena;
-      long long nblk = (I.kind == kDense) ? (long long)I.N * (I.N + 1) / 2 : I.N;
-      arena += nblk * I.P * I.P;
+      if (I.kind == kHmat) {
+        // the pairs the operator's near field needs (a band per row e), the
+        // boundary column f = 0 and row e = N-1 (lifting), and their tables
+        hop_band(I, I.flo);
+        long long band = 0;
+        for (int e = 0; e < I.N; ++e) band += e - I.flo[e] + 1;
+        D.band = band;
+        D.o_flo = arena;
+        arena += I.N;
+        D.o_off = arena;
+        arena += I.N + 1;
+        D.o_c0 = arena;
+        arena += (long long)I.N * I.P;
+        D.o_rN = arena;
+        arena += (long long)I.N * I.P;
+        D.o_M = arena;
+        arena += band * I.P * I.P;
+      } else {
+        D.o_M = arena;
+        long long nblk = (I.kind == kDense) ? (long long)I.N * (I.N + 1) / 2 : I.N;
+        arena += nblk * I.P * I.P;
+      }
       D.o_vec = s->total_nd;
       D.o_z = s->total_nz;
       D.o_N = s->total_N;
@@ -1363,6 +1457,8 @@ static hfsem_system* assemble(int n, const hfsem_problem* probs, void* stream) {
         D.o_T = s->total_T;
         s->total_T += (long long)I.N * (I.N + 1) / 2 * I.P;
         s->any_dense = true;
+      } else if (I.kind == kHmat) {
+        s->any_hmat = true;
       } else {
         D.logL = ceil_log2(2LL * I.N);
         D.L = 1 << D.logL;
@@ -1396,6 +1492,15 @@ static hfsem_system* assemble(int n, const hfsem_problem* probs, void* stream) {
         host[D.o_rs + k] = 0.5;
         host[D.o_cs + k] = I.g0 * 0.5 * std::pow(I.h[k], 1.0 - I.alpha);
       }
+      if (I.kind == kHmat) {
+        long long off = 0;
+        for (int e = 0; e < I.N; ++e) {
+          host[D.o_flo + e] = I.flo[e];
+          host[D.o_off + e] = (double)off;
+          off += e - I.flo[e] + 1;
+        }
+        host[D.o_off + I.N] = (double)off;
+      }
     }
     HF_CHECK(cudaMemcpyAsync(s->arena.p, host.data(), host.size() * sizeof(double),
                              cudaMemcpyHostToDevice, s->st));
@@ -1413,8 +1518,13 @@ static hfsem_system* assemble(int n, const hfsem_problem* probs, void* stream) {
     size_t sm = (size_t)wpc * stride * sizeof(double);
     set_smem((const void*)k_pairs, sm);
     long long maxpairs = 1;
-    for (auto& I : s->ih)
-      maxpairs = std::max(maxpairs, I.kind == kDense ? (long long)I.N * (I.N + 1) / 2 : (long long)I.N);
+    for (size_t i = 0; i < s->ih.size(); ++i) {
+      const InstHost& I = s->ih[i];
+      const long long np = I.kind == kDense  ? (long long)I.N * (I.N + 1) / 2
+                           : I.kind == kHmat ? s->idv[i].band + 2LL * I.N
+                                             : (long long)I.N;
+      maxpairs = std::max(maxpairs, np);
+    }
     long long gx = std::min<long long>((maxpairs + wpc - 1) / wpc, 65535);
     Tick tk(s->st, "pairs");
     k_pairs<<<dim3((unsigned)gx, n), wpc * 32, sm, s->st>>>(s->d_inst.p, s->arena.p, s->gl.p,
@@ -1428,6 +1538,7 @@ static hfsem_system* assemble(int n, const hfsem_problem* probs, void* stream) {
                                                                   s->spec.p, s->tw.p, s->tw_L);
       HF_LAUNCH_CHECK();
     }
+    if (s->any_hmat) build_operator(s);
     HF_CHECK(cudaStreamSynchronize(s->st));
   } catch (...) {
     drain_after_error(s);
@@ -1477,7 +1588,8 @@ size_t system_bytes(const hfsem_system* s) {
   return b(s->d_inst) + b(s->arena) + b(s->spec) + b(s->gl) + b(s->w_x) + b(s->w_y) + b(s->w_z) +
          b(s->w_w) + b(s->w_T) + b(s->w_ylow) + b(s->w_mom) + b(s->w_fa) + b(s->w_fb) +
          b(s->w_rhsdata) + b(s->tw) + b(s->kry.vecs) + b(s->kry.partial) + b(s->kry.bx) +
-         b(s->kry.coff) + b(s->kry.clen) + b(s->kry.flag) + b(s->kry.cols);
+         b(s->kry.coff) + b(s->kry.clen) + b(s->kry.flag) + b(s->kry.cols) + b(s->w_hop) +
+         (s->hop ? factor_bytes(s->hop) : 0);
 }
 }  // namespace hf
 
@@ -1546,6 +1658,8 @@ int hfsem_load_vector(hfsem_system* sys, const hfsem_rhs* rhs, int32_t lifted, d
 void hfsem_system_free(hfsem_system* sys) {
   if (!sys) return;
   cudaStreamSynchronize(sys->st);
+  if (sys->hop) hfsem_factor_free(sys->hop);
+  sys->hop = nullptr;
   delete sys;
 }
 

@@ -25,7 +25,7 @@ HFSEM_ERR_TIMEOUT = 5
 HFSEM_ERR_DEVICE = 6
 HFSEM_ERR_UNSUPPORTED = 7
 
-MATVEC_AUTO, MATVEC_DENSE, MATVEC_TOEPLITZ = 0, 1, 2
+MATVEC_AUTO, MATVEC_DENSE, MATVEC_TOEPLITZ, MATVEC_HMATRIX = 0, 1, 2, 3
 PREC_FP64, PREC_MIXED, PREC_MIXED_TC = 0, 1, 2   # PREC_MIXED_TC: dense leaf products of the H-LU on the tensor cores
 RHS_LOAD_VECTOR, RHS_FRAC_POWERS, RHS_LEGENDRE_AB = 0, 1, 2
 ADM_MAX, ADM_MIN = 0, 1   # admissibility: eq. (admis) as printed, or min(diam) <= lambda dist
@@ -219,7 +219,7 @@ def make_problem(h, P, alpha, theta, rho, a=0.0, b=None, c1=0.0, c2=0.0,
     """One instance: element lengths h (N of them, summing to b - a; b defaults
     to a + sum h), degree P, 1 < alpha < 2, 0 <= theta <= 1, rho >= 0,
     boundary values c1 = u(a), c2 = u(b), operator MATVEC_AUTO / _DENSE /
-    _TOEPLITZ."""
+    _TOEPLITZ / _HMATRIX."""
     h = np.ascontiguousarray(h, dtype=np.float64)
     if b is None:
         b = a + float(h.sum())

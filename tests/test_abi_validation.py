@@ -34,6 +34,7 @@ BAD = [
     dict(rho=-1.0), dict(rho=float("inf")),
     dict(P=0), dict(P=33),
     dict(n_elem=0),
+    dict(matvec=4), dict(matvec=-1),
     dict(h=None),
     dict(h=np.array([0.5, 0.5, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0])),      # zero lengths
     dict(h=np.full(8, 0.2)),                                           # sum(h) != b - a
