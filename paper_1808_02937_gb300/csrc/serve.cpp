@@ -117,10 +117,13 @@ void estimate(const hfsem_problem& p, int nrhs, const hfsem_hopts& o, bool unifo
   const double ts = o.precision == HFSEM_PREC_FP64 ? 8.0 : 4.0;
   double L = 1;
   while (L < 2 * N) L *= 2;
-  const double sys = uniform ? 8.0 * N * P * P + 16.0 * (L + 1) * P * P + 64.0 * N
-                             : 8.0 * P * P * N * (N + 1) / 2 + 64.0 * N;
   const double leaf = std::min(128.0, std::max(P, std::floor(128.0 / P) * P));
   const double lg = std::max(1.0, std::log2(std::max(2.0, Nd / leaf)));
+  // H-matrix operator: near-field pairs plus an FP64 H-matrix of rank 24
+  const double hop = 8.0 * Nd * (6.0 * leaf + 6.0 * kHopRank * lg * 2.0) + 16.0 * N * P * P;
+  const double sys = uniform                           ? 8.0 * N * P * P + 16.0 * (L + 1) * P * P + 64.0 * N
+                     : p.matvec == HFSEM_MATVEC_HMATRIX ? hop
+                                                        : 8.0 * P * P * N * (N + 1) / 2 + 64.0 * N;
   const double fac = ts * Nd * (4.0 * leaf + 6.0 * o.R * lg * 4.0) + 4.0 * Nd * 64 + (1 << 20);
   const double vec = 8.0 * Nd * nrhs * 14 + 8.0 * N * P * nrhs * 4;
   const double op = uniform ? 16.0 * 2 * L * P * nrhs : 0.0;   // FFT buffers

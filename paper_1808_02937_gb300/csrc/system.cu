@@ -1349,8 +1349,6 @@ static void validate(const hfsem_problem& p) {
   }
   if (std::fabs(sum - (p.b - p.a)) > 1e-12 * (p.b - p.a))
     throw Error(HFSEM_ERR_INVALID_ARG, "sum of h differs from b - a");
-  if (p.matvec < HFSEM_MATVEC_AUTO || p.matvec > HFSEM_MATVEC_TOEPLITZ)
-    throw Error(HFSEM_ERR_INVALID_ARG, "unknown matvec kind");
 }
 
 static hfsem_system* assemble(int n, const hfsem_problem* probs, void* stream) {
