@@ -120,7 +120,7 @@ def test_hmatrix_solves_reach_oracle(lib, prec):
 def test_preconditioner_outside_stored_near_field_refused(lib):
     # the paper's max-diameter rule needs far more near-field pairs on a
     # geometric mesh than the operator stores
-    sys_ = H.hfsem_assemble([H.make_problem(W.mesh_geometric_two_sided(64, 0.4), 4, 1.5, 0.5, 1.0,
+    sys_ = H.hfsem_assemble([H.make_problem(W.mesh_geometric_two_sided(256, 0.7), 4, 1.5, 0.5, 1.0,
                                             matvec=HM)])
     with pytest.raises(H.HfsemError) as e:
         H.hfsem_hlu_factor(sys_, H.hopts(R=8, admissibility=H.ADM_MAX))
