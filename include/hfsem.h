@@ -220,6 +220,15 @@ int hfsem_hmatrix_dense(const hfsem_factor *fac, int32_t inst, double *out);
 int hfsem_precond_apply(hfsem_factor *fac, int32_t nrhs, const double *r,
                         double *y);
 
+/* Direct solve of the H-matrix approximation system A~ X = G (Sec. 4.1,
+ * the "H-matrix approximation system" of Sec. 5): X = (L_H U_H)^-1 G with
+ * the load vector of rhs (boundary values lifted), no Krylov iteration.
+ * Its accuracy is that of A~ (the Taylor rank R and Tol_HLU), which the
+ * paper shows falling behind the discretisation error as N grows; solve
+ * with hfsem_solve for the exact discrete solution.  X: N_d x nrhs per
+ * instance (host or device). */
+int hfsem_hlu_solve(hfsem_system *sys, hfsem_factor *fac, const hfsem_rhs *rhs, double *X);
+
 /* Solve A X = G for every instance by BiCGSTAB (Sec. 4.2) right-
  * preconditioned with the H-LU factor `fac` (NULL: no preconditioner),
  * from X = 0.  rhs: n_inst entries, equal nrhs.  A column whose recursive

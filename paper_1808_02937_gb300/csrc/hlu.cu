@@ -4348,6 +4348,44 @@ int hfsem_hmatrix_dense(const hfsem_factor* fac, int32_t inst, double* out) {
   }
 }
 
+int hfsem_hlu_solve(hfsem_system* sys, hfsem_factor* fac, const hfsem_rhs* rhs, double* X) {
+  try {
+    if (!sys || !fac || !rhs || !X) throw Error(HFSEM_ERR_INVALID_ARG, "NULL argument");
+    if (fac->sys != sys) throw Error(HFSEM_ERR_INVALID_ARG, "factor belongs to another system");
+    if (fac->build_only) throw Error(HFSEM_ERR_INVALID_ARG, "factor was built with build_only");
+    const int nrhs = rhs[0].nrhs;
+    if (nrhs < 1 || nrhs > 64) throw Error(HFSEM_ERR_INVALID_ARG, "nrhs must be in [1, 64]");
+    AllocStream as(sys->st);
+    ensure_work(sys, nrhs);
+    const size_t cnt = (size_t)sys->total_nd * nrhs;
+    DevBuf<double> g, y;
+    g.alloc(std::max<size_t>(cnt, 1));
+    y.alloc(std::max<size_t>(cnt, 1));
+    load_vector_em(sys, rhs, 1, g.p);          // G with the boundary lifting
+    fac->apply(nrhs, g.p, y.p);                // (L_H U_H)^-1 G
+    perm_to_paper(sys, nrhs, y.p, sys->w_y.p);
+    HF_CHECK(cudaMemcpyAsync(X, sys->w_y.p, cnt * sizeof(double),
+                             is_device_ptr(X) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                             sys->st));
+    HF_CHECK(cudaStreamSynchronize(sys->st));
+    if (fac->device_status() == HFSEM_ERR_TIMEOUT)
+      throw Error(HFSEM_ERR_TIMEOUT, "an H-solve copy did not complete within its wait limit");
+    return HFSEM_OK;
+  } catch (const Error& e) {
+    set_last_error(e.msg);
+    drain_after_error(sys);
+    return e.code;
+  } catch (const std::bad_alloc&) {
+    set_last_error("host allocation failed");
+    drain_after_error(sys);
+    return HFSEM_ERR_OOM;
+  } catch (...) {
+    set_last_error("unknown error");
+    drain_after_error(sys);
+    return HFSEM_ERR_DEVICE;
+  }
+}
+
 int hfsem_precond_apply(hfsem_factor* fac, int32_t nrhs, const double* r, double* y) {
   try {
     if (!fac || !r || !y || nrhs < 1 || nrhs > 64) throw Error(HFSEM_ERR_INVALID_ARG, "bad arguments");

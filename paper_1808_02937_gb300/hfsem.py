@@ -38,7 +38,7 @@ EXPORTED = ["hfsem_assemble", "hfsem_ndof", "hfsem_apply", "hfsem_load_vector",
             "hfsem_timing_read", "hfsem_apply_noalloc", "hfsem_tc_tile_check",
             "hfsem_last_error", "hfsem_server_create", "hfsem_server_submit",
             "hfsem_server_poll", "hfsem_server_drain", "hfsem_server_counters_read",
-            "hfsem_server_free", "hfsem_alu_peak"]
+            "hfsem_server_free", "hfsem_alu_peak", "hfsem_hlu_solve"]
 
 
 class HfsemError(RuntimeError):
@@ -132,6 +132,7 @@ def load_library():
     lib.hfsem_server_counters_read.argtypes = [vp, C.POINTER(hfsem_server_counters)]
     lib.hfsem_server_free.argtypes = [vp]
     lib.hfsem_server_free.restype = None
+    lib.hfsem_hlu_solve.argtypes = [vp, vp, C.POINTER(hfsem_rhs), vp]
     lib.hfsem_alu_peak.argtypes = [C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                    C.POINTER(C.c_int32)]
     lib.hfsem_timing_enable.argtypes = [C.c_int32]
@@ -365,6 +366,17 @@ def hfsem_precond_apply(fac: Factor, r, nrhs: int = 1):
     _check(load_library().hfsem_precond_apply(fac.h, nrhs, _ptr(r), _ptr(y)),
            "hfsem_precond_apply")
     return y
+
+
+def hfsem_hlu_solve(sys: System, fac: Factor, rhs_list, X=None):
+    """Direct solve of the H-matrix approximation system A~ X = G by the two
+    H-triangular solves (no Krylov iteration); X as in hfsem_solve."""
+    arr, keep = _rhs_array(rhs_list)
+    nrhs = rhs_list[0][1]
+    if X is None:
+        X = np.zeros(sys.total_ndof * nrhs)
+    _check(load_library().hfsem_hlu_solve(sys.h, fac.h, arr, _ptr(X)), "hfsem_hlu_solve")
+    return X
 
 
 def hfsem_solve(sys: System, fac, rhs_list, tol=1e-14, max_iter=200, X=None,

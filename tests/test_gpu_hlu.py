@@ -6,6 +6,7 @@ import pytest
 from oracle.assemble import system_full
 from oracle.basis import Mesh, n_dof
 from oracle.hmatrix import hmatrix_dense
+from oracle.load import load_frac_powers
 from oracle.solve import dense_solve, solve_problem
 from paper_1808_02937_gb300 import hfsem as H
 from paper_1808_02937_gb300 import workloads as W
@@ -129,3 +130,36 @@ def test_factor_is_tied_to_its_system(lib):
     assert code == H.HFSEM_ERR_INVALID_ARG
     X, st, code = H.hfsem_solve(s1, f1, rhs, tol=1e-12, max_iter=20)
     assert code == H.HFSEM_OK
+
+
+def test_direct_hmatrix_solve_falls_behind_with_n(lib):
+    # Sec. 5, Example 1 (graded x_i = 10 (i/N)^5, alpha = 1.6, theta = 1,
+    # rho = 0, P = 3, R = 3, Tol_HLU = 1e-13): the H-matrix approximation
+    # system solved directly (hfsem_hlu_solve) matches the oracle's dense
+    # solve of A~, and its error against the exact discrete solution grows
+    # with N, while BiCGSTAB preconditioned by the same factor reaches the
+    # exact discrete solution at every N
+    a, b, gam, alpha, P, R = 0.0, 10.0, 0.8, 1.6, 3, 3
+    terms, _, _ = W.manufactured_rhs([1.0, -(b - a) ** (1 - gam)], alpha, 1.0, 0.0, a, b,
+                                     powers=[1.0, gam])
+    errs = []
+    for N in (50, 100, 200, 400):
+        h = W.mesh_graded(N, 5.0, a, b)
+        m = Mesh(h, a, b)
+        Nd = n_dof(N, P)
+        A = system_full(m, P, alpha, 1.0, 0.0)
+        Xo, _ = solve_problem(m, P, alpha, 1.0, 0.0, 0.0, 0.0, ("frac_powers", terms), A_full=A)
+        At, _ = hmatrix_dense(m, P, alpha, 1.0, A, R, 1.0, leaf=4)
+        G = load_frac_powers(m, P, terms)[:Nd]
+        XHo, _ = dense_solve(At, G)
+        sys = H.hfsem_assemble([H.make_problem(h, P, alpha, 1.0, 0.0, a=a, b=b)])
+        fac = H.hfsem_hlu_factor(sys, H.hopts(R=R, lam=1.0, tol_hlu=1e-13, precision=H.PREC_FP64,
+                                              leaf_elems=4))
+        XH = H.hfsem_hlu_solve(sys, fac, [H.rhs_frac_powers([terms])])
+        assert rel_err(XH, XHo) < 1e-9, N
+        XK, st, code = H.hfsem_solve(sys, fac, [H.rhs_frac_powers([terms])], tol=1e-14, max_iter=50)
+        assert code == H.HFSEM_OK and rel_err(XK, Xo) < 1e-10, (N, st)
+        errs.append(rel_err(XH, Xo))
+    # measured with the oracle: 2.8e-4, 1.5e-2, 8.0e-2, 2.4e-1
+    assert all(e1 < e2 for e1, e2 in zip(errs, errs[1:])), errs
+    assert errs[-1] > 1e-2, errs
