@@ -65,6 +65,7 @@ def parse():
     ap.add_argument("--workload", default="serve", choices=["serve", "batch"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the config-4 object")
+    ap.add_argument("--slots", type=int, default=SLOTS, help="concurrent requests when serving")
     # profiling only: the first n instances of the config-4 batch (--workload batch)
     ap.add_argument("--batch-instances", type=int, default=512)
     return ap.parse_args()
@@ -264,7 +265,7 @@ def run_serving(H, torch, args, world, rank, local):
     warm_w, timed_w = warm[:max(args.warmup, 3)], warm[max(args.warmup, 3):]
     arms = {}
     for name, prec in (("mixed", H.PREC_MIXED), ("fp64", H.PREC_FP64)):
-        SERVERS[name] = H.Server(slots=SLOTS, cache_factors=256,
+        SERVERS[name] = H.Server(slots=args.slots, cache_factors=256,
                                  hopts_=H.hopts(R=8, lam=1.0, tol_hlu=1e-3, precision=prec,
                                                 admissibility=H.ADM_MIN),
                                  tol=TOL, max_iter=MAX_ITER)
@@ -560,7 +561,7 @@ def main():
                              ">1e45)",
                     "data": "synthetic",
                     "config": {"workload": SERVE_WORKLOAD, "requests_per_step": W_REQ,
-                               "slots": SLOTS, "offered_rate_req_per_s": S["rate"],
+                               "slots": args.slots, "offered_rate_req_per_s": S["rate"],
                                "l2": "working set of a window well above L2 (129 MB): operators and "
                                      "factors of every request stay resident",
                                "krylov_tol": TOL},

@@ -396,8 +396,10 @@ __global__ void k_pairs(const InstDev* __restrict__ inst, double* arena,
   const double* D = arena + I.o_D;
   const double* gjx = arena + I.o_gj;
   const double* gjw = gjx + I.n_gj;
+  // kHmat: the boundary column and row only serve the lifting of c1, c2
+  const bool lift = I.c1 != 0.0 || I.c2 != 0.0;
   const long long np = (I.kind == kDense)  ? (long long)I.N * (I.N + 1) / 2
-                       : (I.kind == kHmat) ? I.band + 2LL * I.N
+                       : (I.kind == kHmat) ? I.band + (lift ? 2LL * I.N : 0LL)
                                            : I.N;
   const double* off = arena + I.o_off;   // kHmat: pairs before row e
   for (long long p = (long long)blockIdx.x * wpc + warp; p < np;
@@ -1022,6 +1024,30 @@ __global__ void k_load_moments(const InstDev* __restrict__ inst, const double* a
             double sgn = (side == 1 && (m & 1)) ? -1.0 : 1.0;
             g[m] += scale * sgn * c;
             c *= (mu - m) / (mu + m + 2.0);
+          }
+        } else if (d0 >= 0.5 * he) {
+          // the singularity of (d0 + o)^mu lies 2 d0 / h beyond the end of
+          // the reference interval: Gauss-Legendre with enough points for
+          // the Bernstein ellipse through it (error ~ rho^-(2n - P), kept
+          // below 1e-16), applied directly
+          const double t = 1.0 + 2.0 * d0 / he;
+          const double rho = t + sqrt(t * t - 1.0);
+          const int nq = min((int)ceil(0.5 * P + 18.5 / log(rho)) + 2, kMaxGL);
+          const double* X = gl + gl_off(nq);
+          const double* Wt = X + nq;
+          for (int q = 0; q < nq; ++q) {
+            const double o = 0.5 * he * (1.0 + X[q]);   // offset from the node nearest the end
+            const double wq = coef * 0.5 * he * Wt[q] * pow(d0 + o, mu);
+            const double xi = (side == 0) ? X[q] : -X[q];
+            double l0 = 1.0, l1 = xi;
+            g[0] += wq;
+            if (P >= 1) g[1] += wq * l1;
+            for (int k = 1; k < P; ++k) {
+              double l2 = ((2 * k + 1) * xi * l1 - k * l0) / (k + 1);
+              g[k + 1] += wq * l2;
+              l0 = l1;
+              l1 = l2;
+            }
           }
         } else {
           // offset o from the node nearest the endpoint, distance d0 + o;
