@@ -157,13 +157,22 @@ struct InstHost {
 // Per-column BiCGSTAB scalars (one column = one instance x one rhs).
 struct KCol {
   double rho, rho_old, alpha, omega, beta, bnorm2, res, snorm, true_res;
-  int status, iters, restarts;
+  int status, iters, restarts, checks;
 };
+
+// Kernels of a region the host enqueued ahead of knowing whether it is
+// needed (a Krylov iteration after every column may already have stopped)
+// take a device flag and return at once while it is 0; nullptr: always run.
+#define HF_GATE(g)                       \
+  do {                                   \
+    if ((g) != nullptr && *(g) == 0) return; \
+  } while (0)
 
 struct KrylovWork {
   DevBuf<double> vecs, partial, bx;
   DevBuf<long long> coff;
   DevBuf<int> clen, flag;
+  DevBuf<int> gates;   // one flag per region of an iteration block
   DevBuf<KCol> cols;
   ~KrylovWork();
 };
@@ -192,6 +201,7 @@ struct hfsem_system_s {
   int max_P = 0, max_N = 0, max_L = 0;
   bool any_dense = false, any_toep = false, any_hmat = false;
   hfsem_factor* hop = nullptr;    // the H-matrix operator of the kHmat instances
+  const int* gate = nullptr;      // device flag of the region being enqueued (HF_GATE)
   // scratch, grown on demand
   hf::DevBuf<double> w_x, w_y, w_z, w_w, w_T, w_ylow, w_mom;
   hf::DevBuf<double2> w_fa, w_fb;
@@ -223,6 +233,12 @@ struct Tick {
   ~Tick();
 };
 void timing_add_work(const char* tag, double work);
+// Timing groups: the launches timed on this thread between begin and end
+// form a group that can be dropped from the records later, once the host
+// learns that the device skipped the region they belong to.
+long long timing_group_begin();
+void timing_group_end();
+void timing_drop_group(long long g);
 hf::Precond* precond_of(hfsem_system* s, hfsem_factor* f);
 void bicgstab(hfsem_system* s, Precond* M, int nrhs, const double* b_em, double* x_em,
               double tol, int max_iter, std::vector<KCol>& out);

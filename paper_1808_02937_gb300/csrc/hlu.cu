@@ -2475,7 +2475,7 @@ __global__ void __launch_bounds__(kHThreads) k_hprog(HProgArgs a, T* har) {
   const int nw = H.nfw;
   // per-wave op counters (two, alternating), used in CTA 0
   __shared__ unsigned s_ctr[2];
-  __shared__ int s_next;
+  __shared__ int s_next[2];   // claimed op index, double-buffered by op parity
   if (threadIdx.x == 0) s_ctr[0] = s_ctr[1] = 0u;
   const unsigned ctr_base = smem_u32(&s_ctr[0]);
   unsigned ctr0;   // the counters of CTA 0 in the cluster's shared window
@@ -2490,17 +2490,20 @@ __global__ void __launch_bounds__(kHThreads) k_hprog(HProgArgs a, T* har) {
     if (crank == 0 && threadIdx.x == 0) s_ctr[(w + 1) & 1] = 0u;
     unsigned long long tw0 = 0, busy = 0, lmax = 0, ltype = 0;
     if (wp) asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(tw0));
-    for (;;) {
-      if (threadIdx.x == 0) {
-        unsigned k;
-        asm volatile("atom.shared::cluster.add.u32 %0, [%1], 1;"
-                     : "=r"(k)
-                     : "r"(ctr0 + 4u * (unsigned)(w & 1))
-                     : "memory");
-        s_next = (int)k;
-      }
-      __syncthreads();
-      const int kk = s_next;
+    // thread 0 claims ops from CTA 0's counter; the first of the wave here,
+    // each later one just before the barrier that closes the previous op,
+    // into the other index slot: one barrier per op, and no thread can see
+    // the index of the op it is executing change
+    const unsigned ctr_w = ctr0 + 4u * (unsigned)(w & 1);
+    int par = 0;
+    if (threadIdx.x == 0) {
+      unsigned k;
+      asm volatile("atom.shared::cluster.add.u32 %0, [%1], 1;" : "=r"(k) : "r"(ctr_w) : "memory");
+      s_next[0] = (int)k;
+    }
+    __syncthreads();
+    for (;; par ^= 1) {
+      const int kk = s_next[par];
       if (kk >= n_w) break;
       const int i = i0 + kk;
       const HOp o = ops[i];
@@ -2531,6 +2534,11 @@ __global__ void __launch_bounds__(kHThreads) k_hprog(HProgArgs a, T* har) {
           break;
         }
         default: break;
+      }
+      if (threadIdx.x == 0) {
+        unsigned k;
+        asm volatile("atom.shared::cluster.add.u32 %0, [%1], 1;" : "=r"(k) : "r"(ctr_w) : "memory");
+        s_next[par ^ 1] = (int)k;
       }
       __syncthreads();
       if (a.prof && threadIdx.x == 0) {   // all CTAs of the instance, summed
@@ -2704,8 +2712,10 @@ __global__ void __launch_bounds__(kHThreads) k_hsolve_cl(const HInstDev* __restr
                                                         const int4* __restrict__ meta, T* har,
                                                         int nrhs, int jmax, int slot_elems,
                                                         int wcols, int* err, double* flops,
-                                                        unsigned long long* sprof) {
+                                                        unsigned long long* sprof,
+                                                        const int* __restrict__ gate) {
   extern __shared__ __align__(16) unsigned char smraw[];
+  HF_GATE(gate);   // every CTA of the cluster returns, before any barrier
   constexpr int kSolveW = solve_w<T>();
   constexpr int V = 128 * kSolveW;
   unsigned long long* bar = reinterpret_cast<unsigned long long*>(smraw);   // [2]
@@ -2946,7 +2956,8 @@ __global__ void __launch_bounds__(kHThreads) k_hsolve_cl(const HInstDev* __restr
 template <class T>
 __global__ void k_hsolve_in(const HInstDev* __restrict__ hi, const InstDev* __restrict__ inst,
                             const double* __restrict__ r, const double* D, T* har, int* ranks,
-                            int nrhs) {
+                            int nrhs, const int* __restrict__ gate) {
+  HF_GATE(gate);
   const HInstDev H = hi[blockIdx.y];
   const InstDev I = inst[H.sys_inst];
   T* rhs = har + H.arena + H.rhs_off;
@@ -2960,7 +2971,9 @@ __global__ void k_hsolve_in(const HInstDev* __restrict__ hi, const InstDev* __re
 
 template <class T>
 __global__ void k_hsolve_out(const HInstDev* __restrict__ hi, const InstDev* __restrict__ inst,
-                             const double* D, const T* har, double* y, int nrhs) {
+                             const double* D, const T* har, double* y, int nrhs,
+                             const int* __restrict__ gate) {
+  HF_GATE(gate);
   const HInstDev H = hi[blockIdx.y];
   const InstDev I = inst[H.sys_inst];
   const T* rhs = har + H.arena + H.rhs_off;
@@ -3819,7 +3832,8 @@ constexpr int kHopRB = 4;   // right-hand sides per pass
 // x~ = D^-1 x on the kHmat instances (instance-local unknowns, rhs-major).
 __global__ void k_hop_scale(const HInstDev* __restrict__ hi, const InstDev* __restrict__ inst,
                             const double* __restrict__ D, const double* __restrict__ x, double* xt,
-                            int nrhs) {
+                            int nrhs, const int* __restrict__ gate) {
+  HF_GATE(gate);
   const HInstDev H = hi[blockIdx.y];
   const InstDev I = inst[H.sys_inst];
   const int r = blockIdx.z;
@@ -3834,7 +3848,8 @@ __global__ void k_hop_scale(const HInstDev* __restrict__ hi, const InstDev* __re
 __global__ void k_hop_proj(const HInstDev* __restrict__ hi, const InstDev* __restrict__ inst,
                            const HopSlot* __restrict__ slots, const int* __restrict__ ranks,
                            const double* __restrict__ ar, const double* __restrict__ xt, double* w,
-                           long long wsize, int nrhs) {
+                           long long wsize, int nrhs, const int* __restrict__ gate) {
+  HF_GATE(gate);
   const HopSlot S = slots[blockIdx.x];
   const HInstDev H = hi[S.inst];
   const InstDev I = inst[H.sys_inst];
@@ -3876,7 +3891,9 @@ __global__ void __launch_bounds__(128) k_hop_rows(const HInstDev* __restrict__ h
                                                   const double* __restrict__ ar,
                                                   const double* __restrict__ xt,
                                                   const double* __restrict__ w, long long wsize,
-                                                  double* y, int nrhs) {
+                                                  double* y, int nrhs,
+                                                  const int* __restrict__ gate) {
+  HF_GATE(gate);
   const HopRow Rw = rows[blockIdx.x];
   const HInstDev H = hi[Rw.inst];
   const InstDev I = inst[H.sys_inst];
@@ -3927,16 +3944,16 @@ void hop_apply(hfsem_system* s, int nrhs, const double* x, double* y) {
   int maxnd = 1;
   for (int i : f->insts) maxnd = std::max(maxnd, s->ih[i].Nd);
   k_hop_scale<<<dim3(std::min(1024, (maxnd + 255) / 256), f->nfi, nrhs), 256, 0, s->st>>>(
-      f->d_hi.p, s->d_inst.p, f->d_D.p, x, xt, nrhs);
+      f->d_hi.p, s->d_inst.p, f->d_D.p, x, xt, nrhs, s->gate);
   HF_LAUNCH_CHECK();
   if (f->hop_nslots > 0) {
     k_hop_proj<<<f->hop_nslots, 256, 0, s->st>>>(f->d_hi.p, s->d_inst.p, f->d_hslot.p, f->d_ranks.p,
-                                                 ar, xt, w, f->hop_wsize, nrhs);
+                                                 ar, xt, w, f->hop_wsize, nrhs, s->gate);
     HF_LAUNCH_CHECK();
   }
   k_hop_rows<<<dim3(f->hop_nrows, (nrhs + kHopRB - 1) / kHopRB), 128, 0, s->st>>>(
       f->d_hi.p, s->d_inst.p, f->d_hrow.p, f->d_hitem.p, f->d_hslot.p, f->d_ranks.p, f->d_D.p, ar,
-      xt, w, f->hop_wsize, y, nrhs);
+      xt, w, f->hop_wsize, y, nrhs, s->gate);
   HF_LAUNCH_CHECK();
 }
 
@@ -4177,13 +4194,13 @@ void hfsem_factor_s::run_leaf_solve(int nrhs) {
                                 (const hf::StepInfo*)d_steps.p, (const hf::StepCta*)d_step_cta.p,
                                 (const float*)d_pack.p, (const int4*)d_meta.p,
                                 reinterpret_cast<float*>(d_arena.p), nrhs, sol_jmax, sol_slot, sol_wcols,
-                                d_err.p, d_flops.p, d_sprof.p));
+                                d_err.p, d_flops.p, d_sprof.p, sys->gate));
   else
     HF_CHECK(cudaLaunchKernelEx(&cfg, hf::k_hsolve_cl<double>, (const hf::HInstDev*)d_hi.p,
                                 (const hf::StepInfo*)d_steps.p, (const hf::StepCta*)d_step_cta.p,
                                 (const double*)d_pack.p, (const int4*)d_meta.p,
                                 reinterpret_cast<double*>(d_arena.p), nrhs, sol_jmax, sol_slot, sol_wcols,
-                                d_err.p, d_flops.p, d_sprof.p));
+                                d_err.p, d_flops.p, d_sprof.p, sys->gate));
   HF_LAUNCH_CHECK();
   if (d_sprof.p) {
     unsigned long long h[8];
@@ -4213,16 +4230,18 @@ void hfsem_factor_s::apply(int nrhs, const double* r_em, double* y_em) {
   dim3 g(std::min(1024, (maxnd * nrhs + 255) / 256), nfi);
   if (tsize == sizeof(float)) {
     float* ar = reinterpret_cast<float*>(d_arena.p);
-    hf::k_hsolve_in<float><<<g, 256, 0, sys->st>>>(d_hi.p, sys->d_inst.p, r_em, d_D.p, ar, d_ranks.p, nrhs);
+    hf::k_hsolve_in<float><<<g, 256, 0, sys->st>>>(d_hi.p, sys->d_inst.p, r_em, d_D.p, ar, d_ranks.p, nrhs,
+                                                      sys->gate);
     HF_LAUNCH_CHECK();
     run_leaf_solve(nrhs);
-    hf::k_hsolve_out<float><<<g, 256, 0, sys->st>>>(d_hi.p, sys->d_inst.p, d_D.p, ar, y_em, nrhs);
+    hf::k_hsolve_out<float><<<g, 256, 0, sys->st>>>(d_hi.p, sys->d_inst.p, d_D.p, ar, y_em, nrhs, sys->gate);
   } else {
     double* ar = reinterpret_cast<double*>(d_arena.p);
-    hf::k_hsolve_in<double><<<g, 256, 0, sys->st>>>(d_hi.p, sys->d_inst.p, r_em, d_D.p, ar, d_ranks.p, nrhs);
+    hf::k_hsolve_in<double><<<g, 256, 0, sys->st>>>(d_hi.p, sys->d_inst.p, r_em, d_D.p, ar, d_ranks.p, nrhs,
+                                                      sys->gate);
     HF_LAUNCH_CHECK();
     run_leaf_solve(nrhs);
-    hf::k_hsolve_out<double><<<g, 256, 0, sys->st>>>(d_hi.p, sys->d_inst.p, d_D.p, ar, y_em, nrhs);
+    hf::k_hsolve_out<double><<<g, 256, 0, sys->st>>>(d_hi.p, sys->d_inst.p, d_D.p, ar, y_em, nrhs, sys->gate);
   }
   HF_LAUNCH_CHECK();
 }

@@ -1,8 +1,16 @@
 // Right-preconditioned BiCGSTAB (Sec. 4.2, eq. (precondsys)) for a batch of
 // columns (instance, right-hand side), all in FP64.
 //
-// Every column carries its own scalars on the device; the host only reads
-// the per-column status flags once per iteration to decide when to stop.
+// Every column carries its own scalars, status and iteration count on the
+// device.  The host enqueues iterations in blocks (2, 4, 8, then 16 at a
+// time) and reads the column states back once per block: before each
+// iteration a one-CTA kernel sets a device flag saying whether any column is
+// still running, and the operator, preconditioner and vector kernels of the
+// iteration return at once while it is 0.  A column whose recursive residual
+// meets tol waits (no work, no count) until the block ends; the host then runs
+// the true-residual check for all such columns at once.  A solve of i
+// iterations costs about log2(i) + 2 host synchronisations, and iterations
+// enqueued past the last one cost empty launches only.
 // Inner products are reduced in a fixed order (per-CTA tree, then a fixed
 // sweep over CTAs), so results are bitwise reproducible run to run.
 //
@@ -21,6 +29,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 
 namespace hf {
@@ -179,6 +188,7 @@ __global__ void k_bicg_scalar(int mode, const int* __restrict__ clen, KCol* cols
   }
   switch (mode) {
     case M_INIT:
+      k.checks = 0;
       k.bnorm2 = s1;
       k.rho = s0;
       k.rho_old = 1.0;
@@ -214,7 +224,7 @@ __global__ void k_bicg_scalar(int mode, const int* __restrict__ clen, KCol* cols
       break;
     case M_X:
       if (k.status != ST_RUN) break;
-      k.iters = iter + 1;
+      k.iters += 1;   // per column: a column waiting for its check does not count
       k.res = sqrt(s0 / k.bnorm2);
       k.rho_old = k.rho;
       k.rho = s1;
@@ -224,7 +234,7 @@ __global__ void k_bicg_scalar(int mode, const int* __restrict__ clen, KCol* cols
         k.status = ST_BREAK;
       } else {
         k.beta = (k.rho / k.rho_old) * (k.alpha / k.omega);
-        if (iter + 1 >= max_iter) k.status = ST_MAXIT;
+        if (k.iters >= max_iter) k.status = ST_MAXIT;
       }
       break;
     case M_RES:
@@ -232,6 +242,7 @@ __global__ void k_bicg_scalar(int mode, const int* __restrict__ clen, KCol* cols
       break;
     case M_TRUE: {
       if (k.status != ST_CHECK) break;
+      k.checks += 1;
       const double t = sqrt(s0 / k.bnorm2);
       if (t <= kTrueSlack * tol) {
         k.status = ST_CONV;
@@ -239,7 +250,7 @@ __global__ void k_bicg_scalar(int mode, const int* __restrict__ clen, KCol* cols
         k.status = ST_BREAK;
       } else if (k.restarts > 0 && !(t < 0.5 * k.true_res)) {
         k.status = ST_FLOOR;          // the last restart did not pay
-      } else if (k.restarts >= kMaxRestarts || iter >= max_iter) {
+      } else if (k.restarts >= kMaxRestarts || k.iters >= max_iter) {
         k.status = ST_MAXIT;
       } else {
         k.status = ST_RESTART;
@@ -292,10 +303,38 @@ __global__ void k_bicg_xs_fin(KCol* cols, const int* flag, int ncols, int iter) 
   if (c >= ncols || !flag[c]) return;
   cols[c].status = ST_CHECK;
   cols[c].res = cols[c].snorm;
-  cols[c].iters = iter + 1;
+  cols[c].iters += 1;
+}
+
+// gate = 1 if any column has status `which`, else 0 (one CTA)
+__global__ void k_bicg_flags(const KCol* __restrict__ cols, int ncols, int which, int* gate) {
+  int any = 0;
+  for (int c = threadIdx.x; c < ncols; c += blockDim.x) any |= cols[c].status == which;
+  any = __syncthreads_or(any);
+  if (threadIdx.x == 0) *gate = any;
 }
 
 KrylovWork::~KrylovWork() = default;
+
+namespace {
+constexpr int kBlockFirst = 2;   // iterations enqueued before the first read
+constexpr int kBlockMax = 16;
+
+// Scope of one gated region: the kernels launched inside read `gate`, and
+// the launches timed inside form one timing group.
+struct Region {
+  hfsem_system* s;
+  long long group;
+  Region(hfsem_system* sys, const int* gate) : s(sys) {
+    s->gate = gate;
+    group = timing_group_begin();
+  }
+  ~Region() {
+    s->gate = nullptr;
+    timing_group_end();
+  }
+};
+}  // namespace
 
 void bicgstab(hfsem_system* s, Precond* M, int nrhs, const double* b_em, double* x_em,
               double tol, int max_iter, std::vector<KCol>& out) {
@@ -319,6 +358,7 @@ void bicgstab(hfsem_system* s, Precond* M, int nrhs, const double* b_em, double*
   W.cols.ensure(ncols);
   W.partial.ensure((size_t)ncols * maxchunk * 2);
   W.flag.ensure(ncols);
+  W.gates.ensure(kBlockMax);
   HF_CHECK(cudaMemcpyAsync(W.coff.p, coff.data(), ncols * sizeof(long long),
                            cudaMemcpyHostToDevice, s->st));
   HF_CHECK(cudaMemcpyAsync(W.clen.p, clen.data(), ncols * sizeof(int), cudaMemcpyHostToDevice,
@@ -341,15 +381,10 @@ void bicgstab(hfsem_system* s, Precond* M, int nrhs, const double* b_em, double*
   }
   dim3 gv(maxchunk, ncols), bv(kDotThreads);
   int sb = (ncols + 127) / 128;
-  // algorithmic bytes of one fused vector pass over every column: 8 bytes
-  // per vector element read or written (running columns only in practice;
-  // counted for all, so the rate is a lower bound)
-  auto vec_bytes = [&](int mode) {
-    static const int touched[10] = {6, 4, 2, 3, 2, 8, 3, 2, 3, 5};
-    return 8.0 * (double)nv * touched[mode];
-  };
+  // the vector passes' algorithmic bytes are added once the per-column
+  // iteration counts are known (below): only live columns touch memory
   auto vec = [&](int mode) {
-    Tick tk(s->st, "krylov_vec", vec_bytes(mode));
+    Tick tk(s->st, "krylov_vec");
     k_bicg_vec<<<gv, bv, 0, s->st>>>(mode, V, W.coff.p, W.clen.p, W.cols.p, W.partial.p,
                                      maxchunk);
     HF_LAUNCH_CHECK();
@@ -364,30 +399,16 @@ void bicgstab(hfsem_system* s, Precond* M, int nrhs, const double* b_em, double*
   vec(M_INIT);
   scal(M_INIT, 0);
   std::vector<KCol> hc(ncols);
-  auto read_status = [&](bool& running, bool& check) {
-    HF_CHECK(cudaMemcpyAsync(hc.data(), W.cols.p, ncols * sizeof(KCol), cudaMemcpyDeviceToHost,
-                             s->st));
-    HF_CHECK(cudaStreamSynchronize(s->st));
-    running = check = false;
-    for (auto& k : hc) {
-      running = running || k.status == ST_RUN;
-      check = check || k.status == ST_CHECK;
-    }
+  // candidates: true residual from t = A x (t is free between iterations);
+  // accepted, restarted from it, or stopped
+  auto check_phase = [&](int it) {
+    apply_operator(s, nrhs, x_em, V.t, 0);
+    vec(M_TRUE);
+    scal(M_TRUE, it);
+    vec(M_RESTART);
+    scal(M_RESTART, it);
   };
-  for (int it = 0;; ++it) {
-    bool running, check;
-    read_status(running, check);
-    if (check) {
-      // candidates: true residual from t = A x (t is free between
-      // iterations); accepted, restarted from it, or stopped
-      apply_operator(s, nrhs, x_em, V.t, 0);
-      vec(M_TRUE);
-      scal(M_TRUE, it);
-      vec(M_RESTART);
-      scal(M_RESTART, it);
-      read_status(running, check);
-    }
-    if (!running || it >= max_iter) break;
+  auto iteration = [&](int it) {
     vec(M_P);
     if (M) M->apply(nrhs, V.p, V.ph);
     apply_operator(s, nrhs, V.ph, V.v, 0);
@@ -407,6 +428,53 @@ void bicgstab(hfsem_system* s, Precond* M, int nrhs, const double* b_em, double*
     scal(M_TS, it);
     vec(M_X);
     scal(M_X, it);
+  };
+  std::vector<long long> groups;
+  std::vector<int> gate_h(kBlockMax);
+  int remaining = max_iter;   // the most iterations a running column may still take
+  auto read_back = [&](bool& running, bool& check) {
+    HF_CHECK(cudaMemcpyAsync(hc.data(), W.cols.p, ncols * sizeof(KCol), cudaMemcpyDeviceToHost,
+                             s->st));
+    if (!groups.empty())
+      HF_CHECK(cudaMemcpyAsync(gate_h.data(), W.gates.p, groups.size() * sizeof(int),
+                               cudaMemcpyDeviceToHost, s->st));
+    HF_CHECK(cudaStreamSynchronize(s->st));
+    if (timing_on()) timing_add_work("krylov_host_reads", 1.0);
+    for (size_t r = 0; r < groups.size(); ++r)
+      if (gate_h[r] == 0) timing_drop_group(groups[r]);
+    groups.clear();
+    running = check = false;
+    remaining = 0;
+    for (auto& k : hc) {
+      if (k.status == ST_RUN) {
+        running = true;
+        remaining = std::max(remaining, max_iter - k.iters);
+      }
+      check = check || k.status == ST_CHECK;
+    }
+  };
+  bool running = true, check = false;   // after init: enqueue a first block
+  int it = 0;                           // iterations enqueued so far
+  // every enqueued iteration advances each running column's own count, and
+  // restarts are bounded, so this cap is never the one that stops the loop
+  const long long it_cap = (long long)(kMaxRestarts + 2) * max_iter;
+  for (int block = kBlockFirst;; block = std::min(2 * block, kBlockMax)) {
+    if (check) {
+      check_phase(it);
+      read_back(running, check);
+      if (running) block = kBlockFirst;   // restarted columns: short blocks again
+    }
+    if (!running || it >= it_cap) break;
+    const int nb = std::min(block, std::max(remaining, 1));
+    for (int k = 0; k < nb; ++k, ++it) {
+      int* g = W.gates.p + groups.size();
+      k_bicg_flags<<<1, 256, 0, s->st>>>(W.cols.p, ncols, ST_RUN, g);
+      HF_LAUNCH_CHECK();
+      Region rg(s, g);
+      iteration(it);
+      groups.push_back(rg.group);
+    }
+    read_back(running, check);
   }
   // true residual
   apply_operator(s, nrhs, x_em, V.v, 0);
@@ -416,9 +484,20 @@ void bicgstab(hfsem_system* s, Precond* M, int nrhs, const double* b_em, double*
   HF_CHECK(cudaMemcpyAsync(out.data(), W.cols.p, ncols * sizeof(KCol), cudaMemcpyDeviceToHost,
                            s->st));
   HF_CHECK(cudaStreamSynchronize(s->st));
+  if (timing_on()) timing_add_work("krylov_host_reads", 1.0);
   for (auto& k : out)
     if (k.status == ST_RUN || k.status == ST_CHECK || k.status == ST_RESTART)
       k.status = ST_MAXIT;
+  if (timing_on()) {
+    // algorithmic bytes of the vector passes, 8 per vector element read or
+    // written: init 6, per iteration 19 (p 4, (rh, v) 2, s 3, (t, s) 2,
+    // x and r 8), per true-residual check 3, per restart 5, final residual 2
+    double bytes = 0.0;
+    for (int c = 0; c < ncols; ++c)
+      bytes += 8.0 * clen[c] *
+               (6.0 + 19.0 * out[c].iters + 3.0 * out[c].checks + 5.0 * out[c].restarts + 2.0);
+    timing_add_work("krylov_vec", bytes);
+  }
 }
 
 int status_code(const KCol& k) {
@@ -459,12 +538,20 @@ extern "C" int hfsem_solve(hfsem_system* sys, hfsem_factor* fac, const hfsem_rhs
                              sys->st));
     HF_CHECK(cudaStreamSynchronize(sys->st));
     int worst = M ? M->device_status() : HFSEM_OK;
+    if (worst != HFSEM_OK) set_last_error("the preconditioner's device work missed a wait limit");
     for (size_t c = 0; c < cols.size(); ++c) {
       stats[c].iters = cols[c].iters;
       stats[c].status = status_code(cols[c]);
       stats[c].rel_residual = cols[c].res;
       stats[c].rel_true_residual = cols[c].true_res;
-      if (stats[c].status != HFSEM_OK && worst == HFSEM_OK) worst = stats[c].status;
+      if (stats[c].status != HFSEM_OK && worst == HFSEM_OK) {
+        worst = stats[c].status;
+        char msg[160];
+        snprintf(msg, sizeof(msg), "column %zu: %s after %d iterations (true residual %.3g)", c,
+                 worst == HFSEM_ERR_BREAKDOWN ? "breakdown" : "not converged", cols[c].iters,
+                 cols[c].true_res);
+        set_last_error(msg);
+      }
     }
     return worst;
   } catch (const Error& e) {

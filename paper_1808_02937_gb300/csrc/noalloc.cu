@@ -14,21 +14,23 @@ namespace hf {
 __global__ void k_perm(const InstDev* __restrict__ inst, const double* __restrict__ in,
                        double* out, int nrhs, int to_elem);
 __global__ void k_gather_z(const InstDev* __restrict__ inst, const double* arena,
-                           const double* __restrict__ x, double* z, int nrhs, int lift);
+                           const double* __restrict__ x, double* z, int nrhs, int lift,
+                           const int* __restrict__ gate);
 __global__ void k_scatter_out(const InstDev* __restrict__ inst, const double* arena,
                               const double* __restrict__ w, const double* __restrict__ x,
-                              double* y, int nrhs, int lift);
+                              double* y, int nrhs, int lift, const int* __restrict__ gate);
 __global__ void k_dense_rows(const InstDev* __restrict__ inst, const double* arena,
                              const double* __restrict__ z, double* ylow, double* T, int nrhs);
 __global__ void k_dense_cols(const InstDev* __restrict__ inst, const double* ylow,
                              const double* T, double* w, int nrhs);
 __global__ void k_toep_fwd(const InstDev* __restrict__ inst, const double* arena,
                            const double* __restrict__ z, double2* F, const double2* tw,
-                           int Lmax, int nrhs);
+                           int Lmax, int nrhs, const int* __restrict__ gate);
 __global__ void k_toep_freq(const InstDev* __restrict__ inst, const double2* spec, double2* F,
-                            int nrhs);
+                            int nrhs, const int* __restrict__ gate);
 __global__ void k_toep_inv(const InstDev* __restrict__ inst, const double* arena,
-                           const double2* F, double* w, const double2* tw, int Lmax, int nrhs);
+                           const double2* F, double* w, const double2* tw, int Lmax, int nrhs,
+                           const int* __restrict__ gate);
 }  // namespace hf
 
 namespace {
@@ -137,7 +139,7 @@ extern "C" int hfsem_apply_noalloc(hfsem_system* s, int32_t nrhs, const double* 
     const long long nmp = (long long)s->max_N * s->max_P;
     k_perm<<<grid_of(nmp, 256, ni, nrhs), 256, 0, s->st>>>(di, x, xe, nrhs, 1);
     HF_LAUNCH_CHECK();
-    k_gather_z<<<grid_of(nmp, 256, ni, nrhs), 256, 0, s->st>>>(di, s->arena.p, xe, z, nrhs, 0);
+    k_gather_z<<<grid_of(nmp, 256, ni, nrhs), 256, 0, s->st>>>(di, s->arena.p, xe, z, nrhs, 0, nullptr);
     HF_LAUNCH_CHECK();
     if (s->any_dense) {
       int W = (s->max_P > 16) ? 4 : 8;
@@ -153,16 +155,16 @@ extern "C" int hfsem_apply_noalloc(hfsem_system* s, int32_t nrhs, const double* 
       set_smem_attr((const void*)k_toep_fwd, sm);
       set_smem_attr((const void*)k_toep_inv, sm);
       k_toep_fwd<<<dim3(2 * s->max_P, ni, nrhs), 256, sm, s->st>>>(di, s->arena.p, z, F, s->tw.p,
-                                                                   s->tw_L, nrhs);
+                                                                   s->tw_L, nrhs, nullptr);
       HF_LAUNCH_CHECK();
-      k_toep_freq<<<grid_of(s->max_L, 128, ni, nrhs), 128, 0, s->st>>>(di, s->spec.p, F, nrhs);
+      k_toep_freq<<<grid_of(s->max_L, 128, ni, nrhs), 128, 0, s->st>>>(di, s->spec.p, F, nrhs, nullptr);
       HF_LAUNCH_CHECK();
       k_toep_inv<<<dim3(s->max_P, ni, nrhs), 256, sm, s->st>>>(di, s->arena.p, F, w, s->tw.p,
-                                                               s->tw_L, nrhs);
+                                                               s->tw_L, nrhs, nullptr);
       HF_LAUNCH_CHECK();
     }
     k_scatter_out<<<grid_of(nmp, 256, ni, nrhs), 256, 0, s->st>>>(di, s->arena.p, w, xe, ye, nrhs,
-                                                                  0);
+                                                                  0, nullptr);
     HF_LAUNCH_CHECK();
     k_perm<<<grid_of(nmp, 256, ni, nrhs), 256, 0, s->st>>>(di, ye, y, nrhs, 0);
     HF_LAUNCH_CHECK();

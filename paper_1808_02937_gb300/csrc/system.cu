@@ -46,6 +46,8 @@ struct Pending {
   cudaEvent_t a, b;
   std::string tag;
   double work;
+  long long group;   // timing group the launch belongs to (0: none)
+  bool dropped;      // its region was skipped on the device: not counted
 };
 std::mutex g_tmu;
 bool g_timing = false;
@@ -67,6 +69,11 @@ cudaEvent_t get_event() {
 void flush_pending() {
   for (auto& p : g_pend) {
     cudaEventSynchronize(p.b);
+    if (p.dropped) {
+      g_evpool.push_back(p.a);
+      g_evpool.push_back(p.b);
+      continue;
+    }
     float ms = 0.f;
     cudaEventElapsedTime(&ms, p.a, p.b);
     TimerRec& r = g_tim[p.tag];
@@ -81,6 +88,25 @@ void flush_pending() {
 }  // namespace
 
 bool timing_on() { return g_timing; }
+
+namespace {
+thread_local long long t_group = 0;
+std::atomic<long long> g_next_group{1};
+}  // namespace
+
+long long timing_group_begin() {
+  t_group = g_next_group.fetch_add(1);
+  return t_group;
+}
+
+void timing_group_end() { t_group = 0; }
+
+void timing_drop_group(long long g) {
+  if (g <= 0) return;
+  std::lock_guard<std::mutex> lk(g_tmu);
+  for (auto& p : g_pend)
+    if (p.group == g) p.dropped = true;
+}
 
 cudaStream_t& alloc_stream() {
   thread_local cudaStream_t s = reinterpret_cast<cudaStream_t>(-1);   // none: cudaMalloc
@@ -110,6 +136,8 @@ Tick::Tick(cudaStream_t s, const char* tag, double work) : st(s) {
   p.b = get_event();
   p.tag = tag;
   p.work = work;
+  p.group = t_group;
+  p.dropped = false;
   cudaEventRecord(p.a, s);
   g_pend.push_back(p);
   id = (int)g_pend.size() - 1;
@@ -143,6 +171,27 @@ __device__ __forceinline__ double2 cmul(double2 a, double2 b) {
   return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
 }
 
+// Legendre three-term recurrence L_{k+1} = a_k x L_k - b_k L_{k-1} with
+// a_k = (2k+1)/(k+1), b_k = k/(k+1), tabulated so that the quadrature loops
+// carry no FP64 division (a costly sequence on this GPU's FP64 pipe)
+constexpr int kRecMax = 128;
+struct LegRec {
+  double a[kRecMax], b[kRecMax];
+};
+constexpr LegRec make_legrec() {
+  LegRec r{};
+  for (int k = 0; k < kRecMax; ++k) {
+    r.a[k] = (2.0 * k + 1.0) / (k + 1.0);
+    r.b[k] = k / (k + 1.0);
+  }
+  return r;
+}
+__constant__ LegRec c_leg = make_legrec();
+
+__device__ __forceinline__ double leg_next(int k, double x, double pk, double pkm1) {
+  return c_leg.a[k] * x * pk - c_leg.b[k] * pkm1;
+}
+
 // Legendre values L_0..L_{n-1} at x into out[k*stride]
 __device__ __forceinline__ void legendre_strided(int n, double x, double* out,
                                                  int stride, double scale) {
@@ -150,7 +199,7 @@ __device__ __forceinline__ void legendre_strided(int n, double x, double* out,
   if (n > 0) out[0] = scale * p0;
   if (n > 1) out[stride] = scale * p1;
   for (int k = 1; k + 1 < n; ++k) {
-    double p2 = ((2 * k + 1) * x * p1 - k * p0) / (k + 1);
+    double p2 = leg_next(k, x, p1, p0);
     out[(k + 1) * stride] = scale * p2;
     p0 = p1;
     p1 = p2;
@@ -176,9 +225,11 @@ struct PairScratch {
   double* su;   // NQ
   double* sv;   // NQ
   double* sk;   // NQ     per-node factors
+  double* K;    // KCH    kernel values of a chunk of box rows
 };
 constexpr int NQ = 40;
-__host__ __device__ inline int pair_scratch_doubles(int P) { return P * P + 3 * P * NQ + 3 * NQ; }
+constexpr int KCH = 256;
+__host__ __device__ inline int pair_scratch_doubles(int P) { return P * P + 3 * P * NQ + 3 * NQ + KCH; }
 
 __device__ inline PairScratch carve(double* base, int P) {
   PairScratch s;
@@ -189,6 +240,7 @@ __device__ inline PairScratch carve(double* base, int P) {
   s.su = s.T + P * NQ;
   s.sv = s.su + NQ;
   s.sk = s.sv + NQ;
+  s.K = s.sk + NQ;
   return s;
 }
 
@@ -212,15 +264,33 @@ __device__ void box_quad(PairScratch& s, int P, double alpha, double he,
   }
   __syncwarp();
   const double ex = 1.0 - alpha;
-  for (int i = lane; i < nq; i += 32) {
-    for (int n = 0; n < P; ++n) s.T[n * NQ + i] = 0.0;
-    double gu = g + s.su[i];
-    for (int j = 0; j < nq; ++j) {
-      double k = pow(gu + s.sv[j], ex);
-      for (int n = 0; n < P; ++n) s.T[n * NQ + i] += k * s.B[n * NQ + j];
+  // (g+u+v)^(1-alpha) = d^(1-alpha) exp((1-alpha) log y), y = (g+u+v)/d, with
+  // d = g + u0 + v0 > 0 the box corner nearest the singular line: every box
+  // is no longer than its distance to that line, so y lies in [1, 3] and the
+  // logarithm stays small (a few ulp, at a fraction of the cost of pow)
+  const double d = g + u0 + v0;
+  const double dinv = 1.0 / d, dex = pow(d, ex);
+  // T[n][i] = sum_j K(u_i, v_j) B[n][j], a chunk of rows i at a time: every
+  // lane evaluates kernel values (nq^2 per box, the costly part), then every
+  // lane forms sums of the chunk
+  const int ib = max(1, min(nq, KCH / nq));
+  for (int i0 = 0; i0 < nq; i0 += ib) {
+    const int ni = min(ib, nq - i0);
+    for (int t = lane; t < ni * nq; t += 32) {
+      const int ii = t / nq, j = t - ii * nq;
+      s.K[t] = dex * exp(ex * log((g + s.su[i0 + ii] + s.sv[j]) * dinv));
     }
+    __syncwarp();
+    for (int t = lane; t < ni * P; t += 32) {
+      const int n = t / ni, ii = t - n * ni;
+      const double* kr = s.K + ii * nq;
+      const double* br = s.B + n * NQ;
+      double a = 0.0;
+      for (int j = 0; j < nq; ++j) a += kr[j] * br[j];
+      s.T[n * NQ + i0 + ii] = a;
+    }
+    __syncwarp();
   }
-  __syncwarp();
   for (int e = lane; e < P * P; e += 32) {
     int m = e / P, n = e % P;
     double a = 0.0;
@@ -244,6 +314,9 @@ __device__ void duffy_tri(PairScratch& s, int P, double alpha, double he,
   const double ex = 1.0 - alpha;
   // c^(3-alpha) 2^(alpha-3) / (he hf), in factors that stay in range
   const double cfac = pow(c, 1.0 - alpha) * (c / he) * (c / hf) * exp2(alpha - 3.0);
+  // the inner weights with the kernel factor (1 + w_j)^(1-alpha), once
+  for (int j = lane; j < nw; j += 32) s.K[j] = 0.5 * Wt[j] * pow(1.0 + 0.5 * (1.0 + X[j]), ex);
+  __syncwarp();
   // per outer node k: T[q][k] = sum_j K_kj * basis_q(inner point (k, j))
   for (int k = lane; k < ngj; k += 32) {
     double rho = 0.5 * (1.0 + gjx[k]);
@@ -256,14 +329,14 @@ __device__ void duffy_tri(PairScratch& s, int P, double alpha, double he,
       legendre_strided(P, 1.0 - 2.0 * c * rho / hf, s.A + k, NQ, wk);
     for (int j = 0; j < nw; ++j) {
       double w = 0.5 * (1.0 + X[j]);
-      double kw = 0.5 * Wt[j] * pow(1.0 + w, ex);
+      double kw = s.K[j];
       double y = (variant == 0) ? 1.0 - 2.0 * c * rho * w / hf
                                 : -1.0 + 2.0 * c * rho * w / he;
       double p0 = 1.0, p1 = y;
       s.T[k] += kw;
       if (P > 1) s.T[NQ + k] += kw * p1;
       for (int q = 1; q + 1 < P; ++q) {
-        double p2 = ((2 * q + 1) * y * p1 - q * p0) / (q + 1);
+        double p2 = leg_next(q, y, p1, p0);
         s.T[(q + 1) * NQ + k] += kw * p2;
         p0 = p1;
         p1 = p2;
@@ -521,7 +594,8 @@ __global__ void k_symbol(const InstDev* __restrict__ inst, const double* arena,
 // matching 1/(h_e h_f).  (lift: boundary hats carry c1, c2 instead of 0)
 __global__ void k_gather_z(const InstDev* __restrict__ inst, const double* arena,
                            const double* __restrict__ x, double* z, int nrhs,
-                           int lift) {
+                           int lift, const int* __restrict__ gate) {
+  HF_GATE(gate);
   const InstDev I = inst[blockIdx.y];
   const int r = blockIdx.z;
   const int P = I.P, N = I.N;
@@ -548,7 +622,8 @@ __global__ void k_gather_z(const InstDev* __restrict__ inst, const double* arena
 // y = Pi^T w + rho M x (lift: the boundary hats' values enter the mass term)
 __global__ void k_scatter_out(const InstDev* __restrict__ inst, const double* arena,
                               const double* __restrict__ w, const double* __restrict__ x,
-                              double* y, int nrhs, int lift) {
+                              double* y, int nrhs, int lift, const int* __restrict__ gate) {
+  HF_GATE(gate);
   const InstDev I = inst[blockIdx.y];
   const int r = blockIdx.z;
   const int P = I.P, N = I.N;
@@ -663,7 +738,9 @@ __global__ void k_dense_rows(const InstDev* __restrict__ inst, const double* are
 // needs of the stored pairs only the column f = 0 and the row e = N-1 (plus
 // the diagonal pairs (0,0) and (N-1,N-1) of the band).
 __global__ void k_lift_hmat(const InstDev* __restrict__ inst, const double* __restrict__ arena,
-                            const double* __restrict__ z, double* w, int nrhs) {
+                            const double* __restrict__ z, double* w, int nrhs,
+                            const int* __restrict__ gate) {
+  HF_GATE(gate);
   const InstDev I = inst[blockIdx.y];
   if (I.kind != kHmat) return;
   const int P = I.P, N = I.N, r = blockIdx.z;
@@ -704,7 +781,8 @@ template <int PT, int RB>
 __global__ void __launch_bounds__(256) k_dense_rowpass(const InstDev* __restrict__ inst,
                                                        const double* __restrict__ arena,
                                                        const double* __restrict__ z, double* w,
-                                                       int nrhs) {
+                                                       int nrhs, const int* __restrict__ gate) {
+  HF_GATE(gate);
   const InstDev I = inst[blockIdx.y];
   if (I.kind != kDense) return;
   const int P = I.P, N = I.N;
@@ -760,7 +838,8 @@ template <int PT, int RB>
 __global__ void __launch_bounds__(256) k_dense_colpass(const InstDev* __restrict__ inst,
                                                        const double* __restrict__ arena,
                                                        const double* __restrict__ z, double* w,
-                                                       int nrhs) {
+                                                       int nrhs, const int* __restrict__ gate) {
+  HF_GATE(gate);
   const InstDev I = inst[blockIdx.y];
   if (I.kind != kDense || I.theta == 1.0) return;
   const int P = I.P, N = I.N;
@@ -814,28 +893,28 @@ __global__ void __launch_bounds__(256) k_dense_colpass(const InstDev* __restrict
 // Launch both passes with the register tile PT >= max P of the batch.
 template <int PT, int RB>
 static void dense_passes(const InstDev* di, const double* arena, const double* z, double* w,
-                         int nrhs, int ni, int maxN, cudaStream_t st) {
+                         int nrhs, int ni, int maxN, cudaStream_t st, const int* gate) {
   dim3 g((maxN + 7) / 8, ni, (nrhs + RB - 1) / RB);
-  k_dense_rowpass<PT, RB><<<g, 256, 0, st>>>(di, arena, z, w, nrhs);
+  k_dense_rowpass<PT, RB><<<g, 256, 0, st>>>(di, arena, z, w, nrhs, gate);
   HF_LAUNCH_CHECK();
-  k_dense_colpass<PT, RB><<<g, 256, 0, st>>>(di, arena, z, w, nrhs);
+  k_dense_colpass<PT, RB><<<g, 256, 0, st>>>(di, arena, z, w, nrhs, gate);
   HF_LAUNCH_CHECK();
 }
 
 void dense_operator(const InstDev* di, const double* arena, const double* z, double* w, int nrhs,
-                    int ni, int maxN, int maxP, cudaStream_t st) {
+                    int ni, int maxN, int maxP, cudaStream_t st, const int* gate) {
   if (maxP <= 4)
-    dense_passes<4, 8>(di, arena, z, w, nrhs, ni, maxN, st);
+    dense_passes<4, 8>(di, arena, z, w, nrhs, ni, maxN, st, gate);
   else if (maxP <= 8)
-    dense_passes<8, 4>(di, arena, z, w, nrhs, ni, maxN, st);
+    dense_passes<8, 4>(di, arena, z, w, nrhs, ni, maxN, st, gate);
   else if (maxP <= 12)
-    dense_passes<12, 4>(di, arena, z, w, nrhs, ni, maxN, st);
+    dense_passes<12, 4>(di, arena, z, w, nrhs, ni, maxN, st, gate);
   else if (maxP <= 16)
-    dense_passes<16, 4>(di, arena, z, w, nrhs, ni, maxN, st);
+    dense_passes<16, 4>(di, arena, z, w, nrhs, ni, maxN, st, gate);
   else if (maxP <= 24)
-    dense_passes<24, 2>(di, arena, z, w, nrhs, ni, maxN, st);
+    dense_passes<24, 2>(di, arena, z, w, nrhs, ni, maxN, st, gate);
   else
-    dense_passes<32, 2>(di, arena, z, w, nrhs, ni, maxN, st);
+    dense_passes<32, 2>(di, arena, z, w, nrhs, ni, maxN, st, gate);
 }
 
 // Dense columns: w[f][n] = theta ylow[f][n] + (1-theta) sum_{e >= f} T[(e,f)][n]
@@ -863,8 +942,9 @@ __global__ void k_dense_cols(const InstDev* __restrict__ inst, const double* ylo
 // (1-theta) Tt R z); uniform meshes use slot 0 only.
 __global__ void k_toep_fwd(const InstDev* __restrict__ inst, const double* arena,
                            const double* __restrict__ z, double2* F,
-                           const double2* tw, int Lmax, int nrhs) {
+                           const double2* tw, int Lmax, int nrhs, const int* __restrict__ gate) {
   extern __shared__ double2 fbuf[];
+  HF_GATE(gate);
   const InstDev I = inst[blockIdx.y];
   if (I.kind != kToeplitz) return;
   const int P = I.P;
@@ -887,7 +967,8 @@ __global__ void k_toep_fwd(const InstDev* __restrict__ inst, const double* arena
 // Frequency mixing, in place: slot 0 <- S(w) a(w); slot 1 <- S(w)^H b(w);
 // uniform: slot 0 <- (theta S + (1-theta) S^H) a.
 __global__ void k_toep_freq(const InstDev* __restrict__ inst, const double2* spec,
-                            double2* F, int nrhs) {
+                            double2* F, int nrhs, const int* __restrict__ gate) {
+  HF_GATE(gate);
   const InstDev I = inst[blockIdx.y];
   if (I.kind != kToeplitz) return;
   const int P = I.P, L = I.L;
@@ -930,8 +1011,9 @@ __global__ void k_toep_freq(const InstDev* __restrict__ inst, const double2* spe
 // Toeplitz inverse: CTA per (component m, instance, rhs); writes w in z-space.
 __global__ void k_toep_inv(const InstDev* __restrict__ inst, const double* arena,
                            const double2* F, double* w, const double2* tw,
-                           int Lmax, int nrhs) {
+                           int Lmax, int nrhs, const int* __restrict__ gate) {
   extern __shared__ double2 fbuf[];
+  HF_GATE(gate);
   const InstDev I = inst[blockIdx.y];
   if (I.kind != kToeplitz) return;
   const int P = I.P, L = I.L, N = I.N;
@@ -994,7 +1076,7 @@ __global__ void k_load_moments(const InstDev* __restrict__ inst, const double* a
         double p0 = 1.0, p1 = s, fv = rd[0];
         if (K >= 1) fv += rd[1] * s;
         for (int k = 1; k < K; ++k) {
-          double p2 = ((2 * k + 1) * s * p1 - k * p0) / (k + 1);
+          double p2 = leg_next(k, s, p1, p0);
           fv += rd[k + 1] * p2;
           p0 = p1;
           p1 = p2;
@@ -1004,7 +1086,7 @@ __global__ void k_load_moments(const InstDev* __restrict__ inst, const double* a
         g[0] += wq;
         if (P >= 1) g[1] += wq * l1;
         for (int k = 1; k < P; ++k) {
-          double l2 = ((2 * k + 1) * X[q] * l1 - k * l0) / (k + 1);
+          double l2 = leg_next(k, X[q], l1, l0);
           g[k + 1] += wq * l2;
           l0 = l1;
           l1 = l2;
@@ -1043,7 +1125,7 @@ __global__ void k_load_moments(const InstDev* __restrict__ inst, const double* a
             g[0] += wq;
             if (P >= 1) g[1] += wq * l1;
             for (int k = 1; k < P; ++k) {
-              double l2 = ((2 * k + 1) * xi * l1 - k * l0) / (k + 1);
+              double l2 = leg_next(k, xi, l1, l0);
               g[k + 1] += wq * l2;
               l0 = l1;
               l1 = l2;
@@ -1069,7 +1151,7 @@ __global__ void k_load_moments(const InstDev* __restrict__ inst, const double* a
             g[0] += wq;
             if (P >= 1) g[1] += wq * l1;
             for (int k = 1; k < P; ++k) {
-              double l2 = ((2 * k + 1) * xi * l1 - k * l0) / (k + 1);
+              double l2 = leg_next(k, xi, l1, l0);
               g[k + 1] += wq * l2;
               l0 = l1;
               l1 = l2;
@@ -1216,7 +1298,7 @@ void apply_operator(hfsem_system* s, int nrhs, const double* x, double* y, int l
   double* z = s->w_z.p;
   double* w = s->w_w.p;
   k_gather_z<<<grid1((long long)s->max_N * s->max_P, 256, ni, nrhs), 256, 0, s->st>>>(
-      di, s->arena.p, x, z, nrhs, lift);
+      di, s->arena.p, x, z, nrhs, lift, s->gate);
   HF_LAUNCH_CHECK();
   if (s->any_dense) {
     // algorithmic work: 2 multiply-adds per stored entry and right-hand side
@@ -1224,7 +1306,7 @@ void apply_operator(hfsem_system* s, int nrhs, const double* x, double* y, int l
     for (auto& I : s->ih)
       if (I.kind == kDense) flops += 4.0 * I.P * I.P * I.N * (I.N + 1) / 2.0 * nrhs;
     Tick tk(s->st, "dense_mv", flops);
-    dense_operator(di, s->arena.p, z, w, nrhs, ni, s->max_N, s->max_P, s->st);
+    dense_operator(di, s->arena.p, z, w, nrhs, ni, s->max_N, s->max_P, s->st, s->gate);
   }
   if (s->any_toep) {
     double bytes = 0.0;   // symbol read + z in + w out
@@ -1235,22 +1317,22 @@ void apply_operator(hfsem_system* s, int nrhs, const double* x, double* y, int l
     set_smem((const void*)k_toep_fwd, sm);
     set_smem((const void*)k_toep_inv, sm);
     k_toep_fwd<<<dim3(2 * s->max_P, ni, nrhs), 256, sm, s->st>>>(di, s->arena.p, z, s->w_fa.p,
-                                                                 s->tw.p, s->tw_L, nrhs);
+                                                                 s->tw.p, s->tw_L, nrhs, s->gate);
     HF_LAUNCH_CHECK();
     k_toep_freq<<<grid1(s->max_L, 128, ni, nrhs), 128, 0, s->st>>>(di, s->spec.p, s->w_fa.p,
-                                                                    nrhs);
+                                                                    nrhs, s->gate);
     HF_LAUNCH_CHECK();
     k_toep_inv<<<dim3(s->max_P, ni, nrhs), 256, sm, s->st>>>(di, s->arena.p, s->w_fa.p, w,
-                                                             s->tw.p, s->tw_L, nrhs);
+                                                             s->tw.p, s->tw_L, nrhs, s->gate);
     HF_LAUNCH_CHECK();
   }
   if (s->any_hmat) {
     k_lift_hmat<<<grid1((long long)s->max_N * s->max_P, 256, ni, nrhs), 256, 0, s->st>>>(
-        di, s->arena.p, z, w, nrhs);
+        di, s->arena.p, z, w, nrhs, s->gate);
     HF_LAUNCH_CHECK();
   }
   k_scatter_out<<<grid1((long long)s->max_N * s->max_P, 256, ni, nrhs), 256, 0, s->st>>>(
-      di, s->arena.p, w, x, y, nrhs, lift);
+      di, s->arena.p, w, x, y, nrhs, lift, s->gate);
   HF_LAUNCH_CHECK();
   if (s->any_hmat) hop_apply(s, nrhs, x, y);   // y += A x on the kHmat instances
 }
