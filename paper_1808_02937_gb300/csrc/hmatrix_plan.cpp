@@ -19,6 +19,7 @@
 #include <array>
 #include <cmath>
 #include <map>
+#include <unordered_map>
 #include <string>
 
 #include "hplan.h"
@@ -589,12 +590,25 @@ int program_levels(const HPlan& p, const std::vector<HOp>& prog, std::vector<int
   }
   for (const auto& t : p.tmps) al.push_back({t.off, t.size, t.ld, -1});
   std::sort(al.begin(), al.end(), [](const Alloc& a, const Alloc& b) { return a.off < b.off; });
-  auto find = [&](long long off) -> const Alloc* {
-    size_t lo = 0, hi = al.size();
-    while (lo < hi) {
-      size_t mid = (lo + hi) / 2;
-      if (al[mid].off <= off) lo = mid + 1; else hi = mid;
+  // coarse index: for every 4096-element bucket of the arena, the number of
+  // allocations that start before the bucket (a lookup then scans the few
+  // allocations that start inside it)
+  constexpr int kShift = 12;
+  long long top = 0;
+  for (const Alloc& a : al) top = std::max(top, a.off + a.size);
+  std::vector<int> first((size_t)(top >> kShift) + 2, 0);
+  {
+    size_t k = 0;
+    for (size_t bk = 0; bk < first.size(); ++bk) {
+      while (k < al.size() && al[k].off < ((long long)bk << kShift)) ++k;
+      first[bk] = (int)k;
     }
+  }
+  auto find = [&](long long off) -> const Alloc* {
+    if (off < 0 || al.empty()) return nullptr;
+    const size_t bk = std::min((size_t)(off >> kShift), first.size() - 1);
+    size_t lo = first[bk];   // allocations [0, lo) start before the bucket
+    while (lo < al.size() && al[lo].off <= off) ++lo;
     if (lo == 0) return nullptr;
     const Alloc& a = al[lo - 1];
     return (off < a.off + a.size) ? &a : nullptr;
@@ -655,19 +669,33 @@ int program_levels(const HPlan& p, const std::vector<HOp>& prog, std::vector<int
   };
   const int cap = 64;
   level.assign(prog.size(), 0);
-  // last writer / readers per storage region are tracked by scanning a window
-  // of recent accesses per allocation base
+  // Per storage region (allocation base) the accesses that can still decide
+  // a later op's level: a write dominates every earlier access it covers
+  // (any later access that meets the covered one meets the write, whose
+  // level is higher), so covered records are dropped; reads of the same
+  // rectangle keep one record with their highest level; a read looks at
+  // writes only.
   struct Rec {
     Rect rc;
-    bool write;
     int lvl;
   };
-  std::map<long long, std::vector<Rec>> hist;   // base (or -1 for raw) -> accesses
-  std::map<int, std::pair<int, int>> slot_state; // slot -> (last write level, max read level)
+  struct Hist {
+    std::vector<Rec> wr, rd;
+  };
+  auto same = [](const Rect& a, const Rect& b) {
+    return a.r0 == b.r0 && a.r1 == b.r1 && a.c0 == b.c0 && a.c1 == b.c1;
+  };
+  auto covers = [](const Rect& a, const Rect& b) {   // a contains b
+    return a.r0 <= b.r0 && b.r1 <= a.r1 && a.c0 <= b.c0 && b.c1 <= a.c1;
+  };
+  std::unordered_map<long long, Hist> hist;      // base (or -1 for raw) -> accesses
+  // slot -> (last write level, max read level); 0: none yet
+  std::vector<std::pair<int, int>> slot_state((size_t)std::max(p.n_slots, 0) + 1, {0, 0});
   int nlev = 0;
+  std::vector<Access> acc;
   for (size_t i = 0; i < prog.size(); ++i) {
     const HOp& o = prog[i];
-    std::vector<Access> acc;
+    acc.clear();
     auto add = [&](const View& v, bool w) {
       if (v.r == 0 || v.c == 0) return;
       acc.push_back({rect_of(v, cap), w});
@@ -684,25 +712,37 @@ int program_levels(const HPlan& p, const std::vector<HOp>& prog, std::vector<int
     }
     int lv = 0;
     for (auto& a : acc) {
-      auto& h = hist[a.rc.base];
-      for (auto& r : h)
-        if ((a.write || r.write) && overlap(a.rc, r.rc)) lv = std::max(lv, r.lvl);
-      if (a.rc.slot >= 0) {   // the view's shape reads the rank of this slot
-        auto it = slot_state.find(a.rc.slot);
-        if (it != slot_state.end()) lv = std::max(lv, it->second.first);
+      auto it = hist.find(a.rc.base);
+      if (it != hist.end()) {
+        for (auto& r : it->second.wr)
+          if (overlap(a.rc, r.rc)) lv = std::max(lv, r.lvl);
+        if (a.write)
+          for (auto& r : it->second.rd)
+            if (overlap(a.rc, r.rc)) lv = std::max(lv, r.lvl);
       }
+      if (a.rc.slot >= 0) lv = std::max(lv, slot_state[a.rc.slot].first);   // reads the slot's rank
     }
-    if (slot_w >= 0) {
-      auto it = slot_state.find(slot_w);
-      if (it != slot_state.end()) lv = std::max(lv, std::max(it->second.first, it->second.second));
-    }
+    if (slot_w >= 0) lv = std::max(lv, std::max(slot_state[slot_w].first, slot_state[slot_w].second));
     lv += 1;
     level[i] = lv;
     nlev = std::max(nlev, lv);
     for (auto& a : acc) {
-      auto& h = hist[a.rc.base];
-      // drop records fully covered by this write at a lower level
-      h.push_back({a.rc, a.write, lv});   // full history: a dropped record could hide a dependency
+      Hist& h = hist[a.rc.base];
+      if (a.write) {
+        auto dominated = [&](const Rec& r) { return covers(a.rc, r.rc); };
+        h.wr.erase(std::remove_if(h.wr.begin(), h.wr.end(), dominated), h.wr.end());
+        h.rd.erase(std::remove_if(h.rd.begin(), h.rd.end(), dominated), h.rd.end());
+        h.wr.push_back({a.rc, lv});
+      } else {
+        bool merged = false;
+        for (auto& r : h.rd)
+          if (same(r.rc, a.rc)) {
+            r.lvl = std::max(r.lvl, lv);
+            merged = true;
+            break;
+          }
+        if (!merged) h.rd.push_back({a.rc, lv});
+      }
       if (a.rc.slot >= 0) {   // only APPEND / TRUNC change a rank (slot_w below)
         auto& st = slot_state[a.rc.slot];
         st.second = std::max(st.second, lv);
