@@ -53,7 +53,8 @@ SERVE_WORKLOAD = ("config 5 stream: Poisson arrivals at 80% of measured capacity
                   "(rank 24) on graded / geometric ones")
 BATCH_WORKLOAD = ("config 4: 512 instances (N U{32..512}, P U{2..12}, uniform / two-sided "
                   "geometric / graded meshes) x 4 rhs, one batch; R=8, lambda=1 (min-diameter "
-                  "admissibility), Tol_HLU=1e-3; Toeplitz / FP64 H-matrix operator")
+                  "admissibility), Tol_HLU=1e-3; Toeplitz / FP64 H-matrix operator; H-LU leaf "
+                  "sizes tuned per class on the batch before the timed steps")
 
 
 def parse():
@@ -68,6 +69,8 @@ def parse():
     ap.add_argument("--slots", type=int, default=SLOTS, help="concurrent requests when serving")
     # profiling only: the first n instances of the config-4 batch (--workload batch)
     ap.add_argument("--batch-instances", type=int, default=512)
+    ap.add_argument("--no-tune", action="store_true",
+                    help="config-4 batch: automatic leaf sizes instead of tuned ones")
     return ap.parse_args()
 
 
@@ -332,7 +335,7 @@ def run_serving(H, torch, args, world, rank, local):
 
 
 # -------------------------------------------------------------- batched --
-def run_batch(H, torch, steps, warmup, world, timing=False, n_inst=512):
+def run_batch(H, torch, steps, warmup, world, timing=False, n_inst=512, tune=True):
     from paper_1808_02937_gb300 import workloads as W
     insts = W.config4()[:n_inst]
     probs = [H.make_problem(p.h, p.P, p.alpha, p.theta, p.rho, matvec=operator_kind(H, p.h))
@@ -345,6 +348,17 @@ def run_batch(H, torch, steps, warmup, world, timing=False, n_inst=512):
     for name, prec in (("mixed", H.PREC_MIXED), ("fp64", H.PREC_FP64)):
         opts = H.hopts(R=8, lam=1.0, tol_hlu=1e-3, precision=prec, admissibility=H.ADM_MIN)
         X = torch.zeros(nd * 4, dtype=torch.float64, device="cuda")
+        tuned = None
+        if tune:
+            # leaf sizes per instance class, chosen by timing this batch's own
+            # instances (untimed; the steps below factor with them)
+            H.hfsem_tune_clear()
+            t0 = time.perf_counter()
+            got = H.hfsem_tune(H.hfsem_assemble(probs), opts, rhs, tol=TOL, max_iter=MAX_ITER)
+            tuned = {"classes": len(got), "seconds": time.perf_counter() - t0,
+                     "changed": sum(1 for e in got if e["leaf_dofs"] != (96 if e["fp64"] else 128)),
+                     "ms_tuned": sum(e["ms"] for e in got),
+                     "ms_automatic": sum(e["ms_default"] for e in got)}
 
         def step():
             sys_ = H.hfsem_assemble(probs)
@@ -382,7 +396,9 @@ def run_batch(H, torch, steps, warmup, world, timing=False, n_inst=512):
                      "p99_ms": percentile(ms, 0.99), "steps": steps,
                      "iters_max": max(iters), "iters_mean": sum(iters) / len(iters),
                      "status_ok": all(c == H.HFSEM_OK for c in codes), "kernels": kern,
-                     "X": X}
+                     "tuned_leaves": tuned, "X": X}
+    if tune:
+        H.hfsem_tune_clear()   # the table served this batch only
     return out
 
 
@@ -542,7 +558,8 @@ def main():
         serve_table = share
         batch = None
         if not args.no_batch:
-            B = run_batch(H, torch, steps=3, warmup=3, world=world, timing=True)
+            B = run_batch(H, torch, steps=3, warmup=3, world=world, timing=True,
+                          tune=not args.no_tune)
             roof, alu, share = roofline(H, B["mixed"]["kernels"], 3, "mixed")
             roof["measured_on"] = "config-4 batch leg, mixed arm (one stream, 3 timed steps)"
             batch = {k: {kk: vv for kk, vv in v.items() if kk not in ("X", "kernels")}
@@ -575,7 +592,7 @@ def main():
             print(json.dumps(line), flush=True)
     else:
         B = run_batch(H, torch, steps=args.steps, warmup=args.warmup, world=world, timing=True,
-                      n_inst=args.batch_instances)
+                      n_inst=args.batch_instances, tune=not args.no_tune)
         roof, alu, share = roofline(H, B["mixed"]["kernels"], args.steps, "mixed")
         if rank == 0:
             m = B["mixed"]

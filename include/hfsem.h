@@ -333,6 +333,44 @@ int hfsem_timing_enable(int32_t on);
 int hfsem_timing_reset(void);
 int hfsem_timing_read(const char *tag, double *total_ms, int64_t *launches, double *work);
 
+/* ---- autotuner of the H-LU leaf size (Sec. 4.1 leaves the leaf size of the
+ * cluster tree open; the kernels take leaves of up to 128 unknowns, 96 in
+ * FP64) ------------------------------------------------------------------
+ *
+ * hfsem_tune groups the instances of sys into classes (factor arithmetic,
+ * uniform or not, P), factors and solves up to 16 instances of each class
+ * with every candidate leaf size (32, 48, 64, 96, 128 unknowns, capped by the
+ * arithmetic), each twice (the first run builds the plans), and keeps the
+ * fastest (factorisation + solve, CUDA events on sys's stream) among those
+ * whose iteration count is within one of the fewest.  opts are the options
+ * the factorisations will use (leaf_elems ignored, build_only must be 0); rhs
+ * one per instance, all with the same nrhs; tol, max_iter as in hfsem_solve.
+ * The choices enter a process-wide table that hfsem_hlu_factor consults for
+ * every instance when opts->leaf_elems == 0 (instances of classes without an
+ * entry keep the automatic size).  path (may be NULL): the whole table is
+ * written there as text, one class per line ("fp64 kind P leaf_unknowns"),
+ * which hfsem_tune_load reads back (entries merge into the table).  out (cap
+ * entries, host, may be NULL when cap == 0) receives this call's choices,
+ * *n_out (may be NULL) their number.  Errors of the tuning runs are
+ * returned; a candidate the kernels cannot take is skipped. */
+typedef struct {
+  int32_t fp64;       /* 1: factored in FP64                                  */
+  int32_t kind;       /* 0: uniform mesh, 1: any other                        */
+  int32_t P;
+  int32_t leaf_dofs;  /* chosen leaf size in unknowns                          */
+  int32_t n_inst;     /* instances timed                                       */
+  double  ms;         /* their factorisation + solve time at that size        */
+  double  ms_default; /* the same at the automatic size                       */
+} hfsem_tune_entry;
+
+int hfsem_tune(hfsem_system *sys, const hfsem_hopts *opts, const hfsem_rhs *rhs,
+               double tol, int32_t max_iter, const char *path, hfsem_tune_entry *out,
+               int32_t cap, int32_t *n_out);
+int hfsem_tune_load(const char *path);
+/* *leaf_dofs = the table's leaf size for a class, 0 if it has none. */
+int hfsem_tune_lookup(int32_t fp64, int32_t kind, int32_t P, int32_t *leaf_dofs);
+int hfsem_tune_clear(void);
+
 /* Measured ALU peak of the current device (measurement support for the
  * roofline fractions; the paper has no counterpart): independent FMA chains,
  * 8 per thread, 64 warps per SM on every SM, best of 3 timed launches.

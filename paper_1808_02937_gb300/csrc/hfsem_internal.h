@@ -260,6 +260,9 @@ void hop_apply(hfsem_system* s, int nrhs, const double* x_em, double* y_em);
 // Near-field band of the kHmat operator: for every element e the first
 // trial element f of the pairs (e, f <= e) its dense blocks need.
 void hop_band(const InstHost& I, std::vector<int>& flo);
+// Leaf size (unknowns) the autotuner chose for I's class under a requested
+// precision; 0 if none.
+int tune_leaf_dofs(const InstHost& I, int precision);
 // Loads, on the current device, the scratch array and the kernels of
 // hfsem_apply_noalloc (once per device), so that its calls allocate nothing.
 void noalloc_prepare();

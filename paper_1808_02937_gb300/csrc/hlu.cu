@@ -53,6 +53,12 @@ struct LRPairDev {  // an admissible pair: tau (rows of the lower block) right o
 };
 
 constexpr int kCluster = 8;   // CTAs (one thread-block cluster) per instance
+// factorisations of at most kWideMaxInst instances, one of at least kWideNd
+// unknowns, run the H-LU program on clusters of kWideCluster CTAs (a
+// non-portable cluster size, used when the device can hold one)
+constexpr int kWideCluster = 16;
+constexpr int kWideMaxInst = 2;
+constexpr int kWideNd = 8192;
 
 struct HInstDev {
   long long arena;   // offset of the instance arena (elements)
@@ -2381,6 +2387,7 @@ struct HProgArgs {
   int n_inst_prof;            // instances in prof (the recompression phases follow them)
   int tc;                     // dense leaf contractions on the tensor cores
   unsigned long long* tcdbg;  // 8 words of diagnostics for a tensor-core wait that ran out
+  int ncl;                    // CTAs per instance (the cluster size of the launch)
 };
 
 // algorithmic flops of one op with its run-time shapes
@@ -2428,8 +2435,8 @@ __device__ __forceinline__ void cluster_barrier() {
                "barrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
-// One thread-block cluster of kCluster CTAs per instance runs the instance's
-// H-LU program wave by wave: the ops of a wave are independent; a CTA that
+// One thread-block cluster of a.ncl CTAs (8, or 16 for a few large
+// instances) per instance runs the instance's H-LU program wave by wave: the ops of a wave are independent; a CTA that
 // becomes free takes the next op of the wave from a counter in the shared
 // memory of CTA 0 (distributed shared memory atomics; the planner orders a
 // wave's ops longest first), and a cluster barrier separates consecutive
@@ -2569,14 +2576,14 @@ __global__ void __launch_bounds__(kHThreads) k_hprog(HProgArgs a, T* har) {
     if (wp) {
       unsigned long long t1;
       asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t1));
-      unsigned long long* q = a.wprof + ((size_t)cid * a.wstride + w) * (1 + 3 * kCluster);
+      unsigned long long* q = a.wprof + ((size_t)cid * a.wstride + w) * (1 + 3 * a.ncl);
       if (crank == 0) q[0] = t1 - tw0;
       q[1 + 3 * crank] = busy;
       q[2 + 3 * crank] = lmax;
       q[3 + 3 * crank] = ltype;
     }
   }
-  if (threadIdx.x == 0) a.flops[((size_t)cid * kCluster + crank) * 2] += fl;
+  if (threadIdx.x == 0) a.flops[((size_t)cid * a.ncl + crank) * 2] += fl;
   if (a.tc) {   // every tensor-core op has completed and been read back
     tc_fence_before();
     __syncthreads();
@@ -3125,6 +3132,7 @@ struct hfsem_factor_s : public hf::Precond {
   long long hop_wsize = 0;        // projection entries per right-hand side
   double hop_flops = 0.0;         // per right-hand side
   int wstride = 0;
+  int ncl = hf::kCluster;   // CTAs per instance in the H-LU program (plans hold ncl workspaces)
   void report(const char* what);
   void report_waves(const char* what);
   void apply(int nrhs, const double* r_em, double* y_em) override;
@@ -3134,6 +3142,39 @@ struct hfsem_factor_s : public hf::Precond {
 };
 
 namespace hf {
+
+// Whether the device can hold one cluster of ncl CTAs of the H-LU program
+// (cluster sizes above 8 are non-portable and must be allowed on the kernel
+// first); decided once per device and kernel.
+static bool wide_clusters_fit(const void* fn, size_t smem, int ncl) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, bool> ok;
+  int dev = 0;
+  HF_CHECK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(mu);
+  auto key = std::make_pair(dev, fn);
+  auto it = ok.find(key);
+  if (it != ok.end()) return it->second;
+  bool fit = false;
+  if (cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)ncl);
+    cfg.blockDim = dim3(kHThreads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = (unsigned)ncl;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int nc = 0;
+    fit = cudaOccupancyMaxActiveClusters(&nc, fn, &cfg) == cudaSuccess && nc >= 1;
+  }
+  cudaGetLastError();   // a refused query leaves no error behind
+  ok[key] = fit;
+  return fit;
+}
 
 template <class T>
 static void set_prog_smem(size_t bytes) {
@@ -3194,8 +3235,8 @@ static void plan_cache_put(const std::string& key, std::shared_ptr<PlanBundle> p
 static std::string plan_key(const InstHost& I, const PlanOpts& o) {
   std::string k(reinterpret_cast<const char*>(I.h.data()), I.h.size() * sizeof(double));
   char buf[128];
-  snprintf(buf, sizeof(buf), "|%d|%d|%.17g|%d|%d|%d|%d|%d|%d", I.N, I.P, o.lambda, o.leaf_elems, o.R,
-           o.kmax, o.max_concat, o.adm_min, o.structure_only);
+  snprintf(buf, sizeof(buf), "|%d|%d|%.17g|%d|%d|%d|%d|%d|%d|%d", I.N, I.P, o.lambda, o.leaf_elems, o.R,
+           o.kmax, o.max_concat, o.adm_min, o.structure_only, o.ncta);
   return k + buf;
 }
 
@@ -3243,6 +3284,14 @@ static hfsem_factor* factor_part(hfsem_system* s, const hfsem_hopts& opt, const 
     const int max_leaf = fp32 ? 128 : 96;
     std::map<std::string, std::shared_ptr<PlanBundle>> cache;
     const int ni = f->nfi;
+    {
+      // a part of one or two large instances (a request of the serving loop)
+      // runs its H-LU program on clusters of 16 CTAs: its waves hold tens of
+      // ops, and 8 CTAs would leave most of the GPU idle
+      int maxnd = 0;
+      for (int i : list) maxnd = std::max(maxnd, s->ih[i].Nd);
+      f->ncl = (!opt.build_only && ni <= kWideMaxInst && maxnd >= kWideNd) ? kWideCluster : kCluster;
+    }
     std::vector<std::string> keys(ni);
     f->plans.resize(ni);
     f->hidev.resize(ni);
@@ -3258,6 +3307,10 @@ static hfsem_factor* factor_part(hfsem_system* s, const hfsem_hopts& opt, const 
       // (in slices of 32 columns) to a block holding up to kKcapMult kmax
       const int leaf_cap = std::min(max_leaf, max_concat - kKcapMult * kmax_eff);
       int leaf = opt.leaf_elems ? opt.leaf_elems : std::max(1, leaf_cap / I.P);
+      if (!opt.leaf_elems && !opt.build_only) {   // a tuned size for the instance's class
+        const int d = tune_leaf_dofs(I, opt.precision);
+        if (d > 0) leaf = std::max(1, d / I.P);
+      }
       if (opt.build_only) {
         // an H-matrix built, never factored: no shared-memory limit on its
         // leaves (128 unknowns by default)
@@ -3273,7 +3326,7 @@ static hfsem_factor* factor_part(hfsem_system* s, const hfsem_hopts& opt, const 
       o.max_concat = max_concat;
       o.max_leaf = max_leaf;
       o.unique_tmp = 1;
-      o.ncta = kCluster;
+      o.ncta = f->ncl;
       popts[i] = o;
       keys[i] = plan_key(I, o) + (fp32 ? "|f32|" : "|f64|") + std::to_string(sol_budget);
     }
@@ -4030,7 +4083,7 @@ void hfsem_factor_s::report(const char* what) {
 // of its longest op takes the wave's time.
 void hfsem_factor_s::report_waves(const char* what) {
   if (!d_wprof.p) return;
-  const int rec = 1 + 3 * hf::kCluster;
+  const int rec = 1 + 3 * ncl;
   std::vector<unsigned long long> h(d_wprof.n);
   cudaMemcpy(h.data(), d_wprof.p, h.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost);
   int worst = 0;
@@ -4055,7 +4108,7 @@ void hfsem_factor_s::report_waves(const char* what) {
     const unsigned long long* q = &h[((size_t)worst * wstride + w) * rec];
     wall += q[0];
     int cm = 0;
-    for (int k = 0; k < hf::kCluster; ++k) {
+    for (int k = 0; k < ncl; ++k) {
       sumbusy += q[1 + 3 * k];
       if (q[1 + 3 * k] > q[1 + 3 * cm]) cm = k;
     }
@@ -4072,7 +4125,7 @@ void hfsem_factor_s::report_waves(const char* what) {
     e.second += 1;
   }
   fprintf(stderr, "[hfsem waves] %s (instance %d): %d waves  wall %.3f ms  max-busy %.3f ms  mean CTA busy %.3f ms\n",
-          what, worst, nw, wall * 1e-6, crit * 1e-6, sumbusy * 1e-6 / hf::kCluster);
+          what, worst, nw, wall * 1e-6, crit * 1e-6, sumbusy * 1e-6 / ncl);
   for (int t = 0; t < 16; ++t)
     if (ntype[t] > 0)
       fprintf(stderr, "  waves led by %-10s %6.0f  %.3f ms\n", names[t], ntype[t], bytype[t] * 1e-6);
@@ -4090,9 +4143,11 @@ void hfsem_factor_s::run_prog() {
     cudaMemset(d_prof.p, 0, d_prof.n * sizeof(unsigned long long));
   }
   if (!d_flops.p) {
-    d_flops.alloc((size_t)nfi * hf::kCluster * 2);
+    d_flops.alloc((size_t)nfi * std::max(ncl, hf::kCluster) * 2);
     cudaMemsetAsync(d_flops.p, 0, d_flops.n * sizeof(double), sys->st);
   }
+  const void* fn = tsize == sizeof(float) ? (const void*)hf::k_hprog<float> : (const void*)hf::k_hprog<double>;
+  if (ncl > hf::kCluster && !hf::wide_clusters_fit(fn, smem, ncl)) ncl = hf::kCluster;
   if (!d_tcdbg.p && precision == HFSEM_PREC_MIXED_TC) {
     d_tcdbg.alloc(8);
     HF_CHECK(cudaMemsetAsync(d_tcdbg.p, 0, 8 * sizeof(unsigned long long), sys->st));
@@ -4103,28 +4158,27 @@ void hfsem_factor_s::run_prog() {
     int nwmax = 1;
     for (auto& H : hidev) nwmax = std::max(nwmax, H.nfw);
     wstride = nwmax;
-    d_wprof.alloc((size_t)nwmax * hidev.size() * (1 + 3 * hf::kCluster));
+    d_wprof.alloc((size_t)nwmax * hidev.size() * (1 + 3 * ncl));
   }
   if (d_wprof.p) cudaMemsetAsync(d_wprof.p, 0, d_wprof.n * sizeof(unsigned long long), sys->st);
   hf::HProgArgs a{d_hi.p, d_waves.p, d_ops.p, d_slots.p, d_ranks.p, d_err.p, tol, d_prof.p, d_flops.p,
                   d_wprof.p, wstride, (long long)(smem / tsize) - 8, nfi,
-                  precision == HFSEM_PREC_MIXED_TC ? 1 : 0, d_tcdbg.p};
+                  precision == HFSEM_PREC_MIXED_TC ? 1 : 0, d_tcdbg.p, ncl};
   hf::Tick tk(sys->st, "hlu_factor");
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(nfi * hf::kCluster));
+  cfg.gridDim = dim3((unsigned)(nfi * ncl));
   cfg.blockDim = dim3(hf::kHThreads);
   cfg.dynamicSmemBytes = smem;
   cfg.stream = sys->st;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = hf::kCluster;
+  attr[0].val.clusterDim.x = ncl;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   if (getenv("HFSEM_PROFILE")) {
     // diagnostic: how many clusters of 8 and of 16 CTAs fit at once
-    const void* fn = tsize == sizeof(float) ? (const void*)hf::k_hprog<float> : (const void*)hf::k_hprog<double>;
     cudaFuncSetAttribute(fn, cudaFuncAttributeNonPortableClusterSizeAllowed, 1);
     for (int cs : {8, 16}) {
       cudaLaunchConfig_t c2 = cfg;
@@ -4222,7 +4276,7 @@ void hfsem_factor_s::apply(int nrhs, const double* r_em, double* y_em) {
     return;
   }
   if (!d_flops.p) {
-    d_flops.alloc((size_t)nfi * hf::kCluster * 2);
+    d_flops.alloc((size_t)nfi * std::max(ncl, hf::kCluster) * 2);
     cudaMemsetAsync(d_flops.p, 0, d_flops.n * sizeof(double), sys->st);
   }
   int maxnd = 1;

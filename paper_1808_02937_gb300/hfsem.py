@@ -38,7 +38,8 @@ EXPORTED = ["hfsem_assemble", "hfsem_ndof", "hfsem_apply", "hfsem_load_vector",
             "hfsem_timing_read", "hfsem_apply_noalloc", "hfsem_tc_tile_check",
             "hfsem_last_error", "hfsem_server_create", "hfsem_server_submit",
             "hfsem_server_poll", "hfsem_server_drain", "hfsem_server_counters_read",
-            "hfsem_server_free", "hfsem_alu_peak", "hfsem_hlu_solve"]
+            "hfsem_server_free", "hfsem_alu_peak", "hfsem_hlu_solve", "hfsem_tune",
+            "hfsem_tune_load", "hfsem_tune_lookup", "hfsem_tune_clear"]
 
 
 class HfsemError(RuntimeError):
@@ -68,6 +69,12 @@ class hfsem_rhs(C.Structure):
 class hfsem_stats(C.Structure):
     _fields_ = [("iters", C.c_int32), ("status", C.c_int32),
                 ("rel_residual", C.c_double), ("rel_true_residual", C.c_double)]
+
+
+class hfsem_tune_entry(C.Structure):
+    _fields_ = [("fp64", C.c_int32), ("kind", C.c_int32), ("P", C.c_int32),
+                ("leaf_dofs", C.c_int32), ("n_inst", C.c_int32), ("ms", C.c_double),
+                ("ms_default", C.c_double)]
 
 
 class hfsem_server_opts(C.Structure):
@@ -135,6 +142,11 @@ def load_library():
     lib.hfsem_hlu_solve.argtypes = [vp, vp, C.POINTER(hfsem_rhs), vp]
     lib.hfsem_alu_peak.argtypes = [C.c_int32, C.POINTER(C.c_double), C.POINTER(C.c_double),
                                    C.POINTER(C.c_int32)]
+    lib.hfsem_tune.argtypes = [vp, C.POINTER(hfsem_hopts), C.POINTER(hfsem_rhs), C.c_double,
+                               C.c_int32, C.c_char_p, C.POINTER(hfsem_tune_entry), C.c_int32,
+                               C.POINTER(C.c_int32)]
+    lib.hfsem_tune_load.argtypes = [C.c_char_p]
+    lib.hfsem_tune_lookup.argtypes = [C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_int32)]
     lib.hfsem_timing_enable.argtypes = [C.c_int32]
     lib.hfsem_timing_read.argtypes = [C.c_char_p, C.POINTER(C.c_double),
                                       C.POINTER(C.c_int64), C.POINTER(C.c_double)]
@@ -411,6 +423,35 @@ def split(sys: System, v, nrhs: int = 1):
         out.append(v[off: off + nd * nrhs].reshape(nrhs, nd).T)
         off += nd * nrhs
     return out
+
+
+def hfsem_tune(sys: System, opts: hfsem_hopts, rhs_list, tol=1e-14, max_iter=100, path=None):
+    """Leaf-size autotuner: per class of the system's instances, the fastest
+    candidate leaf size enters the process-wide table that later
+    factorisations with leaf_elems = 0 use.  Returns this call's choices."""
+    arr, keep = _rhs_array(rhs_list)
+    cap = 256
+    out = (hfsem_tune_entry * cap)()
+    n = C.c_int32()
+    _check(load_library().hfsem_tune(sys.h, C.byref(opts), arr, tol, max_iter,
+                                     path.encode() if path else None, out, cap, C.byref(n)),
+           "hfsem_tune")
+    return [dict(fp64=e.fp64, kind=e.kind, P=e.P, leaf_dofs=e.leaf_dofs, n_inst=e.n_inst,
+                 ms=e.ms, ms_default=e.ms_default) for e in out[:min(n.value, cap)]]
+
+
+def hfsem_tune_load(path: str):
+    _check(load_library().hfsem_tune_load(path.encode()), "hfsem_tune_load")
+
+
+def hfsem_tune_lookup(fp64: int, kind: int, P: int) -> int:
+    d = C.c_int32()
+    _check(load_library().hfsem_tune_lookup(fp64, kind, P, C.byref(d)), "hfsem_tune_lookup")
+    return d.value
+
+
+def hfsem_tune_clear():
+    _check(load_library().hfsem_tune_clear(), "hfsem_tune_clear")
 
 
 def hfsem_alu_peak(kind: int):

@@ -163,3 +163,27 @@ def test_direct_hmatrix_solve_falls_behind_with_n(lib):
     # measured with the oracle: 2.8e-4, 1.5e-2, 8.0e-2, 2.4e-1
     assert all(e1 < e2 for e1, e2 in zip(errs, errs[1:])), errs
     assert errs[-1] > 1e-2, errs
+
+
+@pytest.mark.parametrize("prec", [H.PREC_MIXED, H.PREC_FP64])
+def test_wide_cluster_factor_matches_the_batched_one(lib, prec):
+    # one large instance alone runs its H-LU program on a cluster of 16 CTAs,
+    # the same instance in a batch of three on clusters of 8: the ops of a
+    # wave are independent and each op's arithmetic does not depend on the
+    # CTA that runs it, so the preconditioned solves agree to rounding
+    h = W.mesh_graded(1024, 2.0)
+    P = 9                                  # N_d = 9215
+    prob = H.make_problem(h, P, 1.4, 0.6, 0.5, matvec=H.MATVEC_HMATRIX)
+    opts = H.hopts(R=8, lam=1.0, tol_hlu=1e-3, precision=prec, admissibility=H.ADM_MIN)
+    terms = [[(1.0, 0.5, "a"), (-0.5, 1.5, "b")]]
+    alone = H.hfsem_assemble([prob])
+    fa = H.hfsem_hlu_factor(alone, opts)
+    Xa, sa, ca = H.hfsem_solve(alone, fa, [H.rhs_frac_powers(terms)], tol=1e-14, max_iter=60)
+    batch = H.hfsem_assemble([prob, prob, prob])
+    fb = H.hfsem_hlu_factor(batch, opts)
+    Xb, sb, cb = H.hfsem_solve(batch, fb, [H.rhs_frac_powers(terms)] * 3, tol=1e-14, max_iter=60)
+    assert ca == H.HFSEM_OK and cb == H.HFSEM_OK
+    assert sa[0]["iters"] == sb[0]["iters"], (sa, sb)
+    xb = H.split(batch, Xb)
+    for k in range(3):
+        assert rel_err(xb[k][:, 0], Xa) < 1e-13, k
