@@ -59,6 +59,11 @@ constexpr int kCluster = 8;   // CTAs (one thread-block cluster) per instance
 constexpr int kWideCluster = 16;
 constexpr int kWideMaxInst = 2;
 constexpr int kWideNd = 8192;
+// factorisations of at least kNarrowMinInst instances run it on clusters of
+// kNarrowCluster CTAs: the instances, not the ops of one program, fill the
+// device then, and small clusters pack its SMs more densely
+constexpr int kNarrowCluster = 4;
+constexpr int kNarrowMinInst = 32;
 
 struct HInstDev {
   long long arena;   // offset of the instance arena (elements)
@@ -2710,7 +2715,10 @@ __device__ __forceinline__ void solve_prefetch(int a, int nj, long long pk0, con
 // low-rank columns and keeps their w in its own shared memory, every CTA
 // keeps the solutions of the last kRing leaves, and the partial sums of the
 // gathers and of the inverse product meet through distributed shared memory:
-// two cluster barriers per step.
+// two cluster barriers per step.  The right-hand sides go in chunks of
+// solve_w<T>() columns; nsplit clusters share an instance, each taking a
+// contiguous range of its chunks (they read the same factor and write
+// disjoint columns of the right-hand-side area).
 template <class T>
 __global__ void __launch_bounds__(kHThreads) k_hsolve_cl(const HInstDev* __restrict__ hi,
                                                         const StepInfo* __restrict__ sinfo,
@@ -2720,7 +2728,7 @@ __global__ void __launch_bounds__(kHThreads) k_hsolve_cl(const HInstDev* __restr
                                                         int nrhs, int jmax, int slot_elems,
                                                         int wcols, int* err, double* flops,
                                                         unsigned long long* sprof,
-                                                        const int* __restrict__ gate) {
+                                                        const int* __restrict__ gate, int nsplit) {
   extern __shared__ __align__(16) unsigned char smraw[];
   HF_GATE(gate);   // every CTA of the cluster returns, before any barrier
   constexpr int kSolveW = solve_w<T>();
@@ -2739,7 +2747,8 @@ __global__ void __launch_bounds__(kHThreads) k_hsolve_cl(const HInstDev* __restr
   int4* mbb = reinterpret_cast<int4*>(sx + (long long)jmax * kSolveW);   // [2][jmax]
   const unsigned crank = cluster_rank();
   const unsigned cid = cluster_id();
-  const HInstDev H = hi[cid];
+  const unsigned inst = cid / (unsigned)nsplit, part = cid % (unsigned)nsplit;
+  const HInstDev H = hi[inst];
   T* ar = har + H.arena;
   const StepInfo* si = sinfo + H.st0;
   const StepCta* sc = scta + H.st0 * kCluster;
@@ -2748,7 +2757,8 @@ __global__ void __launch_bounds__(kHThreads) k_hsolve_cl(const HInstDev* __restr
   const long long ld = H.nd;
   const int nst = H.nst;
   const int nchunk = (nrhs + kSolveW - 1) / kSolveW;
-  const int total = nst * nchunk;
+  const int ch0 = (int)(part * nchunk / nsplit), ch1 = (int)((part + 1) * nchunk / nsplit);
+  const int total = nst * (ch1 - ch0);
   double fl = 0.0;
   bool ok = true;
   long long qfail = -1;   // part whose copy did not arrive in time
@@ -2803,7 +2813,7 @@ __global__ void __launch_bounds__(kHThreads) k_hsolve_cl(const HInstDev* __restr
     ++qn;
   };
   for (int g = 0; g < total; ++g) {
-    const int s = g % nst, c0 = (g / nst) * kSolveW;
+    const int s = g % nst, c0 = (ch0 + g / nst) * kSolveW;
     const int nc = min(kSolveW, nrhs - c0);
     T* b = ar + H.rhs_off + (long long)c0 * ld;
     if (s == 0) {   // a new chunk of right-hand sides: clear this CTA's w
@@ -2949,14 +2959,14 @@ __global__ void __launch_bounds__(kHThreads) k_hsolve_cl(const HInstDev* __restr
   if (!ok) {
     // a copy never arrived: flag it and give the copies in flight a bounded
     // time to land before the shared memory is released
-    if (tid == 0) atomicExch(err + cid, 2);
+    if (tid == 0) atomicExch(err + inst, 2);
     if (qfail >= 0) {
       long long spins = 0;
       while (!mbar_try_wait(&bar[qfail & 1], (unsigned)((qfail >> 1) & 1)) && ++spins < (1LL << 20)) {
       }
     }
   }
-  if (tid == 0) flops[((size_t)cid * kCluster + crank) * 2 + 1] += fl;
+  if (tid == 0) atomicAdd(&flops[((size_t)inst * kCluster + crank) * 2 + 1], fl);
 }
 
 // rhs area <- D r (element-major FP64 -> T); rank slot n_slots <- nrhs
@@ -3290,7 +3300,8 @@ static hfsem_factor* factor_part(hfsem_system* s, const hfsem_hopts& opt, const 
       // ops, and 8 CTAs would leave most of the GPU idle
       int maxnd = 0;
       for (int i : list) maxnd = std::max(maxnd, s->ih[i].Nd);
-      f->ncl = (!opt.build_only && ni <= kWideMaxInst && maxnd >= kWideNd) ? kWideCluster : kCluster;
+      f->ncl = (!opt.build_only && ni <= kWideMaxInst && maxnd >= kWideNd) ? kWideCluster
+               : (ni >= kNarrowMinInst ? kNarrowCluster : kCluster);
     }
     std::vector<std::string> keys(ni);
     f->plans.resize(ni);
@@ -4232,7 +4243,12 @@ void hfsem_factor_s::run_leaf_solve(int nrhs) {
   }
   hf::Tick tk(sys->st, "hlu_solve");
   cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(nfi * hf::kCluster));
+  // a few instances with several chunks of right-hand sides: the chunks are
+  // split over clusters (at most ~15 clusters of 8 fit the device at once)
+  const int nchunk = (nrhs + (tsize == sizeof(float) ? hf::solve_w<float>() : hf::solve_w<double>()) - 1) /
+                     (tsize == sizeof(float) ? hf::solve_w<float>() : hf::solve_w<double>());
+  const int nsplit = std::max(1, std::min(nchunk, 15 / std::max(nfi, 1)));
+  cfg.gridDim = dim3((unsigned)(nfi * nsplit * hf::kCluster));
   cfg.blockDim = dim3(hf::kHThreads);
   cfg.dynamicSmemBytes = sol_smem;
   cfg.stream = sys->st;
@@ -4248,13 +4264,13 @@ void hfsem_factor_s::run_leaf_solve(int nrhs) {
                                 (const hf::StepInfo*)d_steps.p, (const hf::StepCta*)d_step_cta.p,
                                 (const float*)d_pack.p, (const int4*)d_meta.p,
                                 reinterpret_cast<float*>(d_arena.p), nrhs, sol_jmax, sol_slot, sol_wcols,
-                                d_err.p, d_flops.p, d_sprof.p, sys->gate));
+                                d_err.p, d_flops.p, d_sprof.p, sys->gate, nsplit));
   else
     HF_CHECK(cudaLaunchKernelEx(&cfg, hf::k_hsolve_cl<double>, (const hf::HInstDev*)d_hi.p,
                                 (const hf::StepInfo*)d_steps.p, (const hf::StepCta*)d_step_cta.p,
                                 (const double*)d_pack.p, (const int4*)d_meta.p,
                                 reinterpret_cast<double*>(d_arena.p), nrhs, sol_jmax, sol_slot, sol_wcols,
-                                d_err.p, d_flops.p, d_sprof.p, sys->gate));
+                                d_err.p, d_flops.p, d_sprof.p, sys->gate, nsplit));
   HF_LAUNCH_CHECK();
   if (d_sprof.p) {
     unsigned long long h[8];

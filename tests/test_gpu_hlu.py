@@ -187,3 +187,48 @@ def test_wide_cluster_factor_matches_the_batched_one(lib, prec):
     xb = H.split(batch, Xb)
     for k in range(3):
         assert rel_err(xb[k][:, 0], Xa) < 1e-13, k
+
+
+@pytest.mark.parametrize("prec", [H.PREC_MIXED, H.PREC_FP64])
+def test_rhs_chunks_split_over_clusters(lib, prec):
+    # one instance with 16 right-hand sides: its H-solves split the chunks of
+    # right-hand sides over several clusters; in a batch of 16 copies every
+    # instance's chunks run on its own cluster in turn.  Same arithmetic per
+    # chunk, so the solutions agree to rounding
+    h = W.mesh_graded(400, 2.0)
+    prob = H.make_problem(h, 8, 1.7, 0.3, 1.0, matvec=H.MATVEC_HMATRIX)
+    opts = H.hopts(R=8, lam=1.0, tol_hlu=1e-3, precision=prec, admissibility=H.ADM_MIN)
+    terms = [[(1.0, 0.3 + 0.2 * k, "a"), (0.5 - 0.05 * k, 1.0 + 0.1 * k, "b")] for k in range(16)]
+    rhs = H.rhs_frac_powers(terms)
+    alone = H.hfsem_assemble([prob])
+    fa = H.hfsem_hlu_factor(alone, opts)
+    Xa, sa, ca = H.hfsem_solve(alone, fa, [rhs], tol=1e-14, max_iter=60)
+    batch = H.hfsem_assemble([prob] * 16)
+    fb = H.hfsem_hlu_factor(batch, opts)
+    Xb, sb, cb = H.hfsem_solve(batch, fb, [rhs] * 16, tol=1e-14, max_iter=60)
+    assert ca == H.HFSEM_OK and cb == H.HFSEM_OK
+    xa = H.split(alone, Xa, 16)[0]
+    for k, xb in enumerate(H.split(batch, Xb, 16)):
+        for r in range(16):
+            assert rel_err(xb[:, r], xa[:, r]) < 1e-14, (k, r)
+    assert [s["iters"] for s in sa] == [s["iters"] for s in sb[:16]]
+
+
+@pytest.mark.parametrize("prec", [H.PREC_MIXED, H.PREC_FP64])
+def test_narrow_cluster_factor_matches_the_single_one(lib, prec):
+    # a batch of 40 instances runs its H-LU programs on clusters of 4 CTAs,
+    # one instance alone on a cluster of 8: same factor, same solutions
+    h = W.mesh_geometric_two_sided(96, 0.6)
+    prob = H.make_problem(h, 6, 1.25, 0.8, 0.2, matvec=H.MATVEC_HMATRIX)
+    opts = H.hopts(R=8, lam=1.0, tol_hlu=1e-3, precision=prec, admissibility=H.ADM_MIN)
+    rhs = H.rhs_frac_powers([[(1.0, 0.7, "a"), (2.0, 0.2, "b")]])
+    alone = H.hfsem_assemble([prob])
+    fa = H.hfsem_hlu_factor(alone, opts)
+    Xa, sa, ca = H.hfsem_solve(alone, fa, [rhs], tol=1e-14, max_iter=60)
+    batch = H.hfsem_assemble([prob] * 40)
+    fb = H.hfsem_hlu_factor(batch, opts)
+    Xb, sb, cb = H.hfsem_solve(batch, fb, [rhs] * 40, tol=1e-14, max_iter=60)
+    assert ca == H.HFSEM_OK and cb == H.HFSEM_OK
+    for k, xb in enumerate(H.split(batch, Xb)):
+        assert rel_err(xb[:, 0], Xa) < 1e-14, k
+    assert all(s["iters"] == sa[0]["iters"] for s in sb)
