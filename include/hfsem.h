@@ -338,8 +338,9 @@ int hfsem_timing_read(const char *tag, double *total_ms, int64_t *launches, doub
  * FP64) ------------------------------------------------------------------
  *
  * hfsem_tune groups the instances of sys into classes (factor arithmetic,
- * uniform or not, P), factors and solves up to 16 instances of each class
- * with every candidate leaf size (32, 48, 64, 96, 128 unknowns, capped by the
+ * uniform or not, P), factors and solves 32 instances of each class (its
+ * first 32, repeated when it has fewer, so that the runs launch like a large
+ * batch) with every candidate leaf size (32, 48, 64, 96, 128 unknowns, capped by the
  * arithmetic), each twice (the first run builds the plans), and keeps the
  * fastest (factorisation + solve, CUDA events on sys's stream) among those
  * whose iteration count is within one of the fewest.  opts are the options

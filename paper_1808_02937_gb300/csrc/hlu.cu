@@ -660,6 +660,7 @@ struct HCtx {
   unsigned long long* tcdbg;   // diagnostics of a tensor-core wait that ran out
   double tol;
   int* err;
+  int leaf32;   // leaf LUs in FP32 arithmetic (FP64 arena kept for its range)
 };
 
 template <class T>
@@ -1307,11 +1308,12 @@ __device__ __forceinline__ void nbar_arrive(int id) {
 // is published once, after which each warp eliminates its own columns
 // without any barrier.  The outer loop over column blocks of 8 is unrolled so
 // that every register index is static.
-__device__ void getrf_inv_reg(const HOp& o, HCtx<float>& c) {
+template <class T>
+__device__ void getrf_inv_reg(const HOp& o, HCtx<T>& c) {
   const int n = o.C.r;
-  float* ar = c.ar;
-  float* colb = c.sm;            // [2][128] multipliers of a step
-  float* Ut = c.sm + 256;        // [128][129] scaled upper factor (row-major, padded)
+  T* ar = c.ar;                  // FP32 arithmetic whatever the arena's type
+  float* colb = reinterpret_cast<float*>(c.sm);   // [2][128] multipliers of a step
+  float* Ut = colb + 256;        // [128][129] scaled upper factor (row-major, padded)
   float* diag = Ut + 128 * 129;  // [128]
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
   unsigned long long tq = 0;
@@ -1329,7 +1331,7 @@ __device__ void getrf_inv_reg(const HOp& o, HCtx<float>& c) {
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const int i = tx + 32 * r, j = ty + 8 * q;
-      S[r][q] = (i < n && j < n) ? ar[vidx(o.C, i, j)] : 0.f;
+      S[r][q] = (i < n && j < n) ? (float)ar[vidx(o.C, i, j)] : 0.f;
       X[r][q] = (i == j && i < n) ? 1.f : 0.f;
     }
   // publish the multipliers of step kn from local column cc, pivot in
@@ -1419,7 +1421,7 @@ __device__ void getrf_inv_reg(const HOp& o, HCtx<float>& c) {
 #pragma unroll
     for (int q = 0; q < 16; ++q) {
       const int i = tx + 32 * r, j = ty + 8 * q;
-      if (i < n && j < n) ar[vidx(o.A, i, j)] = X[r][q];
+      if (i < n && j < n) ar[vidx(o.A, i, j)] = (T)X[r][q];
       if (i == j && i < n) diag[i] = S[r][q];
     }
   __syncthreads();
@@ -1469,7 +1471,7 @@ __device__ void getrf_inv_reg(const HOp& o, HCtx<float>& c) {
 #pragma unroll
     for (int r = 0; r < 4; ++r) {
       const int i = tx + 32 * r;
-      if (i < n) ar[vidx(o.B, i, j)] = X[r][q] * cj;
+      if (i < n) ar[vidx(o.B, i, j)] = (T)(X[r][q] * cj);
     }
   }
   tmk(3);
@@ -1479,11 +1481,9 @@ template <class T>
 __device__ void op_getrf_inv(const HOp& o, HCtx<T>& c) {
   const int n = o.C.r;
   if (n <= 0) return;
-  if constexpr (sizeof(T) == 4) {
-    if (n <= 128) {
-      getrf_inv_reg(o, c);
-      return;
-    }
+  if (n <= 128 && (sizeof(T) == 4 || c.leaf32)) {
+    getrf_inv_reg(o, c);
+    return;
   }
   T* ar = c.ar;
   T* S = c.sm;             // n x n, [i + j n]
@@ -2393,6 +2393,7 @@ struct HProgArgs {
   int tc;                     // dense leaf contractions on the tensor cores
   unsigned long long* tcdbg;  // 8 words of diagnostics for a tensor-core wait that ran out
   int ncl;                    // CTAs per instance (the cluster size of the launch)
+  int leaf32;                 // FP64 factor: leaf LUs in FP32 arithmetic
 };
 
 // algorithmic flops of one op with its run-time shapes
@@ -2462,6 +2463,7 @@ __global__ void __launch_bounds__(kHThreads) k_hprog(HProgArgs a, T* har) {
   c.tprof = a.prof ? a.prof + (size_t)a.n_inst_prof * 32 : nullptr;
   c.tol = a.tol;
   c.err = a.err + cid;
+  c.leaf32 = a.leaf32;
   // tensor memory (256 columns of FP32 accumulators) and the MMA mbarrier
   __shared__ unsigned s_tmem;
   __shared__ __align__(8) unsigned long long s_tcbar;
@@ -2617,6 +2619,7 @@ __global__ void __launch_bounds__(kHThreads) k_tc_tile_check(float* ar, int N, i
   c.tprof = nullptr;
   c.tol = 0.0;
   c.err = err + crank;
+  c.leaf32 = 0;
   unsigned tcphase = 0;
   c.tc = 1;
   c.tcbar = &s_tcbar;
@@ -3143,6 +3146,7 @@ struct hfsem_factor_s : public hf::Precond {
   double hop_flops = 0.0;         // per right-hand side
   int wstride = 0;
   int ncl = hf::kCluster;   // CTAs per instance in the H-LU program (plans hold ncl workspaces)
+  int leaf32 = 0;           // FP64 part of a mixed factor: leaf LUs in FP32 arithmetic
   void report(const char* what);
   void report_waves(const char* what);
   void apply(int nrhs, const double* r_em, double* y_em) override;
@@ -3279,6 +3283,9 @@ static hfsem_factor* factor_part(hfsem_system* s, const hfsem_hopts& opt, const 
     f->precision = precision;
     f->insts = list;
     f->nfi = (int)list.size();
+    // the FP64 part of a mixed-precision factor is in FP64 for the range of
+    // its meshes' entries; its leaf LUs keep the FP32 arithmetic of the mode
+    f->leaf32 = (precision == HFSEM_PREC_FP64 && opt.precision != HFSEM_PREC_FP64) ? 1 : 0;
     f->build_only = opt.build_only;
     f->tol = opt.tol_hlu;
     f->R = opt.R;
@@ -4174,7 +4181,7 @@ void hfsem_factor_s::run_prog() {
   if (d_wprof.p) cudaMemsetAsync(d_wprof.p, 0, d_wprof.n * sizeof(unsigned long long), sys->st);
   hf::HProgArgs a{d_hi.p, d_waves.p, d_ops.p, d_slots.p, d_ranks.p, d_err.p, tol, d_prof.p, d_flops.p,
                   d_wprof.p, wstride, (long long)(smem / tsize) - 8, nfi,
-                  precision == HFSEM_PREC_MIXED_TC ? 1 : 0, d_tcdbg.p, ncl};
+                  precision == HFSEM_PREC_MIXED_TC ? 1 : 0, d_tcdbg.p, ncl, leaf32};
   hf::Tick tk(sys->st, "hlu_factor");
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((unsigned)(nfi * ncl));

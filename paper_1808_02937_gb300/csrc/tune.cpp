@@ -96,13 +96,19 @@ extern "C" int hfsem_tune(hfsem_system* sys, const hfsem_hopts* opts, const hfse
     const int nrhs = rhs[0].nrhs;
     for (int i = 0; i < sys->n_inst; ++i)
       if (rhs[i].nrhs != nrhs) throw Error(HFSEM_ERR_INVALID_ARG, "every instance needs the same nrhs");
-    // classes and their instances (at most kTuneInst each, in order)
-    constexpr int kTuneInst = 16;
+    // classes and their instances: kTuneInst per class, the class's own
+    // instances in order, repeated when it has fewer, so that every timing
+    // run launches the way a large batch does (clusters of 4 CTAs for the
+    // H-LU program, one cluster per instance for the H-solves)
+    constexpr int kTuneInst = 32;
     std::map<Key, std::vector<int>> cls;
     for (int i = 0; i < sys->n_inst; ++i) {
       auto& v = cls[key_of(sys->ih[i], opts->precision)];
       if ((int)v.size() < kTuneInst) v.push_back(i);
     }
+    for (auto& kv : cls)
+      for (size_t k = 0, n0 = kv.second.size(); kv.second.size() < (size_t)kTuneInst; ++k)
+        kv.second.push_back(kv.second[k % n0]);
     std::vector<hfsem_tune_entry> res;
     Timer tm(sys->st);
     for (auto& kv : cls) {

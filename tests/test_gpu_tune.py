@@ -37,7 +37,7 @@ def test_tuned_leaf_is_used_and_reloads(lib, tmp_path):
     got = H.hfsem_tune(sys_, _opts(), rhs, tol=1e-14, max_iter=100, path=path)
     assert len(got) == 1
     e = got[0]
-    assert (e["fp64"], e["kind"], e["P"]) == (0, 0, 5) and e["n_inst"] == len(insts)
+    assert (e["fp64"], e["kind"], e["P"]) == (0, 0, 5) and e["n_inst"] == 32
     assert e["leaf_dofs"] in (32, 48, 64, 96, 128)
     assert e["ms"] > 0 and e["ms_default"] > 0
     assert H.hfsem_tune_lookup(0, 0, 5) == e["leaf_dofs"]
