@@ -556,6 +556,7 @@ namespace {
 // matrix starting at `base` with leading dimension ld (rank dims -> capacity)
 struct Rect {
   long long base;
+  int bucket;   // index of the access history the rectangle belongs to
   int ld;
   long long r0, r1, c0, c1;
   int slot;   // LR slot whose rank is read (-1 none)
@@ -606,9 +607,16 @@ int program_levels(const HPlan& p, const std::vector<HOp>& prog, std::vector<int
   }
   auto find = [&](long long off) -> const Alloc* {
     if (off < 0 || al.empty()) return nullptr;
-    const size_t bk = std::min((size_t)(off >> kShift), first.size() - 1);
-    size_t lo = first[bk];   // allocations [0, lo) start before the bucket
-    while (lo < al.size() && al[lo].off <= off) ++lo;
+    const size_t bk = std::min((size_t)(off >> kShift), first.size() - 2);
+    // allocations [0, first[bk]) start before the bucket, [first[bk],
+    // first[bk + 1]) inside it: the last one starting at or before off
+    size_t lo = first[bk], hi = std::max<size_t>(first[bk + 1], lo);
+    while (lo < hi) {
+      const size_t mid = (lo + hi) / 2;
+      if (al[mid].off <= off) lo = mid + 1;
+      else hi = mid;
+    }
+    while (lo < al.size() && al[lo].off <= off) ++lo;   // off past the last bucket
     if (lo == 0) return nullptr;
     const Alloc& a = al[lo - 1];
     return (off < a.off + a.size) ? &a : nullptr;
@@ -623,6 +631,7 @@ int program_levels(const HPlan& p, const std::vector<HOp>& prog, std::vector<int
     if (sc < 0) slot = -1 - sc;
     if (a && a->slot >= 0) {   // LR factor: whole factor, rank read
       r.base = a->off;
+      r.bucket = 2 + (int)(a - al.data());
       r.ld = a->ld;
       r.r0 = 0;
       r.r1 = a->ld;
@@ -635,6 +644,7 @@ int program_levels(const HPlan& p, const std::vector<HOp>& prog, std::vector<int
     if (a) {
       long long rel = v.off - a->off;
       r.base = a->off;
+      r.bucket = 2 + (int)(a - al.data());
       r.ld = a->ld;
       r.r0 = rel % a->ld;
       r.c0 = rel / a->ld;
@@ -642,11 +652,13 @@ int program_levels(const HPlan& p, const std::vector<HOp>& prog, std::vector<int
       long long rel = v.off - p.rhs_off;
       int ldr = std::max(p.Nd, 1);
       r.base = p.rhs_off;
+      r.bucket = 1;
       r.ld = ldr;
       r.r0 = rel % ldr;
       r.c0 = rel / ldr;
     } else {   // temporaries: by raw address
       r.base = -1;
+      r.bucket = 0;
       r.ld = v.ld;
       r.r0 = v.off % std::max(v.ld, 1);
       r.c0 = v.off / std::max(v.ld, 1);
@@ -688,7 +700,9 @@ int program_levels(const HPlan& p, const std::vector<HOp>& prog, std::vector<int
   auto covers = [](const Rect& a, const Rect& b) {   // a contains b
     return a.r0 <= b.r0 && b.r1 <= a.r1 && a.c0 <= b.c0 && b.c1 <= a.c1;
   };
-  std::unordered_map<long long, Hist> hist;      // base (or -1 for raw) -> accesses
+  // access histories: 0 raw addresses, 1 the right-hand-side area, 2 + k
+  // allocation k
+  std::vector<Hist> hist(al.size() + 2);
   // slot -> (last write level, max read level); 0: none yet
   std::vector<std::pair<int, int>> slot_state((size_t)std::max(p.n_slots, 0) + 1, {0, 0});
   int nlev = 0;
@@ -712,14 +726,12 @@ int program_levels(const HPlan& p, const std::vector<HOp>& prog, std::vector<int
     }
     int lv = 0;
     for (auto& a : acc) {
-      auto it = hist.find(a.rc.base);
-      if (it != hist.end()) {
-        for (auto& r : it->second.wr)
+      const Hist& hh = hist[a.rc.bucket];
+      for (auto& r : hh.wr)
+        if (overlap(a.rc, r.rc)) lv = std::max(lv, r.lvl);
+      if (a.write)
+        for (auto& r : hh.rd)
           if (overlap(a.rc, r.rc)) lv = std::max(lv, r.lvl);
-        if (a.write)
-          for (auto& r : it->second.rd)
-            if (overlap(a.rc, r.rc)) lv = std::max(lv, r.lvl);
-      }
       if (a.rc.slot >= 0) lv = std::max(lv, slot_state[a.rc.slot].first);   // reads the slot's rank
     }
     if (slot_w >= 0) lv = std::max(lv, std::max(slot_state[slot_w].first, slot_state[slot_w].second));
@@ -727,7 +739,7 @@ int program_levels(const HPlan& p, const std::vector<HOp>& prog, std::vector<int
     level[i] = lv;
     nlev = std::max(nlev, lv);
     for (auto& a : acc) {
-      Hist& h = hist[a.rc.base];
+      Hist& h = hist[a.rc.bucket];
       if (a.write) {
         auto dominated = [&](const Rec& r) { return covers(a.rc, r.rc); };
         h.wr.erase(std::remove_if(h.wr.begin(), h.wr.end(), dominated), h.wr.end());
