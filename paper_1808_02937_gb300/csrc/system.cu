@@ -207,11 +207,14 @@ __device__ __forceinline__ void legendre_strided(int n, double x, double* out,
 }
 
 // Gauss points needed in one direction of a box whose distance to the
-// kernel's singular line is r times its length (Bernstein ellipse argument).
+// kernel's singular line is r times its length (Bernstein ellipse argument:
+// the error of an n-point rule on the kernel times degree-(P-1) polynomials
+// falls like rhoB^-(2n - P + 1), kept near 1e-15 per box, below the rounding
+// of the FP64 sums it enters).
 __device__ __forceinline__ int box_points(int P, double r) {
   double t = 1.0 + 2.0 * r;
   double rhoB = t + sqrt(t * t - 1.0);
-  int n = (int)ceil(0.5 * (P - 1) + 19.6 / log(rhoB)) + 1;
+  int n = (int)ceil(0.5 * (P - 1) + 17.3 / log(rhoB)) + 1;
   n = max(n, (P + 2) / 2);
   return min(n, 40);
 }
