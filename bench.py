@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--batch-instances", type=int, default=512)
     ap.add_argument("--no-tune", action="store_true",
                     help="config-4 batch: automatic leaf sizes instead of tuned ones")
+    ap.add_argument("--tc", action="store_true",
+                    help="config-4 batch: mixed arm with the tensor-core (BF16x3) H-LU products")
     return ap.parse_args()
 
 
@@ -335,7 +337,7 @@ def run_serving(H, torch, args, world, rank, local):
 
 
 # -------------------------------------------------------------- batched --
-def run_batch(H, torch, steps, warmup, world, timing=False, n_inst=512, tune=True):
+def run_batch(H, torch, steps, warmup, world, timing=False, n_inst=512, tune=True, tc=False):
     from paper_1808_02937_gb300 import workloads as W
     insts = W.config4()[:n_inst]
     probs = [H.make_problem(p.h, p.P, p.alpha, p.theta, p.rho, matvec=operator_kind(H, p.h))
@@ -345,7 +347,8 @@ def run_batch(H, torch, steps, warmup, world, timing=False, n_inst=512, tune=Tru
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")   # 256 MB > L2
     stream = torch.cuda.current_stream()
     out = {}
-    for name, prec in (("mixed", H.PREC_MIXED), ("fp64", H.PREC_FP64)):
+    mixed = H.PREC_MIXED_TC if tc else H.PREC_MIXED
+    for name, prec in (("mixed", mixed), ("fp64", H.PREC_FP64)):
         opts = H.hopts(R=8, lam=1.0, tol_hlu=1e-3, precision=prec, admissibility=H.ADM_MIN)
         X = torch.zeros(nd * 4, dtype=torch.float64, device="cuda")
         tuned = None
@@ -592,7 +595,7 @@ def main():
             print(json.dumps(line), flush=True)
     else:
         B = run_batch(H, torch, steps=args.steps, warmup=args.warmup, world=world, timing=True,
-                      n_inst=args.batch_instances, tune=not args.no_tune)
+                      n_inst=args.batch_instances, tune=not args.no_tune, tc=args.tc)
         roof, alu, share = roofline(H, B["mixed"]["kernels"], args.steps, "mixed")
         if rank == 0:
             m = B["mixed"]
@@ -600,7 +603,9 @@ def main():
                     "n_gpus": world, "steps": args.steps, "warmup": max(args.warmup, 3),
                     "ms_per_step": m["ms_per_step"], "higher_is_better": True,
                     "scaling": "weak", "vs_baseline": None,
-                    "dtype": "f64 Krylov/operator/assembly, f32 H-LU", "data": "synthetic",
+                    "dtype": ("f64 Krylov/operator/assembly, f32 H-LU with bf16x3 tensor-core leaf "
+                              "products" if args.tc else "f64 Krylov/operator/assembly, f32 H-LU"),
+                    "data": "synthetic",
                     "config": {"workload": BATCH_WORKLOAD if args.batch_instances == 512 else
                                f"REDUCED (profiling only): first {args.batch_instances} "
                                f"instances of config 4", "l2": "flushed between steps"},

@@ -79,11 +79,12 @@ extern "C" {
 #define HFSEM_PREC_MIXED_TC 2     /* as HFSEM_PREC_MIXED, with the dense leaf
                                      products of the H-LU (128-row GEMMs and
                                      the multiplies by inverted diagonal
-                                     leaves) on the tensor cores: BF16 operands,
-                                     FP32 accumulation (Sec. 4.1 H-LU).  The
-                                     preconditioner is weaker (more Krylov
-                                     iterations); the Krylov loop still
-                                     reaches the requested FP64 tolerance   */
+                                     leaves) on the tensor cores: each FP32
+                                     operand split into BF16 head and tail,
+                                     three MMAs per K step, FP32 accumulation
+                                     (Sec. 4.1 H-LU); products to ~2^-16
+                                     relative, the preconditioner as strong
+                                     as HFSEM_PREC_MIXED's                   */
 
 #define HFSEM_RHS_LOAD_VECTOR  0  /* G given directly                        */
 #define HFSEM_RHS_FRAC_POWERS  1  /* f = sum c_k (x-a)^mu_k + sum d_k (b-x)^nu_k */
@@ -187,14 +188,14 @@ int hfsem_apply(hfsem_system *sys, int32_t nrhs, const double *x, double *y);
  * race on it. */
 int hfsem_apply_noalloc(hfsem_system *sys, int32_t nrhs, const double *x, double *y);
 
-/* Self-check of the BF16 tensor-core tile that HFSEM_PREC_MIXED_TC uses (the
+/* Self-check of the BF16x3 tensor-core tile that HFSEM_PREC_MIXED_TC uses (the
  * paper has no counterpart; its H-LU runs on CPU cores): one thread-block
  * cluster computes C = A B, A 128 x K and B K x N with fixed entries in
  * [-0.5, 0.5], reps times per CTA on one completion barrier, and compares
  * every entry with the product in FP64.  16 <= N <= 128 and 64 <= K <= 128,
  * both multiples of 16; 1 <= reps <= 8.  *max_rel_err receives
- * max |C - A B| / sum_k |a_mk b_kn| over the entries (BF16 rounding of both
- * operands bounds it by about 2^-8 + K 2^-24).  HFSEM_ERR_DEVICE when a
+ * max |C - A B| / sum_k |a_mk b_kn| over the entries (the head/tail split
+ * of both operands bounds it by about 2^-16 + 3K 2^-24).  HFSEM_ERR_DEVICE when a
  * product did not complete within its wait limit (about 2 ms). */
 int hfsem_tc_tile_check(int32_t N, int32_t K, int32_t reps, double *max_rel_err);
 

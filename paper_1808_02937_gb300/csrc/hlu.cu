@@ -676,10 +676,13 @@ __device__ T block_sum(T v, T* red) {
   return s;
 }
 
-// BF16 tensor-core tile: D (128 x N) = A (128 x K) B (K x N) with FP32
-// accumulation in tensor memory (tcgen05), A and B read from FP32 views and
-// rounded to bf16 into shared memory as K-major core matrices; then
-// C = beta C + alpha D, with C stored 128 x N (ctr = 0) or N x 128 (ctr = 1).
+// BF16x3 tensor-core tile: D (128 x N) = A (128 x K) B (K x N) with FP32
+// accumulation in tensor memory (tcgen05).  A and B are read from FP32 views
+// and split into a BF16 head and a BF16 tail (x = hi + lo, lo the rounded
+// remainder), each stored in shared memory as K-major core matrices; three
+// MMAs per K step (hi hi, hi lo, lo hi) give the products to about 2^-16
+// relative, close to FP32 operands.  Then C = beta C + alpha D, with C stored
+// 128 x N (ctr = 0) or N x 128 (ctr = 1).
 // K a multiple of 16, N a multiple of 16 in [16, 256].  One thread issues the
 // MMAs; all threads wait on the mbarrier they commit to (bounded), then read
 // the accumulators back, warp w covering rows 32 (w mod 4) ...
@@ -689,17 +692,29 @@ __device__ bool tc_gemm128(HCtx<float>& c, const View& A, const View& B, const V
   // operands on 1024-byte boundaries
   const unsigned base = smem_u32(c.sm);
   const unsigned pad = ((base + 1023u) & ~1023u) - base;
-  __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(c.sm) + pad);   // 128 x K
-  __nv_bfloat16* Bs = As + (((size_t)128 * K + 511) & ~(size_t)511);                                      // N x K
+  // heads and tails of A (128 x K) and B (N x K), each on a 1024-byte boundary
+  const size_t sa = ((size_t)128 * K + 511) & ~(size_t)511, sb = ((size_t)N * K + 511) & ~(size_t)511;
+  __nv_bfloat16* As = reinterpret_cast<__nv_bfloat16*>(reinterpret_cast<unsigned char*>(c.sm) + pad);
+  __nv_bfloat16* Al = As + sa;
+  __nv_bfloat16* Bs = Al + sa;
+  __nv_bfloat16* Bl = Bs + sb;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int nc8 = N >> 3;
   for (int t = tid; t < 128 * K; t += nt) {
     const int m = t & 127, k = t >> 7;
-    As[((k >> 3) * 16 + (m >> 3)) * 64 + (m & 7) * 8 + (k & 7)] = __float2bfloat16_rn(ar[vidx(A, m, k)]);
+    const float x = ar[vidx(A, m, k)];
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    const int i = ((k >> 3) * 16 + (m >> 3)) * 64 + (m & 7) * 8 + (k & 7);
+    As[i] = h;
+    Al[i] = __float2bfloat16_rn(x - __bfloat162float(h));
   }
   for (int t = tid; t < K * N; t += nt) {
     const int k = t % K, n = t / K;
-    Bs[((k >> 3) * nc8 + (n >> 3)) * 64 + (n & 7) * 8 + (k & 7)] = __float2bfloat16_rn(ar[vidx(B, k, n)]);
+    const float x = ar[vidx(B, k, n)];
+    const __nv_bfloat16 h = __float2bfloat16_rn(x);
+    const int i = ((k >> 3) * nc8 + (n >> 3)) * 64 + (n & 7) * 8 + (k & 7);
+    Bs[i] = h;
+    Bl[i] = __float2bfloat16_rn(x - __bfloat162float(h));
   }
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   __syncthreads();
@@ -707,9 +722,13 @@ __device__ bool tc_gemm128(HCtx<float>& c, const View& A, const View& B, const V
     tc_fence_after();
     const unsigned idesc = tc_idesc_bf16(128, N);
     for (int s = 0; s < K / 16; ++s) {
-      const unsigned long long ad = tc_sdesc(As + s * 2 * 16 * 64, 16 * 64 * 2, 128);
-      const unsigned long long bd = tc_sdesc(Bs + s * 2 * nc8 * 64, nc8 * 64 * 2, 128);
-      tc_mma(c.tmem, ad, bd, idesc, s > 0);
+      const unsigned long long ah = tc_sdesc(As + s * 2 * 16 * 64, 16 * 64 * 2, 128);
+      const unsigned long long al = tc_sdesc(Al + s * 2 * 16 * 64, 16 * 64 * 2, 128);
+      const unsigned long long bh = tc_sdesc(Bs + s * 2 * nc8 * 64, nc8 * 64 * 2, 128);
+      const unsigned long long bl = tc_sdesc(Bl + s * 2 * nc8 * 64, nc8 * 64 * 2, 128);
+      tc_mma(c.tmem, ah, bh, idesc, s > 0);
+      tc_mma(c.tmem, ah, bl, idesc, 1);
+      tc_mma(c.tmem, al, bh, idesc, 1);
     }
     tc_commit(c.tcbar);
   }
@@ -783,7 +802,7 @@ __device__ void op_gemm(const HOp& o, HCtx<T>& c) {
   if constexpr (sizeof(T) == 4) {
     // dense leaf products on the tensor cores
     if (c.tc && m == 128 && n >= 16 && n <= 256 && (n & 15) == 0 && k >= 64 && (k & 15) == 0 &&
-        (long long)(128 + n) * k / 2 + 1024 <= c.smcap) {
+        (long long)(128 + n) * k + 1024 <= c.smcap) {
       if (tc_gemm128(c, o.A, o.B, o.C, 0, n, k, alpha, beta)) return;
     }
   }
@@ -1111,7 +1130,7 @@ __device__ void op_trmm_l(const HOp& o, HCtx<T>& c) {
   if constexpr (sizeof(T) == 4) {
     // C <- A C on the tensor cores (C staged before it is overwritten)
     if (c.tc && n == 128 && cc >= 16 && cc <= 256 && (cc & 15) == 0 &&
-        (long long)(128 + cc) * 128 / 2 + 1024 <= c.smcap) {
+        (long long)(128 + cc) * 128 + 1024 <= c.smcap) {
       if (tc_gemm128(c, o.A, o.C, o.C, 0, cc, 128, 1.f, 0.f)) return;
     }
   }
@@ -1201,7 +1220,7 @@ __device__ void op_trmm_r(const HOp& o, HCtx<T>& c) {
   if constexpr (sizeof(T) == 4) {
     // (C A)^T = A^T C^T on the tensor cores: M = n = 128, N = m, stored back transposed
     if (c.tc && n == 128 && m >= 16 && m <= 256 && (m & 15) == 0 &&
-        (long long)(128 + m) * 128 / 2 + 1024 <= c.smcap) {
+        (long long)(128 + m) * 128 + 1024 <= c.smcap) {
       const View At{o.A.off, o.A.c, o.A.r, o.A.ld, !o.A.tr};
       const View Ct{o.C.off, o.C.c, o.C.r, o.C.ld, !o.C.tr};
       if (tc_gemm128(c, At, Ct, o.C, 1, m, 128, 1.f, 0.f)) return;
@@ -4544,7 +4563,7 @@ extern "C" int hfsem_tc_tile_check(int32_t N, int32_t K, int32_t reps, double* m
     HF_CHECK(cudaMemcpy(d.p, h.data(), na * sizeof(float), cudaMemcpyHostToDevice));
     HF_CHECK(cudaMemset(de.p, 0, kCluster * sizeof(int)));
     HF_CHECK(cudaMemset(dd.p, 0, 8 * sizeof(unsigned long long)));
-    const int smem = 96 * 1024;   // operands (128 + N) x K bf16 on a 1024-byte boundary
+    const int smem = 160 * 1024;   // heads and tails of the operands, (128 + N) x K bf16 each
     allow_dyn_smem((const void*)k_tc_tile_check, smem);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(kCluster);
