@@ -682,11 +682,12 @@ __device__ T block_sum(T v, T* red) {
 // remainder), each stored in shared memory as K-major core matrices; three
 // MMAs per K step (hi hi, hi lo, lo hi) give the products to about 2^-16
 // relative, close to FP32 operands.  Then C = beta C + alpha D, with C stored
-// 128 x N (ctr = 0) or N x 128 (ctr = 1).
+// 128 x N (ctr = 0) or N x 128 (ctr = 1).  Not inlined: its staging code
+// would otherwise push the H-LU program past the register file (spills).
 // K a multiple of 16, N a multiple of 16 in [16, 256].  One thread issues the
 // MMAs; all threads wait on the mbarrier they commit to (bounded), then read
 // the accumulators back, warp w covering rows 32 (w mod 4) ...
-__device__ bool tc_gemm128(HCtx<float>& c, const View& A, const View& B, const View& Cv, int ctr, int N,
+__device__ __noinline__ bool tc_gemm128(HCtx<float>& c, const View& A, const View& B, const View& Cv, int ctr, int N,
                            int K, float alpha, float beta) {
   float* ar = c.ar;
   // operands on 1024-byte boundaries
@@ -785,6 +786,148 @@ __device__ bool tc_gemm128(HCtx<float>& c, const View& A, const View& B, const V
   return true;
 }
 
+// FP32 arithmetic on an FP64 arena (the FP64 part of a mixed-precision
+// factor keeps FP64 storage for the range of its entries; its products keep
+// the mode's FP32 arithmetic): operands converted to FP32 on their way into
+// shared memory, sums in FP32, results converted back.
+// C = beta C + alpha A B, 64 x 64 output tiles, k in chunks of 16, 4 x 4 per thread.
+__device__ void gemm_f32_on_f64(const HOp& o, HCtx<double>& c, int m, int n, int k, float alpha,
+                                float beta) {
+  double* ar = c.ar;
+  float* As = reinterpret_cast<float*>(c.sm);   // [16][64]
+  float* Bs = As + 16 * 64;                     // [16][64]
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tx = tid & 15, ty = tid >> 4;
+  for (int m0 = 0; m0 < m; m0 += 64)
+    for (int n0 = 0; n0 < n; n0 += 64) {
+      float acc[4][4];
+#pragma unroll
+      for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+      for (int k0 = 0; k0 < k; k0 += 16) {
+        for (int t = tid; t < 16 * 64; t += nt) {
+          const int kk = t / 64, ii = t % 64;
+          const int gi = m0 + ii, gk = k0 + kk, gj = n0 + ii;
+          As[kk * 64 + ii] = (gi < m && gk < k) ? (float)ar[vidx(o.A, gi, gk)] : 0.f;
+          Bs[kk * 64 + ii] = (gj < n && gk < k) ? (float)ar[vidx(o.B, gk, gj)] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < 16; ++kk) {
+          float a[4], b[4];
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            a[q] = As[kk * 64 + ty * 4 + q];
+            b[q] = Bs[kk * 64 + tx * 4 + q];
+          }
+#pragma unroll
+          for (int p = 0; p < 4; ++p)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[p][q] += a[p] * b[q];
+        }
+        __syncthreads();
+      }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int gi = m0 + ty * 4 + p, gj = n0 + tx * 4 + q;
+          if (gi < m && gj < n) {
+            const long long ci = vidx(o.C, gi, gj);
+            const float cv = beta == 0.f ? 0.f : beta * (float)ar[ci];
+            ar[ci] = (double)(cv + alpha * acc[p][q]);
+          }
+        }
+    }
+}
+
+// C <- A C (A n x n, n <= 128) in FP32 arithmetic on an FP64 arena: A and a
+// 32-column panel of C staged as FP32.
+__device__ void trmm_l_f32_on_f64(const HOp& o, HCtx<double>& c, int n, int cc) {
+  double* ar = c.ar;
+  float* As = reinterpret_cast<float*>(c.sm);   // n x n, [i + k n]
+  float* Pn = As + n * n;                       // n x 32, [k * 33 + j]
+  const int tid = threadIdx.x;
+  for (int t = tid; t < n * n; t += blockDim.x) As[t] = (float)ar[vidx(o.A, t % n, t / n)];
+  const int tx = tid & 7, ty = tid >> 3;
+  for (int c0 = 0; c0 < cc; c0 += 32) {
+    const int cp = min(32, cc - c0);
+    __syncthreads();
+    for (int t = tid; t < n * cp; t += blockDim.x) {
+      const int i = t % n, j = t / n;
+      Pn[i * 33 + j] = (float)ar[vidx(o.C, i, c0 + j)];
+    }
+    __syncthreads();
+    for (int rb = ty * 4; rb < n; rb += 128) {
+      float acc[4][4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] = 0.f;
+      for (int k = 0; k < n; ++k) {
+        float a[4], b[4];
+#pragma unroll
+        for (int p = 0; p < 4; ++p) a[p] = (rb + p < n) ? As[rb + p + k * n] : 0.f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) b[q] = Pn[k * 33 + tx + 8 * q];
+#pragma unroll
+        for (int p = 0; p < 4; ++p)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) acc[p][q] += a[p] * b[q];
+      }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          if (rb + p < n && tx + 8 * q < cp) ar[vidx(o.C, rb + p, c0 + tx + 8 * q)] = (double)acc[p][q];
+    }
+  }
+  __syncthreads();
+}
+
+// C <- C A (A n x n, n <= 128) in FP32 arithmetic on an FP64 arena: A (row-
+// major, padded row) and a 32-row panel of C staged as FP32.
+__device__ void trmm_r_f32_on_f64(const HOp& o, HCtx<double>& c, int m, int n) {
+  double* ar = c.ar;
+  const int lda = n + 1;
+  float* As = reinterpret_cast<float*>(c.sm);   // n x n, [k lda + j]
+  float* Pn = As + n * lda;                     // 32 x n, [i + k * 32]
+  const int tid = threadIdx.x;
+  for (int t = tid; t < n * n; t += blockDim.x) As[(t % n) * lda + t / n] = (float)ar[vidx(o.A, t % n, t / n)];
+  const int tx = tid & 31, ty = tid >> 5;
+  for (int r0 = 0; r0 < m; r0 += 32) {
+    const int rp = min(32, m - r0);
+    __syncthreads();
+    for (int t = tid; t < rp * n; t += blockDim.x)
+      Pn[(t % rp) + (t / rp) * 32] = (float)ar[vidx(o.C, r0 + t % rp, t / rp)];
+    __syncthreads();
+    float acc[4][4];
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[p][q] = 0.f;
+    for (int k = 0; k < n; ++k) {
+      float a[4], b[4];
+#pragma unroll
+      for (int p = 0; p < 4; ++p) a[p] = Pn[ty * 4 + p + k * 32];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) b[q] = (tx + 32 * q < n) ? As[k * lda + tx + 32 * q] : 0.f;
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] += a[p] * b[q];
+    }
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        if (ty * 4 + p < rp && tx + 32 * q < n)
+          ar[vidx(o.C, r0 + ty * 4 + p, tx + 32 * q)] = (double)acc[p][q];
+  }
+  __syncthreads();
+}
+
 template <class T>
 __device__ void op_gemm(const HOp& o, HCtx<T>& c) {
   const int m = dimv(o.C.r, c.rk), n = dimv(o.C.c, c.rk), k = dimv(o.A.c, c.rk);
@@ -798,6 +941,14 @@ __device__ void op_gemm(const HOp& o, HCtx<T>& c) {
       ar[ci] = (beta == (T)0) ? (T)0 : beta * ar[ci];
     }
     return;
+  }
+  if constexpr (sizeof(T) == 8) {
+    // FP64 part of a mixed factor: products of any size in FP32 arithmetic
+    // (the small ones stay on their latency-bound FP64 paths)
+    if (c.leaf32 && m >= 16 && n >= 16 && k >= 16) {
+      gemm_f32_on_f64(o, c, m, n, k, (float)o.alpha, (float)o.beta);
+      return;
+    }
   }
   if constexpr (sizeof(T) == 4) {
     // dense leaf products on the tensor cores
@@ -1127,6 +1278,12 @@ __device__ void op_trmm_l(const HOp& o, HCtx<T>& c) {
   const int n = dimv(o.C.r, c.rk), cc = dimv(o.C.c, c.rk);
   if (n <= 0 || cc <= 0) return;
   T* ar = c.ar;
+  if constexpr (sizeof(T) == 8) {
+    if (c.leaf32 && cc > 4) {   // FP64 part of a mixed factor: FP32 arithmetic
+      trmm_l_f32_on_f64(o, c, n, cc);
+      return;
+    }
+  }
   if constexpr (sizeof(T) == 4) {
     // C <- A C on the tensor cores (C staged before it is overwritten)
     if (c.tc && n == 128 && cc >= 16 && cc <= 256 && (cc & 15) == 0 &&
@@ -1217,6 +1374,12 @@ __device__ void op_trmm_r(const HOp& o, HCtx<T>& c) {
   const int m = dimv(o.C.r, c.rk), n = dimv(o.C.c, c.rk);
   if (m <= 0 || n <= 0) return;
   T* ar = c.ar;
+  if constexpr (sizeof(T) == 8) {
+    if (c.leaf32) {   // FP64 part of a mixed factor: FP32 arithmetic
+      trmm_r_f32_on_f64(o, c, m, n);
+      return;
+    }
+  }
   if constexpr (sizeof(T) == 4) {
     // (C A)^T = A^T C^T on the tensor cores: M = n = 128, N = m, stored back transposed
     if (c.tc && n == 128 && m >= 16 && m <= 256 && (m & 15) == 0 &&
