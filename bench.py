@@ -208,8 +208,8 @@ def arrival_offsets(n, rate, seed):
     return np.cumsum(rng.exponential(1.0 / rate, size=n)) - 0.0
 
 
-KERNEL_TAGS = ("pairs", "symbol", "toeplitz_mv", "dense_mv", "hmat_mv", "hlu_factor",
-               "hlu_solve", "solve_pack", "krylov_vec")
+KERNEL_TAGS = ("pairs", "symbol", "load_vector", "toeplitz_mv", "dense_mv", "hmat_mv",
+               "hlu_factor", "hlu_solve", "solve_pack", "krylov_vec")
 
 
 def kernel_table(H):
@@ -411,6 +411,7 @@ BOUND_OF = {   # kernel tag -> (bound, unit of its counted work)
     "hmat_mv": ("alu_fp64", "flop"),       # 2 flops per stored H-matrix entry and rhs
     "pairs": ("alu_fp64", None),           # element-pair quadrature (work not counted)
     "symbol": ("alu_fp64", None),
+    "load_vector": ("alu_fp64", None),     # load-vector quadrature (work not counted)
     "toeplitz_mv": ("hbm", "byte"),        # symbol + vectors per apply
     "hlu_factor": ("alu_fp32", "flop"),    # flops of the executed shapes
     "hlu_solve": ("alu_fp32", "flop"),

@@ -1096,6 +1096,53 @@ __global__ void k_load_moments(const InstDev* __restrict__ inst, const double* a
         }
       }
     } else {  // fractional powers
+      // Terms whose element lies at least half its length from their
+      // endpoint share one Gauss-Legendre rule per side, with enough points
+      // for the Bernstein ellipse through the singularity 2 d0 / h beyond
+      // the end of the reference interval (error ~ rho^-(2n - P), kept below
+      // 1e-16): (d0 + o)^mu = d0^mu (1 + o/d0)^mu, the power of d0 once per
+      // term and element, the second factor exp(mu log1p(o/d0)) per point
+      // with log1p(o/d0) in [0, log 3] (a few ulp), and the Legendre values
+      // once per point for a chunk of terms.
+      constexpr int kTermChunk = 8;
+      for (int side = 0; side < 2; ++side) {
+        const double d0 = (side == 0) ? dl[e] : dr[e + 1];
+        if (!(d0 >= 0.5 * he)) continue;
+        const double tt = 1.0 + 2.0 * d0 / he;
+        const double rho = tt + sqrt(tt * tt - 1.0);
+        const int nq = min((int)ceil(0.5 * P + 18.5 / log(rho)) + 2, kMaxGL);
+        const double* X = gl + gl_off(nq);
+        const double* Wt = X + nq;
+        const double id0 = 1.0 / d0;
+        for (int t0 = 0; t0 < n_terms; t0 += kTermChunk) {
+          double cp[kTermChunk], mu[kTermChunk];
+          int nt = 0;
+          for (int t = t0; t < min(n_terms, t0 + kTermChunk); ++t)
+            if ((int)rd[3 * t + 2] == side) {
+              mu[nt] = rd[3 * t + 1];
+              cp[nt] = rd[3 * t] * pow(d0, mu[nt]);
+              ++nt;
+            }
+          if (nt == 0) continue;
+          for (int q = 0; q < nq; ++q) {
+            const double o = 0.5 * he * (1.0 + X[q]);   // offset from the node nearest the end
+            const double lg = log1p(o * id0);
+            double S = 0.0;
+            for (int j = 0; j < nt; ++j) S += cp[j] * exp(mu[j] * lg);
+            const double wq = 0.5 * he * Wt[q] * S;
+            const double xi = (side == 0) ? X[q] : -X[q];
+            double l0 = 1.0, l1 = xi;
+            g[0] += wq;
+            if (P >= 1) g[1] += wq * l1;
+            for (int k = 1; k < P; ++k) {
+              double l2 = leg_next(k, xi, l1, l0);
+              g[k + 1] += wq * l2;
+              l0 = l1;
+              l1 = l2;
+            }
+          }
+        }
+      }
       for (int t = 0; t < n_terms; ++t) {
         double coef = rd[3 * t], mu = rd[3 * t + 1];
         int side = (int)rd[3 * t + 2];
@@ -1111,29 +1158,7 @@ __global__ void k_load_moments(const InstDev* __restrict__ inst, const double* a
             c *= (mu - m) / (mu + m + 2.0);
           }
         } else if (d0 >= 0.5 * he) {
-          // the singularity of (d0 + o)^mu lies 2 d0 / h beyond the end of
-          // the reference interval: Gauss-Legendre with enough points for
-          // the Bernstein ellipse through it (error ~ rho^-(2n - P), kept
-          // below 1e-16), applied directly
-          const double t = 1.0 + 2.0 * d0 / he;
-          const double rho = t + sqrt(t * t - 1.0);
-          const int nq = min((int)ceil(0.5 * P + 18.5 / log(rho)) + 2, kMaxGL);
-          const double* X = gl + gl_off(nq);
-          const double* Wt = X + nq;
-          for (int q = 0; q < nq; ++q) {
-            const double o = 0.5 * he * (1.0 + X[q]);   // offset from the node nearest the end
-            const double wq = coef * 0.5 * he * Wt[q] * pow(d0 + o, mu);
-            const double xi = (side == 0) ? X[q] : -X[q];
-            double l0 = 1.0, l1 = xi;
-            g[0] += wq;
-            if (P >= 1) g[1] += wq * l1;
-            for (int k = 1; k < P; ++k) {
-              double l2 = leg_next(k, xi, l1, l0);
-              g[k + 1] += wq * l2;
-              l0 = l1;
-              l1 = l2;
-            }
-          }
+          continue;   // done above
         } else {
           // offset o from the node nearest the endpoint, distance d0 + o;
           // exponential map o = d0((1+h/d0)^s - 1), s in [0,1], makes the
@@ -1418,6 +1443,7 @@ void load_vector_em(hfsem_system* s, const hfsem_rhs* rhs, int lifted, double* G
     const int n_terms = 0;   // per instance, from the table
     // moments: sum over instances of N (P+1) = total_nz + sum N, per rhs
     s->w_mom.ensure((size_t)(s->total_nz + s->total_N) * nrhs);
+    Tick tk(s->st, "load_vector");
     k_load_moments<<<grid1(s->max_N, 128, ni, nrhs), 128, 0, s->st>>>(
         s->d_inst.p, s->arena.p, s->gl.p, s->w_rhsdata.p, d_roff, kind, n_terms, nrhs,
         s->w_mom.p);
