@@ -979,6 +979,18 @@ void build_leaf_solve(const HPlan& p, int ncta, size_t budget, int ts, int sw, L
   if (solve_smem(jcap, nm, wc, ts, sw) > budget)
     throw Error(HFSEM_ERR_UNSUPPORTED, "leaf solve does not fit in shared memory");
   pb.jcap = jcap;
+  {
+    size_t total = 0;
+    for (int d = 0; d < 2; ++d)
+      for (int q = 0; q < nl; ++q)
+        total += gat[d][q].size() + sca[d][q].size() + (size_t)(p.C[lf[q]].d1 - p.C[lf[q]].d0);
+    pb.jobs.reserve(total);
+    pb.steps.reserve(2 * (size_t)nl);
+    pb.step_cta.reserve(2 * (size_t)nl * ncta);
+  }
+  // per-CTA job lists of a step (kept across steps: capacity reused)
+  std::vector<std::array<std::vector<SolJob>, 3>> per(ncta);
+  std::vector<int> load(ncta, 0);
   for (int st = 0; st < 2 * nl; ++st) {
     const int d = st < nl ? 0 : 1;
     const int q = d == 0 ? st : 2 * nl - 1 - st;
@@ -988,8 +1000,9 @@ void build_leaf_solve(const HPlan& p, int ncta, size_t budget, int ts, int sw, L
     if (n > 128) throw Error(HFSEM_ERR_UNSUPPORTED, "leaf larger than the solve kernel supports");
     pb.steps.push_back(StepInfo{c.d0, n, q % kRing});
     const long long dinv = inv[lf[q]] + (d ? (long long)n * n : 0LL);
-    std::vector<std::array<std::vector<SolJob>, 3>> per(ncta);
-    std::vector<int> load(ncta, 0);
+    for (auto& a : per)
+      for (auto& v : a) v.clear();
+    std::fill(load.begin(), load.end(), 0);
     for (const OJ& o : gat[d][q])
       if (o.owner >= 0) {
         per[o.owner][0].push_back(o.j);
