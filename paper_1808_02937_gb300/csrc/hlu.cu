@@ -682,12 +682,11 @@ __device__ T block_sum(T v, T* red) {
 // remainder), each stored in shared memory as K-major core matrices; three
 // MMAs per K step (hi hi, hi lo, lo hi) give the products to about 2^-16
 // relative, close to FP32 operands.  Then C = beta C + alpha D, with C stored
-// 128 x N (ctr = 0) or N x 128 (ctr = 1).  Not inlined: its staging code
-// would otherwise push the H-LU program past the register file (spills).
+// 128 x N (ctr = 0) or N x 128 (ctr = 1).
 // K a multiple of 16, N a multiple of 16 in [16, 256].  One thread issues the
 // MMAs; all threads wait on the mbarrier they commit to (bounded), then read
 // the accumulators back, warp w covering rows 32 (w mod 4) ...
-__device__ __noinline__ bool tc_gemm128(HCtx<float>& c, const View& A, const View& B, const View& Cv, int ctr, int N,
+__device__ bool tc_gemm128(HCtx<float>& c, const View& A, const View& B, const View& Cv, int ctr, int N,
                            int K, float alpha, float beta) {
   float* ar = c.ar;
   // operands on 1024-byte boundaries
