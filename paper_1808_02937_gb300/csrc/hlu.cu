@@ -2578,30 +2578,33 @@ struct HProgArgs {
 };
 
 // algorithmic flops of one op with its run-time shapes
-__device__ double op_flops(const HOp& o, const int* rk, const SlotDev* sl) {
+// (integer arithmetic: the thread that counts also claims the next op, and
+// FP64 instructions are slow on this GPU's FP64 pipe)
+__device__ unsigned long long op_flops(const HOp& o, const int* rk, const SlotDev* sl) {
+  using u64 = unsigned long long;
   switch (o.type) {
     case OP_GEMM: {
-      double m = dimv(o.C.r, rk), n = dimv(o.C.c, rk), k = dimv(o.A.c, rk);
-      return 2.0 * m * n * k;
+      const u64 m = dimv(o.C.r, rk), n = dimv(o.C.c, rk), k = dimv(o.A.c, rk);
+      return 2ull * m * n * k;
     }
-    case OP_GETRF_INV: {
-      double n = o.C.r;
-      return (2.0 / 3.0) * n * n * n + (2.0 / 3.0) * n * n * n;
+    case OP_GETRF_INV: {   // LU and the two triangular inverses: 4/3 n^3
+      const u64 n = o.C.r;
+      return 4ull * n * n * n / 3ull;
     }
     case OP_TRMM_L: {
-      double n = dimv(o.C.r, rk), c = dimv(o.C.c, rk);
-      return 2.0 * n * n * c;
+      const u64 n = dimv(o.C.r, rk), c = dimv(o.C.c, rk);
+      return 2ull * n * n * c;
     }
     case OP_TRMM_R: {
-      double m = dimv(o.C.r, rk), n = dimv(o.C.c, rk);
-      return 2.0 * m * n * n;
+      const u64 m = dimv(o.C.r, rk), n = dimv(o.C.c, rk);
+      return 2ull * m * n * n;
     }
     case OP_TRUNC: {
-      double K = rk[o.slot], m = sl[o.slot].m, n = sl[o.slot].n;
-      return 4.0 * (m + n) * K * K + 2.0 * K * K * K;
+      const u64 K = rk[o.slot], m = sl[o.slot].m, n = sl[o.slot].n;
+      return 4ull * (m + n) * K * K + 2ull * K * K * K;
     }
     default:
-      return 0.0;
+      return 0ull;
   }
 }
 
@@ -2676,7 +2679,7 @@ __global__ void __launch_bounds__(kHThreads) k_hprog(HProgArgs a, T* har) {
   unsigned ctr0;   // the counters of CTA 0 in the cluster's shared window
   asm volatile("mapa.shared::cluster.u32 %0, %1, 0;" : "=r"(ctr0) : "r"(ctr_base));
   cluster_barrier();
-  double fl = 0.0;
+  unsigned long long fl = 0ull;
   const bool wp = a.wprof && threadIdx.x == 0;
   for (int w = 0; w < nw; ++w) {
     const int i0 = waves[w], n_w = waves[w + 1] - i0;
@@ -2771,7 +2774,7 @@ __global__ void __launch_bounds__(kHThreads) k_hprog(HProgArgs a, T* har) {
       q[3 + 3 * crank] = ltype;
     }
   }
-  if (threadIdx.x == 0) a.flops[((size_t)cid * a.ncl + crank) * 2] += fl;
+  if (threadIdx.x == 0) a.flops[((size_t)cid * a.ncl + crank) * 2] += (double)fl;
   if (a.tc) {   // every tensor-core op has completed and been read back
     tc_fence_before();
     __syncthreads();
@@ -2943,7 +2946,7 @@ __global__ void __launch_bounds__(kHThreads) k_hsolve_cl(const HInstDev* __restr
   const int nchunk = (nrhs + kSolveW - 1) / kSolveW;
   const int ch0 = (int)(part * nchunk / nsplit), ch1 = (int)((part + 1) * nchunk / nsplit);
   const int total = nst * (ch1 - ch0);
-  double fl = 0.0;
+  unsigned long long fl = 0ull;   // integer: FP64 instructions are slow here
   bool ok = true;
   long long qfail = -1;   // part whose copy did not arrive in time
   // optional phase timer (cluster 0, CTA 0): waits, A, barrier, B, barrier, C
@@ -3045,7 +3048,7 @@ __global__ void __launch_bounds__(kHThreads) k_hsolve_cl(const HInstDev* __restr
 #pragma unroll
           for (int c = 0; c < kSolveW; ++c) acc[c] += a * sx[jl * kSolveW + c];
         }
-      if (tid == 0) fl += 2.0 * n * nc * (e - x);
+      if (tid == 0) fl += 2ull * (unsigned long long)n * nc * (e - x);
       __syncthreads();
       x = e;
     }
@@ -3082,7 +3085,7 @@ __global__ void __launch_bounds__(kHThreads) k_hsolve_cl(const HInstDev* __restr
 #pragma unroll
           for (int c = 0; c < kSolveW; ++c) acc[c] += a * r[c * 128 + kk];
         }
-      if (tid == 0) fl += 2.0 * n * nc * (e - x);
+      if (tid == 0) fl += 2ull * (unsigned long long)n * nc * (e - x);
       x = e;
     }
     if (h == 1)
@@ -3131,7 +3134,7 @@ __global__ void __launch_bounds__(kHThreads) k_hsolve_cl(const HInstDev* __restr
         if (lane == 0)
           for (int c = 0; c < nc; ++c) wl[m.x * kSolveW + c] += pa_[c];
       }
-      if (tid == 0) fl += 2.0 * n * nc * (e - x);
+      if (tid == 0) fl += 2ull * (unsigned long long)n * nc * (e - x);
       x = e;
     }
     // every part of the step is begun (keeps the prefetch chain in order)
@@ -3150,7 +3153,7 @@ __global__ void __launch_bounds__(kHThreads) k_hsolve_cl(const HInstDev* __restr
       }
     }
   }
-  if (tid == 0) atomicAdd(&flops[((size_t)inst * kCluster + crank) * 2 + 1], fl);
+  if (tid == 0) atomicAdd(&flops[((size_t)inst * kCluster + crank) * 2 + 1], (double)fl);
 }
 
 // rhs area <- D r (element-major FP64 -> T); rank slot n_slots <- nrhs
