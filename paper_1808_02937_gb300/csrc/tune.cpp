@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <memory>
 #include <mutex>
 #include <string>
 #include <tuple>
@@ -136,6 +137,8 @@ extern "C" int hfsem_tune(hfsem_system* sys, const hfsem_hopts* opts, const hfse
       hfsem_system* sub = nullptr;
       int e = hfsem_assemble((int32_t)probs.size(), probs.data(), sys->st, &sub);
       if (e != HFSEM_OK) return e;
+      // the tuning system is freed on every way out of this class
+      std::unique_ptr<hfsem_system, void (*)(hfsem_system*)> own(sub, hfsem_system_free);
       int nd = 0;
       for (int i : ids) nd += sys->ih[i].Nd;
       std::vector<double> X((size_t)nd * nrhs);
@@ -166,10 +169,11 @@ extern "C" int hfsem_tune(hfsem_system* sys, const hfsem_hopts* opts, const hfse
             ok = false;
             break;
           }
+          std::unique_ptr<hfsem_factor, void (*)(hfsem_factor*)> fown(f, hfsem_factor_free);
           tm.start();
           int es = hfsem_solve(sub, f, rs.data(), tol, max_iter, X.data(), st.data());
           float sms = tm.stop();
-          hfsem_factor_free(f);
+          fown.reset();
           if (es != HFSEM_OK) {
             ok = false;
             break;
@@ -189,7 +193,7 @@ extern "C" int hfsem_tune(hfsem_system* sys, const hfsem_hopts* opts, const hfse
           best_ms = t.second.first;
           best = t.first;
         }
-      hfsem_system_free(sub);
+      own.reset();
       if (best > 0) {
         {
           std::lock_guard<std::mutex> lk(g_mu);
