@@ -844,21 +844,20 @@ void schedule_program(const HPlan& p, std::vector<HOp>& prog, std::vector<int>& 
   for (int l : lv) cnt[l]++;
   waves.assign(nl + 1, 0);
   for (int l = 1; l <= nl; ++l) waves[l] = waves[l - 1] + cnt[l];
+  // op indices by level, in program order within a level
   std::vector<int> pos(waves.begin(), waves.end());
-  prog.assign(out.size(), HOp());
-  for (size_t i = 0; i < out.size(); ++i) prog[pos[lv[i] - 1]++] = out[i];
+  std::vector<int> idx(out.size());
+  for (size_t i = 0; i < out.size(); ++i) idx[pos[lv[i] - 1]++] = (int)i;
   // 4. within a wave, the longest ops first: the CTAs take ops in this order
   // as they become free (a counter per wave), longest-processing-time first
-  std::vector<HOp> tmp;
-  for (int w = 0; w < nl; ++w) {
-    const int a = waves[w], b = waves[w + 1];
-    std::vector<std::pair<double, int>> ord;
-    for (int i = a; i < b; ++i) ord.push_back({-op_cost(p, prog[i]), i});
-    std::stable_sort(ord.begin(), ord.end());
-    tmp.clear();
-    for (auto& q : ord) tmp.push_back(prog[q.second]);
-    std::copy(tmp.begin(), tmp.end(), prog.begin() + a);
-  }
+  // (ties keep program order)
+  std::vector<double> cost(out.size());
+  for (size_t i = 0; i < out.size(); ++i) cost[i] = op_cost(p, out[i]);
+  for (int w = 0; w < nl; ++w)
+    std::stable_sort(idx.begin() + waves[w], idx.begin() + waves[w + 1],
+                     [&](int x, int y) { return cost[x] > cost[y]; });
+  prog.resize(out.size());
+  for (size_t k = 0; k < out.size(); ++k) prog[k] = out[idx[k]];
 }
 
 }  // namespace hf
